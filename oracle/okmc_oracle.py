@@ -1,0 +1,627 @@
+"""Plain, slow, FP64 CPU oracle of the OkMC-with-exact-elasticity hot path.
+
+TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may use this module.
+It shares no code with the CUDA path and imports nothing from it.
+
+What it computes, in the paper's order (Santos-Gueemes, Ortiz, Segurado,
+"An FFT based approach to account for elastic interactions in OkMC"):
+
+1. Defect eigenstrains (Sec. 3.1, Eq. eig_shearloop for prismatic loops; the
+   point-defect eigenstrain from the relaxation volume, Sec. 3.1) rasterised on
+   the voxel grid of Sec. 3.4 (voxel centres x_k = (L/N)(1/2 + n_k)).
+2. The periodic elastic problem with eigenstrain (Sec. 3.2, Eqs.
+   EIG_elastic_real / EIG_elastic_fourier / basicgammacomplete / summaryEL),
+   solved by direct substitution in Fourier space on the discrete frequencies
+   of Sec. 3.4 (Eq. frequencies).  The FFT is numpy's (a library primitive).
+3. Interaction energies (Sec. 2, Eq. interaction_energy3), written as
+   E_i(Y) = -int eps*_i(Y) : sigma^(-i) dV, with sigma^(-i) the stress of all
+   defects except i.
+4. Rates (Sec. 5, Eqs. unbiased_boltzmann, biased_forward/backward_boltzmann),
+   the frequency line and jump selection (Eqs. frequency_line, selection_jump),
+   the fixed time step and Poisson event counts (Eqs. time_step, poisson;
+   Appendix A, Algorithm 1), and a residence-time (one event per step) variant.
+
+Readings where the paper is silent or ambiguous (each is repeated in the
+repository's design notes):
+
+* Green operator indices (Eq. basicgammacomplete is garbled): the standard
+  form eps_hat = sym(m (x) K(m)^-1 (tau_hat . m)), K_ik = C_ijkl m_j m_l,
+  tau_hat = C : eps*_hat, m = xi/|xi|; sigma_hat = C : (eps_hat - eps*_hat).
+* Zero frequency: MEAN_STRESS_ZERO (sigma_hat(0) = 0) or MEAN_STRAIN_ZERO
+  (eps_hat(0) = 0, hence sigma_hat(0) = -C : eps*_hat(0); Appendix B).
+* Even grid edges: the Nyquist index uses n = -N/2 (Eq. frequencies) and the
+  stress is the real part of the inverse transform (the field is real).
+* Loop eigenstrain: slab |(x-X).n| <= h/2, in-plane radius <= R, 4x4x4
+  subsamples per voxel, weights renormalised so that sum(w) V_vox equals the
+  exact shape volume pi R^2 h; pure prismatic interstitial loop, n = b/|b|,
+  eps* = sym(b (x) n)/h (Eq. eig_shearloop with e = h).
+* SIA cluster of s atoms: sphere of radius r = max(h, (3 s Omega / 4 pi)^(1/3)),
+  Omega = a0^3/2, dilatational eigenstrain with trace integral 1.5 s Omega.
+* Lattice parameter a0 equals the voxel edge h; positions are integers in
+  units of a0/2 on the bcc lattice (all even or all odd); the parity is the
+  rasterisation class.
+* Rates: nu_ij = (1/z_i) nu0 exp(-(E_m,i + (E_i(X+lambda_j) - E_i(X))/2)/k_B T)
+  over the z_i allowed jumps (Eq. biased_forward_boltzmann generalised from
+  z = 2 to z jumps).
+
+Units: length nm, stress GPa, energy eV.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+PI = 3.141592653589793
+KAPPA = 6.241509074            # eV per (GPa nm^3)
+KB = 8.617333262e-5            # Boltzmann constant, eV/K
+NU0_DEFAULT = 1.0e13           # attempt frequency, 1/s
+
+LOOP_111, LOOP_100, SIA_CLUSTER = 0, 1, 2
+IMMOBILE, ONE_D, THREE_D = 0, 1, 2
+MEAN_STRESS_ZERO, MEAN_STRAIN_ZERO = 0, 1
+
+AXES_111 = np.array([[1, 1, 1], [-1, 1, 1], [1, -1, 1], [1, 1, -1]], dtype=np.int64)
+AXES_100 = np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.int64)
+# six independent components of a symmetric tensor, in this order
+VOIGT = [(0, 0), (1, 1), (2, 2), (1, 2), (0, 2), (0, 1)]
+# jump j <-> lambda_j = (a0/2)(sx, sy, sz), j = 4 (sx>0) + 2 (sy>0) + (sz>0)
+JUMPS = np.array([[1 if (j >> 2) & 1 else -1, 1 if (j >> 1) & 1 else -1, 1 if j & 1 else -1]
+                  for j in range(8)], dtype=np.int64)
+
+
+# --------------------------------------------------------------------------
+# material (Table 1 and the isotropic reduction of Sec. 4)
+# --------------------------------------------------------------------------
+def stiffness_cubic(C11, C12, C44):
+    """Full C_ijkl of a cubic crystal whose cube axes are the grid axes (Table 1)."""
+    C = np.zeros((3, 3, 3, 3))
+    for i in range(3):
+        for j in range(3):
+            for k in range(3):
+                for l in range(3):
+                    v = 0.0
+                    if i == j and k == l:
+                        v += C12
+                    if i == k and j == l:
+                        v += C44
+                    if i == l and j == k:
+                        v += C44
+                    if i == j == k == l:
+                        v += C11 - C12 - 2.0 * C44
+                    C[i, j, k, l] = v
+    return C
+
+
+def isotropic_cubic_constants(mu, nu):
+    """(C11, C12, C44) of an isotropic solid with shear modulus mu, Poisson ratio nu."""
+    lam = 2.0 * mu * nu / (1.0 - 2.0 * nu)
+    return lam + 2.0 * mu, lam, mu
+
+
+def zener_isotropic_moduli(C11, C12):
+    """Young's modulus and Poisson ratio of the Sec. 4 isotropic reduction
+    (C11, C12 kept, C44 := (C11 - C12)/2)."""
+    nu = C12 / (C11 + C12)
+    E = (C11 - C12) * (C11 + 2.0 * C12) / (C11 + C12)
+    return E, nu
+
+
+def to_tensor(v6):
+    """(6, ...) symmetric components -> (3, 3, ...) tensor."""
+    v6 = np.asarray(v6)
+    t = np.zeros((3, 3) + v6.shape[1:], dtype=v6.dtype)
+    for a, (i, j) in enumerate(VOIGT):
+        t[i, j] = v6[a]
+        t[j, i] = v6[a]
+    return t
+
+
+def to_voigt6(t):
+    """(3, 3, ...) symmetric tensor -> (6, ...) components."""
+    return np.stack([t[i, j] for (i, j) in VOIGT])
+
+
+def ddot6(a6, b6):
+    """a : b for symmetric tensors held as 6 components (off-diagonals count twice)."""
+    return (a6[0] * b6[0] + a6[1] * b6[1] + a6[2] * b6[2]
+            + 2.0 * (a6[3] * b6[3] + a6[4] * b6[4] + a6[5] * b6[5]))
+
+
+# --------------------------------------------------------------------------
+# defects -> eigenstrain stencils (Sec. 3.1, Eq. eig_shearloop; Sec. 3.4 grid)
+# --------------------------------------------------------------------------
+def defect_geometry(d, h):
+    """Shape, eigenstrain tensor e (3x3) and shape volume of one defect record."""
+    t = int(d['type'])
+    if t in (LOOP_111, LOOP_100):
+        a = (AXES_111 if t == LOOP_111 else AXES_100)[int(d['axis'])]
+        a2 = int(a @ a)
+        n = a / math.sqrt(a2)
+        blen = (math.sqrt(3.0) / 2.0) * h if t == LOOP_111 else h      # |b|, a0 = h
+        R = float(d['radius_nm'])
+        # eps* = sym(b (x) n)/e with b = |b| n and slab thickness e = h
+        e = (blen / h) * np.outer(n, n)
+        t_ = 8.0 * R / h
+        return dict(kind='disk', a=a, a2=a2, n=n, b=blen * n, R=R,
+                    Rq=float(a2) * (t_ * t_),
+                    v_over_h3=PI * (R / h) ** 2,
+                    extent=int(math.ceil(R / h)) + 2, e=e)
+    if t == SIA_CLUSTER:
+        s = int(d['size'])
+        # sphere radius rho = r/h = max(1, (3 s Omega/(4 pi))^(1/3)) with Omega = h^3/2;
+        # the inside test |x|^2 <= rho^2 is done on cubes: |x|^6 <= rho^6 (integers in h/8)
+        q = 3.0 * s / (8.0 * PI)                          # rho^3 when rho > 1
+        rho3 = q if q > 1.0 else 1.0
+        T6 = 262144.0 * (rho3 * rho3)                      # (8 rho)^6
+        v = (4.0 * PI / 3.0) * rho3                        # V_shape / h^3
+        # trace of the integrated eigenstrain = relaxation volume 1.5 s Omega
+        e = np.eye(3) * (1.5 * s * 0.5) / (3.0 * v)
+        return dict(kind='sphere', s=s, T6=T6, v_over_h3=v,
+                    extent=int(math.ceil(rho3 ** (1.0 / 3.0))) + 2, e=e)
+    raise ValueError('unknown defect type %d' % t)
+
+
+def stencil(d, cls, h):
+    """Coverage stencil of defect d for rasterisation class cls (0 or 1).
+
+    Returns (offsets (k, 3) int [dx, dy, dz] relative to the base voxel
+    floor(pos/2), counts (k,) int in 1..64, alpha) with voxel weight
+    w = count * alpha and sum(w) h^3 = shape volume.  Entries are sorted by
+    (dz, dy, dx).  Subsample coordinates relative to the defect centre are
+    integers in units of h/8: s = 8 v + 2 i + 1 - 4 cls, i = 0..3.
+    """
+    g = defect_geometry(d, h)
+    E = g['extent']
+    r = np.arange(-E, E + 1, dtype=np.int64)
+    s1 = 8 * r[:, None] + 2 * np.arange(4, dtype=np.int64)[None, :] + 1 - 4 * cls   # (nv, 4)
+    sx = s1[:, :, None, None, None, None]
+    sy = s1[None, None, :, :, None, None]
+    sz = s1[None, None, None, None, :, :]
+    ss = sx * sx + sy * sy + sz * sz
+    if g['kind'] == 'disk':
+        a = g['a']
+        sa = a[0] * sx + a[1] * sy + a[2] * sz
+        inside = (sa * sa <= 16 * g['a2']) & ((g['a2'] * ss - sa * sa).astype(np.float64) <= g['Rq'])
+    else:
+        inside = (ss * ss * ss).astype(np.float64) <= g['T6']
+    counts = inside.sum(axis=(1, 3, 5))            # [x, y, z]
+    cz = np.transpose(counts, (2, 1, 0))            # [z, y, x]
+    iz, iy, ix = np.nonzero(cz)
+    offs = np.stack([r[ix], r[iy], r[iz]], axis=1)
+    cnt = cz[iz, iy, ix].astype(np.int64)
+    if np.any(np.abs(offs) == E):
+        raise AssertionError('stencil reached its scan box edge')
+    alpha = g['v_over_h3'] / float(cnt.sum())
+    return offs, cnt, alpha
+
+
+def base_voxel(pos):
+    """Voxel that holds a defect at half-lattice position pos (floor(pos/2))."""
+    return np.floor_divide(np.asarray(pos, dtype=np.int64), 2)
+
+
+def pos_class(pos):
+    p = np.asarray(pos, dtype=np.int64)
+    c = int(p[0] & 1)
+    if not np.all((p & 1) == c):
+        raise ValueError('position %s is not a bcc site' % (p,))
+    return c
+
+
+def eigenstrain_field(defects, n, h, only=None, exclude=None, positions=None):
+    """Sum of the voxelised eigenstrains, (6, nx, ny, nz) FP64 (Sec. 3.1, 3.4)."""
+    n = tuple(int(v) for v in n)
+    eps = np.zeros((6,) + n)
+    flat = eps.reshape(6, -1)
+    for i, d in enumerate(defects):
+        if only is not None and i not in only:
+            continue
+        if exclude is not None and i in exclude:
+            continue
+        pos = np.asarray(d['pos'] if positions is None else positions[i], dtype=np.int64)
+        c = pos_class(pos)
+        offs, cnt, alpha = stencil(d, c, h)
+        e6 = to_voigt6(defect_geometry(d, h)['e'])
+        v = np.mod(base_voxel(pos)[None, :] + offs, np.array(n)[None, :])
+        lin = np.ravel_multi_index((v[:, 0], v[:, 1], v[:, 2]), n)
+        w = cnt * alpha
+        for a in range(6):
+            np.add.at(flat[a], lin, w * e6[a])
+    return eps
+
+
+# --------------------------------------------------------------------------
+# periodic elastic solve (Sec. 3.2 and 3.4)
+# --------------------------------------------------------------------------
+def frequencies(N, L):
+    """xi = 2 pi n / L with n from Eq. frequencies, in numpy's FFT index order."""
+    return 2.0 * PI * (np.fft.fftfreq(N) * N) / L
+
+
+def green_sigma_hat(C, xi, eps_hat_t, k0_mode, zero_mask):
+    """sigma_hat = C:(Gamma_hat:(C:eps*_hat) - eps*_hat) at the given frequencies.
+
+    xi: (..., 3) real; eps_hat_t: (3, 3, ...) complex; Eq. EIG_elastic_fourier,
+    Eq. basicgammacomplete (standard index reading) and Eq. summaryEL.
+    """
+    tau = np.einsum('ijkl,kl...->ij...', C, eps_hat_t)
+    nrm = np.sqrt(np.sum(xi * xi, axis=-1))
+    safe = np.where(zero_mask, 1.0, nrm)
+    m = xi / safe[..., None]
+    K = np.einsum('ijkl,...j,...l->...ik', C, m, m)
+    K = np.where(zero_mask[..., None, None], np.eye(3), K)
+    v = np.einsum('ij...,...j->...i', tau, m)
+    w = np.linalg.solve(K, v[..., None])[..., 0]                   # (..., 3)
+    eps_c = 0.5 * (np.einsum('...i,...j->ij...', m, w) + np.einsum('...j,...i->ij...', m, w))
+    sig = np.einsum('ijkl,kl...->ij...', C, eps_c) - tau
+    if np.any(zero_mask):
+        if k0_mode == MEAN_STRESS_ZERO:
+            sig[:, :, zero_mask] = 0.0
+        elif k0_mode == MEAN_STRAIN_ZERO:
+            sig[:, :, zero_mask] = -tau[:, :, zero_mask]
+        else:
+            raise ValueError('k0_mode')
+    return sig
+
+
+def solve_stress(eps6, C, h, k0_mode=MEAN_STRESS_ZERO, dft=None):
+    """Stress (6, nx, ny, nz) of the periodic eigenstrain field eps6 (same shape).
+
+    Forward transform of eps*, the Green operator on every discrete frequency,
+    inverse transform, real part.  ``dft`` may replace numpy's FFT by another
+    transform pair (forward, inverse) acting on the last three axes.
+    """
+    fwd, inv = dft if dft is not None else (
+        lambda a: np.fft.fftn(a, axes=(-3, -2, -1)),
+        lambda a: np.fft.ifftn(a, axes=(-3, -2, -1)))
+    n = eps6.shape[1:]
+    L = [n[a] * h for a in range(3)]
+    xs = [frequencies(n[a], L[a]) for a in range(3)]
+    eh6 = fwd(eps6.astype(np.complex128))
+    sh6 = np.empty_like(eh6)
+    for ix in range(n[0]):                      # one x-slab at a time keeps memory small
+        XI = np.stack(np.meshgrid(np.full(1, xs[0][ix]), xs[1], xs[2], indexing='ij'), axis=-1)[0]
+        zero = np.all(XI == 0.0, axis=-1)
+        sig = green_sigma_hat(C, XI, to_tensor(eh6[:, ix]), k0_mode, zero)
+        sh6[:, ix] = to_voigt6(sig)
+    return inv(sh6).real
+
+
+def naive_dft_pair(n):
+    """O(N^2) DFT along each of the last three axes, written out from the definition."""
+    mats = []
+    for N in n:
+        j = np.arange(N)
+        mats.append(np.exp(-2j * PI * np.outer(j, j) / N))
+
+    def fwd(a):
+        a = np.einsum('...xyz,ux->...uyz', a, mats[0])
+        a = np.einsum('...xyz,vy->...xvz', a, mats[1])
+        return np.einsum('...xyz,wz->...xyw', a, mats[2])
+
+    def inv(a):
+        a = np.einsum('...xyz,ux->...uyz', a, mats[0].conj()) / n[0]
+        a = np.einsum('...xyz,vy->...xvz', a, mats[1].conj()) / n[1]
+        return np.einsum('...xyz,wz->...xyw', a, mats[2].conj()) / n[2]
+    return fwd, inv
+
+
+# --------------------------------------------------------------------------
+# interaction energies (Sec. 2, Eq. interaction_energy3; Sec. 3.3)
+# --------------------------------------------------------------------------
+def energy_of_stencil(d, pos_Y, sigma6, h):
+    """-kappa V_vox sum_v eps*_d(Y)(v) : sigma(v) for defect d placed at pos_Y."""
+    n = np.array(sigma6.shape[1:])
+    c = pos_class(pos_Y)
+    offs, cnt, alpha = stencil(d, c, h)
+    e6 = to_voigt6(defect_geometry(d, h)['e'])
+    v = np.mod(base_voxel(pos_Y)[None, :] + offs, n[None, :])
+    sig = sigma6[:, v[:, 0], v[:, 1], v[:, 2]]          # (6, k)
+    s = np.sum(cnt * alpha * ddot6(e6, sig))
+    return -KAPPA * h ** 3 * s
+
+
+def as_record(d):
+    """Plain dict copy of a defect record (dict or numpy structured row)."""
+    if isinstance(d, dict):
+        return dict(d)
+    return {k: (np.array(d[k]) if np.ndim(d[k]) else d[k].item()) for k in d.dtype.names}
+
+
+def candidate_positions(pos):
+    pos = np.asarray(pos, dtype=np.int64)
+    return [pos + JUMPS[j] for j in range(8)]
+
+
+def allowed_jumps(d):
+    """Boolean mask over the 8 jumps for the defect's mobility (Sec. 5)."""
+    mob = int(d['mobility'])
+    if mob == IMMOBILE:
+        return np.zeros(8, bool)
+    if mob == THREE_D:
+        return np.ones(8, bool)
+    ax = AXES_111[int(d['axis'])]
+    return np.array([np.array_equal(JUMPS[j], ax) or np.array_equal(JUMPS[j], -ax)
+                     for j in range(8)])
+
+
+def energies_bruteforce(defects, n, h, C, k0_mode=MEAN_STRESS_ZERO, dft=None):
+    """E_i(X_i) and E_i(X_i + lambda_j) from the plain definition: one solve of all
+    defects except i per defect (N_d + 1 solves in total counting the base field).
+    Returns (E (n_d,), Ec (n_d, 8))."""
+    nd = len(defects)
+    E = np.zeros(nd)
+    Ec = np.zeros((nd, 8))
+    for i in range(nd):
+        sig = solve_stress(eigenstrain_field(defects, n, h, exclude={i}), C, h, k0_mode, dft)
+        E[i] = energy_of_stencil(defects[i], defects[i]['pos'], sig, h)
+        for j, Y in enumerate(candidate_positions(defects[i]['pos'])):
+            Ec[i, j] = energy_of_stencil(defects[i], Y, sig, h)
+    return E, Ec
+
+
+def energies_self_field(defects, n, h, C, k0_mode=MEAN_STRESS_ZERO, sample=None,
+                        sigma_total=None):
+    """Same quantities through sigma^(-i) = sigma - sigma_i (linearity); sigma_i is the
+    solve of defect i alone.  ``sample`` limits the defects evaluated."""
+    if sigma_total is None:
+        sigma_total = solve_stress(eigenstrain_field(defects, n, h), C, h, k0_mode)
+    idx = range(len(defects)) if sample is None else sample
+    out = {}
+    for i in idx:
+        sig_i = solve_stress(eigenstrain_field(defects, n, h, only={i}), C, h, k0_mode)
+        sig = sigma_total - sig_i
+        e0 = energy_of_stencil(defects[i], defects[i]['pos'], sig, h)
+        ec = np.array([energy_of_stencil(defects[i], Y, sig, h)
+                       for Y in candidate_positions(defects[i]['pos'])])
+        out[int(i)] = (e0, ec)
+    return out, sigma_total
+
+
+def self_term_table(d, n, h, C, k0_mode=MEAN_STRESS_ZERO):
+    """W(c, k): energy of defect d's own stencil placed at the current position (k = 0)
+    or at jump k-1 against the field of d alone at a reference site of class c.
+    Translation invariance under whole-voxel shifts makes it position independent."""
+    W = np.zeros((2, 9))
+    for c in (0, 1):
+        ref = np.array([c, c, c], dtype=np.int64)
+        dd = as_record(d)
+        dd['pos'] = ref
+        sig = solve_stress(eigenstrain_field([dd], n, h), C, h, k0_mode)
+        W[c, 0] = energy_of_stencil(d, ref, sig, h)
+        for j, Y in enumerate(candidate_positions(ref)):
+            W[c, 1 + j] = energy_of_stencil(d, Y, sig, h)
+    return W
+
+
+def green_operator_matrix(C, xi):
+    """Gamma_hat(xi) as a map on symmetric tensors (3,3,3,3), extracted from the solve of
+    Eq. EIG_elastic_fourier: for a polarisation tau, eps_hat = C^-1:sigma_hat + eps*_hat
+    with eps*_hat = C^-1:tau."""
+    C66 = stiffness_matrix(C)
+    S66 = np.linalg.inv(C66)
+    G = np.zeros((3, 3, 3, 3))
+    for a, (k, l) in enumerate(VOIGT):
+        tau6 = np.zeros(6)
+        tau6[a] = 1.0
+        tau = to_tensor(tau6)
+        if k != l:
+            tau = tau * 0.5            # unit symmetric tensor with tau_kl = tau_lk = 1/2
+        epsstar = strain_from_engineering(S66 @ stress_vec(tau))
+        sig = green_sigma_hat(C, np.asarray(xi, float)[None, :], epsstar[:, :, None].astype(complex),
+                              MEAN_STRESS_ZERO, np.zeros(1, bool))[:, :, 0].real
+        eps = strain_from_engineering(S66 @ stress_vec(sig)) + epsstar
+        G[:, :, k, l] = eps
+        G[:, :, l, k] = eps
+    return G
+
+
+# 6x6 helpers used only to invert C: stresses as plain VOIGT vectors, strains with
+# engineering shears
+def stress_vec(t):
+    return np.array([t[0, 0], t[1, 1], t[2, 2], t[1, 2], t[0, 2], t[0, 1]])
+
+
+def strain_from_engineering(v):
+    return np.array([[v[0], v[5] / 2, v[4] / 2], [v[5] / 2, v[1], v[3] / 2], [v[4] / 2, v[3] / 2, v[2]]])
+
+
+def stiffness_matrix(C):
+    """6x6 stiffness acting on engineering strains, giving stresses in VOIGT order."""
+    M = np.zeros((6, 6))
+    for a, (i, j) in enumerate(VOIGT):
+        for b, (k, l) in enumerate(VOIGT):
+            M[a, b] = C[i, j, k, l]
+    return M
+
+
+def self_term_table_fourier(d, n, h, C, k0_mode=MEAN_STRESS_ZERO):
+    """The table of ``self_term_table`` by Parseval: with w_c the count field of the
+    class-c stencil placed at the origin, q(xi) = e : sigma_hat[e](xi) (the stress
+    spectrum of a unit-amplitude eigenstrain e),
+      W(c, 0)     = -kappa h^3 a_c^2 / N  sum_xi q |w_c|^2
+      W(c, 1 + j) = -kappa h^3 a_c a_c' / N  Re sum_xi q conj(w_c') exp(+i xi.d_cj) w_c
+    where c' = 1 - c and d_cj is the whole-voxel shift between the two stencils."""
+    n = tuple(int(v) for v in n)
+    N = n[0] * n[1] * n[2]
+    e = defect_geometry(d, h)['e']
+    e6 = to_voigt6(e)
+    what, alpha = [], []
+    for c in (0, 1):
+        offs, cnt, a = stencil(d, c, h)
+        f = np.zeros(n)
+        v = np.mod(offs, np.array(n)[None, :])
+        np.add.at(f, (v[:, 0], v[:, 1], v[:, 2]), cnt.astype(float))
+        what.append(np.fft.fftn(f))
+        alpha.append(a)
+    xs = [frequencies(n[a], n[a] * h) for a in range(3)]
+    fr = [np.fft.fftfreq(n[a]) * n[a] for a in range(3)]
+    q = np.empty(n)
+    for ix in range(n[0]):
+        XI = np.stack(np.meshgrid(np.full(1, xs[0][ix]), xs[1], xs[2], indexing='ij'), axis=-1)[0]
+        zero = np.all(XI == 0.0, axis=-1)
+        eh = np.broadcast_to(e[:, :, None, None], (3, 3) + XI.shape[:2]).astype(complex)
+        sig = green_sigma_hat(C, XI, eh, k0_mode, zero)
+        q[ix] = ddot6(e6[:, None, None], to_voigt6(sig).real)
+    W = np.zeros((2, 9))
+    pref = -KAPPA * h ** 3 / N
+    for c in (0, 1):
+        cp = 1 - c
+        W[c, 0] = pref * alpha[c] ** 2 * np.sum(q * np.abs(what[c]) ** 2)
+        ref = np.array([c, c, c], dtype=np.int64)
+        for j in range(8):
+            dvec = base_voxel(ref + JUMPS[j]) - base_voxel(ref)
+            ph = 2.0 * PI * (fr[0][:, None, None] * dvec[0] / n[0] + fr[1][None, :, None] * dvec[1] / n[1]
+                             + fr[2][None, None, :] * dvec[2] / n[2])
+            W[c, 1 + j] = pref * alpha[c] * alpha[cp] * np.sum(
+                q * (np.conj(what[cp]) * np.exp(1j * ph) * what[c])).real
+    return W
+
+
+# --------------------------------------------------------------------------
+# rates and event selection (Sec. 5; Appendix A, Algorithm 1)
+# --------------------------------------------------------------------------
+def nominal_frequency(Em, T, nu0=NU0_DEFAULT):
+    """Eq. unbiased_boltzmann."""
+    return nu0 * math.exp(-Em / (KB * T))
+
+
+def jump_rates(Em, E0, Ec, allowed, T, nu0=NU0_DEFAULT):
+    """Biased frequencies of the allowed jumps (Eqs. biased_forward/backward_boltzmann
+    with prefactor 1/z, z = number of allowed jumps); zero for the others."""
+    z = int(np.sum(allowed))
+    r = np.zeros(8)
+    if z == 0:
+        return r
+    for j in range(8):
+        if allowed[j]:
+            r[j] = (nu0 / z) * math.exp(-(Em + 0.5 * (Ec[j] - E0)) / (KB * T))
+    return r
+
+
+def select_on_line(rates, u):
+    """First index k with R_{k-1} < u R_tot <= R_k on the running sum (Eq. selection_jump)."""
+    R = np.cumsum(rates)
+    target = u * R[-1]
+    k = int(np.searchsorted(R, target, side='left'))
+    return min(k, len(rates) - 1), R
+
+
+# ---- Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), from its published definition
+_M0, _M1 = 0xD2511F53, 0xCD9E8D57
+_W0, _W1 = 0x9E3779B9, 0xBB67AE85
+_MASK = 0xFFFFFFFF
+
+
+def philox4x32_10(ctr, key):
+    x = [int(v) & _MASK for v in ctr]
+    k0, k1 = int(key[0]) & _MASK, int(key[1]) & _MASK
+    for r in range(10):
+        if r:
+            k0 = (k0 + _W0) & _MASK
+            k1 = (k1 + _W1) & _MASK
+        p0 = _M0 * x[0]
+        p1 = _M1 * x[2]
+        hi0, lo0 = p0 >> 32, p0 & _MASK
+        hi1, lo1 = p1 >> 32, p1 & _MASK
+        x = [hi1 ^ x[1] ^ k0, lo1, hi0 ^ x[3] ^ k1, lo0]
+    return x
+
+
+def u53(lo, hi):
+    """Uniform on (0, 1] from 53 bits: ((hi << 21) | (lo >> 11)) + 1 over 2^53."""
+    return float(((hi << 21) | (lo >> 11)) + 1) * (2.0 ** -53)
+
+
+def uniforms(seed, ctr):
+    """Two uniforms from one Philox block; key = seed (64 bit), counter = ctr (4 words)."""
+    x = philox4x32_10(ctr, (seed & _MASK, (seed >> 32) & _MASK))
+    return u53(x[0], x[1]), u53(x[2], x[3])
+
+
+TAG_RESIDENCE, TAG_FIXED_DT = 0, 1
+NO_DEFECT = 0xFFFFFFFF
+
+
+def residence_uniforms(seed, step):
+    return uniforms(seed, (step & _MASK, (step >> 32) & _MASK, NO_DEFECT, TAG_RESIDENCE))
+
+
+def fixed_dt_uniforms(seed, step, i):
+    return uniforms(seed, (step & _MASK, (step >> 32) & _MASK, i, TAG_FIXED_DT))
+
+
+def residence_step(defects, E, Ec, T, seed, step, n, nu0=NU0_DEFAULT):
+    """One residence-time event: every allowed jump of every defect on one frequency
+    line; returns (i, j, dt, R_tot) and moves defect i in place."""
+    rates = np.concatenate([jump_rates(float(d['Em_eV']), E[i], Ec[i], allowed_jumps(d), T, nu0)
+                            for i, d in enumerate(defects)])
+    u1, u2 = residence_uniforms(seed, step)
+    k, R = select_on_line(rates, u1)
+    i, j = divmod(k, 8)
+    dt = -math.log(u2) / R[-1]
+    p = np.mod(np.asarray(defects[i]['pos'], dtype=np.int64) + JUMPS[j], 2 * np.asarray(n))
+    defects[i]['pos'] = p
+    return i, j, dt, R[-1]
+
+
+def fixed_dt(defects, T, nu0=NU0_DEFAULT):
+    """delta t = 1/nu_max over the mobile defects, nominal barriers (Eq. time_step)."""
+    nus = [nominal_frequency(float(d['Em_eV']), T, nu0) for d in defects
+           if int(d['mobility']) != IMMOBILE]
+    return 1.0 / max(nus)
+
+
+def fixed_dt_step(defects, E, Ec, T, seed, step, n, dt, nu0=NU0_DEFAULT):
+    """One synchronous step of Algorithm 1: each mobile defect draws its Poisson count
+    with the nominal frequency; if it is > 0 it selects one jump on its biased
+    frequency line.  All decisions use the start-of-step energies; moves are applied
+    together.  Returns the list of (i, j) jumps."""
+    moves = []
+    for i, d in enumerate(defects):
+        al = allowed_jumps(d)
+        if not al.any():
+            continue
+        up, us = fixed_dt_uniforms(seed, step, i)
+        mu = nominal_frequency(float(d['Em_eV']), T, nu0) * dt
+        if up <= math.exp(-mu):             # N_i = 0 by CDF inversion (Eq. poisson)
+            continue
+        r = jump_rates(float(d['Em_eV']), E[i], Ec[i], al, T, nu0)
+        j, _ = select_on_line(r, us)
+        moves.append((i, j))
+    for i, j in moves:
+        defects[i]['pos'] = np.mod(np.asarray(defects[i]['pos'], dtype=np.int64) + JUMPS[j],
+                                   2 * np.asarray(n))
+    return moves
+
+
+# --------------------------------------------------------------------------
+# dipole-limit helpers for the far-field pin (Sec. 2.1, Eqs. interaction_energy4, dipole_DL)
+# --------------------------------------------------------------------------
+def loop_dipole_tensor(C, b, A):
+    """P = (1/2) C : (b (x) A + A (x) b) (Eq. dipole_DL)."""
+    S = 0.5 * (np.outer(b, A) + np.outer(A, b))
+    return np.einsum('ijkl,kl->ij', C, S)
+
+
+def kelvin_green(x, mu, nu):
+    """Isotropic infinite-body Green's function G_ik(x) (Kelvin solution)."""
+    r = np.linalg.norm(x)
+    return ((3.0 - 4.0 * nu) * np.eye(3) + np.outer(x, x) / r ** 2) / (16.0 * PI * mu * (1.0 - nu) * r)
+
+
+def dipole_dipole_energy(P1, P2, d, mu, nu, step=1e-3):
+    """E = P1_ij P2_kl d_j d_l G_ik(d), second derivatives by central differences."""
+    s = step * np.linalg.norm(d)
+    D = np.zeros((3, 3, 3, 3))       # D[i,k,j,l] = d_j d_l G_ik
+    I = np.eye(3)
+    for j in range(3):
+        for l in range(3):
+            g = (kelvin_green(d + s * I[j] + s * I[l], mu, nu)
+                 - kelvin_green(d + s * I[j] - s * I[l], mu, nu)
+                 - kelvin_green(d - s * I[j] + s * I[l], mu, nu)
+                 + kelvin_green(d - s * I[j] - s * I[l], mu, nu)) / (4.0 * s * s)
+            D[:, :, j, l] = g
+    return float(np.einsum('ij,kl,ikjl->', P1, P2, D))

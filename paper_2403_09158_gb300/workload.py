@@ -1,0 +1,189 @@
+"""Seeded synthetic workloads: defect lists in the paper's setting.
+
+Only random draws and placement live here (no eigenstrain, solve, energy or
+rate arithmetic), so that the CUDA path and the CPU oracle can be fed the very
+same inputs.  Defect mix, sizes and temperatures follow the paper's OkMC
+setting for bcc Fe (Sec. 5: 1/2<111> loops migrating in 1D with E_m = 0.1 eV,
+<100> loops immobile, SIAs migrating in 3D; Sec. 5.3: ~6e18 cm^-3 SIA density).
+
+Records use ``DEFECT_DTYPE``, whose memory layout is the C struct
+``okmc_defect`` of ``include/okmc.h`` (48 bytes, little endian).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+LOOP_111, LOOP_100, SIA_CLUSTER = 0, 1, 2
+IMMOBILE, ONE_D, THREE_D = 0, 1, 2
+
+DEFECT_DTYPE = np.dtype([
+    ('type', '<i4'), ('pos', '<i4', (3,)), ('axis', '<i4'), ('size', '<i4'),
+    ('mobility', '<i4'), ('reserved', '<i4'), ('radius_nm', '<f8'), ('Em_eV', '<f8'),
+])
+assert DEFECT_DTYPE.itemsize == 48
+
+FE_CUBIC = (243.0, 145.0, 116.0)         # C11, C12, C44 in GPa (synthetic Fe constants)
+FE_ISO = (82.0, 0.29)                    # mu (GPa), nu
+FE_TABLE1 = (289.34, 152.34, 107.43)     # Table 1 of the paper
+VOXEL_NM = 0.2855                        # a0 = voxel edge h
+
+
+@dataclass
+class Workload:
+    name: str
+    n: tuple
+    voxel_nm: float
+    defects: np.ndarray
+    T_K: float
+    C: tuple = FE_CUBIC
+    seed: int = 0
+    events: int = 0
+    extra: dict = field(default_factory=dict)
+
+
+def _shape_radius_nm(kind, radius_nm, size, h):
+    if kind == SIA_CLUSTER:
+        return max(h, (3.0 * size * 0.5 * h ** 3 / (4.0 * math.pi)) ** (1.0 / 3.0))
+    return radius_nm
+
+
+def place(rng, n, h, kinds, radii, sizes, max_tries=20000):
+    """Uniform bcc sites (integer half-lattice coordinates, all even or all odd),
+    rejecting a site closer than R_i + R_j + 2h (minimum image) to an earlier one."""
+    n = np.asarray(n)
+    L = n * h
+    pos = np.zeros((len(kinds), 3), dtype=np.int64)
+    centres = []
+    rr = []
+    for i, (k, R, s) in enumerate(zip(kinds, radii, sizes)):
+        Ri = _shape_radius_nm(k, R, s, h)
+        for _ in range(max_tries):
+            c = int(rng.integers(0, 2))
+            p = 2 * rng.integers(0, n) + c
+            x = p * (h / 2.0)
+            ok = True
+            for xc, Rj in zip(centres, rr):
+                dvec = x - xc
+                dvec -= L * np.round(dvec / L)
+                if np.sqrt(dvec @ dvec) < Ri + Rj + 2.0 * h:
+                    ok = False
+                    break
+            if ok:
+                break
+        else:
+            raise RuntimeError('could not place defect %d' % i)
+        pos[i] = p
+        centres.append(x)
+        rr.append(Ri)
+    return pos
+
+
+def make_defects(kinds, pos, axes, radii, sizes, Em, mobility):
+    d = np.zeros(len(kinds), dtype=DEFECT_DTYPE)
+    d['type'] = kinds
+    d['pos'] = pos
+    d['axis'] = axes
+    d['radius_nm'] = radii
+    d['size'] = sizes
+    d['Em_eV'] = Em
+    d['mobility'] = mobility
+    return d
+
+
+def mixed_population(n, n_defects, seed, frac=(0.6, 0.3, 0.1), r111=(0.5, 2.5),
+                     r100=(1.0, 3.0), p_geom=0.3, h=VOXEL_NM, single_sia_3d=True,
+                     em_loop=0.1, em_sia=0.3):
+    """SIA clusters (size ~ Geometric(p)), 1/2<111> loops and <100> loops in the given
+    fractions, uniform positions and orientations."""
+    rng = np.random.default_rng(seed)
+    n_sia = int(round(frac[0] * n_defects))
+    n_111 = int(round(frac[1] * n_defects))
+    n_100 = n_defects - n_sia - n_111
+    kinds = np.array([SIA_CLUSTER] * n_sia + [LOOP_111] * n_111 + [LOOP_100] * n_100)
+    sizes = np.zeros(n_defects, dtype=np.int64)
+    sizes[:n_sia] = rng.geometric(p_geom, n_sia)
+    radii = np.zeros(n_defects)
+    radii[n_sia:n_sia + n_111] = rng.uniform(r111[0], r111[1], n_111)
+    radii[n_sia + n_111:] = rng.uniform(r100[0], r100[1], n_100)
+    axes = np.zeros(n_defects, dtype=np.int64)
+    axes[:n_sia + n_111] = rng.integers(0, 4, n_sia + n_111)
+    axes[n_sia + n_111:] = rng.integers(0, 3, n_100)
+    # place large defects first so rejection sampling converges
+    order = np.argsort(-np.array([_shape_radius_nm(k, r, s, h) for k, r, s in zip(kinds, radii, sizes)]),
+                       kind='stable')
+    pos_sorted = place(rng, n, h, kinds[order], radii[order], sizes[order])
+    pos = np.zeros_like(pos_sorted)
+    pos[order] = pos_sorted
+    Em = np.where(kinds == SIA_CLUSTER, em_sia, np.where(kinds == LOOP_111, em_loop, 1.0))
+    mob = np.where(kinds == LOOP_100, IMMOBILE, ONE_D)
+    if single_sia_3d:
+        mob = np.where((kinds == SIA_CLUSTER) & (sizes == 1), THREE_D, mob)
+    return make_defects(kinds, pos, axes, radii, sizes, Em, mob)
+
+
+def config_small(seed=1001, n=32, h=VOXEL_NM):
+    """32^3 box: two 1/2[111] loops (R = 1 nm) at a seeded separation of 2-6 nm and
+    8 SIA clusters of 1-10 atoms migrating in 1D (E_m = 0.3 eV); 300 K."""
+    rng = np.random.default_rng(seed)
+    L = n * h
+    for _ in range(1000):
+        sep = rng.uniform(2.0, 6.0)
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        p0 = 2 * (np.array([n, n, n]) // 2)
+        dp = np.round(u * sep / (h / 2.0)).astype(np.int64)
+        if np.any((dp & 1) != (dp[0] & 1)):
+            dp = 2 * np.round(u * sep / h).astype(np.int64)
+        p1 = np.mod(p0 + dp, 2 * n)
+        if 2.0 <= np.linalg.norm(dp * h / 2.0) <= 6.0 + h:
+            break
+    loops = make_defects([LOOP_111, LOOP_111], np.stack([p0, p1]), [0, 0], [1.0, 1.0], [0, 0],
+                         [0.1, 0.1], [ONE_D, ONE_D])
+    sizes = rng.integers(1, 11, 8)
+    kinds = [SIA_CLUSTER] * 8
+    occupied = [(p0 * h / 2.0, 1.0), (p1 * h / 2.0, 1.0)]
+    pos = []
+    for s in sizes:
+        Ri = _shape_radius_nm(SIA_CLUSTER, 0.0, s, h)
+        while True:
+            c = int(rng.integers(0, 2))
+            p = 2 * rng.integers(0, n, 3) + c
+            x = p * h / 2.0
+            ok = True
+            for xc, Rj in occupied:
+                dv = x - xc
+                dv -= L * np.round(dv / L)
+                if np.linalg.norm(dv) < Ri + Rj + 2.0 * h:
+                    ok = False
+                    break
+            if ok:
+                break
+        occupied.append((x, Ri))
+        pos.append(p)
+    sias = make_defects(kinds, np.array(pos), rng.integers(0, 4, 8), np.zeros(8), sizes,
+                        np.full(8, 0.3), np.full(8, ONE_D))
+    d = np.concatenate([loops, sias])
+    return Workload('small_32cubed_2loops_8sia', (n, n, n), h, d, 300.0, FE_CUBIC, seed, 100)
+
+
+def config_medium(seed=1002, n=128, n_defects=200):
+    """128^3 box, 200 defects: 60 % SIA clusters, 30 % 1/2<111> loops R ~ U(0.5, 2.5) nm,
+    10 % <100> loops R ~ U(1, 3) nm; 400 K."""
+    d = mixed_population((n, n, n), n_defects, seed, r111=(0.5, 2.5), r100=(1.0, 3.0))
+    return Workload('medium_128cubed_200defects', (n, n, n), VOXEL_NM, d, 400.0, FE_CUBIC, seed, 10000)
+
+
+def config_large(seed=1003, n=256, n_defects=2000):
+    """256^3 box, 2000 defects with the same mix, all loop radii ~ U(0.5, 4) nm; 500 K."""
+    d = mixed_population((n, n, n), n_defects, seed, r111=(0.5, 4.0), r100=(0.5, 4.0))
+    return Workload('large_256cubed_2000defects', (n, n, n), VOXEL_NM, d, 500.0, FE_CUBIC, seed, 10000)
+
+
+def scaled_population(n, n_defects, seed, T_K=500.0, r111=(0.5, 4.0), r100=(0.5, 4.0)):
+    """Any grid with the large-config mix (used for ragged and intermediate sizes)."""
+    n = tuple(int(v) for v in (n if np.ndim(n) else (n, n, n)))
+    d = mixed_population(n, n_defects, seed, r111=r111, r100=r100)
+    return Workload('mix_%dx%dx%d_%d' % (n + (n_defects,)), n, VOXEL_NM, d, T_K, FE_CUBIC, seed, 0)

@@ -1,0 +1,431 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a naive DFT,
+closed forms, invariants, the paper's printed numbers (tests/golden/), brute
+force on tiny grids, or a statistical law.  No GPU needed.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2403_09158_gb300.workload import DEFECT_DTYPE, make_defects
+
+GOLD = os.path.join(os.path.dirname(__file__), 'golden')
+H = 0.2855
+C_CUBIC = O.stiffness_cubic(243.0, 145.0, 116.0)
+
+
+def _defects_small(n=16):
+    """A loop, a <100> loop and two SIA clusters inside a small box."""
+    return make_defects(
+        [O.LOOP_111, O.LOOP_100, O.SIA_CLUSTER, O.SIA_CLUSTER],
+        np.array([[4, 4, 4], [19, 13, 21], [10, 26, 6], [27, 7, 15]]),
+        [1, 2, 0, 3], [0.55, 0.5, 0.0, 0.0], [0, 0, 3, 1], [0.1, 1.0, 0.3, 0.3],
+        [O.ONE_D, O.IMMOBILE, O.ONE_D, O.THREE_D])
+
+
+# ---------------------------------------------------------------- P1: transforms
+@pytest.mark.parametrize('n', [(6, 10, 15), (8, 12, 5), (16, 6, 9)])
+def test_p1_solve_with_naive_dft_matches(n):
+    rng = np.random.default_rng(1)
+    eps = rng.normal(size=(6,) + n)
+    a = O.solve_stress(eps, C_CUBIC, H, O.MEAN_STRESS_ZERO)
+    b = O.solve_stress(eps, C_CUBIC, H, O.MEAN_STRESS_ZERO, dft=O.naive_dft_pair(n))
+    assert np.linalg.norm(a - b) <= 1e-12 * np.linalg.norm(a)
+    fwd, _ = O.naive_dft_pair(n)
+    x = rng.normal(size=n)
+    assert np.allclose(fwd(x), np.fft.fftn(x), rtol=0, atol=1e-10)
+
+
+def test_p1_frequencies_follow_paper_convention():
+    # Eq. frequencies: n = m - N/2 (even N) after centring: the set {-N/2 .. N/2-1}
+    f = O.frequencies(8, 8.0) * 8.0 / (2 * np.pi)
+    assert sorted(np.round(f).astype(int).tolist()) == list(range(-4, 4))
+    f = O.frequencies(7, 7.0) * 7.0 / (2 * np.pi)
+    assert sorted(np.round(f).astype(int).tolist()) == list(range(-3, 4))
+
+
+# ---------------------------------------------------------------- P2: uniform eigenstrain
+@pytest.mark.parametrize('n', [(8, 8, 8), (6, 10, 5)])
+def test_p2_uniform_eigenstrain(n):
+    e6 = np.array([1e-3, -2e-3, 5e-4, 3e-4, -1e-4, 2e-4])
+    eps = np.broadcast_to(e6[:, None, None, None], (6,) + n).copy()
+    s0 = O.solve_stress(eps, C_CUBIC, H, O.MEAN_STRESS_ZERO)
+    assert np.abs(s0).max() < 1e-13
+    s1 = O.solve_stress(eps, C_CUBIC, H, O.MEAN_STRAIN_ZERO)
+    expect = -O.to_voigt6(np.einsum('ijkl,kl->ij', C_CUBIC, O.to_tensor(e6)))
+    assert np.abs(s1 - expect[:, None, None, None]).max() < 1e-13
+
+
+# ---------------------------------------------------------------- P3: per-frequency identities
+def test_p3_idempotence_equilibrium_compatibility():
+    rng = np.random.default_rng(2)
+    C9 = C_CUBIC.reshape(9, 9)
+    for _ in range(20):
+        xi = rng.normal(size=3)
+        G = O.green_operator_matrix(C_CUBIC, xi)
+        G9 = G.reshape(9, 9)
+        assert np.abs(G9 @ C9 @ G9 - G9).max() < 1e-13 * np.abs(G9).max() * 50
+        # sigma_hat = C:(Gamma:tau - eps*) must satisfy m . sigma_hat = 0 (equilibrium)
+        tau = O.to_tensor(rng.normal(size=6))
+        eps_star = O.strain_from_engineering(np.linalg.solve(O.stiffness_matrix(C_CUBIC), O.stress_vec(tau)))
+        sig = O.green_sigma_hat(C_CUBIC, xi[None, :], eps_star[:, :, None].astype(complex),
+                                O.MEAN_STRESS_ZERO, np.zeros(1, bool))[:, :, 0]
+        m = xi / np.linalg.norm(xi)
+        assert np.abs(sig @ m).max() < 1e-12 * np.abs(sig).max()
+        # the total strain Gamma:tau is compatible: P_perp eps P_perp = 0
+        eps = np.einsum('ijkl,kl->ij', G, tau)
+        P = np.eye(3) - np.outer(m, m)
+        assert np.abs(P @ eps @ P).max() < 1e-13 * np.abs(eps).max() * 10
+
+
+def test_p3_real_space_equilibrium_on_odd_grid():
+    # odd edges have no Nyquist index, so discrete equilibrium holds at every frequency
+    n = (9, 7, 11)
+    rng = np.random.default_rng(3)
+    sig = O.solve_stress(rng.normal(size=(6,) + n), C_CUBIC, H, O.MEAN_STRESS_ZERO)
+    sh = O.to_tensor(np.fft.fftn(sig, axes=(1, 2, 3)))
+    xs = [O.frequencies(n[a], n[a] * H) for a in range(3)]
+    XI = np.stack(np.meshgrid(*xs, indexing='ij'), axis=0)
+    div = np.einsum('ij...,j...->i...', sh, XI)
+    assert np.abs(div).max() < 1e-11 * np.abs(sh).max()
+
+
+# ---------------------------------------------------------------- P4: isotropic closed form
+def test_p4_isotropic_matches_moulinec_suquet():
+    mu, nu = 82.0, 0.29
+    C11, C12, C44 = O.isotropic_cubic_constants(mu, nu)
+    lam = C12
+    C = O.stiffness_cubic(C11, C12, C44)
+    d = np.eye(3)
+    rng = np.random.default_rng(4)
+    for _ in range(10):
+        xi = rng.normal(size=3)
+        x2 = xi @ xi
+        ref = (np.einsum('ki,h,j->khij', d, xi, xi) + np.einsum('hi,k,j->khij', d, xi, xi)
+               + np.einsum('kj,h,i->khij', d, xi, xi) + np.einsum('hj,k,i->khij', d, xi, xi)) / (4 * mu * x2)
+        ref -= (lam + mu) / (mu * (lam + 2 * mu)) * np.einsum('i,j,k,h->khij', xi, xi, xi, xi) / x2 ** 2
+        G = O.green_operator_matrix(C, xi)
+        assert np.abs(G - ref).max() < 1e-14 * 1e3 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- P5/P6: energies
+def test_p5_reciprocity():
+    n = (16, 16, 16)
+    d = _defects_small()
+    i, j = 0, 2
+    s_j = O.solve_stress(O.eigenstrain_field(d, n, H, only={j}), C_CUBIC, H)
+    s_i = O.solve_stress(O.eigenstrain_field(d, n, H, only={i}), C_CUBIC, H)
+    Eij = O.energy_of_stencil(d[i], d[i]['pos'], s_j, H)
+    Eji = O.energy_of_stencil(d[j], d[j]['pos'], s_i, H)
+    assert abs(Eij) > 1e-4
+    assert abs(Eij - Eji) <= 1e-10 * abs(Eij)
+
+
+def test_p6_bruteforce_equals_self_field_and_table():
+    n = (16, 16, 16)
+    d = _defects_small()
+    E, Ec = O.energies_bruteforce(d, n, H, C_CUBIC)
+    res, sig = O.energies_self_field(d, n, H, C_CUBIC)
+    for i in range(len(d)):
+        assert abs(res[i][0] - E[i]) <= 1e-10 * max(1.0, abs(E[i]))
+        assert np.abs(res[i][1] - Ec[i]).max() <= 1e-10 * max(1.0, np.abs(Ec[i]).max())
+        # table route: total-field energy minus the translation-invariant self term
+        W = O.self_term_table(d[i], n, H, C_CUBIC)
+        Wf = O.self_term_table_fourier(d[i], n, H, C_CUBIC)
+        assert np.abs(W - Wf).max() <= 1e-10 * np.abs(W).max()
+        c = O.pos_class(d[i]['pos'])
+        e0 = O.energy_of_stencil(d[i], d[i]['pos'], sig, H) - W[c, 0]
+        assert abs(e0 - E[i]) <= 1e-9 * max(1.0, np.abs(W).max())
+        for jj, Y in enumerate(O.candidate_positions(d[i]['pos'])):
+            ej = O.energy_of_stencil(d[i], Y, sig, H) - W[c, 1 + jj]
+            assert abs(ej - Ec[i, jj]) <= 1e-9 * max(1.0, np.abs(W).max())
+
+
+def test_p6_paper_form_equals_eigenstrain_form():
+    # Eq. interaction_energy3: int sigma_ext : eps^{d,e} = -int sigma_ext : eps*_d.  Exact on
+    # odd edges; on even edges the averaged Nyquist operator breaks it by a few 1e-3.
+    n = (15, 15, 15)
+    d = _defects_small()
+    i = 1
+    s_ext = O.solve_stress(O.eigenstrain_field(d, n, H, exclude={i}), C_CUBIC, H)
+    eps_i = O.eigenstrain_field(d, n, H, only={i})
+    s_i = O.solve_stress(eps_i, C_CUBIC, H)
+    S = np.linalg.inv(O.stiffness_matrix(C_CUBIC))
+    # elastic strain of defect i alone, eps^{d,e} = C^-1 : sigma_i (engineering -> tensor)
+    eng = np.einsum('ab,b...->a...', S, s_i)
+    eps_e = eng.copy()
+    eps_e[3:] *= 0.5
+    lhs = O.KAPPA * H ** 3 * np.sum(O.ddot6(s_ext, eps_e))
+    rhs = -O.KAPPA * H ** 3 * np.sum(O.ddot6(s_ext, eps_i))
+    assert abs(lhs - rhs) <= 1e-10 * abs(rhs)
+
+
+# ---------------------------------------------------------------- P7: zero-frequency modes
+def test_p7_k0_modes():
+    n = (16, 16, 16)
+    d = _defects_small()
+    E0, Ec0 = O.energies_bruteforce(d, n, H, C_CUBIC, O.MEAN_STRESS_ZERO)
+    E1, Ec1 = O.energies_bruteforce(d, n, H, C_CUBIC, O.MEAN_STRAIN_ZERO)
+    dE0 = Ec0 - E0[:, None]
+    dE1 = Ec1 - E1[:, None]
+    assert np.abs(dE0 - dE1).max() < 1e-10
+    Vtot = np.prod(n) * H ** 3
+    for i in range(len(d)):
+        e_others = O.eigenstrain_field(d, n, H, exclude={i}).reshape(6, -1).mean(axis=1)
+        sbar = -O.to_voigt6(np.einsum('ijkl,kl->ij', C_CUBIC, O.to_tensor(e_others)))
+        int_eps_i = O.eigenstrain_field(d, n, H, only={i}).reshape(6, -1).sum(axis=1) * H ** 3
+        shift = -O.KAPPA * O.ddot6(int_eps_i, sbar)
+        assert abs((E1[i] - E0[i]) - shift) < 1e-10 * max(1.0, abs(shift))
+    assert Vtot > 0
+
+
+# ---------------------------------------------------------------- P8: dipole far field
+def test_p8_dipole_limit_isotropic():
+    """Far field (Sec. 2.1, Eq. interaction_energy4 with P from Appendix B): the energy
+    change between separations along a ray tends to the Kelvin dipole-dipole value as
+    (R/d)^2 -> 0, and the periodic solution differs from the infinite body by a constant
+    (the box's mean field) that scales as 1/V."""
+    mu, nu = 82.0, 0.29
+    C = O.stiffness_cubic(*O.isotropic_cubic_constants(mu, nu))
+    offsets = {}
+    for N in (64, 96):
+        n = (N, N, N)
+        c0 = np.array([N, N, N])
+        loop = dict(type=O.LOOP_111, pos=c0, axis=0, radius_nm=0.35, size=0, Em_eV=0.1,
+                    mobility=O.ONE_D)
+        eps = O.eigenstrain_field([loop], n, H)
+        s0 = O.solve_stress(eps, C, H, O.MEAN_STRAIN_ZERO)
+        P = np.einsum('ijkl,kl->ij', C, O.to_tensor(eps.reshape(6, -1).sum(axis=1) * H ** 3))
+        rows = []
+        for step in (6, 8, 10, 12, 14):
+            p2 = c0 + step * np.array([2, 1, -1])
+            E = O.energy_of_stencil(dict(loop, pos=p2), p2, s0, H)
+            Ed = O.dipole_dipole_energy(P, P, (p2 - c0) * H / 2.0, mu, nu) * O.KAPPA
+            rows.append((E, Ed))
+        offsets[N] = rows[3][0] - rows[3][1]
+        if N == 96:
+            errs = [abs((rows[k + 1][0] - rows[k][0]) / (rows[k + 1][1] - rows[k][1]) - 1.0)
+                    for k in range(len(rows) - 1)]
+            assert all(errs[k + 1] < errs[k] for k in range(len(errs) - 1)), errs
+            assert errs[-1] < 5e-3
+    ratio = offsets[64] / offsets[96]
+    assert abs(ratio / (96.0 / 64.0) ** 3 - 1.0) < 0.15, offsets
+
+
+def test_p11_integrated_eigenstrain_and_dipole_identity():
+    n = (16, 16, 16)
+    loop = dict(type=O.LOOP_111, pos=np.array([9, 9, 9]), axis=2, radius_nm=0.7, size=0,
+                Em_eV=0.1, mobility=O.ONE_D)
+    eps = O.eigenstrain_field([loop], n, H)
+    int_eps = eps.reshape(6, -1).sum(axis=1) * H ** 3
+    g = O.defect_geometry(loop, H)
+    A = np.pi * 0.7 ** 2 * g['n']
+    expect = O.to_voigt6(0.5 * (np.outer(g['b'], A) + np.outer(A, g['b'])))
+    assert np.abs(int_eps - expect).max() < 1e-12
+    s = O.solve_stress(eps, C_CUBIC, H, O.MEAN_STRAIN_ZERO)
+    P_field = -s.reshape(6, -1).sum(axis=1) * H ** 3
+    P_app_b = O.to_voigt6(O.loop_dipole_tensor(C_CUBIC, g['b'], A))
+    assert np.abs(P_field - P_app_b).max() < 1e-12 * np.abs(P_app_b).max()
+    sia = dict(type=O.SIA_CLUSTER, pos=np.array([8, 8, 8]), axis=0, radius_nm=0.0, size=4,
+               Em_eV=0.3, mobility=O.ONE_D)
+    tr = O.eigenstrain_field([sia], n, H).reshape(6, -1).sum(axis=1)[:3].sum() * H ** 3
+    assert abs(tr - 1.5 * 4 * H ** 3 / 2.0) < 1e-14
+
+
+# ---------------------------------------------------------------- P10: translation invariance
+def test_p10_shift_invariance():
+    n = (16, 16, 16)
+    d = _defects_small()
+    E, Ec = O.energies_bruteforce(d, n, H, C_CUBIC)
+    d2 = d.copy()
+    d2['pos'] = np.mod(d2['pos'] + np.array([6, -4, 10]), 32)
+    E2, Ec2 = O.energies_bruteforce(d2, n, H, C_CUBIC)
+    assert np.abs(E2 - E).max() < 1e-12 and np.abs(Ec2 - Ec).max() < 1e-12
+
+
+# ---------------------------------------------------------------- stencils
+@pytest.mark.parametrize('rec', [
+    dict(type=0, axis=0, radius_nm=1.3, size=0), dict(type=0, axis=3, radius_nm=0.52, size=0),
+    dict(type=1, axis=1, radius_nm=0.9, size=0), dict(type=2, axis=0, radius_nm=0.0, size=1),
+    dict(type=2, axis=0, radius_nm=0.0, size=40)])
+def test_stencil_volume_and_real_coordinate_coverage(rec):
+    rec = dict(rec, pos=np.array([0, 0, 0]), Em_eV=0.1, mobility=0)
+    g = O.defect_geometry(rec, H)
+    rng = np.random.default_rng(5)
+    for c in (0, 1):
+        offs, cnt, alpha = O.stencil(rec, c, H)
+        assert abs(cnt.sum() * alpha - g['v_over_h3']) < 1e-12 * g['v_over_h3']
+        # recount a few voxels from real coordinates (centre at c*(h/2) per axis)
+        X = np.full(3, c * H / 2.0)
+        table = {tuple(o): k for o, k in zip(offs.tolist(), cnt.tolist())}
+        cand = list(table.keys())[:12] + [tuple(v) for v in rng.integers(-3, 4, (12, 3))]
+        for v in cand:
+            k = 0
+            for i in range(4):
+                for j in range(4):
+                    for l in range(4):
+                        x = (np.array(v) + (np.array([i, j, l]) + 0.5) / 4.0) * H - X
+                        if g['kind'] == 'disk':
+                            t = x @ g['n']
+                            inside = abs(t) <= H / 2 + 1e-12 and (x @ x - t * t) <= g['R'] ** 2 + 1e-12
+                        else:
+                            inside = x @ x <= (g['v_over_h3'] * 3 / (4 * np.pi)) ** (2 / 3) * H ** 2 + 1e-12
+                        k += inside
+            assert k == table.get(tuple(v), 0), (c, v)
+
+
+def test_stencil_point_symmetry():
+    rec = dict(type=0, axis=2, radius_nm=1.1, size=0, pos=np.array([0, 0, 0]), Em_eV=0.1, mobility=0)
+    o1, c1, _ = O.stencil(rec, 1, H)        # centre at a voxel centre: v -> -v
+    t1 = {tuple(o): k for o, k in zip(o1.tolist(), c1.tolist())}
+    assert all(t1[tuple(-np.array(o))] == k for o, k in t1.items())
+    o0, c0, _ = O.stencil(rec, 0, H)        # centre at a voxel corner: v -> -v - 1
+    t0 = {tuple(o): k for o, k in zip(o0.tolist(), c0.tolist())}
+    assert all(t0[tuple(-np.array(o) - 1)] == k for o, k in t0.items())
+
+
+# ---------------------------------------------------------------- Nyquist reading
+def test_nyquist_reading_equals_half_spectrum_with_averaged_operator():
+    """On even edges the real part of the inverse equals applying, on the Nyquist
+    planes, the average of the operator over the sign of the Nyquist components."""
+    n = (8, 6, 10)
+    rng = np.random.default_rng(6)
+    eps = rng.normal(size=(6,) + n)
+    ref = O.solve_stress(eps, C_CUBIC, H, O.MEAN_STRESS_ZERO)
+    eh = np.fft.rfftn(eps, axes=(3, 2, 1))        # half spectrum along x (axis 1)
+    eh = np.fft.rfftn(eps.transpose(0, 3, 2, 1), axes=(1, 2, 3))  # (6, nz, ny, nx//2+1)
+    nz, ny, nxh = eh.shape[1:]
+    out = np.zeros_like(eh)
+    for kz in range(nz):
+        for ky in range(ny):
+            for kx in range(nxh):
+                fr = np.array([kx if kx < n[0] // 2 else -n[0] // 2,
+                               ky if ky < n[1] // 2 else ky - n[1],
+                               kz if kz < n[2] // 2 else kz - n[2]], dtype=float)
+                nyq = np.array([kx == n[0] // 2, ky == n[1] // 2, kz == n[2] // 2])
+                xi = 2 * np.pi * fr / (np.array(n) * H)
+                e3 = O.to_tensor(eh[:, kz, ky, kx])[:, :, None]
+                zero = np.array([not xi.any()])
+                s = O.green_sigma_hat(C_CUBIC, xi[None], e3, O.MEAN_STRESS_ZERO, zero)
+                if nyq.any():
+                    xi2 = np.where(nyq, -xi, xi)
+                    s = 0.5 * (s + O.green_sigma_hat(C_CUBIC, xi2[None], e3, O.MEAN_STRESS_ZERO, zero))
+                out[:, kz, ky, kx] = O.to_voigt6(s[:, :, 0])
+    sig = np.fft.irfftn(out, s=(n[2], n[1], n[0]), axes=(1, 2, 3)).transpose(0, 3, 2, 1)
+    assert np.abs(sig - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- kinetics
+def test_philox_known_answers():
+    with open(os.path.join(GOLD, 'philox4x32_10_kat.txt')) as f:
+        for line in f:
+            if line.startswith('#') or not line.strip():
+                continue
+            w = [int(t, 16) for t in line.split()]
+            assert O.philox4x32_10(w[0:4], w[4:6]) == w[6:10]
+
+
+def test_u53_range():
+    assert O.u53(0, 0) == 2.0 ** -53
+    assert O.u53(0xFFFFFFFF, 0xFFFFFFFF) == 1.0
+
+
+def test_p12_unbiased_walk_msd_and_residence_time():
+    """No interaction: every jump of a 3D walker is (+-1,+-1,+-1) half-lattice units, so
+    E|X_K|^2 = 3K (Var = 6K^2 per walker), and the mean residence time is 1/R_tot."""
+    n = (1000, 1000, 1000)
+    T = 300.0
+    E = np.zeros(1)
+    Ec = np.zeros((1, 8))
+    W, K = 200, 100
+    msd, dts = [], []
+    for w in range(W):
+        d = make_defects([O.SIA_CLUSTER], np.array([[1, 1, 1]]), [0], [0.0], [1], [0.34], [O.THREE_D])
+        disp = np.zeros(3, dtype=np.int64)
+        for step in range(K):
+            i, j, dt, R = O.residence_step(d, E, Ec, T, 1000 + w, step, n)
+            dts.append(dt)
+            disp += O.JUMPS[j]
+        msd.append(float(disp @ disp))
+    nu = O.nominal_frequency(0.34, T)
+    assert abs(R - nu) < 1e-9 * nu                    # z = 8 jumps at nu/8 each
+    assert abs(np.mean(dts) - 1.0 / R) < 5.0 / R / np.sqrt(W * K)
+    assert abs(np.mean(msd) - 3 * K) < 5 * np.sqrt(6.0) * K / np.sqrt(W)
+
+
+def test_p12_p14_paper_time_step():
+    g = json.load(open(os.path.join(GOLD, 'paper_table1.json')))
+    d = make_defects([O.LOOP_111], np.array([[0, 0, 0]]), [0], [1.0], [0], [g['dl_Em_eV']], [O.ONE_D])
+    dt = O.fixed_dt(d, g['dl_T_K'])
+    assert abs(dt * 1e12 - g['dl_time_step_ps']) < 0.01
+
+
+def test_p13_detailed_balance_on_ring():
+    """Stationary occupancy of a ring with a frozen potential is Boltzmann."""
+    K = 12
+    T = 400.0
+    rng = np.random.default_rng(7)
+    Ek = rng.normal(scale=0.05, size=K)
+    Q = np.zeros((K, K))
+    for k in range(K):
+        for step, jj in ((1, 7), (-1, 0)):          # jumps +lambda / -lambda on the ring
+            Ec = np.zeros(8)
+            Ec[jj] = Ek[(k + step) % K]
+            allowed = np.zeros(8, bool)
+            allowed[[0, 7]] = True
+            Ec[7 - jj] = Ek[(k - step) % K]
+            r = O.jump_rates(0.2, Ek[k], Ec, allowed, T)
+            Q[k, (k + step) % K] += r[jj]
+    np.fill_diagonal(Q, -Q.sum(axis=1))
+    A = np.vstack([Q.T, np.ones(K)])
+    b = np.zeros(K + 1)
+    b[-1] = 1.0
+    pi = np.linalg.lstsq(A, b, rcond=None)[0]
+    boltz = np.exp(-Ek / (O.KB * T))
+    boltz /= boltz.sum()
+    assert np.abs(pi - boltz).max() < 1e-12
+
+
+def test_selection_rule_boundaries():
+    rates = np.array([1.0, 2.0, 0.0, 1.0])
+    assert O.select_on_line(rates, 0.25)[0] == 0       # R_0/R = 0.25 -> inclusive on the right
+    assert O.select_on_line(rates, 0.2500001)[0] == 1
+    assert O.select_on_line(rates, 0.75)[0] == 1
+    assert O.select_on_line(rates, 0.7500001)[0] == 3  # zero-rate entry never selected
+    assert O.select_on_line(rates, 1.0)[0] == 3
+
+
+def test_fixed_dt_step_moves_only_mobile():
+    d = make_defects([O.LOOP_111, O.LOOP_100], np.array([[0, 0, 0], [10, 10, 10]]), [0, 0],
+                     [1.0, 1.0], [0, 0], [0.1, 1.0], [O.ONE_D, O.IMMOBILE])
+    dt = O.fixed_dt(d, 300.0)
+    moved = 0
+    for step in range(200):
+        mv = O.fixed_dt_step(d, np.zeros(2), np.zeros((2, 8)), 300.0, 99, step, (64, 64, 64), dt)
+        moved += len(mv)
+        assert all(i == 0 for i, _ in mv)
+    # the fastest defect jumps with probability 1 - e^-1 per step
+    assert abs(moved / 200 - (1 - np.exp(-1))) < 4 * np.sqrt(0.25 / 200)
+    assert np.array_equal(d['pos'][1], [10, 10, 10])
+
+
+# ---------------------------------------------------------------- P14: Table 1
+def test_p14_table1_conversions():
+    g = json.load(open(os.path.join(GOLD, 'paper_table1.json')))
+    E, nu = O.zener_isotropic_moduli(g['C11_GPa'], g['C12_GPa'])
+    assert abs(E - g['E_iso_GPa']) < 0.01 and abs(nu - g['nu_iso']) < 1e-3
+    a0 = g['a0_A'] / 10.0                      # nm
+    omega = a0 ** 3 / 2.0
+    assert abs(omega * 1000 - g['V_at_A3']) < 0.01
+    b = math.sqrt(3.0) / 2.0 * a0
+    r = math.sqrt(800 * omega / b / math.pi) * 10.0
+    assert abs(r - g['loop_800_SIA_radius_A']) < g['loop_radius_rel_tol'] * g['loop_800_SIA_radius_A']
+    P = g['P_SIA_eV']
+    B = (g['C11_GPa'] + 2 * g['C12_GPa']) / 3.0
+    dv = (P['P11'] + P['P22'] + P['P33']) / O.KAPPA / (3 * B)      # nm^3
+    assert abs(dv / omega - g['relaxation_volume_over_Vat']) < 2e-3
