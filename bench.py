@@ -1,0 +1,260 @@
+"""Benchmark: OkMC residence-time steps with exact FFT elastic interactions.
+
+One step = one pass of the whole hot path on the 256^3 workload (2000 defects):
+incremental eigenstrain update of the moved defect, forward R2C transform of the
+six eigenstrain components, Green operator, inverse C2R transform, interaction
+energies at every defect site and after each of the eight jumps, rates, one
+residence-time event.  Metric: voxel stress+energy updates per second
+(N voxels x steps / s); OkMC events/s and the HBM roofline fraction of the
+dominant kernel are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank runs an independent replica (replicas only: the path has
+no exchange step); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = 'voxel stress+energy updates/s'
+UNIT = 'voxel updates/s'
+
+
+def _peaks():
+    p = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d['hbm_gbs']), 'measured'
+    return 6800.0, 'fallback'
+
+
+def _dist():
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    return ws, rank
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile('w+', suffix='.csv', delete=False)
+        q = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,'
+             'clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,'
+             'clocks_event_reasons.sw_power_cap')
+        try:
+            self.p = subprocess.Popen(['nvidia-smi', '-i', str(gpu_index), '--query-gpu=' + q, '--format=csv,noheader,nounits',
+                                       '-lms', '100'], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(',') for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace('.', '').isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace('.', '').isdigit()]
+        reasons = set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for r in rows:
+            if len(r) < 9:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == 'active':
+                    reasons.add(nm)
+        return {'sm_mhz': statistics.median(sm) if sm else None, 'sm_max_mhz': max(mx) if mx else None,
+                'reasons': sorted(reasons), 'samples': len(sm)}
+
+
+def kernel_bytes(name, n):
+    """Algorithmic HBM bytes of one launch (FP32 fields, int32 fixed-point eigenstrain):
+    each pass reads and writes the six-component field once."""
+    nx, ny, nz = n
+    N = nx * ny * nz
+    spec = 6 * nz * (nx // 2 + 1) * ny * 8
+    return {'plane_fwd': 6 * N * 4 + spec, 'pencil_green': 2 * spec, 'plane_inv': spec + 6 * N * 4}.get(name)
+
+
+def run_ours(args, ws, rank):
+    import torch
+
+    from paper_2403_09158_gb300 import okmc as ok
+    from paper_2403_09158_gb300.workload import config_large
+
+    torch.cuda.set_device(int(os.environ.get('LOCAL_RANK', '0')))
+    dev = torch.cuda.current_device()
+    w = config_large(seed=1003 + rank)
+    stream = torch.cuda.current_stream()
+    g = ok.Grid(w.n, w.voxel_nm, *w.C, precision=ok.FP32_FIELDS, seed=20231 + rank, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    g.set_defects(w.defects)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    N = int(np.prod(w.n))
+    for _ in range(args.warmup):
+        g.step(w.T_K, 1)
+    torch.cuda.synchronize()
+    stats0 = g.stats()
+    g.reset_kernel_times()
+    g.set_profiling(True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(dev)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        g.step(w.T_K, 1)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1)
+    g.set_profiling(False)
+    kt = g.kernel_times()
+    stats1 = g.stats()
+    events = stats1['events'] - stats0['events']
+    # end to end through the C ABI with host buffers: positions in (pinned), step,
+    # positions and site energies out
+    pos_h = torch.from_numpy(g.get_positions()).pin_memory()
+    pos_out = torch.empty_like(pos_h).pin_memory()
+    e_out = torch.empty(g.nd, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    k_e2e = max(3, args.steps // 2)
+    t0 = time.perf_counter()
+    for _ in range(k_e2e):
+        g.set_positions(pos_h.numpy())
+        g.step(w.T_K, 1)
+        g.get_positions(pos_out.numpy())
+        g.interaction_energies(e_out.numpy())
+        pos_h.copy_(pos_out)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / k_e2e
+    g.close()
+    t = torch.tensor([ms], dtype=torch.float64)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return dict(ms=float(t.item()), N=N, events=events, kt=kt, clocks=clocks, setup_s=setup_s, e2e_s=e2e_s,
+                nd=len(w.defects), n=w.n, T=w.T_K)
+
+
+def cpu_sample(seconds_hint=True):
+    """The oracle as it stands on a bounded sample: one FP64 stress solve and the
+    site + candidate energies of 4 defects on a 96^3 grid at the 256^3 workload's
+    defect density (~112 defects)."""
+    import oracle as O
+    from paper_2403_09158_gb300.workload import scaled_population
+    w = scaled_population((96, 96, 96), 112, seed=77, T_K=500.0)
+    C = O.stiffness_cubic(*w.C)
+    t0 = time.perf_counter()
+    sig = O.solve_stress(O.eigenstrain_field(w.defects, w.n, w.voxel_nm), C, w.voxel_nm)
+    for i in range(4):
+        d = w.defects[i]
+        O.energy_of_stencil(d, d['pos'], sig, w.voxel_nm)
+        for Y in O.candidate_positions(d['pos']):
+            O.energy_of_stencil(d, Y, sig, w.voxel_nm)
+    dt = time.perf_counter() - t0
+    return dict(value=96 ** 3 / dt, seconds=dt, cores=1,
+                sample='one FP64 oracle stress solve + 36 stencil energies on a 96^3 grid '
+                       '(112 defects, same density and mix as the 256^3 workload); numpy, 1 thread')
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=30)
+    ap.add_argument('--warmup', type=int, default=5)
+    ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    args = ap.parse_args()
+    ws, rank = _dist()
+    if args.impl == 'reference':
+        return run_reference(args, ws, rank)
+    import torch
+    if ws > 1:
+        torch.distributed.init_process_group('nccl' if torch.cuda.is_available() else 'gloo')
+    import __graft_entry__
+    __graft_entry__.build()
+    r = run_ours(args, ws, rank)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+    steps = args.steps
+    value = ws * r['N'] * steps / (r['ms'] / 1e3)
+    hbm, src = _peaks()
+    kt = r['kt']
+    dom = max((k for k in kt if kernel_bytes(k, r['n'])), key=lambda k: kt[k][0])
+    d_ms, d_cnt = kt[dom]
+    achieved = kernel_bytes(dom, r['n']) / (d_ms / d_cnt / 1e3) / 1e9
+    solve_ms = sum(kt[k][0] for k in ('plane_fwd', 'pencil_green', 'plane_inv') if k in kt) / max(1, kt.get('plane_fwd', (0, 1))[1])
+    pipe_gbs = 96 * r['N'] / (solve_ms / 1e3) / 1e9
+    launches = sum(c for (_, c) in kt.values())
+    out = {
+        'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': ws, 'steps': steps, 'warmup': args.warmup,
+        'ms_per_step': r['ms'] / steps, 'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
+        'dtype': 'f32 fields / f64 energies', 'data': 'synthetic',
+        'config': {'workload': 'large_256cubed_2000defects (256^3 voxels, h=0.2855 nm, 2000 defects: 60% SIA clusters, '
+                               '30% 1/2<111> loops, 10% <100> loops, R~U(0.5,4) nm, 500 K, residence-time steps)',
+                   'grid': list(r['n']), 'defects': r['nd'], 'mode': 'residence',
+                   'l2': 'inputs larger than L2 (6-component fields of 403 MB each)', 'parallelism': 'replicas'},
+        'events_per_s': ws * r['events'] / (r['ms'] / 1e3),
+        'setup_s': r['setup_s'],
+        'roofline': {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': hbm, 'unit': 'GB/s',
+                     'frac': achieved / hbm, 'traffic': None, 'peak_source': src + ' copy bandwidth'},
+        'pipeline_roofline': {'solve_ms': solve_ms, 'algorithmic_bytes': 96 * r['N'], 'achieved_gbs': pipe_gbs,
+                              'frac': pipe_gbs / hbm},
+        'kernel_ms': {k: v[0] / v[1] for k, v in kt.items()},
+        'gpu_launches': int(launches),
+        'clocks': r['clocks'],
+        'e2e': {'value': r['N'] / r['e2e_s'], 'unit': UNIT, 'h2d_bytes_per_step': r['nd'] * 12,
+                'd2h_bytes_per_step': r['nd'] * 12 + r['nd'] * 8},
+    }
+    if not args.no_cpu_baseline:
+        cb = cpu_sample()
+        out['cpu_baseline'] = {'value': cb['value'], 'unit': UNIT, 'cores': cb['cores'], 'kind': 'oracle',
+                               'sample': cb['sample']}
+    print(json.dumps(out))
+    return 0
+
+
+def run_reference(args, ws, rank):
+    """The CPU FP64 oracle as the reference arm, on this arm's metric and unit."""
+    if rank != 0:
+        return 0
+    times = []
+    for k in range(args.warmup + args.steps):
+        cb = cpu_sample()
+        if k >= args.warmup:
+            times.append(cb['seconds'])
+    per = float(np.mean(times))
+    value = 96 ** 3 / per
+    out = {'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': 1, 'steps': args.steps,
+           'warmup': args.warmup, 'ms_per_step': per * 1e3, 'higher_is_better': True, 'scaling': 'weak',
+           'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+           'config': {'workload': 'large_256cubed_2000defects, sampled as a 96^3 grid at the same defect density'},
+           'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': 1, 'kind': 'oracle', 'sample': cb['sample']},
+           'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(out))
+    return 0
+
+
+if __name__ == '__main__':
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * okmc.h -- C ABI of the GB300 hot path of object kinetic Monte Carlo with exact
+ * FFT elastic interactions (Santos-Gueemes, Ortiz, Segurado, arXiv:2403.09158).
+ *
+ * One handle (okmc_grid) owns one periodic voxel grid on one GPU: the voxelised
+ * eigenstrain of all defects, its stress, the defect table, the per-defect
+ * coverage stencils and self-term tables, and the kinetic state.  All device
+ * memory is allocated and freed by the library.  No C++ exception crosses this
+ * boundary; every call returns an okmc_status and okmc_last_error() gives the
+ * message of the last failure on that handle.  A handle is not thread safe: use
+ * one handle per host thread (handles on different streams run concurrently).
+ *
+ * Units: lengths nm, stresses GPa, energies eV, frequencies 1/s, time s.
+ * Symmetric tensors are stored as 6 components in the order
+ * (xx, yy, zz, yz, xz, xy) -- true tensor components, so a : b counts the three
+ * off-diagonal products twice.  Fields are structure-of-arrays,
+ * field[c][z][y][x] with x fastest (c = component).
+ * Defect positions are integers in units of a0/2 on the bcc lattice (all three
+ * coordinates even or all odd), 0 <= pos[a] < 2 n[a]; the lattice parameter a0
+ * equals the voxel edge h.  The parity of a position is its rasterisation class.
+ */
+#ifndef OKMC_H
+#define OKMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  OKMC_OK = 0,
+  OKMC_EINVAL = 1,    /* bad argument (sizes, defect records, null pointers)      */
+  OKMC_ENOMEM = 2,    /* device allocation failed or exceeded hbm_budget          */
+  OKMC_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed              */
+  OKMC_ETIMEOUT = 4,  /* a bounded device-side wait gave up                       */
+  OKMC_ESTATE = 5,    /* call out of order (e.g. energies before set_defects)     */
+  OKMC_ERANGE = 6     /* a value left the representable range (eigenstrain sum)  */
+} okmc_status;
+
+enum { OKMC_LOOP_111 = 0, OKMC_LOOP_100 = 1, OKMC_SIA_CLUSTER = 2 };
+enum { OKMC_IMMOBILE = 0, OKMC_ONE_D = 1, OKMC_THREE_D = 2 };
+enum { OKMC_MEAN_STRESS_ZERO = 0, OKMC_MEAN_STRAIN_ZERO = 1 };
+enum { OKMC_FP32_FIELDS = 0, OKMC_FP64_FIELDS = 1 };
+enum { OKMC_RESIDENCE = 0, OKMC_FIXED_DT = 1 };
+
+typedef struct okmc_grid okmc_grid;
+
+/* Grid description.  n[a]: edges; each a multiple of 16 of the form 2^p 3^q 5^r,
+ * 16 <= n[a] <= 512.  voxel_nm: voxel edge h (= a0).  C11, C12, C44: cubic
+ * stiffness in GPa along the grid axes (an isotropic solid passes
+ * C44 = (C11 - C12)/2).  k0_mode: OKMC_MEAN_STRESS_ZERO (the stress has zero
+ * mean) or OKMC_MEAN_STRAIN_ZERO (the strain has zero mean, Appendix B).
+ * precision: OKMC_FP32_FIELDS (FP32 transforms, FP64 energies) or
+ * OKMC_FP64_FIELDS (FP64 everywhere).  nu0: attempt frequency (Eq.
+ * unbiased_boltzmann; 0 selects 1e13 1/s).  seed: Philox4x32-10 key.
+ * stream: cudaStream_t to run on (NULL = the legacy default stream).
+ * hbm_budget: upper bound on the handle's device bytes (0 = no bound). */
+typedef struct {
+  int32_t n[3];
+  int32_t k0_mode;
+  int32_t precision;
+  int32_t reserved;
+  double voxel_nm;
+  double C11, C12, C44;
+  double nu0;
+  uint64_t seed;
+  void* stream;
+  size_t hbm_budget;
+} okmc_grid_desc;
+
+/* One defect (48 bytes).  type: OKMC_LOOP_111 (prismatic interstitial loop with
+ * b = (a0/2)<111>, normal n = b/|b|), OKMC_LOOP_100 (b = a0<100>), or
+ * OKMC_SIA_CLUSTER (size self-interstitial atoms, relaxation volume 1.5 Omega
+ * per atom).  axis: index into {[111],[-111],[1-11],[11-1]} (loops 111 and SIA
+ * clusters) or {[100],[010],[001]} (loops 100); a 1D migrant jumps +-(a0/2)*axis.
+ * radius_nm: loop radius (ignored for SIA clusters).  Em_eV: migration barrier.
+ * mobility: OKMC_IMMOBILE, OKMC_ONE_D (needs a <111> axis) or OKMC_THREE_D (all
+ * eight (a0/2)<111> jumps).  reserved must be 0. */
+typedef struct {
+  int32_t type;
+  int32_t pos[3];
+  int32_t axis;
+  int32_t size;
+  int32_t mobility;
+  int32_t reserved;
+  double radius_nm;
+  double Em_eV;
+} okmc_defect;
+
+/* Step parameters.  T_K: temperature.  mode: OKMC_RESIDENCE (one event per
+ * step on the frequency line of every allowed jump of every defect; clock
+ * advance -ln(u)/R_tot) or OKMC_FIXED_DT (Algorithm 1: delta t = 1/nu_max with
+ * nominal barriers, Poisson event counts, one jump per defect that fires, all
+ * decisions from the start-of-step field).  t_end: if > 0, okmc_step stops
+ * early once the clock reaches it. */
+typedef struct {
+  double T_K;
+  int32_t mode;
+  int32_t reserved;
+  double t_end;
+} okmc_step_params;
+
+/* Cumulative kinetic statistics of a handle since okmc_set_defects. */
+typedef struct {
+  int64_t events;             /* executed jumps                                  */
+  int64_t steps;              /* okmc_step iterations                            */
+  int64_t solves;             /* stress solves                                   */
+  int64_t negative_barriers;  /* jumps whose E_m + dE/2 was < 0 (not clamped)     */
+  double clock;               /* simulated time, s                               */
+  double dt_last;             /* last time increment, s                          */
+} okmc_step_stats;
+
+/* Create a grid handle and allocate its device memory.  Errors: EINVAL (sizes,
+ * constants, k0_mode, precision), ENOMEM (allocation or budget), ECUDA. */
+int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out);
+
+/* Free everything the handle owns; NULL is accepted. */
+int okmc_grid_destroy(okmc_grid* g);
+
+/* Message of the last failing call on g (static text for g == NULL). */
+const char* okmc_last_error(const okmc_grid* g);
+
+/* Change the stream later work runs on (cudaStream_t; NULL = legacy stream). */
+int okmc_set_stream(okmc_grid* g, void* stream);
+
+/* Replace the defect set (host array, copied).  Builds the coverage stencils of
+ * every defect for both rasterisation classes (Sec. 3.1 eigenstrains on the
+ * Sec. 3.4 voxel grid), the self-term tables W (the energy of a defect's own
+ * eigenstrain at its current site or after a jump, against its own field), and
+ * the voxelised eigenstrain.  Resets the step counter and the statistics.
+ * Errors: EINVAL (type, axis, mobility, parity, radius, stencil larger than
+ * half the grid), ENOMEM, ECUDA. */
+int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t n);
+
+/* Copy the current defect records (positions included) to host memory. */
+int okmc_get_defects(okmc_grid* g, okmc_defect* out, int32_t n);
+
+/* Positions as int32[n][3].  set: the field is updated incrementally for the
+ * defects whose position changed (parity must be kept consistent per defect).
+ * on_device != 0 means the pointer is device memory. */
+int okmc_set_positions(okmc_grid* g, const int32_t* pos, int32_t n, int on_device);
+int okmc_get_positions(okmc_grid* g, int32_t* pos, int32_t n, int on_device);
+
+/* Periodic elastic solve (Sec. 3.2 Eqs. EIG_elastic_fourier, basicgammacomplete,
+ * summaryEL, on the discrete frequencies of Sec. 3.4): forward 3D R2C transform
+ * of the six eigenstrain components, Green operator per frequency, inverse C2R.
+ * sigma_out (nullable): 6*nx*ny*nz values, float for FP32 fields and double for
+ * FP64 fields, layout [c][z][y][x]; out_on_device says where it lives.  The
+ * stress stays resident for the energy calls. */
+int okmc_solve_stress(okmc_grid* g, void* sigma_out, int out_on_device);
+
+/* The voxelised eigenstrain eps* (6*nx*ny*nz, same type and layout as sigma). */
+int okmc_eigenstrain(okmc_grid* g, void* eps_out, int out_on_device);
+
+/* Interaction energy of each defect at its site (Eq. interaction_energy3 in the
+ * form E_i = -int eps*_i : (sigma - sigma_i) dV): E[n] in eV (FP64).  Solves
+ * first if the stress is stale. */
+int okmc_interaction_energies(okmc_grid* g, double* E, int out_on_device);
+
+/* The same energy after each of the eight jumps lambda_j = (a0/2)(sx,sy,sz),
+ * j = 4(sx>0) + 2(sy>0) + (sz>0): E[n][8] (FP64).  valid[n][8] (nullable)
+ * marks the jumps the defect's mobility allows (Sec. 5). */
+int okmc_candidate_energies(okmc_grid* g, double* E, uint8_t* valid, int out_on_device);
+
+/* Self-term table W[n][2][9] in eV (FP64): W[i][c][0] is the self energy of
+ * defect i's eigenstrain at a class-c site against its own periodic field,
+ * W[i][c][1+j] the same after jump j.  Translation invariant. */
+int okmc_self_terms(okmc_grid* g, double* W, int out_on_device);
+
+/* Coverage stencil of defect i, class c: k entries of (dx, dy, dz) voxel offsets
+ * from the base voxel floor(pos/2) and subsample counts 1..64, sorted by
+ * (dz, dy, dx); the voxel weight is count*alpha.  Pass capacity 0 to query k.
+ * offs: int32[k][3], counts: int32[k] (host). */
+int okmc_get_stencil(okmc_grid* g, int32_t i, int32_t c, int32_t* offs, int32_t* counts,
+                     int32_t capacity, int32_t* k, double* alpha);
+
+/* Run n_steps kinetic steps (Sec. 5, Algorithm 1), each: solve if stale,
+ * energies at the sites and after every jump, rates (Eqs.
+ * biased_forward/backward_boltzmann with prefactor 1/z over the z allowed jumps),
+ * selection on the frequency line (Eqs. frequency_line, selection_jump),
+ * position update and incremental eigenstrain update.  Uniforms come from
+ * Philox4x32-10 with key = seed and counter = (step, defect or 0xFFFFFFFF, mode).
+ * out (nullable, host): the cumulative statistics after the last step. */
+int okmc_step(okmc_grid* g, const okmc_step_params* p, int64_t n_steps, okmc_step_stats* out);
+
+/* Cumulative statistics (host). */
+int okmc_get_stats(okmc_grid* g, okmc_step_stats* out);
+
+/* Device bytes held by the handle. */
+size_t okmc_device_bytes(const okmc_grid* g);
+
+/* Kernel timing: when enabled, every kernel launch of the handle is bracketed
+ * with CUDA events on the handle's stream and its time is accumulated per
+ * kernel name.  okmc_kernel_times fills up to cap entries (names point to static
+ * strings, ms = total milliseconds, count = launches) and returns how many
+ * kernels were seen; okmc_reset_kernel_times clears the totals. */
+int okmc_set_profiling(okmc_grid* g, int enable);
+int okmc_kernel_times(okmc_grid* g, const char** names, double* ms, int64_t* count, int cap);
+int okmc_reset_kernel_times(okmc_grid* g);
+
+/* Number of CTAs in each launch of the pass kernels and the cluster size the
+ * handle picked for its grid (diagnostics): out[0..2] = cluster size of the
+ * forward plane pass, CTAs of the pencil pass, cluster size of the inverse pass. */
+int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OKMC_H */

@@ -1,0 +1,69 @@
+"""Compile the CUDA library (csrc/*.cu) for sm_103a into _lib/libokmc.so.
+
+Plain nvcc, one object per translation unit compiled in parallel, then one link.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(HERE, 'csrc')
+OUT = os.path.join(HERE, '_lib')
+LIB = os.path.join(OUT, 'libokmc.so')
+SOURCES = ['solve.cu', 'defects.cu', 'okmc_api.cu']
+ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
+FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '-I' + os.path.join(ROOT, 'include')]
+
+
+def nvcc_path():
+    for cand in (os.environ.get('NVCC'), shutil.which('nvcc'), '/usr/local/cuda/bin/nvcc'):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError('nvcc not found')
+
+
+def _stale():
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    deps = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(ROOT, 'include', 'okmc.h'), __file__]
+    return any(os.path.getmtime(p) > t for p in deps)
+
+
+def build(force=False, verbose=False):
+    """Build the library if a source is newer than it; return its path."""
+    if not force and not _stale():
+        return LIB
+    os.makedirs(OUT, exist_ok=True)
+    nvcc = nvcc_path()
+    procs = []
+    objs = []
+    for s in SOURCES:
+        obj = os.path.join(OUT, s.replace('.cu', '.o'))
+        objs.append(obj)
+        cmd = [nvcc] + ARCH + FLAGS + ['-c', os.path.join(SRC, s), '-o', obj]
+        if verbose:
+            print(' '.join(cmd), file=sys.stderr)
+        procs.append((s, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    errs = []
+    for s, p in procs:
+        out, _ = p.communicate()
+        if p.returncode != 0:
+            errs.append('%s:\n%s' % (s, out.decode(errors='replace')))
+    if errs:
+        raise RuntimeError('nvcc failed:\n' + '\n'.join(errs))
+    tmp = LIB + '.tmp'
+    cmd = [nvcc] + ARCH + ['-shared', '-o', tmp] + objs
+    r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
+    if r.returncode != 0:
+        raise RuntimeError('link failed:\n' + r.stdout.decode(errors='replace'))
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == '__main__':
+    print(build(force='--force' in sys.argv, verbose=True))

@@ -1,0 +1,775 @@
+// Defect-side kernels: eigenstrain stencils (paper Sec. 3.1, Eq. eig_shearloop;
+// Sec. 3.4 voxel grid), voxelisation, incremental position updates, the
+// self-term table, interaction and candidate energies (Sec. 2, Eq.
+// interaction_energy3), rates and event selection (Sec. 5, Eqs.
+// unbiased_boltzmann, biased_forward/backward_boltzmann, frequency_line,
+// selection_jump, time_step, poisson; Appendix A, Algorithm 1).
+#include <cstdio>
+
+#include "okmc_internal.cuh"
+
+namespace okmc {
+
+// ---------------------------------------------------------------- setup
+// Geometry of one defect (a0 = h).  Loop: slab |(x-X).n| <= h/2 and in-plane
+// radius <= R with n = a/|a|; eps* = sym(b (x) n)/h = (|b|/h) n (x) n.  SIA
+// cluster of s atoms: sphere of radius h*max(1, (3 s / 8 pi)^(1/3)) (Omega =
+// h^3/2) with dilatational eps* whose integral has trace 1.5 s Omega.
+__global__ void k_defect_setup(const okmc_defect* __restrict__ d, DefGeo* __restrict__ G, int nd, double h) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  const okmc_defect r = d[i];
+  DefGeo g = {};
+  if (r.type == OKMC_LOOP_111 || r.type == OKMC_LOOP_100) {
+    int a[3];
+    if (r.type == OKMC_LOOP_111) {
+      a[0] = (r.axis == 1) ? -1 : 1;
+      a[1] = (r.axis == 2) ? -1 : 1;
+      a[2] = (r.axis == 3) ? -1 : 1;
+    } else {
+      a[0] = r.axis == 0;
+      a[1] = r.axis == 1;
+      a[2] = r.axis == 2;
+    }
+    const int a2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    const double bh = (r.type == OKMC_LOOP_111) ? 0.86602540378443864676 : 1.0;  // |b|/h
+    const double f = bh / (double)a2;
+    g.e6[0] = f * a[0] * a[0];
+    g.e6[1] = f * a[1] * a[1];
+    g.e6[2] = f * a[2] * a[2];
+    g.e6[3] = f * a[1] * a[2];
+    g.e6[4] = f * a[0] * a[2];
+    g.e6[5] = f * a[0] * a[1];
+    const double t = 8.0 * r.radius_nm / h;
+    g.thr = (double)a2 * (t * t);
+    const double rh = r.radius_nm / h;
+    g.v_over_h3 = kPi * (rh * rh);
+    g.kind = 0;
+    g.a[0] = a[0];
+    g.a[1] = a[1];
+    g.a[2] = a[2];
+    g.a2 = a2;
+    g.extent = (int)ceil(rh) + 2;
+  } else {
+    const double q = 3.0 * r.size / (8.0 * kPi);
+    const double rho3 = q > 1.0 ? q : 1.0;
+    g.thr = 262144.0 * (rho3 * rho3);
+    g.v_over_h3 = (4.0 * kPi / 3.0) * rho3;
+    const double e = (1.5 * r.size * 0.5) / (3.0 * g.v_over_h3);
+    g.e6[0] = g.e6[1] = g.e6[2] = e;
+    g.kind = 1;
+    g.extent = (int)ceil(cbrt(rho3)) + 2;
+  }
+  int mask = 0;
+  if (r.mobility == OKMC_THREE_D) mask = 0xFF;
+  if (r.mobility == OKMC_ONE_D) {
+    const int sx = (r.axis == 1) ? -1 : 1, sy = (r.axis == 2) ? -1 : 1, sz = (r.axis == 3) ? -1 : 1;
+    const int jp = 4 * (sx > 0) + 2 * (sy > 0) + (sz > 0);
+    mask = (1 << jp) | (1 << (7 - jp));
+  }
+  g.allowed = mask;
+  g.z = __popc(mask);
+  G[i] = g;
+}
+
+// subsample coordinates relative to the centre, in units of h/8: s = 8 v + 2 i + 1 - 4 c
+__device__ __forceinline__ int coverage(const DefGeo& g, int c, int dx, int dy, int dz) {
+  int cnt = 0;
+  for (int i = 0; i < 4; ++i) {
+    const int sx = 8 * dx + 2 * i + 1 - 4 * c;
+    for (int j = 0; j < 4; ++j) {
+      const int sy = 8 * dy + 2 * j + 1 - 4 * c;
+      for (int l = 0; l < 4; ++l) {
+        const int sz = 8 * dz + 2 * l + 1 - 4 * c;
+        const long long ss = (long long)sx * sx + (long long)sy * sy + (long long)sz * sz;
+        bool in;
+        if (g.kind == 0) {
+          const long long sa = (long long)g.a[0] * sx + (long long)g.a[1] * sy + (long long)g.a[2] * sz;
+          in = (sa * sa <= 16ll * g.a2) && ((double)(g.a2 * ss - sa * sa) <= g.thr);
+        } else {
+          in = (double)(ss * ss * ss) <= g.thr;
+        }
+        cnt += in;
+      }
+    }
+  }
+  return cnt;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < nw; ++k) t += sh[k];  // fixed order: deterministic
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ long long block_sum_ll(long long v, long long* sh) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  __syncthreads();
+  long long t = 0;
+  for (int k = 0; k < nw; ++k) t += sh[k];
+  __syncthreads();
+  return t;
+}
+
+// One block per (defect, class): number of stencil entries and total subsample count.
+__global__ void k_stencil_count(const DefGeo* __restrict__ G, int* __restrict__ nnz, long long* __restrict__ sumcnt) {
+  __shared__ long long sh[32];
+  const int i = blockIdx.x >> 1, c = blockIdx.x & 1;
+  const DefGeo g = G[i];
+  const int E = g.extent, side = 2 * E + 1;
+  const int nv = side * side * side;
+  long long n = 0, s = 0;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const int dx = v % side - E, dy = (v / side) % side - E, dz = v / (side * side) - E;
+    const int k = coverage(g, c, dx, dy, dz);
+    n += (k > 0);
+    s += k;
+  }
+  n = block_sum_ll(n, sh);
+  s = block_sum_ll(s, sh);
+  if (threadIdx.x == 0) {
+    nnz[blockIdx.x] = (int)n;
+    sumcnt[blockIdx.x] = s;
+  }
+}
+
+// One block per (defect, class): entries in (dz, dy, dx) order; alpha = V/(h^3 sum count).
+__global__ void k_stencil_fill(const DefGeo* __restrict__ G, const int* __restrict__ ptr,
+                               const long long* __restrict__ sumcnt, int* __restrict__ off,
+                               uint8_t* __restrict__ cnt, double* __restrict__ alpha, int* __restrict__ err) {
+  __shared__ int wsum[32];
+  __shared__ int base_s;
+  const int i = blockIdx.x >> 1, c = blockIdx.x & 1;
+  const DefGeo g = G[i];
+  const int E = g.extent, side = 2 * E + 1;
+  const int nv = side * side * side;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (threadIdx.x == 0) base_s = ptr[blockIdx.x];
+  __syncthreads();
+  for (int v0 = 0; v0 < nv; v0 += blockDim.x) {
+    const int v = v0 + threadIdx.x;
+    int k = 0, dx = 0, dy = 0, dz = 0;
+    if (v < nv) {
+      dx = v % side - E;
+      dy = (v / side) % side - E;
+      dz = v / (side * side) - E;
+      k = coverage(g, c, dx, dy, dz);
+    }
+    const int flag = k > 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    int pre = 0, tot = 0;
+    for (int q = 0; q < nw; ++q) {
+      if (q < w) pre += wsum[q];
+      tot += wsum[q];
+    }
+    if (flag) {
+      const int at = base_s + pre + rank;
+      if (at < ptr[blockIdx.x + 1]) {
+        off[at] = pack_off(dx, dy, dz);
+        cnt[at] = (uint8_t)k;
+      } else {
+        atomicExch(err, 2);
+      }
+      if (dx == -E || dx == E || dy == -E || dy == E || dz == -E || dz == E) atomicExch(err, 3);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) base_s += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (base_s != ptr[blockIdx.x + 1]) atomicExch(err, 2);
+    alpha[blockIdx.x] = g.v_over_h3 / (double)sumcnt[blockIdx.x];
+  }
+}
+
+// ---------------------------------------------------------------- voxelisation
+template <class Q>
+__device__ __forceinline__ void fixed_add(Q* p, long long v);
+template <>
+__device__ __forceinline__ void fixed_add<int32_t>(int32_t* p, long long v) {
+  atomicAdd(reinterpret_cast<int*>(p), (int)v);
+}
+template <>
+__device__ __forceinline__ void fixed_add<int64_t>(int64_t* p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), (unsigned long long)v);
+}
+
+__device__ __forceinline__ int wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+// Adds sign * (count * alpha * eps*) of the class-c stencil of defect i placed at
+// half-lattice position pos to the fixed-point field (quantum q, limit lim).
+template <class Q>
+__device__ void scatter_stencil(Q* __restrict__ eps, int3 n, size_t N, const DefGeo& g, const int* __restrict__ ptr,
+                                const int* __restrict__ off, const uint8_t* __restrict__ cnt, const double* __restrict__ alpha,
+                                int i, const int pos[3], int sign, double rq, double lim, int* err) {
+  const int c = pos[0] & 1;
+  const int bx = floor_div2(pos[0]), by = floor_div2(pos[1]), bz = floor_div2(pos[2]);
+  const int s = ptr[2 * i + c], e = ptr[2 * i + c + 1];
+  const double a = alpha[2 * i + c];
+  for (int k = s + threadIdx.x; k < e; k += blockDim.x) {
+    int dx, dy, dz;
+    unpack_off(off[k], dx, dy, dz);
+    const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
+    const double w = (double)cnt[k] * a;
+    for (int comp = 0; comp < 6; ++comp) {
+      const double val = w * g.e6[comp] * rq;
+      if (fabs(val) > lim) atomicExch(err, 4);
+      const long long iv = __double2ll_rn(val);
+      if (iv) fixed_add<Q>(eps + comp * N + v, sign * iv);
+    }
+  }
+}
+
+template <class Q>
+__global__ void k_voxelise(Q* __restrict__ eps, int3 n, const okmc_defect* __restrict__ d, const DefGeo* __restrict__ G,
+                           const int* __restrict__ ptr, const int* __restrict__ off, const uint8_t* __restrict__ cnt,
+                           const double* __restrict__ alpha, double rq, double lim, int* err) {
+  const int i = blockIdx.x;
+  const size_t N = (size_t)n.x * n.y * n.z;
+  const int pos[3] = {d[i].pos[0], d[i].pos[1], d[i].pos[2]};
+  scatter_stencil<Q>(eps, n, N, G[i], ptr, off, cnt, alpha, i, pos, +1, rq, lim, err);
+}
+
+// One block per move: remove the old stencil, add the new one (exact in fixed point).
+template <class Q>
+__global__ void k_apply_moves(Q* __restrict__ eps, int3 n, const DefGeo* __restrict__ G, const int* __restrict__ ptr,
+                              const int* __restrict__ off, const uint8_t* __restrict__ cnt, const double* __restrict__ alpha,
+                              const Move* __restrict__ moves, const DevState* __restrict__ st, double rq, double lim, int* err) {
+  if ((int)blockIdx.x >= st->nmoves) return;
+  const Move m = moves[blockIdx.x];
+  const size_t N = (size_t)n.x * n.y * n.z;
+  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.old_pos, -1, rq, lim, err);
+  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.new_pos, +1, rq, lim, err);
+}
+
+// Moves recorded from a host-side position update.
+__global__ void k_diff_positions(okmc_defect* __restrict__ d, const int* __restrict__ pos, int nd, Move* moves,
+                                 DevState* st) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  const int p0 = pos[3 * i], p1 = pos[3 * i + 1], p2 = pos[3 * i + 2];
+  if (p0 != d[i].pos[0] || p1 != d[i].pos[1] || p2 != d[i].pos[2]) {
+    const int k = atomicAdd(&st->nmoves, 1);
+    Move m;
+    m.i = i;
+    m.old_pos[0] = d[i].pos[0];
+    m.old_pos[1] = d[i].pos[1];
+    m.old_pos[2] = d[i].pos[2];
+    m.new_pos[0] = p0;
+    m.new_pos[1] = p1;
+    m.new_pos[2] = p2;
+    moves[k] = m;
+    d[i].pos[0] = p0;
+    d[i].pos[1] = p1;
+    d[i].pos[2] = p2;
+  }
+}
+
+__global__ void k_gather_positions(const okmc_defect* __restrict__ d, int* __restrict__ pos, int nd) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nd) return;
+  pos[3 * i] = d[i].pos[0];
+  pos[3 * i + 1] = d[i].pos[1];
+  pos[3 * i + 2] = d[i].pos[2];
+}
+
+template <class Q, class T>
+__global__ void k_fixed_to_real(const Q* __restrict__ eps, T* __restrict__ out, size_t total, double q) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x)
+    out[k] = (T)((double)eps[k] * q);
+}
+
+// ---------------------------------------------------------------- self-term table
+// Scalar count fields of up to six stencils (defect i0 + f/2, class f%2), each
+// placed with its base voxel at the origin.
+template <class Q>
+__global__ void k_wfields(Q* __restrict__ f, int3 n, const int* __restrict__ ptr, const int* __restrict__ off,
+                          const uint8_t* __restrict__ cnt, int i0, int nf) {
+  const int fi = blockIdx.x;
+  if (fi >= nf) return;
+  const size_t N = (size_t)n.x * n.y * n.z;
+  const int i = i0 + fi / 2, c = fi & 1;
+  for (int k = ptr[2 * i + c] + threadIdx.x; k < ptr[2 * i + c + 1]; k += blockDim.x) {
+    int dx, dy, dz;
+    unpack_off(off[k], dx, dy, dz);
+    const size_t v = ((size_t)wrap(dz, n.z) * n.y + wrap(dy, n.y)) * n.x + wrap(dx, n.x);
+    fixed_add<Q>(f + fi * N + v, (long long)cnt[k]);
+  }
+}
+
+// q(xi) = e : M(xi) : e with M = C Gamma C - C: for xi != 0, q = v . K^-1 v - tau : e with
+// tau = C:e and v = tau m; at xi = 0, q = 0 (zero mean stress) or -tau : e (zero mean
+// strain).  Averaged over the Nyquist sign as in the solve.
+template <class T>
+__device__ __forceinline__ T q_of(const T* tau, T te, T m0, T m1, T m2, T C11, T C12, T C44) {
+  const T A = C11 - C12 - T(2) * C44, B = C12 + C44;
+  const T k00 = C44 + (A + B) * m0 * m0, k11 = C44 + (A + B) * m1 * m1, k22 = C44 + (A + B) * m2 * m2;
+  const T k01 = B * m0 * m1, k02 = B * m0 * m2, k12 = B * m1 * m2;
+  const T i00 = k11 * k22 - k12 * k12, i01 = k02 * k12 - k01 * k22, i02 = k01 * k12 - k02 * k11;
+  const T i11 = k00 * k22 - k02 * k02, i12 = k01 * k02 - k00 * k12, i22 = k00 * k11 - k01 * k01;
+  const T det = k00 * i00 + k01 * i01 + k02 * i02;
+  const T v0 = tau[0] * m0 + tau[5] * m1 + tau[4] * m2;
+  const T v1 = tau[5] * m0 + tau[1] * m1 + tau[3] * m2;
+  const T v2 = tau[4] * m0 + tau[3] * m1 + tau[2] * m2;
+  const T vkv = v0 * (i00 * v0 + i01 * v1 + i02 * v2) + v1 * (i01 * v0 + i11 * v1 + i12 * v2) +
+                v2 * (i02 * v0 + i12 * v1 + i22 * v2);
+  return vkv / det - te;
+}
+
+
+// q(xi) is evaluated in FP64 whatever the field precision: it is a difference of two
+// terms of similar size, and an FP32 evaluation biases the self terms by ~2e-7
+// relative (tens of micro-eV on a 100 eV self energy).
+template <class T>
+__global__ void __launch_bounds__(256) k_selfterm_partial(const C2<T>* __restrict__ spec, PassCfg c, WBatch b,
+                                                          const double2* __restrict__ phx, const double2* __restrict__ phy,
+                                                          const double2* __restrict__ phz, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const size_t P = (size_t)(c.H + 1) * c.ny;
+  const size_t total = P * c.nz;
+  double tau[3][6], te[3];
+  for (int d = 0; d < 3; ++d) {
+    const double* e = b.e6[d];
+    const double tr = e[0] + e[1] + e[2];
+    for (int a = 0; a < 3; ++a) tau[d][a] = c.C12 * tr + (c.C11 - c.C12) * e[a];
+    for (int a = 3; a < 6; ++a) tau[d][a] = 2.0 * c.C44 * e[a];
+    te[d] = tau[d][0] * e[0] + tau[d][1] * e[1] + tau[d][2] * e[2] +
+            2.0 * (tau[d][3] * e[3] + tau[d][4] * e[4] + tau[d][5] * e[5]);
+  }
+  double acc[3][10];
+  for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < 10; ++k) acc[d][k] = 0.0;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int kz = (int)(idx / P);
+    const int p = (int)(idx % P);
+    const int kx = p / c.ny, ky = p % c.ny;
+    const int fx = kx < c.H ? kx : kx - c.nx;
+    const int fy = ky < c.ny / 2 ? ky : ky - c.ny;
+    const int fz = kz < c.nz / 2 ? kz : kz - c.nz;
+    const double wgt = (kx == 0 || kx == c.H) ? 1.0 : 2.0;
+    double qd[3];
+    if (fx == 0 && fy == 0 && fz == 0) {
+      for (int d = 0; d < 3; ++d) qd[d] = (c.k0_mode == OKMC_MEAN_STRAIN_ZERO) ? -te[d] : 0.0;
+    } else {
+      const double qx = (double)fx / c.nx, qy = (double)fy / c.ny, qz = (double)fz / c.nz;
+      const double rn = 1.0 / sqrt(qx * qx + qy * qy + qz * qz);
+      const double m0 = qx * rn, m1 = qy * rn, m2 = qz * rn;
+      const bool nx_ = (kx == c.H), ny_ = (2 * ky == c.ny), nz_ = (2 * kz == c.nz);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double v = q_of<double>(tau[d], te[d], m0, m1, m2, c.C11, c.C12, c.C44);
+        if (nx_ || ny_ || nz_)
+          v = 0.5 * (v + q_of<double>(tau[d], te[d], nx_ ? -m0 : m0, ny_ ? -m1 : m1, nz_ ? -m2 : m2, c.C11, c.C12, c.C44));
+        qd[d] = v;
+      }
+    }
+    const double2 ex = phx[kx], ey = phy[ky], ez = phz[kz];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const C2<T> w0 = spec[((size_t)(2 * d) * c.nz + kz) * P + p];
+      const C2<T> w1 = spec[((size_t)(2 * d + 1) * c.nz + kz) * P + p];
+      const double q = wgt * qd[d];
+      const double a0r = w0.x, a0i = w0.y, a1r = w1.x, a1i = w1.y;
+      acc[d][0] += q * (a0r * a0r + a0i * a0i);
+      acc[d][1] += q * (a1r * a1r + a1i * a1i);
+      // conj(w1) * w0
+      const double cr = a1r * a0r + a1i * a0i, ci = a1r * a0i - a1i * a0r;
+      // d = (dx, dy, dz) in {-1, 0}^3, index 4(dx==0) + 2(dy==0) + (dz==0) ... times exp(i xi.d)
+      for (int s = 0; s < 8; ++s) {
+        double pr = cr, pi = ci;
+        if (!(s & 4)) {  // dx = -1: multiply by conj(ex)
+          const double r = pr * ex.x + pi * ex.y, im = pi * ex.x - pr * ex.y;
+          pr = r;
+          pi = im;
+        }
+        if (!(s & 2)) {
+          const double r = pr * ey.x + pi * ey.y, im = pi * ey.x - pr * ey.y;
+          pr = r;
+          pi = im;
+        }
+        if (!(s & 1)) {
+          const double r = pr * ez.x + pi * ez.y, im = pi * ez.x - pr * ez.y;
+          pr = r;
+          pi = im;
+        }
+        acc[d][2 + s] += q * pr;
+      }
+    }
+  }
+  for (int d = 0; d < 3; ++d)
+    for (int k = 0; k < 10; ++k) {
+      const double t = block_sum_d(acc[d][k], sh);
+      if (threadIdx.x == 0) partial[(size_t)blockIdx.x * 30 + d * 10 + k] = t;
+    }
+}
+
+// W[i][c][0] = pref a_c^2 S_cc;  W[i][0][1+j] = pref a_0 a_1 X[d0(lambda_j)],
+// d0 = (lambda - 1)/2 in {-1,0}^3;  W[i][1][1+j] = W[i][0][1+(7-j)] (the reverse jump).
+__global__ void k_selfterm_final(const double* __restrict__ partial, int nblocks, int i0, int nb,
+                                 const double* __restrict__ alpha, double pref, double* __restrict__ W) {
+  const int d = threadIdx.x / 10, k = threadIdx.x % 10;
+  __shared__ double S[30];
+  if (threadIdx.x < 30) {
+    double t = 0.0;
+    for (int bl = 0; bl < nblocks; ++bl) t += partial[(size_t)bl * 30 + threadIdx.x];
+    S[threadIdx.x] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x >= 30 || d >= nb || k) return;
+  const int i = i0 + d;
+  const double a0 = alpha[2 * i], a1 = alpha[2 * i + 1];
+  double* w = W + (size_t)i * 18;
+  w[0] = pref * a0 * a0 * S[d * 10 + 0];
+  w[9] = pref * a1 * a1 * S[d * 10 + 1];
+  for (int j = 0; j < 8; ++j) {
+    // lambda_j components sx = +-1 -> d0 = 0 (sx = +1) or -1 (sx = -1); s bit set means d = 0
+    const int s = j;  // bit 2: sx > 0, bit 1: sy > 0, bit 0: sz > 0 -- same encoding as s
+    w[1 + j] = pref * a0 * a1 * S[d * 10 + 2 + s];
+  }
+  for (int j = 0; j < 8; ++j) w[10 + j] = w[1 + (7 - j)];
+}
+
+// ---------------------------------------------------------------- energies
+// E_i(Y) = -kappa h^3 alpha sum_v count(v - base(Y)) e_i : sigma(v) - W_i(c, lambda),
+// FP32 (or FP64) loads, FP64 accumulation, for Y = X_i and the eight jumps.
+template <class T>
+__global__ void __launch_bounds__(128) k_energies(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
+                                                  const DefGeo* __restrict__ G, const int* __restrict__ ptr,
+                                                  const int* __restrict__ off, const uint8_t* __restrict__ cnt,
+                                                  const double* __restrict__ alpha, const double* __restrict__ W,
+                                                  double pref, int want_cand, double* __restrict__ E,
+                                                  double* __restrict__ Ec) {
+  __shared__ double sh[32];
+  const int i = blockIdx.x;
+  const size_t N = (size_t)n.x * n.y * n.z;
+  const okmc_defect r = d[i];
+  const DefGeo g = G[i];
+  const int c = r.pos[0] & 1;
+  T ew[6];
+  for (int a = 0; a < 6; ++a) ew[a] = T(a < 3 ? g.e6[a] : 2.0 * g.e6[a]);
+  const int bx = floor_div2(r.pos[0]), by = floor_div2(r.pos[1]), bz = floor_div2(r.pos[2]);
+  double acc0 = 0.0;
+  for (int k = ptr[2 * i + c] + threadIdx.x; k < ptr[2 * i + c + 1]; k += blockDim.x) {
+    int dx, dy, dz;
+    unpack_off(off[k], dx, dy, dz);
+    const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
+    T dot = T(0);
+    for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
+    acc0 += (double)cnt[k] * (double)dot;
+  }
+  acc0 = block_sum_d(acc0, sh);
+  if (threadIdx.x == 0) E[i] = pref * alpha[2 * i + c] * acc0 - W[(size_t)i * 18 + c * 9];
+  if (!want_cand) return;
+  const int cp = 1 - c;
+  double acc[8];
+  int jb[8][3];
+  for (int j = 0; j < 8; ++j) {
+    acc[j] = 0.0;
+    jb[j][0] = floor_div2(r.pos[0] + jump_comp(j, 0));
+    jb[j][1] = floor_div2(r.pos[1] + jump_comp(j, 1));
+    jb[j][2] = floor_div2(r.pos[2] + jump_comp(j, 2));
+  }
+  for (int k = ptr[2 * i + cp] + threadIdx.x; k < ptr[2 * i + cp + 1]; k += blockDim.x) {
+    int dx, dy, dz;
+    unpack_off(off[k], dx, dy, dz);
+    const double w = (double)cnt[k];
+    for (int j = 0; j < 8; ++j) {
+      const size_t v = ((size_t)wrap(jb[j][2] + dz, n.z) * n.y + wrap(jb[j][1] + dy, n.y)) * n.x + wrap(jb[j][0] + dx, n.x);
+      T dot = T(0);
+      for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
+      acc[j] += w * (double)dot;
+    }
+  }
+  for (int j = 0; j < 8; ++j) {
+    const double t = block_sum_d(acc[j], sh);
+    if (threadIdx.x == 0) Ec[(size_t)i * 8 + j] = pref * alpha[2 * i + cp] * t - W[(size_t)i * 18 + c * 9 + 1 + j];
+  }
+}
+
+// ---------------------------------------------------------------- events
+__device__ __forceinline__ double jump_rate(double nu0z, double Em, double dE, double kT, long long* negb) {
+  const double barrier = Em + 0.5 * dE;
+  if (barrier < 0.0 && negb) atomicAdd(reinterpret_cast<unsigned long long*>(negb), 1ull);
+  return nu0z * exp(-barrier / kT);
+}
+
+__device__ __forceinline__ void new_position(const int p[3], int j, int3 n, int q[3]) {
+  const int L[3] = {2 * n.x, 2 * n.y, 2 * n.z};
+  for (int a = 0; a < 3; ++a) {
+    int v = p[a] + jump_comp(j, a);
+    if (v < 0) v += L[a];
+    if (v >= L[a]) v -= L[a];
+    q[a] = v;
+  }
+}
+
+// Residence-time event: every allowed jump of every defect on one frequency line
+// (i-major, j-minor), selection of the first entry whose running sum reaches
+// u1 * R_tot (u1 in (0,1]), clock advance -ln(u2)/R_tot.  One block.
+constexpr int kEventThreads = 1024;
+__global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __restrict__ d, const DefGeo* __restrict__ G, int nd,
+                                                             const double* __restrict__ E, const double* __restrict__ Ec,
+                                                             double nu0, double kT, int3 n, uint32_t key0, uint32_t key1,
+                                                             Move* __restrict__ moves, DevState* __restrict__ st) {
+  __shared__ double part[kEventThreads];
+  __shared__ int sel_t;
+  const int t = threadIdx.x;
+  const long long items = (long long)nd * 8;
+  const long long per = (items + blockDim.x - 1) / blockDim.x;
+  const long long k0 = t * per, k1 = min(items, k0 + per);
+  double s = 0.0;
+  for (long long k = k0; k < k1; ++k) {
+    const int i = (int)(k >> 3), j = (int)(k & 7);
+    const DefGeo& g = G[i];
+    if (g.allowed >> j & 1) s += jump_rate(nu0 / g.z, d[i].Em_eV, Ec[k] - E[i], kT, &st->negative_barriers);
+  }
+  part[t] = s;
+  __syncthreads();
+  // inclusive scan (Hillis-Steele), deterministic
+  for (int o = 1; o < blockDim.x; o <<= 1) {
+    const double v = (t >= o) ? part[t - o] : 0.0;
+    __syncthreads();
+    part[t] += v;
+    __syncthreads();
+  }
+  const double R = part[blockDim.x - 1];
+  const long long step = st->step;
+  const uint32_t ctr[4] = {(uint32_t)step, (uint32_t)(step >> 32), 0xFFFFFFFFu, 0u};
+  uint32_t x[4];
+  philox4x32_10(ctr, key0, key1, x);
+  const double u1 = u53(x[0], x[1]), u2 = u53(x[2], x[3]);
+  const double target = u1 * R;
+  if (t == 0) sel_t = 0x7fffffff;
+  __syncthreads();
+  const double excl = (t > 0) ? part[t - 1] : 0.0;
+  if (s > 0.0 && part[t] >= target) atomicMin(&sel_t, t);
+  __syncthreads();
+  if (t == 0 && sel_t == 0x7fffffff) {
+    for (int q = blockDim.x - 1; q >= 0; --q) {
+      const double sq = part[q] - (q > 0 ? part[q - 1] : 0.0);
+      if (sq > 0.0) {
+        sel_t = q;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  if (t != sel_t) return;
+  double run = excl;
+  long long pick = -1, last = -1;
+  for (long long k = k0; k < k1; ++k) {
+    const int i = (int)(k >> 3), j = (int)(k & 7);
+    const DefGeo& g = G[i];
+    if (!(g.allowed >> j & 1)) continue;
+    const double r = jump_rate(nu0 / g.z, d[i].Em_eV, Ec[k] - E[i], kT, nullptr);
+    if (r <= 0.0) continue;
+    last = k;
+    run += r;
+    if (run >= target) {
+      pick = k;
+      break;
+    }
+  }
+  if (pick < 0) pick = last;
+  if (pick < 0 || !(R > 0.0)) {
+    st->err = 5;
+    st->nmoves = 0;
+    return;
+  }
+  const int i = (int)(pick >> 3), j = (int)(pick & 7);
+  Move m;
+  m.i = i;
+  for (int a = 0; a < 3; ++a) m.old_pos[a] = d[i].pos[a];
+  new_position(m.old_pos, j, n, m.new_pos);
+  for (int a = 0; a < 3; ++a) d[i].pos[a] = m.new_pos[a];
+  moves[0] = m;
+  st->nmoves = 1;
+  st->dt_last = -log(u2) / R;
+  st->clock += st->dt_last;
+  st->events += 1;
+  st->step = step + 1;
+}
+
+// Fixed time step (Algorithm 1): delta t = 1/max nominal nu over mobile defects;
+// defect i fires when its Poisson count is > 0 (u_p > exp(-nu_i delta t)) and then
+// selects a jump on its own biased frequency line with u_s.  One block.
+__global__ void __launch_bounds__(kEventThreads) k_fixed_dt(okmc_defect* __restrict__ d, const DefGeo* __restrict__ G, int nd,
+                                                            const double* __restrict__ E, const double* __restrict__ Ec,
+                                                            double nu0, double kT, int3 n, uint32_t key0, uint32_t key1,
+                                                            Move* __restrict__ moves, DevState* __restrict__ st) {
+  __shared__ double red[32];
+  __shared__ int cnt_s;
+  const int t = threadIdx.x;
+  double mx = 0.0;
+  for (int i = t; i < nd; i += blockDim.x)
+    if (G[i].z > 0) mx = fmax(mx, nu0 * exp(-d[i].Em_eV / kT));
+  for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((t & 31) == 0) red[t >> 5] = mx;
+  if (t == 0) cnt_s = 0;
+  __syncthreads();
+  double vmax = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) vmax = fmax(vmax, red[w]);
+  const double dt = 1.0 / vmax;
+  const long long step = st->step;
+  for (int i = t; i < nd; i += blockDim.x) {
+    const DefGeo g = G[i];
+    if (g.z == 0) continue;
+    const uint32_t ctr[4] = {(uint32_t)step, (uint32_t)(step >> 32), (uint32_t)i, 1u};
+    uint32_t x[4];
+    philox4x32_10(ctr, key0, key1, x);
+    const double up = u53(x[0], x[1]), us = u53(x[2], x[3]);
+    const double mu = nu0 * exp(-d[i].Em_eV / kT) * dt;
+    if (up <= exp(-mu)) continue;
+    double r[8], tot = 0.0;
+    for (int j = 0; j < 8; ++j) {
+      r[j] = (g.allowed >> j & 1) ? jump_rate(nu0 / g.z, d[i].Em_eV, Ec[(size_t)i * 8 + j] - E[i], kT, &st->negative_barriers) : 0.0;
+      tot += r[j];
+    }
+    const double target = us * tot;
+    double run = 0.0;
+    int pick = -1, last = -1;
+    for (int j = 0; j < 8; ++j) {
+      if (r[j] <= 0.0) continue;
+      last = j;
+      run += r[j];
+      if (run >= target) {
+        pick = j;
+        break;
+      }
+    }
+    if (pick < 0) pick = last;
+    Move m;
+    m.i = i;
+    for (int a = 0; a < 3; ++a) m.old_pos[a] = d[i].pos[a];
+    new_position(m.old_pos, pick, n, m.new_pos);
+    const int k = atomicAdd(&cnt_s, 1);
+    moves[k] = m;
+  }
+  __syncthreads();
+  // apply all moves after every decision was taken from the start-of-step energies
+  for (int k = t; k < cnt_s; k += blockDim.x) {
+    const Move m = moves[k];
+    for (int a = 0; a < 3; ++a) d[m.i].pos[a] = m.new_pos[a];
+  }
+  if (t == 0) {
+    st->nmoves = cnt_s;
+    st->dt_fixed = dt;
+    st->dt_last = dt;
+    st->clock += dt;
+    st->events += cnt_s;
+    st->step = step + 1;
+  }
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_defect_setup(const okmc_defect* d, DefGeo* G, int nd, double h, cudaStream_t st) {
+  k_defect_setup<<<(nd + 127) / 128, 128, 0, st>>>(d, G, nd, h);
+  return cudaGetLastError();
+}
+cudaError_t launch_stencil_count(const DefGeo* G, int nd, int* nnz, long long* sumcnt, cudaStream_t st) {
+  k_stencil_count<<<2 * nd, 256, 0, st>>>(G, nnz, sumcnt);
+  return cudaGetLastError();
+}
+cudaError_t launch_stencil_fill(const DefGeo* G, int nd, const int* ptr, const long long* sumcnt, int* off, uint8_t* cnt,
+                                double* alpha, int* err, cudaStream_t st) {
+  k_stencil_fill<<<2 * nd, 256, 0, st>>>(G, ptr, sumcnt, off, cnt, alpha, err);
+  return cudaGetLastError();
+}
+template <class Q>
+cudaError_t launch_voxelise(Q* eps, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr, const int* off,
+                            const uint8_t* cnt, const double* alpha, double rq, double lim, int* err, cudaStream_t st) {
+  if (nd == 0) return cudaSuccess;
+  k_voxelise<Q><<<nd, 256, 0, st>>>(eps, n, d, G, ptr, off, cnt, alpha, rq, lim, err);
+  return cudaGetLastError();
+}
+template <class Q>
+cudaError_t launch_apply_moves(Q* eps, int3 n, const DefGeo* G, int maxmoves, const int* ptr, const int* off,
+                               const uint8_t* cnt, const double* alpha, const Move* moves, const DevState* stt, double rq,
+                               double lim, int* err, cudaStream_t st) {
+  if (maxmoves == 0) return cudaSuccess;
+  k_apply_moves<Q><<<maxmoves, 256, 0, st>>>(eps, n, G, ptr, off, cnt, alpha, moves, stt, rq, lim, err);
+  return cudaGetLastError();
+}
+cudaError_t launch_diff_positions(okmc_defect* d, const int* pos, int nd, Move* moves, DevState* stt, cudaStream_t st) {
+  k_diff_positions<<<(nd + 127) / 128, 128, 0, st>>>(d, pos, nd, moves, stt);
+  return cudaGetLastError();
+}
+cudaError_t launch_gather_positions(const okmc_defect* d, int* pos, int nd, cudaStream_t st) {
+  k_gather_positions<<<(nd + 127) / 128, 128, 0, st>>>(d, pos, nd);
+  return cudaGetLastError();
+}
+template <class Q, class T>
+cudaError_t launch_fixed_to_real(const Q* eps, T* out, size_t total, double q, cudaStream_t st) {
+  k_fixed_to_real<Q, T><<<1216, 256, 0, st>>>(eps, out, total, q);
+  return cudaGetLastError();
+}
+template <class Q>
+cudaError_t launch_wfields(Q* f, int3 n, const int* ptr, const int* off, const uint8_t* cnt, int i0, int nf, cudaStream_t st) {
+  k_wfields<Q><<<nf, 256, 0, st>>>(f, n, ptr, off, cnt, i0, nf);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b, const double2* phx, const double2* phy,
+                            const double2* phz, double* partial, int nblocks, int i0, const double* alpha, double pref,
+                            double* W, cudaStream_t st) {
+  k_selfterm_partial<T><<<nblocks, 256, 0, st>>>(spec, c, b, phx, phy, phz, partial);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_selfterm_final<<<1, 32, 0, st>>>(partial, nblocks, i0, b.nb, alpha, pref, W);
+  return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
+                            const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
+                            int want_cand, double* E, double* Ec, cudaStream_t st) {
+  if (nd == 0) return cudaSuccess;
+  k_energies<T><<<nd, 128, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, E, Ec);
+  return cudaGetLastError();
+}
+cudaError_t launch_residence(okmc_defect* d, const DefGeo* G, int nd, const double* E, const double* Ec, double nu0,
+                             double kT, int3 n, uint64_t seed, Move* moves, DevState* stt, cudaStream_t st) {
+  k_residence<<<1, kEventThreads, 0, st>>>(d, G, nd, E, Ec, nu0, kT, n, (uint32_t)seed, (uint32_t)(seed >> 32), moves, stt);
+  return cudaGetLastError();
+}
+cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* E, const double* Ec, double nu0,
+                            double kT, int3 n, uint64_t seed, Move* moves, DevState* stt, cudaStream_t st) {
+  k_fixed_dt<<<1, kEventThreads, 0, st>>>(d, G, nd, E, Ec, nu0, kT, n, (uint32_t)seed, (uint32_t)(seed >> 32), moves, stt);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_voxelise<int32_t>(int32_t*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
+                                              const uint8_t*, const double*, double, double, int*, cudaStream_t);
+template cudaError_t launch_voxelise<int64_t>(int64_t*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
+                                              const uint8_t*, const double*, double, double, int*, cudaStream_t);
+template cudaError_t launch_apply_moves<int32_t>(int32_t*, int3, const DefGeo*, int, const int*, const int*, const uint8_t*,
+                                                 const double*, const Move*, const DevState*, double, double, int*, cudaStream_t);
+template cudaError_t launch_apply_moves<int64_t>(int64_t*, int3, const DefGeo*, int, const int*, const int*, const uint8_t*,
+                                                 const double*, const Move*, const DevState*, double, double, int*, cudaStream_t);
+template cudaError_t launch_fixed_to_real<int32_t, float>(const int32_t*, float*, size_t, double, cudaStream_t);
+template cudaError_t launch_fixed_to_real<int64_t, double>(const int64_t*, double*, size_t, double, cudaStream_t);
+template cudaError_t launch_wfields<int32_t>(int32_t*, int3, const int*, const int*, const uint8_t*, int, int, cudaStream_t);
+template cudaError_t launch_wfields<int64_t>(int64_t*, int3, const int*, const int*, const uint8_t*, int, int, cudaStream_t);
+template cudaError_t launch_selfterm<float>(const C2<float>*, const PassCfg&, const WBatch&, const double2*, const double2*,
+                                           const double2*, double*, int, int, const double*, double, double*, cudaStream_t);
+template cudaError_t launch_selfterm<double>(const C2<double>*, const PassCfg&, const WBatch&, const double2*, const double2*,
+                                            const double2*, double*, int, int, const double*, double, double*, cudaStream_t);
+template cudaError_t launch_energies<float>(const float*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
+                                           const uint8_t*, const double*, const double*, double, int, double*, double*,
+                                           cudaStream_t);
+template cudaError_t launch_energies<double>(const double*, int3, const okmc_defect*, const DefGeo*, int, const int*,
+                                            const int*, const uint8_t*, const double*, const double*, double, int, double*,
+                                            double*, cudaStream_t);
+
+}  // namespace okmc

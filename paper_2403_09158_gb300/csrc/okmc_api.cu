@@ -1,0 +1,831 @@
+// Host side of the C ABI declared in include/okmc.h: handle life cycle, device
+// memory under an optional budget, validation, and the order of kernel launches
+// of each call.  All arithmetic of the method runs in the kernels of solve.cu
+// and defects.cu; this file only marshals, validates and sequences.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "okmc_internal.cuh"
+
+using namespace okmc;
+
+namespace okmc {
+template <class T> int pick_cluster(int H, int ny, size_t limit);
+template <class T> int pick_tile(int ny, int nz, size_t limit);
+template <class T, class Q> cudaError_t launch_plane_fwd(const Q* eps, C2<T>* spec, const PassCfg& c, cudaStream_t st);
+template <class T> cudaError_t launch_plane_inv(const C2<T>* spec, T* sig, const PassCfg& c, cudaStream_t st);
+template <class T> cudaError_t launch_pencil(C2<T>* spec, const PassCfg& c, cudaStream_t st);
+cudaError_t launch_defect_setup(const okmc_defect* d, DefGeo* G, int nd, double h, cudaStream_t st);
+cudaError_t launch_stencil_count(const DefGeo* G, int nd, int* nnz, long long* sumcnt, cudaStream_t st);
+cudaError_t launch_stencil_fill(const DefGeo* G, int nd, const int* ptr, const long long* sumcnt, int* off, uint8_t* cnt,
+                                double* alpha, int* err, cudaStream_t st);
+template <class Q>
+cudaError_t launch_voxelise(Q* eps, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr, const int* off,
+                            const uint8_t* cnt, const double* alpha, double rq, double lim, int* err, cudaStream_t st);
+template <class Q>
+cudaError_t launch_apply_moves(Q* eps, int3 n, const DefGeo* G, int maxmoves, const int* ptr, const int* off,
+                               const uint8_t* cnt, const double* alpha, const Move* moves, const DevState* stt, double rq,
+                               double lim, int* err, cudaStream_t st);
+cudaError_t launch_diff_positions(okmc_defect* d, const int* pos, int nd, Move* moves, DevState* stt, cudaStream_t st);
+cudaError_t launch_gather_positions(const okmc_defect* d, int* pos, int nd, cudaStream_t st);
+template <class Q, class T> cudaError_t launch_fixed_to_real(const Q* eps, T* out, size_t total, double q, cudaStream_t st);
+template <class Q>
+cudaError_t launch_wfields(Q* f, int3 n, const int* ptr, const int* off, const uint8_t* cnt, int i0, int nf, cudaStream_t st);
+template <class T>
+cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b, const double2* phx, const double2* phy,
+                            const double2* phz, double* partial, int nblocks, int i0, const double* alpha, double pref,
+                            double* W, cudaStream_t st);
+template <class T>
+cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
+                            const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
+                            int want_cand, double* E, double* Ec, cudaStream_t st);
+cudaError_t launch_residence(okmc_defect* d, const DefGeo* G, int nd, const double* E, const double* Ec, double nu0,
+                             double kT, int3 n, uint64_t seed, Move* moves, DevState* stt, cudaStream_t st);
+cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* E, const double* Ec, double nu0,
+                            double kT, int3 n, uint64_t seed, Move* moves, DevState* stt, cudaStream_t st);
+}  // namespace okmc
+
+namespace {
+constexpr size_t kSmemLimit = 225 * 1024;
+constexpr int kSelfBlocks = 608;
+
+struct Pending {
+  const char* name;
+  cudaEvent_t a, b;
+};
+
+struct Status {
+  int code;
+  std::string msg;
+};
+
+int factor_ok(int n) {
+  if (n < 16 || n > 512 || n % 16) return 0;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  while (n % 5 == 0) n /= 5;
+  return n == 1;
+}
+
+LinePlan make_plan(int L) {
+  LinePlan p = {};
+  p.L = L;
+  int m = L, a = 0, b = 0, c = 0;
+  while (m % 2 == 0) m /= 2, ++a;
+  while (m % 3 == 0) m /= 3, ++b;
+  while (m % 5 == 0) m /= 5, ++c;
+  std::vector<int> r;
+  const int q = a / 3, rem = a % 3;
+  if (rem == 0) {
+    for (int i = 0; i < q; ++i) r.push_back(8);
+  } else if (rem == 1) {
+    if (q >= 1) {
+      for (int i = 0; i < q - 1; ++i) r.push_back(8);
+      r.push_back(4);
+      r.push_back(4);
+    } else {
+      r.push_back(2);
+    }
+  } else {
+    for (int i = 0; i < q; ++i) r.push_back(8);
+    r.push_back(4);
+  }
+  for (int i = 0; i < b; ++i) r.push_back(3);
+  for (int i = 0; i < c; ++i) r.push_back(5);
+  if (r.size() == 1) {  // the engine wants two stages at least
+    const int R = r[0];
+    r.clear();
+    if (R == 8) { r.push_back(2); r.push_back(4); }
+    else if (R == 4) { r.push_back(2); r.push_back(2); }
+    else r.push_back(R);
+  }
+  p.nst = (int)r.size();
+  for (int i = 0; i < p.nst; ++i) p.rad[i] = r[i];
+  return p;
+}
+
+template <class T>
+void twiddles(std::vector<C2<T>>& out, int L, int count, double sign) {
+  for (int k = 0; k < count; ++k) {
+    const double ang = 2.0 * kPi * (double)k / (double)L;
+    out.push_back(C2<T>{(T)std::cos(ang), (T)(sign * std::sin(ang))});
+  }
+}
+}  // namespace
+
+struct okmc_grid {
+  okmc_grid_desc desc{};
+  int n[3] = {0, 0, 0};
+  int H = 0;
+  size_t N = 0, P = 0;
+  double h = 0, nu0 = 1e13;
+  int prec = 0;
+  cudaStream_t st = nullptr;
+  size_t bytes = 0;
+  std::vector<std::pair<void*, size_t>> allocs;
+  void* eps = nullptr;
+  void* sig = nullptr;
+  void* spec = nullptr;
+  void* tw = nullptr;
+  double2* ph = nullptr;
+  PassCfg cfg{};
+  int nd = 0;
+  okmc_defect* d_def = nullptr;
+  DefGeo* d_geo = nullptr;
+  int* d_ptr = nullptr;
+  int* d_off = nullptr;
+  uint8_t* d_cnt = nullptr;
+  double* d_alpha = nullptr;
+  long long* d_sumcnt = nullptr;
+  int* d_nnz = nullptr;
+  double* d_W = nullptr;
+  double* d_E = nullptr;
+  double* d_Ec = nullptr;
+  Move* d_moves = nullptr;
+  DevState* d_state = nullptr;
+  int* d_err = nullptr;
+  int* d_pos = nullptr;
+  double* d_partial = nullptr;
+  std::vector<okmc_defect> h_def;
+  bool sigma_valid = false;
+  bool any_mobile = false;
+  long long solves = 0;
+  std::string err;
+  bool profiling = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+  std::map<std::string, std::pair<double, long long>> prof;
+  std::vector<std::string> prof_names;
+};
+
+namespace {
+
+int fail(okmc_grid* g, int code, const std::string& m) {
+  if (g) g->err = m;
+  return code;
+}
+int cuda_fail(okmc_grid* g, cudaError_t e, const char* where) {
+  return fail(g, OKMC_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+int dalloc(okmc_grid* g, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  if (g->desc.hbm_budget && g->bytes + bytes > g->desc.hbm_budget)
+    return fail(g, OKMC_ENOMEM, "device allocation exceeds hbm_budget");
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(g, OKMC_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  g->allocs.push_back({*p, bytes});
+  g->bytes += bytes;
+  return OKMC_OK;
+}
+void dfree(okmc_grid* g, void* p) {
+  if (!p) return;
+  for (size_t k = 0; k < g->allocs.size(); ++k)
+    if (g->allocs[k].first == p) {
+      g->bytes -= g->allocs[k].second;
+      g->allocs.erase(g->allocs.begin() + k);
+      break;
+    }
+  cudaFree(p);
+}
+
+cudaEvent_t get_event(okmc_grid* g) {
+  if (!g->free_events.empty()) {
+    cudaEvent_t e = g->free_events.back();
+    g->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void drain_profile(okmc_grid* g) {
+  if (g->pending.empty()) return;
+  cudaStreamSynchronize(g->st);
+  for (auto& p : g->pending) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    auto& slot = g->prof[p.name];
+    slot.first += ms;
+    slot.second += 1;
+    g->free_events.push_back(p.a);
+    g->free_events.push_back(p.b);
+  }
+  g->pending.clear();
+}
+
+// Launch wrapper: optional per-kernel CUDA events on the handle's stream.
+template <class F>
+int run(okmc_grid* g, const char* name, F f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (g->profiling) {
+    a = get_event(g);
+    b = get_event(g);
+    cudaEventRecord(a, g->st);
+  }
+  cudaError_t e = f();
+  if (e != cudaSuccess) return cuda_fail(g, e, name);
+  if (g->profiling) {
+    cudaEventRecord(b, g->st);
+    g->pending.push_back({name, a, b});
+    if (g->pending.size() > 4096) drain_profile(g);
+  }
+  return OKMC_OK;
+}
+
+#define OKMC_TRY(x)              \
+  do {                           \
+    int _rc = (x);               \
+    if (_rc != OKMC_OK) return _rc; \
+  } while (0)
+
+int3 dims(const okmc_grid* g) { return make_int3(g->n[0], g->n[1], g->n[2]); }
+bool fp64(const okmc_grid* g) { return g->prec == OKMC_FP64_FIELDS; }
+double quantum(const okmc_grid* g) { return fp64(g) ? std::ldexp(1.0, -40) : std::ldexp(1.0, -26); }
+double qlimit(const okmc_grid* g) { return fp64(g) ? std::ldexp(1.0, 62) : 2147483647.0; }
+size_t qsize(const okmc_grid* g) { return fp64(g) ? 8 : 4; }
+size_t tsize(const okmc_grid* g) { return fp64(g) ? 8 : 4; }
+
+int solve(okmc_grid* g) {
+  if (g->sigma_valid) return OKMC_OK;
+  PassCfg c = g->cfg;
+  c.q = quantum(g);
+  c.ncomp = 6;
+  c.forward_only = 0;
+  if (fp64(g)) {
+    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<double, int64_t>((const int64_t*)g->eps, (C2<double>*)g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil<double>((C2<double>*)g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_inv<double>((const C2<double>*)g->spec, (double*)g->sig, c, g->st); }));
+  } else {
+    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<float, int32_t>((const int32_t*)g->eps, (C2<float>*)g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil<float>((C2<float>*)g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_inv<float>((const C2<float>*)g->spec, (float*)g->sig, c, g->st); }));
+  }
+  g->sigma_valid = true;
+  g->solves += 1;
+  return OKMC_OK;
+}
+
+int energies(okmc_grid* g, int want_cand) {
+  OKMC_TRY(solve(g));
+  const double pref = -kKappa * g->h * g->h * g->h;
+  return run(g, "energies", [&] {
+    if (fp64(g))
+      return launch_energies<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
+                                     g->d_alpha, g->d_W, pref, want_cand, g->d_E, g->d_Ec, g->st);
+    return launch_energies<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
+                                  g->d_alpha, g->d_W, pref, want_cand, g->d_E, g->d_Ec, g->st);
+  });
+}
+
+int apply_moves(okmc_grid* g, int maxmoves) {
+  return run(g, "apply_moves", [&] {
+    if (fp64(g))
+      return launch_apply_moves<int64_t>((int64_t*)g->eps, dims(g), g->d_geo, maxmoves, g->d_ptr, g->d_off, g->d_cnt,
+                                         g->d_alpha, g->d_moves, g->d_state, 1.0 / quantum(g), qlimit(g), g->d_err, g->st);
+    return launch_apply_moves<int32_t>((int32_t*)g->eps, dims(g), g->d_geo, maxmoves, g->d_ptr, g->d_off, g->d_cnt,
+                                       g->d_alpha, g->d_moves, g->d_state, 1.0 / quantum(g), qlimit(g), g->d_err, g->st);
+  });
+}
+
+int check_device_error(okmc_grid* g) {
+  int e = 0;
+  cudaError_t ce = cudaMemcpyAsync(&e, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(g->st);
+  if (ce != cudaSuccess) return cuda_fail(g, ce, "device error check");
+  if (e == 4) return fail(g, OKMC_ERANGE, "eigenstrain contribution outside the fixed-point range");
+  if (e) return fail(g, OKMC_ECUDA, "stencil construction inconsistency (code " + std::to_string(e) + ")");
+  return OKMC_OK;
+}
+
+int copy_out(okmc_grid* g, void* dst, const void* src, size_t bytes, int on_device) {
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess && !on_device) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "copy out");
+  return OKMC_OK;
+}
+
+int validate_defects(okmc_grid* g, const okmc_defect* d, int nd) {
+  const int nmin = std::min(g->n[0], std::min(g->n[1], g->n[2]));
+  for (int i = 0; i < nd; ++i) {
+    const okmc_defect& r = d[i];
+    const std::string at = "defect " + std::to_string(i) + ": ";
+    if (r.reserved != 0) return fail(g, OKMC_EINVAL, at + "reserved field must be 0");
+    if (r.type < 0 || r.type > 2) return fail(g, OKMC_EINVAL, at + "unknown type");
+    const int par = r.pos[0] & 1;
+    for (int a = 0; a < 3; ++a) {
+      if (r.pos[a] < 0 || r.pos[a] >= 2 * g->n[a]) return fail(g, OKMC_EINVAL, at + "position outside [0, 2n)");
+      if ((r.pos[a] & 1) != par) return fail(g, OKMC_EINVAL, at + "position is not a bcc site");
+    }
+    if (!std::isfinite(r.Em_eV)) return fail(g, OKMC_EINVAL, at + "E_m not finite");
+    if (r.mobility < 0 || r.mobility > 2) return fail(g, OKMC_EINVAL, at + "unknown mobility");
+    int extent;
+    if (r.type == OKMC_SIA_CLUSTER) {
+      if (r.size < 1 || r.size > 1000000) return fail(g, OKMC_EINVAL, at + "cluster size out of range");
+      if (r.axis < 0 || r.axis > 3) return fail(g, OKMC_EINVAL, at + "axis out of range");
+      const double q = 3.0 * r.size / (8.0 * kPi);
+      extent = (int)std::ceil(std::cbrt(q > 1.0 ? q : 1.0)) + 3;
+    } else {
+      if (!(r.radius_nm > 0.0) || !std::isfinite(r.radius_nm)) return fail(g, OKMC_EINVAL, at + "radius must be > 0");
+      if (r.axis < 0 || r.axis > (r.type == OKMC_LOOP_111 ? 3 : 2)) return fail(g, OKMC_EINVAL, at + "axis out of range");
+      extent = (int)std::ceil(r.radius_nm / g->h) + 2;
+    }
+    if (r.type == OKMC_LOOP_100 && r.mobility != OKMC_IMMOBILE)
+      return fail(g, OKMC_EINVAL, at + "<100> loops are immobile");
+    if (2 * extent + 1 > nmin) return fail(g, OKMC_EINVAL, at + "defect larger than half the grid");
+  }
+  return OKMC_OK;
+}
+
+template <class T, class Q>
+int build_self_terms(okmc_grid* g) {
+  const size_t N = g->N;
+  const int3 n = dims(g);
+  cudaError_t e = cudaMemsetAsync(g->eps, 0, 6 * N * sizeof(Q), g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "memset");
+  PassCfg c = g->cfg;
+  c.q = 1.0;
+  c.ncomp = 6;
+  c.forward_only = 1;
+  const double pref = -kKappa * g->h * g->h * g->h / (double)N;
+  const double2* phx = g->ph;
+  const double2* phy = g->ph + (g->H + 1);
+  const double2* phz = phy + g->n[1];
+  for (int i0 = 0; i0 < g->nd; i0 += 3) {
+    WBatch b{};
+    b.nb = std::min(3, g->nd - i0);
+    for (int d = 0; d < b.nb; ++d) {
+      // the eigenstrain tensor of each defect is read back from the setup kernel's output
+      DefGeo geo;
+      e = cudaMemcpyAsync(&geo, g->d_geo + i0 + d, sizeof(DefGeo), cudaMemcpyDeviceToHost, g->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "geometry read back");
+      for (int a = 0; a < 6; ++a) b.e6[d][a] = geo.e6[a];
+    }
+    OKMC_TRY(run(g, "self_fields", [&] { return launch_wfields<Q>((Q*)g->eps, n, g->d_ptr, g->d_off, g->d_cnt, i0, 2 * b.nb, g->st); }));
+    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil<T>((C2<T>*)g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "self_terms", [&] {
+      return launch_selfterm<T>((const C2<T>*)g->spec, c, b, phx, phy, phz, g->d_partial, kSelfBlocks, i0, g->d_alpha, pref,
+                                g->d_W, g->st);
+    }));
+    e = cudaMemsetAsync(g->eps, 0, 6 * N * sizeof(Q), g->st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "memset");
+  }
+  return OKMC_OK;
+}
+
+int voxelise_all(okmc_grid* g) {
+  cudaError_t e = cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "memset");
+  g->sigma_valid = false;
+  return run(g, "voxelise", [&] {
+    if (fp64(g))
+      return launch_voxelise<int64_t>((int64_t*)g->eps, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
+                                      g->d_alpha, 1.0 / quantum(g), qlimit(g), g->d_err, g->st);
+    return launch_voxelise<int32_t>((int32_t*)g->eps, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
+                                    g->d_alpha, 1.0 / quantum(g), qlimit(g), g->d_err, g->st);
+  });
+}
+
+void free_defects(okmc_grid* g) {
+  void** bufs[] = {(void**)&g->d_def, (void**)&g->d_geo, (void**)&g->d_ptr, (void**)&g->d_off, (void**)&g->d_cnt,
+                   (void**)&g->d_alpha, (void**)&g->d_sumcnt, (void**)&g->d_nnz, (void**)&g->d_W, (void**)&g->d_E,
+                   (void**)&g->d_Ec, (void**)&g->d_moves, (void**)&g->d_pos};
+  for (void** b : bufs) {
+    dfree(g, *b);
+    *b = nullptr;
+  }
+  g->nd = 0;
+}
+
+}  // namespace
+
+// ================================================================== C ABI
+extern "C" {
+
+const char* okmc_last_error(const okmc_grid* g) {
+  if (!g) return "null handle";
+  return g->err.c_str();
+}
+
+int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
+  if (!d || !out) return OKMC_EINVAL;
+  *out = nullptr;
+  for (int a = 0; a < 3; ++a)
+    if (!factor_ok(d->n[a])) return OKMC_EINVAL;
+  if (!(d->voxel_nm > 0.0) || !std::isfinite(d->voxel_nm)) return OKMC_EINVAL;
+  if (!std::isfinite(d->C11) || !std::isfinite(d->C12) || !std::isfinite(d->C44)) return OKMC_EINVAL;
+  if (!(d->C11 - d->C12 > 0.0) || !(d->C11 + 2.0 * d->C12 > 0.0) || !(d->C44 > 0.0)) return OKMC_EINVAL;
+  if (d->k0_mode != OKMC_MEAN_STRESS_ZERO && d->k0_mode != OKMC_MEAN_STRAIN_ZERO) return OKMC_EINVAL;
+  if (d->precision != OKMC_FP32_FIELDS && d->precision != OKMC_FP64_FIELDS) return OKMC_EINVAL;
+  if (d->nu0 < 0.0 || !std::isfinite(d->nu0)) return OKMC_EINVAL;
+  okmc_grid* g = new (std::nothrow) okmc_grid();
+  if (!g) return OKMC_ENOMEM;
+  g->desc = *d;
+  for (int a = 0; a < 3; ++a) g->n[a] = d->n[a];
+  g->H = g->n[0] / 2;
+  g->N = (size_t)g->n[0] * g->n[1] * g->n[2];
+  g->P = (size_t)(g->H + 1) * g->n[1];
+  g->h = d->voxel_nm;
+  g->nu0 = d->nu0 > 0.0 ? d->nu0 : 1e13;
+  g->prec = d->precision;
+  g->st = (cudaStream_t)d->stream;
+  const bool f64 = fp64(g);
+  const int cs = f64 ? pick_cluster<double>(g->H, g->n[1], kSmemLimit) : pick_cluster<float>(g->H, g->n[1], kSmemLimit);
+  const int tw = f64 ? pick_tile<double>(g->n[1], g->n[2], kSmemLimit) : pick_tile<float>(g->n[1], g->n[2], kSmemLimit);
+  if (!cs || !tw) {
+    delete g;
+    return OKMC_EINVAL;
+  }
+  int rc = OKMC_OK;
+  auto cleanup = [&](int code) {
+    okmc_grid_destroy(g);
+    return code;
+  };
+  if ((rc = dalloc(g, &g->eps, 6 * g->N * qsize(g)))) return cleanup(rc);
+  if ((rc = dalloc(g, &g->sig, 6 * g->N * tsize(g)))) return cleanup(rc);
+  if ((rc = dalloc(g, &g->spec, 6 * g->n[2] * g->P * 2 * tsize(g)))) return cleanup(rc);
+  if ((rc = dalloc(g, (void**)&g->d_state, sizeof(DevState)))) return cleanup(rc);
+  if ((rc = dalloc(g, (void**)&g->d_err, sizeof(int)))) return cleanup(rc);
+  if ((rc = dalloc(g, (void**)&g->d_partial, sizeof(double) * 30 * kSelfBlocks))) return cleanup(rc);
+  // twiddle tables: w_H^k, w_ny^k, w_nz^k, exp(-2 pi i k/nx) for k <= H
+  size_t off_tw[4];
+  cudaError_t e;
+  if (f64) {
+    std::vector<C2<double>> t;
+    off_tw[0] = t.size(); twiddles(t, g->H, g->H, -1.0);
+    off_tw[1] = t.size(); twiddles(t, g->n[1], g->n[1], -1.0);
+    off_tw[2] = t.size(); twiddles(t, g->n[2], g->n[2], -1.0);
+    off_tw[3] = t.size(); twiddles(t, g->n[0], g->H + 1, -1.0);
+    if ((rc = dalloc(g, &g->tw, t.size() * sizeof(t[0])))) return cleanup(rc);
+    e = cudaMemcpy(g->tw, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice);
+    for (int k = 0; k < 4; ++k) off_tw[k] *= sizeof(C2<double>);
+  } else {
+    std::vector<C2<float>> t;
+    off_tw[0] = t.size(); twiddles(t, g->H, g->H, -1.0);
+    off_tw[1] = t.size(); twiddles(t, g->n[1], g->n[1], -1.0);
+    off_tw[2] = t.size(); twiddles(t, g->n[2], g->n[2], -1.0);
+    off_tw[3] = t.size(); twiddles(t, g->n[0], g->H + 1, -1.0);
+    if ((rc = dalloc(g, &g->tw, t.size() * sizeof(t[0])))) return cleanup(rc);
+    e = cudaMemcpy(g->tw, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice);
+    for (int k = 0; k < 4; ++k) off_tw[k] *= sizeof(C2<float>);
+  }
+  if (e != cudaSuccess) return cleanup(OKMC_ECUDA);
+  // phase tables exp(+2 pi i f / n) for the self-term shifts (f: signed frequency)
+  {
+    std::vector<double2> ph;
+    auto add = [&](int nn, int count, int half) {
+      for (int k = 0; k < count; ++k) {
+        const int f = (half ? (k < nn / 2 ? k : k - nn) : (k < nn / 2 ? k : k - nn));
+        const double ang = 2.0 * kPi * (double)f / (double)nn;
+        ph.push_back(make_double2(std::cos(ang), std::sin(ang)));
+      }
+    };
+    add(g->n[0], g->H + 1, 1);
+    add(g->n[1], g->n[1], 0);
+    add(g->n[2], g->n[2], 0);
+    if ((rc = dalloc(g, (void**)&g->ph, ph.size() * sizeof(double2)))) return cleanup(rc);
+    e = cudaMemcpy(g->ph, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cleanup(OKMC_ECUDA);
+  }
+  PassCfg& c = g->cfg;
+  c.nx = g->n[0];
+  c.ny = g->n[1];
+  c.nz = g->n[2];
+  c.H = g->H;
+  c.ncomp = 6;
+  c.cs = cs;
+  c.tw_w = tw;
+  c.k0_mode = d->k0_mode;
+  c.forward_only = 0;
+  c.q = quantum(g);
+  c.C11 = d->C11;
+  c.C12 = d->C12;
+  c.C44 = d->C44;
+  c.pH = make_plan(g->H);
+  c.pY = make_plan(g->n[1]);
+  c.pZ = make_plan(g->n[2]);
+  c.twH = (const char*)g->tw + off_tw[0];
+  c.twY = (const char*)g->tw + off_tw[1];
+  c.twZ = (const char*)g->tw + off_tw[2];
+  c.untw = (const char*)g->tw + off_tw[3];
+  if (cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
+  if (cudaMemsetAsync(g->d_state, 0, sizeof(DevState), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
+  if (cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
+  if (cudaStreamSynchronize(g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
+  *out = g;
+  return OKMC_OK;
+}
+
+int okmc_grid_destroy(okmc_grid* g) {
+  if (!g) return OKMC_OK;
+  if (g->st || true) cudaStreamSynchronize(g->st);
+  for (auto& p : g->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto ev : g->free_events) cudaEventDestroy(ev);
+  for (auto& a : g->allocs) cudaFree(a.first);
+  delete g;
+  return OKMC_OK;
+}
+
+int okmc_set_stream(okmc_grid* g, void* stream) {
+  if (!g) return OKMC_EINVAL;
+  drain_profile(g);
+  cudaStreamSynchronize(g->st);
+  g->st = (cudaStream_t)stream;
+  return OKMC_OK;
+}
+
+int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
+  if (!g) return OKMC_EINVAL;
+  if (nd < 0 || (nd > 0 && !defs)) return fail(g, OKMC_EINVAL, "bad defect array");
+  try {
+    OKMC_TRY(validate_defects(g, defs, nd));
+    cudaStreamSynchronize(g->st);
+    free_defects(g);
+    g->h_def.assign(defs, defs + nd);
+    g->nd = nd;
+    g->any_mobile = false;
+    for (int i = 0; i < nd; ++i) g->any_mobile |= defs[i].mobility != OKMC_IMMOBILE;
+    const size_t n1 = nd > 0 ? nd : 1;
+    OKMC_TRY(dalloc(g, (void**)&g->d_def, n1 * sizeof(okmc_defect)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_geo, n1 * sizeof(DefGeo)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_ptr, (2 * n1 + 1) * sizeof(int)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_alpha, 2 * n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_sumcnt, 2 * n1 * sizeof(long long)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_nnz, 2 * n1 * sizeof(int)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_W, 18 * n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_E, n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_Ec, 8 * n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_moves, n1 * sizeof(Move)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_pos, 3 * n1 * sizeof(int)));
+    cudaError_t e = cudaSuccess;
+    if (nd) e = cudaMemcpyAsync(g->d_def, defs, nd * sizeof(okmc_defect), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_state, 0, sizeof(DevState), g->st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "upload");
+    g->solves = 0;
+    std::vector<int> ptr(2 * n1 + 1, 0);
+    if (nd) {
+      OKMC_TRY(run(g, "defect_setup", [&] { return launch_defect_setup(g->d_def, g->d_geo, nd, g->h, g->st); }));
+      OKMC_TRY(run(g, "stencil_count", [&] { return launch_stencil_count(g->d_geo, nd, g->d_nnz, g->d_sumcnt, g->st); }));
+      std::vector<int> nnz(2 * nd);
+      e = cudaMemcpyAsync(nnz.data(), g->d_nnz, 2 * nd * sizeof(int), cudaMemcpyDeviceToHost, g->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "stencil sizes");
+      long long tot = 0;
+      for (int k = 0; k < 2 * nd; ++k) {
+        ptr[k] = (int)tot;
+        tot += nnz[k];
+      }
+      ptr[2 * nd] = (int)tot;
+      if (tot > 0x7fffffffll) return fail(g, OKMC_ENOMEM, "too many stencil entries");
+      OKMC_TRY(dalloc(g, (void**)&g->d_off, (size_t)tot * sizeof(int)));
+      OKMC_TRY(dalloc(g, (void**)&g->d_cnt, (size_t)tot));
+    } else {
+      OKMC_TRY(dalloc(g, (void**)&g->d_off, 16));
+      OKMC_TRY(dalloc(g, (void**)&g->d_cnt, 16));
+    }
+    e = cudaMemcpyAsync(g->d_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice, g->st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "stencil offsets");
+    if (nd) {
+      OKMC_TRY(run(g, "stencil_fill", [&] {
+        return launch_stencil_fill(g->d_geo, nd, g->d_ptr, g->d_sumcnt, g->d_off, g->d_cnt, g->d_alpha, g->d_err, g->st);
+      }));
+      OKMC_TRY(check_device_error(g));
+      OKMC_TRY((fp64(g) ? build_self_terms<double, int64_t>(g) : build_self_terms<float, int32_t>(g)));
+    }
+    OKMC_TRY(voxelise_all(g));
+    OKMC_TRY(check_device_error(g));
+    g->sigma_valid = false;
+    return OKMC_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(g, OKMC_ENOMEM, "host allocation failed");
+  }
+}
+
+int okmc_get_defects(okmc_grid* g, okmc_defect* out, int32_t n) {
+  if (!g || (n > 0 && !out)) return OKMC_EINVAL;
+  if (n != g->nd) return fail(g, OKMC_EINVAL, "count differs from the defect set");
+  if (!n) return OKMC_OK;
+  return copy_out(g, out, g->d_def, n * sizeof(okmc_defect), 0);
+}
+
+int okmc_set_positions(okmc_grid* g, const int32_t* pos, int32_t n, int on_device) {
+  if (!g || (n > 0 && !pos)) return OKMC_EINVAL;
+  if (n != g->nd) return fail(g, OKMC_EINVAL, "count differs from the defect set");
+  if (!n) return OKMC_OK;
+  if (!on_device) {
+    for (int i = 0; i < n; ++i) {
+      const int par = pos[3 * i] & 1;
+      for (int a = 0; a < 3; ++a) {
+        if (pos[3 * i + a] < 0 || pos[3 * i + a] >= 2 * g->n[a]) return fail(g, OKMC_EINVAL, "position outside [0, 2n)");
+        if ((pos[3 * i + a] & 1) != par) return fail(g, OKMC_EINVAL, "position is not a bcc site");
+      }
+    }
+  }
+  cudaError_t e = cudaMemcpyAsync(g->d_pos, pos, 3 * n * sizeof(int), on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(&g->d_state->nmoves, 0, sizeof(int), g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "positions upload");
+  OKMC_TRY(run(g, "diff_positions", [&] { return launch_diff_positions(g->d_def, g->d_pos, n, g->d_moves, g->d_state, g->st); }));
+  OKMC_TRY(apply_moves(g, n));
+  g->sigma_valid = false;
+  return OKMC_OK;
+}
+
+int okmc_get_positions(okmc_grid* g, int32_t* pos, int32_t n, int on_device) {
+  if (!g || (n > 0 && !pos)) return OKMC_EINVAL;
+  if (n != g->nd) return fail(g, OKMC_EINVAL, "count differs from the defect set");
+  if (!n) return OKMC_OK;
+  OKMC_TRY(run(g, "gather_positions", [&] { return launch_gather_positions(g->d_def, g->d_pos, n, g->st); }));
+  return copy_out(g, pos, g->d_pos, 3 * n * sizeof(int), on_device);
+}
+
+int okmc_solve_stress(okmc_grid* g, void* sigma_out, int out_on_device) {
+  if (!g) return OKMC_EINVAL;
+  OKMC_TRY(solve(g));
+  if (sigma_out) return copy_out(g, sigma_out, g->sig, 6 * g->N * tsize(g), out_on_device);
+  return OKMC_OK;
+}
+
+int okmc_eigenstrain(okmc_grid* g, void* eps_out, int out_on_device) {
+  if (!g || !eps_out) return OKMC_EINVAL;
+  void* tmp = nullptr;
+  OKMC_TRY(dalloc(g, &tmp, 6 * g->N * tsize(g)));
+  int rc = run(g, "fixed_to_real", [&] {
+    if (fp64(g)) return launch_fixed_to_real<int64_t, double>((const int64_t*)g->eps, (double*)tmp, 6 * g->N, quantum(g), g->st);
+    return launch_fixed_to_real<int32_t, float>((const int32_t*)g->eps, (float*)tmp, 6 * g->N, quantum(g), g->st);
+  });
+  if (rc == OKMC_OK) rc = copy_out(g, eps_out, tmp, 6 * g->N * tsize(g), out_on_device);
+  cudaStreamSynchronize(g->st);
+  dfree(g, tmp);
+  return rc;
+}
+
+int okmc_interaction_energies(okmc_grid* g, double* E, int out_on_device) {
+  if (!g || !E) return OKMC_EINVAL;
+  if (!g->nd) return OKMC_OK;
+  OKMC_TRY(energies(g, 0));
+  return copy_out(g, E, g->d_E, g->nd * sizeof(double), out_on_device);
+}
+
+int okmc_candidate_energies(okmc_grid* g, double* E, uint8_t* valid, int out_on_device) {
+  if (!g || !E) return OKMC_EINVAL;
+  if (!g->nd) return OKMC_OK;
+  OKMC_TRY(energies(g, 1));
+  OKMC_TRY(copy_out(g, E, g->d_Ec, g->nd * 8 * sizeof(double), out_on_device));
+  if (valid) {
+    std::vector<uint8_t> v(8 * g->nd, 0);
+    for (int i = 0; i < g->nd; ++i) {
+      const okmc_defect& r = g->h_def[i];
+      int mask = 0;
+      if (r.mobility == OKMC_THREE_D) mask = 0xFF;
+      if (r.mobility == OKMC_ONE_D) {
+        const int jp = 4 * (r.axis != 1) + 2 * (r.axis != 2) + (r.axis != 3);
+        mask = (1 << jp) | (1 << (7 - jp));
+      }
+      for (int j = 0; j < 8; ++j) v[8 * i + j] = (mask >> j) & 1;
+    }
+    cudaError_t e = cudaMemcpyAsync(valid, v.data(), v.size(), out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "valid mask");
+  }
+  return OKMC_OK;
+}
+
+int okmc_self_terms(okmc_grid* g, double* W, int out_on_device) {
+  if (!g || !W) return OKMC_EINVAL;
+  if (!g->nd) return OKMC_OK;
+  return copy_out(g, W, g->d_W, g->nd * 18 * sizeof(double), out_on_device);
+}
+
+int okmc_get_stencil(okmc_grid* g, int32_t i, int32_t c, int32_t* offs, int32_t* counts, int32_t capacity, int32_t* k,
+                     double* alpha) {
+  if (!g || i < 0 || i >= g->nd || c < 0 || c > 1 || !k) return OKMC_EINVAL;
+  int p[2];
+  cudaError_t e = cudaMemcpyAsync(p, g->d_ptr + 2 * i + c, 2 * sizeof(int), cudaMemcpyDeviceToHost, g->st);
+  double a = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&a, g->d_alpha + 2 * i + c, sizeof(double), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "stencil query");
+  *k = p[1] - p[0];
+  if (alpha) *alpha = a;
+  if (capacity <= 0) return OKMC_OK;
+  if (capacity < *k || !offs || !counts) return fail(g, OKMC_EINVAL, "capacity too small");
+  std::vector<int> o(*k);
+  std::vector<uint8_t> cn(*k);
+  e = cudaMemcpyAsync(o.data(), g->d_off + p[0], *k * sizeof(int), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(cn.data(), g->d_cnt + p[0], *k, cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "stencil copy");
+  for (int q = 0; q < *k; ++q) {
+    unpack_off(o[q], offs[3 * q], offs[3 * q + 1], offs[3 * q + 2]);
+    counts[q] = cn[q];
+  }
+  return OKMC_OK;
+}
+
+int okmc_get_stats(okmc_grid* g, okmc_step_stats* out) {
+  if (!g || !out) return OKMC_EINVAL;
+  DevState s;
+  cudaError_t e = cudaMemcpyAsync(&s, g->d_state, sizeof(s), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "stats");
+  out->events = s.events;
+  out->steps = s.step;
+  out->solves = g->solves;
+  out->negative_barriers = s.negative_barriers;
+  out->clock = s.clock;
+  out->dt_last = s.dt_last;
+  if (s.err) return fail(g, OKMC_ESTATE, "no mobile defect with a positive rate");
+  return OKMC_OK;
+}
+
+int okmc_step(okmc_grid* g, const okmc_step_params* p, int64_t n_steps, okmc_step_stats* out) {
+  if (!g || !p) return OKMC_EINVAL;
+  if (!(p->T_K > 0.0) || !std::isfinite(p->T_K)) return fail(g, OKMC_EINVAL, "temperature must be > 0");
+  if (p->mode != OKMC_RESIDENCE && p->mode != OKMC_FIXED_DT) return fail(g, OKMC_EINVAL, "unknown mode");
+  if (n_steps < 0) return fail(g, OKMC_EINVAL, "negative step count");
+  if (!g->nd || !g->any_mobile) return fail(g, OKMC_ESTATE, "no mobile defect");
+  const double kT = kBoltzmann * p->T_K;
+  for (int64_t s = 0; s < n_steps; ++s) {
+    OKMC_TRY(energies(g, 1));
+    if (p->mode == OKMC_RESIDENCE) {
+      OKMC_TRY(run(g, "event_residence", [&] {
+        return launch_residence(g->d_def, g->d_geo, g->nd, g->d_E, g->d_Ec, g->nu0, kT, dims(g), g->desc.seed, g->d_moves,
+                                g->d_state, g->st);
+      }));
+      OKMC_TRY(apply_moves(g, 1));
+    } else {
+      OKMC_TRY(run(g, "event_fixed_dt", [&] {
+        return launch_fixed_dt(g->d_def, g->d_geo, g->nd, g->d_E, g->d_Ec, g->nu0, kT, dims(g), g->desc.seed, g->d_moves,
+                               g->d_state, g->st);
+      }));
+      OKMC_TRY(apply_moves(g, g->nd));
+    }
+    g->sigma_valid = false;
+    if (p->t_end > 0.0) {
+      okmc_step_stats tmp;
+      OKMC_TRY(okmc_get_stats(g, &tmp));
+      if (tmp.clock >= p->t_end) break;
+    }
+  }
+  if (out) OKMC_TRY(okmc_get_stats(g, out));
+  return OKMC_OK;
+}
+
+size_t okmc_device_bytes(const okmc_grid* g) { return g ? g->bytes : 0; }
+
+int okmc_set_profiling(okmc_grid* g, int enable) {
+  if (!g) return OKMC_EINVAL;
+  drain_profile(g);
+  g->profiling = enable != 0;
+  return OKMC_OK;
+}
+
+int okmc_kernel_times(okmc_grid* g, const char** names, double* ms, int64_t* count, int cap) {
+  if (!g) return OKMC_EINVAL;
+  drain_profile(g);
+  g->prof_names.clear();
+  for (auto& kv : g->prof) g->prof_names.push_back(kv.first);
+  int k = 0;
+  for (auto& kv : g->prof) {
+    if (k < cap) {
+      if (names) names[k] = g->prof_names[k].c_str();
+      if (ms) ms[k] = kv.second.first;
+      if (count) count[k] = kv.second.second;
+    }
+    ++k;
+  }
+  return k;
+}
+
+int okmc_reset_kernel_times(okmc_grid* g) {
+  if (!g) return OKMC_EINVAL;
+  drain_profile(g);
+  g->prof.clear();
+  return OKMC_OK;
+}
+
+int okmc_launch_shape(const okmc_grid* g, int32_t out[3]) {
+  if (!g || !out) return OKMC_EINVAL;
+  out[0] = g->cfg.cs;
+  out[1] = (int32_t)(g->P / g->cfg.tw_w);
+  out[2] = g->cfg.cs;
+  return OKMC_OK;
+}
+
+}  // extern "C"

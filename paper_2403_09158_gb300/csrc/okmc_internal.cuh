@@ -1,0 +1,281 @@
+// Internal declarations of the GB300 OkMC elastic-interaction library.
+//
+// Data layout in device memory (one handle, one grid of nx*ny*nz voxels, x fastest):
+//   eps   : eigenstrain, 6 components [c][z][y][x], fixed point (int32 with
+//           quantum 2^-26 for FP32 fields, int64 with quantum 2^-40 for FP64
+//           fields) so that incremental add/subtract of stencils is exact.
+//   sigma : stress, 6 components [c][z][y][x] in T (float or double).
+//   spec  : half spectrum, 6 components, per component nz planes of
+//           P = (nx/2 + 1) * ny complex values in kx-major order p = kx*ny + ky
+//           ("transposed plane"): the forward plane pass writes whole kx columns,
+//           the pencil pass reads TW consecutive ky at one kx for every kz.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "okmc.h"
+
+namespace okmc {
+
+constexpr double kPi = 3.141592653589793;
+constexpr double kKappa = 6.241509074;      // eV per GPa nm^3
+constexpr double kBoltzmann = 8.617333262e-5;  // eV/K
+
+// ---------------------------------------------------------------- complex
+template <class T>
+struct alignas(2 * sizeof(T)) C2 {
+  T x, y;
+};
+
+template <class T> __host__ __device__ __forceinline__ C2<T> operator+(C2<T> a, C2<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T> __host__ __device__ __forceinline__ C2<T> operator-(C2<T> a, C2<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <class T> __host__ __device__ __forceinline__ C2<T> operator*(C2<T> a, C2<T> b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class T> __host__ __device__ __forceinline__ C2<T> operator*(T s, C2<T> a) { return {s * a.x, s * a.y}; }
+template <class T> __host__ __device__ __forceinline__ C2<T> conjg(C2<T> a) { return {a.x, -a.y}; }
+// multiply by -i (forward transform) or +i (inverse transform)
+template <class T, bool INV> __device__ __forceinline__ C2<T> rot(C2<T> v) {
+  return INV ? C2<T>{-v.y, v.x} : C2<T>{v.y, -v.x};
+}
+
+// ---------------------------------------------------------------- small DFTs
+// X_k = sum_n x_n exp(-+2 pi i n k / R): minus sign forward, plus sign inverse.
+template <class T, bool INV> __device__ __forceinline__ void dft2(C2<T>* v) {
+  C2<T> a = v[0];
+  v[0] = a + v[1];
+  v[1] = a - v[1];
+}
+template <class T, bool INV> __device__ __forceinline__ void dft3(C2<T>* v) {
+  const T s = T(0.86602540378443864676);  // sin(2 pi / 3)
+  C2<T> t1 = v[1] + v[2], t2 = v[1] - v[2];
+  C2<T> m = v[0] - T(0.5) * t1;
+  C2<T> r = s * rot<T, INV>(t2);
+  v[0] = v[0] + t1;
+  v[1] = m + r;
+  v[2] = m - r;
+}
+template <class T, bool INV> __device__ __forceinline__ void dft4(C2<T>* v) {
+  C2<T> a = v[0] + v[2], b = v[0] - v[2], c = v[1] + v[3], d = rot<T, INV>(v[1] - v[3]);
+  v[0] = a + c;
+  v[2] = a - c;
+  v[1] = b + d;
+  v[3] = b - d;
+}
+template <class T, bool INV> __device__ __forceinline__ void dft5(C2<T>* v) {
+  const T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);  // cos(2pi/5), cos(4pi/5)
+  const T s1 = T(0.95105651629515357212), s2 = T(0.58778525229247312917);   // sin(2pi/5), sin(4pi/5)
+  C2<T> a1 = v[1] + v[4], b1 = v[1] - v[4], a2 = v[2] + v[3], b2 = v[2] - v[3];
+  C2<T> m1 = v[0] + c1 * a1 + c2 * a2;
+  C2<T> m2 = v[0] + c2 * a1 + c1 * a2;
+  C2<T> n1 = rot<T, INV>(s1 * b1 + s2 * b2);
+  C2<T> n2 = rot<T, INV>(s2 * b1 - s1 * b2);
+  v[0] = v[0] + a1 + a2;
+  v[1] = m1 + n1;
+  v[4] = m1 - n1;
+  v[2] = m2 + n2;
+  v[3] = m2 - n2;
+}
+template <class T, bool INV> __device__ __forceinline__ void dft8(C2<T>* v) {
+  const T h = T(0.70710678118654752440);  // sqrt(1/2)
+  C2<T> e[4] = {v[0], v[2], v[4], v[6]};
+  C2<T> o[4] = {v[1], v[3], v[5], v[7]};
+  dft4<T, INV>(e);
+  dft4<T, INV>(o);
+  // twiddles w8^k, w8 = exp(-+ i pi/4)
+  C2<T> o1 = INV ? C2<T>{h * (o[1].x - o[1].y), h * (o[1].x + o[1].y)}
+                 : C2<T>{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};
+  C2<T> o2 = rot<T, INV>(o[2]);
+  C2<T> o3 = INV ? C2<T>{h * (-o[3].x - o[3].y), h * (o[3].x - o[3].y)}
+                 : C2<T>{h * (o[3].y - o[3].x), h * (-o[3].x - o[3].y)};
+  v[0] = e[0] + o[0];
+  v[4] = e[0] - o[0];
+  v[1] = e[1] + o1;
+  v[5] = e[1] - o1;
+  v[2] = e[2] + o2;
+  v[6] = e[2] - o2;
+  v[3] = e[3] + o3;
+  v[7] = e[3] - o3;
+}
+template <class T, bool INV, int R> __device__ __forceinline__ void dftR(C2<T>* v) {
+  if constexpr (R == 2) dft2<T, INV>(v);
+  else if constexpr (R == 3) dft3<T, INV>(v);
+  else if constexpr (R == 4) dft4<T, INV>(v);
+  else if constexpr (R == 5) dft5<T, INV>(v);
+  else dft8<T, INV>(v);
+}
+
+// ---------------------------------------------------------------- line FFT engine
+// A length-L transform runs as a sequence of Stockham autosort stages (the
+// formulation of Govindaraju et al., SC'08) of radix 2, 3, 4, 5 or 8, one warp
+// per line.  Stage s reads element j + r*(L/R), multiplies by w_L^(r*(j mod
+// Ns)*L/(Ns*R)), does a radix-R DFT and writes element (j - j mod Ns)*R + j mod Ns
+// + r*Ns, with Ns the product of the earlier radices; output is in natural order.
+struct LinePlan {
+  int L;
+  int nst;
+  int rad[8];
+};
+
+template <class T>
+struct SLine {  // strided line in shared, distributed-shared or global memory
+  C2<T>* p;
+  int s;
+  __device__ __forceinline__ C2<T> ld(int i) const { return p[i * s]; }
+  __device__ __forceinline__ void st(int i, C2<T> v) const { p[i * s] = v; }
+};
+
+template <class T, bool INV, int R, class In, class Out>
+__device__ __forceinline__ void fft_stage(In in, Out out, const C2<T>* __restrict__ tw, int L, int Ns, int lane) {
+  const int nb = L / R;
+  const int tws = L / (Ns * R);
+  for (int j = lane; j < nb; j += 32) {
+    const int jm = j % Ns;
+    C2<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in.ld(j + r * nb);
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C2<T> w = tw[r * jm * tws];
+        if (INV) w.y = -w.y;
+        v[r] = v[r] * w;
+      }
+    }
+    dftR<T, INV, R>(v);
+    const int o = (j - jm) * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out.st(o + r * Ns, v[r]);
+  }
+}
+
+template <class T, bool INV, class In, class Out>
+__device__ __forceinline__ void fft_stage_any(int R, In in, Out out, const C2<T>* tw, int L, int Ns, int lane) {
+  switch (R) {
+    case 2: fft_stage<T, INV, 2>(in, out, tw, L, Ns, lane); break;
+    case 3: fft_stage<T, INV, 3>(in, out, tw, L, Ns, lane); break;
+    case 4: fft_stage<T, INV, 4>(in, out, tw, L, Ns, lane); break;
+    case 5: fft_stage<T, INV, 5>(in, out, tw, L, Ns, lane); break;
+    default: fft_stage<T, INV, 8>(in, out, tw, L, Ns, lane); break;
+  }
+}
+
+// Transform of the line src into dst by one warp.  bufA/bufB: ping-pong lines of
+// length L that alias neither src nor dst (bufB may alias src when src is a
+// writable line that is no longer needed); plans have at least two stages.
+template <class T, bool INV, class In, class Out>
+__device__ void line_fft(In src, Out dst, C2<T>* bufA, C2<T>* bufB, const C2<T>* tw, const LinePlan& p, int lane) {
+  SLine<T> a{bufA, 1}, b{bufB, 1};
+  int Ns = 1;
+  fft_stage_any<T, INV>(p.rad[0], src, a, tw, p.L, Ns, lane);
+  __syncwarp();
+  Ns *= p.rad[0];
+  for (int s = 1; s < p.nst - 1; ++s) {
+    if (s & 1) fft_stage_any<T, INV>(p.rad[s], a, b, tw, p.L, Ns, lane);
+    else fft_stage_any<T, INV>(p.rad[s], b, a, tw, p.L, Ns, lane);
+    __syncwarp();
+    Ns *= p.rad[s];
+  }
+  if ((p.nst - 2) & 1) fft_stage_any<T, INV>(p.rad[p.nst - 1], b, dst, tw, p.L, Ns, lane);
+  else fft_stage_any<T, INV>(p.rad[p.nst - 1], a, dst, tw, p.L, Ns, lane);
+  __syncwarp();
+}
+
+// ---------------------------------------------------------------- pass configuration
+struct PassCfg {
+  int nx, ny, nz, H;   // H = nx/2
+  int ncomp;           // components (planes per z)
+  int cs;              // cluster size of the plane passes
+  int tw_w;            // pencil tile width (consecutive ky per kx)
+  int k0_mode;
+  int forward_only;    // pencil pass: stop after the forward z transform
+  double q;            // fixed-point quantum of the eigenstrain input
+  double C11, C12, C44;
+  LinePlan pH, pY, pZ;
+  const void* twH;     // C2<T>[H]      w_H^k
+  const void* twY;     // C2<T>[ny]
+  const void* twZ;     // C2<T>[nz]
+  const void* untw;    // C2<T>[H+1]    exp(-2 pi i k / nx)
+};
+
+// ---------------------------------------------------------------- defects
+struct DefGeo {
+  double e6[6];       // eigenstrain tensor (xx, yy, zz, yz, xz, xy)
+  double v_over_h3;   // shape volume / h^3
+  double thr;         // disk: |a|^2 (8R/h)^2; sphere: (8 rho)^6
+  int kind;           // 0 disk, 1 sphere
+  int a[3];           // disk axis (integer vector)
+  int a2;
+  int extent;         // scan half-width in voxels
+  int allowed;        // bit j set: jump j allowed
+  int z;              // number of allowed jumps
+};
+
+struct Move {
+  int i;
+  int old_pos[3];
+  int new_pos[3];
+};
+
+// Kinetic state kept on the device (one per handle).
+struct DevState {
+  double clock;
+  double dt_last;
+  long long events;
+  long long negative_barriers;
+  long long step;
+  int nmoves;
+  int err;
+  double dt_fixed;
+};
+
+// Eigenstrain tensors of the (at most three) defects whose self terms one batch computes.
+struct WBatch {
+  double e6[3][6];
+  int nb;
+};
+
+__host__ __device__ __forceinline__ int pack_off(int dx, int dy, int dz) {
+  return (dx + 512) | ((dy + 512) << 10) | ((dz + 512) << 20);
+}
+__host__ __device__ __forceinline__ void unpack_off(int p, int& dx, int& dy, int& dz) {
+  dx = (p & 1023) - 512;
+  dy = ((p >> 10) & 1023) - 512;
+  dz = ((p >> 20) & 1023) - 512;
+}
+
+__host__ __device__ __forceinline__ int floor_div2(int p) { return p >= 0 ? p / 2 : -((1 - p) / 2); }
+
+// jump j <-> (sx, sy, sz), j = 4(sx>0) + 2(sy>0) + (sz>0)
+__host__ __device__ __forceinline__ int jump_comp(int j, int a) { return ((j >> (2 - a)) & 1) ? 1 : -1; }
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11)
+__host__ __device__ __forceinline__ void philox4x32_10(const uint32_t ctr_in[4], uint32_t k0, uint32_t k1, uint32_t out[4]) {
+  uint32_t x0 = ctr_in[0], x1 = ctr_in[1], x2 = ctr_in[2], x3 = ctr_in[3];
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)0xD2511F53u * x0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * x2;
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    x0 = hi1 ^ x1 ^ k0;
+    x1 = lo1;
+    x2 = hi0 ^ x3 ^ k1;
+    x3 = lo0;
+  }
+  out[0] = x0;
+  out[1] = x1;
+  out[2] = x2;
+  out[3] = x3;
+}
+// uniform on (0, 1]: ((hi << 21) | (lo >> 11)) + 1 over 2^53
+__host__ __device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
+  const uint64_t k = (((uint64_t)hi << 21) | (lo >> 11)) + 1ull;
+  return (double)k * 1.1102230246251565404e-16;
+}
+
+}  // namespace okmc

@@ -1,0 +1,416 @@
+// Periodic elastic solve with eigenstrain on the voxel grid (paper Sec. 3.2 and
+// 3.4): forward 3D real-to-complex transform of the six eigenstrain components,
+// Green operator at every discrete frequency, inverse complex-to-real transform.
+//
+// Three passes over HBM:
+//   plane_fwd : per (component, z) plane, a cluster of CS CTAs.  Each CTA
+//               transforms its rows along x (real rows of length nx as complex
+//               rows of length nx/2, then the real-to-complex untangling) and
+//               writes every result column straight into the shared memory of
+//               the CTA that owns that kx range (distributed shared memory).
+//               After a cluster barrier each CTA transforms its kx columns along
+//               y and stores them as contiguous kx-major lines.
+//   pencil    : per tile of TW consecutive ky at one kx, all six components and
+//               all kz: forward z transform, Green operator, inverse z transform.
+//   plane_inv : per plane, inverse y transform of the owned kx columns, a
+//               cluster barrier, then each CTA gathers full kx rows from the
+//               cluster (distributed shared memory reads), untangles and runs
+//               the inverse x transform, and writes real stress rows.
+#include <cooperative_groups.h>
+
+#include <cstdio>
+
+#include "okmc_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace okmc {
+
+constexpr int kWarps = 8;
+constexpr int kThreads = kWarps * 32;
+
+// ---------------------------------------------------------------- accessors
+template <class T, class Q>
+struct RowSrcQ;  // fixed-point real row read as complex pairs (x[2i], x[2i+1])
+
+template <>
+struct RowSrcQ<float, int32_t> {
+  const int32_t* p;
+  float q;
+  __device__ __forceinline__ C2<float> ld(int i) const {
+    const int2 v = __ldg(reinterpret_cast<const int2*>(p) + i);
+    return {__int2float_rn(v.x) * q, __int2float_rn(v.y) * q};
+  }
+};
+template <>
+struct RowSrcQ<double, int64_t> {
+  const int64_t* p;
+  double q;
+  __device__ __forceinline__ C2<double> ld(int i) const {
+    const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(p) + i);
+    return {__ll2double_rn(v.x) * q, __ll2double_rn(v.y) * q};
+  }
+};
+
+template <class T>
+struct GreenC {
+  T C11, C12, C44;
+};
+
+// sigma_hat = C:(sym(m (x) K(m)^-1 (tau m)) - eps*_hat), tau = C:eps*_hat, for a unit
+// direction m and cubic C (paper Eqs. EIG_elastic_fourier, basicgammacomplete,
+// summaryEL with the standard index reading of Gamma).
+template <class T>
+__device__ __forceinline__ void sigma_of(const C2<T>* e, T m0, T m1, T m2, const GreenC<T>& C, C2<T>* s) {
+  const T A = C.C11 - C.C12 - T(2) * C.C44;
+  const T B = C.C12 + C.C44;
+  const T k00 = C.C44 + (A + B) * m0 * m0, k11 = C.C44 + (A + B) * m1 * m1, k22 = C.C44 + (A + B) * m2 * m2;
+  const T k01 = B * m0 * m1, k02 = B * m0 * m2, k12 = B * m1 * m2;
+  const T i00 = k11 * k22 - k12 * k12, i01 = k02 * k12 - k01 * k22, i02 = k01 * k12 - k02 * k11;
+  const T i11 = k00 * k22 - k02 * k02, i12 = k01 * k02 - k00 * k12, i22 = k00 * k11 - k01 * k01;
+  const T rdet = T(1) / (k00 * i00 + k01 * i01 + k02 * i02);
+  const T d = C.C11 - C.C12, g = T(2) * C.C44;
+  const C2<T> tr = e[0] + e[1] + e[2];
+  const C2<T> t0 = C.C12 * tr + d * e[0], t1 = C.C12 * tr + d * e[1], t2 = C.C12 * tr + d * e[2];
+  const C2<T> t3 = g * e[3], t4 = g * e[4], t5 = g * e[5];
+  const C2<T> v0 = m0 * t0 + m1 * t5 + m2 * t4;
+  const C2<T> v1 = m0 * t5 + m1 * t1 + m2 * t3;
+  const C2<T> v2 = m0 * t4 + m1 * t3 + m2 * t2;
+  const C2<T> w0 = rdet * (i00 * v0 + i01 * v1 + i02 * v2);
+  const C2<T> w1 = rdet * (i01 * v0 + i11 * v1 + i12 * v2);
+  const C2<T> w2 = rdet * (i02 * v0 + i12 * v1 + i22 * v2);
+  const C2<T> g0 = m0 * w0, g1 = m1 * w1, g2 = m2 * w2;
+  const C2<T> g3 = T(0.5) * (m1 * w2 + m2 * w1), g4 = T(0.5) * (m0 * w2 + m2 * w0), g5 = T(0.5) * (m0 * w1 + m1 * w0);
+  const C2<T> trg = g0 + g1 + g2;
+  s[0] = C.C12 * trg + d * g0 - t0;
+  s[1] = C.C12 * trg + d * g1 - t1;
+  s[2] = C.C12 * trg + d * g2 - t2;
+  s[3] = g * g3 - t3;
+  s[4] = g * g4 - t4;
+  s[5] = g * g5 - t5;
+}
+
+// Green operator at half-spectrum index (kx, ky, kz), in place on e[6], scaled by
+// 1/N.  Frequencies follow Eq. frequencies (n = k for k < N/2, k - N otherwise,
+// so the Nyquist index is -N/2); on Nyquist planes the operator is averaged over
+// the sign of the Nyquist components, which is what the real part of the inverse
+// of the full spectrum computes.
+template <class T>
+__device__ __forceinline__ void green_point(C2<T>* e, int kx, int ky, int kz, const PassCfg& c, T scale) {
+  const GreenC<T> C{T(c.C11), T(c.C12), T(c.C44)};
+  const int fx = kx < c.H ? kx : kx - c.nx;
+  const int fy = ky < c.ny / 2 ? ky : ky - c.ny;
+  const int fz = kz < c.nz / 2 ? kz : kz - c.nz;
+  C2<T> s[6];
+  if (fx == 0 && fy == 0 && fz == 0) {
+    if (c.k0_mode == OKMC_MEAN_STRAIN_ZERO) {
+      const T d = C.C11 - C.C12, g = T(2) * C.C44;
+      const C2<T> tr = e[0] + e[1] + e[2];
+      s[0] = T(-1) * (C.C12 * tr + d * e[0]);
+      s[1] = T(-1) * (C.C12 * tr + d * e[1]);
+      s[2] = T(-1) * (C.C12 * tr + d * e[2]);
+      s[3] = T(-1) * (g * e[3]);
+      s[4] = T(-1) * (g * e[4]);
+      s[5] = T(-1) * (g * e[5]);
+    } else {
+      for (int a = 0; a < 6; ++a) s[a] = C2<T>{T(0), T(0)};
+    }
+  } else {
+    const T qx = T(fx) / T(c.nx), qy = T(fy) / T(c.ny), qz = T(fz) / T(c.nz);
+    const T rn = T(1) / sqrt(qx * qx + qy * qy + qz * qz);
+    const T m0 = qx * rn, m1 = qy * rn, m2 = qz * rn;
+    sigma_of<T>(e, m0, m1, m2, C, s);
+    const bool nx_ = (kx == c.H), ny_ = (2 * ky == c.ny), nz_ = (2 * kz == c.nz);
+    if (nx_ || ny_ || nz_) {
+      C2<T> s2[6];
+      sigma_of<T>(e, nx_ ? -m0 : m0, ny_ ? -m1 : m1, nz_ ? -m2 : m2, C, s2);
+      for (int a = 0; a < 6; ++a) s[a] = T(0.5) * (s[a] + s2[a]);
+    }
+  }
+  for (int a = 0; a < 6; ++a) e[a] = scale * s[a];
+}
+
+// ---------------------------------------------------------------- smem layout
+template <class T>
+struct PlaneSmem {
+  C2<T>* col;   // [ncol_max][ny + 1]
+  C2<T>* twH;   // [H]
+  C2<T>* twY;   // [ny]
+  C2<T>* untw;  // [H + 1]
+  C2<T>* scr;   // [kWarps][2][lmax]
+  int lmax;
+};
+
+template <class T>
+__host__ __device__ inline size_t plane_smem_bytes(int H, int ny, int cs) {
+  const int ncol = H / cs + 1;
+  const int lmax = H > ny ? H : ny;
+  return sizeof(C2<T>) * ((size_t)ncol * (ny + 1) + H + ny + (H + 1) + (size_t)kWarps * 2 * lmax);
+}
+
+template <class T>
+__device__ inline PlaneSmem<T> carve_plane(unsigned char* raw, const PassCfg& c) {
+  PlaneSmem<T> s;
+  C2<T>* p = reinterpret_cast<C2<T>*>(raw);
+  const int ncol = c.H / c.cs + 1;
+  s.col = p;
+  p += (size_t)ncol * (c.ny + 1);
+  s.twH = p;
+  p += c.H;
+  s.twY = p;
+  p += c.ny;
+  s.untw = p;
+  p += c.H + 1;
+  s.scr = p;
+  s.lmax = c.H > c.ny ? c.H : c.ny;
+  return s;
+}
+
+template <class T>
+__device__ inline void load_twiddles(const PlaneSmem<T>& s, const PassCfg& c) {
+  const C2<T>* gH = reinterpret_cast<const C2<T>*>(c.twH);
+  const C2<T>* gY = reinterpret_cast<const C2<T>*>(c.twY);
+  const C2<T>* gU = reinterpret_cast<const C2<T>*>(c.untw);
+  for (int i = threadIdx.x; i < c.H; i += blockDim.x) s.twH[i] = gH[i];
+  for (int i = threadIdx.x; i < c.ny; i += blockDim.x) s.twY[i] = gY[i];
+  for (int i = threadIdx.x; i <= c.H; i += blockDim.x) s.untw[i] = gU[i];
+}
+
+// ---------------------------------------------------------------- forward plane pass
+template <class T, class Q>
+__global__ void __launch_bounds__(kThreads) k_plane_fwd(const Q* __restrict__ eps, C2<T>* __restrict__ spec, PassCfg c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PlaneSmem<T> s = carve_plane<T>(smem_raw, c);
+  const int cs = c.cs;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int h = cs > 1 ? (int)cluster.block_rank() : 0;
+  const int plane = blockIdx.y;  // component * nz + z
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H = c.H, ny = c.ny, ldc = ny + 1;
+  const int cols_per = H / cs;
+  const size_t P = (size_t)(H + 1) * ny;
+  load_twiddles(s, c);
+  __syncthreads();
+
+  C2<T>* bufA = s.scr + (size_t)warp * 2 * s.lmax;
+  C2<T>* bufB = bufA + s.lmax;
+  C2<T>* res = ((c.pH.nst - 1) & 1) ? bufB : bufA;  // where line_fft's last stage lands
+  const int rows_per = ny / cs;
+  const int y0 = h * rows_per;
+  for (int r = warp; r < rows_per; r += kWarps) {
+    const int y = y0 + r;
+    RowSrcQ<T, Q> src{eps + ((size_t)plane * ny + y) * c.nx, T(c.q)};
+    line_fft<T, false>(src, SLine<T>{res, 1}, bufA, bufB, s.twH, c.pH, lane);
+    // real-to-complex untangling: X[k] = (A + B)/2 - (i/2) w^k (A - B),
+    // A = Z[k mod H], B = conj Z[(H - k) mod H], w = exp(-2 pi i / nx)
+    for (int k = lane; k <= H; k += 32) {
+      const C2<T> A = res[k == H ? 0 : k];
+      const C2<T> B = conjg(res[k == 0 ? 0 : H - k]);
+      const C2<T> sum = A + B, dif = s.untw[k] * (A - B);
+      const C2<T> X{T(0.5) * (sum.x + dif.y), T(0.5) * (sum.y - dif.x)};
+      int owner = k / cols_per;
+      if (owner >= cs) owner = cs - 1;
+      const int col = k - owner * cols_per;
+      C2<T>* dst = s.col;
+      if (cs > 1 && owner != h) dst = cluster.map_shared_rank(s.col, owner);
+      dst[(size_t)col * ldc + y] = X;
+    }
+    __syncwarp();
+  }
+  if (cs > 1) cluster.sync();
+  else __syncthreads();
+
+  const int ncol = (h == cs - 1) ? cols_per + 1 : cols_per;
+  const int k0 = h * cols_per;
+  for (int cc = warp; cc < ncol; cc += kWarps) {
+    SLine<T> src{s.col + (size_t)cc * ldc, 1};
+    SLine<T> dst{spec + (size_t)plane * P + (size_t)(k0 + cc) * ny, 1};
+    line_fft<T, false>(src, dst, bufA, bufB, s.twY, c.pY, lane);
+  }
+}
+
+// ---------------------------------------------------------------- inverse plane pass
+template <class T>
+struct RowDst {
+  T* p;
+  __device__ __forceinline__ void st(int i, C2<T> v) const { reinterpret_cast<C2<T>*>(p)[i] = v; }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_plane_inv(const C2<T>* __restrict__ spec, T* __restrict__ sig, PassCfg c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const PlaneSmem<T> s = carve_plane<T>(smem_raw, c);
+  const int cs = c.cs;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int h = cs > 1 ? (int)cluster.block_rank() : 0;
+  const int plane = blockIdx.y;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int H = c.H, ny = c.ny, ldc = ny + 1;
+  const int cols_per = H / cs;
+  const size_t P = (size_t)(H + 1) * ny;
+  load_twiddles(s, c);
+  __syncthreads();
+
+  C2<T>* bufA = s.scr + (size_t)warp * 2 * s.lmax;
+  C2<T>* bufB = bufA + s.lmax;
+  const int ncol = (h == cs - 1) ? cols_per + 1 : cols_per;
+  const int k0 = h * cols_per;
+  for (int cc = warp; cc < ncol; cc += kWarps) {
+    SLine<T> src{const_cast<C2<T>*>(spec) + (size_t)plane * P + (size_t)(k0 + cc) * ny, 1};
+    SLine<T> dst{s.col + (size_t)cc * ldc, 1};
+    line_fft<T, true>(src, dst, bufA, bufB, s.twY, c.pY, lane);
+  }
+  if (cs > 1) cluster.sync();
+  else __syncthreads();
+
+  const int rows_per = ny / cs;
+  const int y0 = h * rows_per;
+  for (int r = warp; r < rows_per; r += kWarps) {
+    const int y = y0 + r;
+    // complex-to-real untangling: Z[k] = E + i O, E = X[k] + conj X[H-k],
+    // O = (X[k] - conj X[H-k]) exp(+2 pi i k / nx), then an inverse transform of
+    // length H gives (x[2m], x[2m+1]) as (Re, Im).
+    for (int k = lane; k < H; k += 32) {
+      int o1 = k / cols_per;
+      if (o1 >= cs) o1 = cs - 1;
+      int o2 = (H - k) / cols_per;
+      if (o2 >= cs) o2 = cs - 1;
+      const C2<T>* b1 = (cs > 1 && o1 != h) ? cluster.map_shared_rank(s.col, o1) : s.col;
+      const C2<T>* b2 = (cs > 1 && o2 != h) ? cluster.map_shared_rank(s.col, o2) : s.col;
+      const C2<T> Xk = b1[(size_t)(k - o1 * cols_per) * ldc + y];
+      const C2<T> Xc = conjg(b2[(size_t)(H - k - o2 * cols_per) * ldc + y]);
+      const C2<T> E = Xk + Xc;
+      const C2<T> O = conjg(s.untw[k]) * (Xk - Xc);
+      bufB[k] = C2<T>{E.x - O.y, E.y + O.x};
+    }
+    __syncwarp();
+    RowDst<T> dst{sig + ((size_t)plane * ny + y) * c.nx};
+    line_fft<T, true>(SLine<T>{bufB, 1}, dst, bufA, bufB, s.twH, c.pH, lane);
+  }
+  if (cs > 1) cluster.sync();  // peers may still read this CTA's columns
+}
+
+// ---------------------------------------------------------------- pencil pass
+template <class T>
+__host__ __device__ inline size_t pencil_smem_bytes(int nz, int tw) {
+  return sizeof(C2<T>) * ((size_t)6 * tw * (nz + 1) + nz + (size_t)kWarps * 2 * nz);
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pencil(C2<T>* __restrict__ spec, PassCfg c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int TW = c.tw_w, nz = c.nz, ldl = nz + 1;
+  const int nlines = c.ncomp * TW;
+  C2<T>* lines = reinterpret_cast<C2<T>*>(smem_raw);
+  C2<T>* twZ = lines + (size_t)nlines * ldl;
+  C2<T>* scr = twZ + nz;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t P = (size_t)(c.H + 1) * c.ny;
+  const size_t p0 = (size_t)blockIdx.x * TW;
+  const int kx = (int)(p0 / c.ny), ky0 = (int)(p0 % c.ny);
+  const C2<T>* gZ = reinterpret_cast<const C2<T>*>(c.twZ);
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) twZ[i] = gZ[i];
+  const int total = c.ncomp * nz * TW;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int t = idx % TW, kz = (idx / TW) % nz, comp = idx / (TW * nz);
+    lines[(size_t)(comp * TW + t) * ldl + kz] = spec[((size_t)comp * nz + kz) * P + p0 + t];
+  }
+  __syncthreads();
+  C2<T>* bufA = scr + (size_t)warp * 2 * nz;
+  C2<T>* bufB = bufA + nz;
+  for (int l = warp; l < nlines; l += kWarps) {
+    SLine<T> ln{lines + (size_t)l * ldl, 1};
+    line_fft<T, false>(ln, ln, bufA, bufB, twZ, c.pZ, lane);
+  }
+  __syncthreads();
+  if (!c.forward_only) {
+    const T scale = T(1) / (T(c.nx) * T(c.ny) * T(c.nz));
+    for (int idx = threadIdx.x; idx < TW * nz; idx += blockDim.x) {
+      const int t = idx / nz, kz = idx % nz;
+      C2<T> e[6];
+      for (int a = 0; a < 6; ++a) e[a] = lines[(size_t)(a * TW + t) * ldl + kz];
+      green_point<T>(e, kx, ky0 + t, kz, c, scale);
+      for (int a = 0; a < 6; ++a) lines[(size_t)(a * TW + t) * ldl + kz] = e[a];
+    }
+    __syncthreads();
+    for (int l = warp; l < nlines; l += kWarps) {
+      SLine<T> ln{lines + (size_t)l * ldl, 1};
+      line_fft<T, true>(ln, ln, bufA, bufB, twZ, c.pZ, lane);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int t = idx % TW, kz = (idx / TW) % nz, comp = idx / (TW * nz);
+    spec[((size_t)comp * nz + kz) * P + p0 + t] = lines[(size_t)(comp * TW + t) * ldl + kz];
+  }
+}
+
+// ---------------------------------------------------------------- host launchers
+template <class T>
+int pick_cluster(int H, int ny, size_t limit) {
+  for (int cs = 1; cs <= 8; cs *= 2) {
+    if (H % cs || ny % cs) continue;
+    if (plane_smem_bytes<T>(H, ny, cs) <= limit) return cs;
+  }
+  return 0;
+}
+template int pick_cluster<float>(int, int, size_t);
+template int pick_cluster<double>(int, int, size_t);
+
+template <class T>
+int pick_tile(int ny, int nz, size_t limit) {
+  for (int tw = 8; tw >= 1; tw /= 2) {
+    if (ny % tw) continue;
+    if (pencil_smem_bytes<T>(nz, tw) <= limit) return tw;
+  }
+  return 0;
+}
+template int pick_tile<float>(int, int, size_t);
+template int pick_tile<double>(int, int, size_t);
+
+template <class KernelT, class... Args>
+static cudaError_t launch(KernelT k, dim3 grid, size_t smem, int cluster, cudaStream_t st, Args... args) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (cluster > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <class T, class Q>
+cudaError_t launch_plane_fwd(const Q* eps, C2<T>* spec, const PassCfg& c, cudaStream_t st) {
+  const size_t smem = plane_smem_bytes<T>(c.H, c.ny, c.cs);
+  return launch(k_plane_fwd<T, Q>, dim3(c.cs, c.ncomp * c.nz), smem, c.cs, st, eps, spec, c);
+}
+template <class T>
+cudaError_t launch_plane_inv(const C2<T>* spec, T* sig, const PassCfg& c, cudaStream_t st) {
+  const size_t smem = plane_smem_bytes<T>(c.H, c.ny, c.cs);
+  return launch(k_plane_inv<T>, dim3(c.cs, c.ncomp * c.nz), smem, c.cs, st, spec, sig, c);
+}
+template <class T>
+cudaError_t launch_pencil(C2<T>* spec, const PassCfg& c, cudaStream_t st) {
+  const size_t smem = pencil_smem_bytes<T>(c.nz, c.tw_w);
+  const size_t P = (size_t)(c.H + 1) * c.ny;
+  return launch(k_pencil<T>, dim3((unsigned)(P / c.tw_w)), smem, 1, st, spec, c);
+}
+
+template cudaError_t launch_plane_fwd<float, int32_t>(const int32_t*, C2<float>*, const PassCfg&, cudaStream_t);
+template cudaError_t launch_plane_fwd<double, int64_t>(const int64_t*, C2<double>*, const PassCfg&, cudaStream_t);
+template cudaError_t launch_plane_inv<float>(const C2<float>*, float*, const PassCfg&, cudaStream_t);
+template cudaError_t launch_plane_inv<double>(const C2<double>*, double*, const PassCfg&, cudaStream_t);
+template cudaError_t launch_pencil<float>(C2<float>*, const PassCfg&, cudaStream_t);
+template cudaError_t launch_pencil<double>(C2<double>*, const PassCfg&, cudaStream_t);
+
+}  // namespace okmc

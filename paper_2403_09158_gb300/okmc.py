@@ -1,0 +1,255 @@
+"""ctypes binding of the C ABI in include/okmc.h (argument marshalling only).
+
+Every function here forwards to the CUDA library ``_lib/libokmc.so``; nothing
+of the method is computed in Python.  Loading fails loudly when the library is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from .workload import DEFECT_DTYPE
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, '_lib', 'libokmc.so')
+
+OKMC_OK, OKMC_EINVAL, OKMC_ENOMEM, OKMC_ECUDA, OKMC_ETIMEOUT, OKMC_ESTATE, OKMC_ERANGE = range(7)
+LOOP_111, LOOP_100, SIA_CLUSTER = 0, 1, 2
+IMMOBILE, ONE_D, THREE_D = 0, 1, 2
+MEAN_STRESS_ZERO, MEAN_STRAIN_ZERO = 0, 1
+FP32_FIELDS, FP64_FIELDS = 0, 1
+RESIDENCE, FIXED_DT = 0, 1
+
+EXPORTED = [
+    'okmc_grid_create', 'okmc_grid_destroy', 'okmc_last_error', 'okmc_set_stream', 'okmc_set_defects',
+    'okmc_get_defects', 'okmc_set_positions', 'okmc_get_positions', 'okmc_solve_stress', 'okmc_eigenstrain',
+    'okmc_interaction_energies', 'okmc_candidate_energies', 'okmc_self_terms', 'okmc_get_stencil', 'okmc_step',
+    'okmc_get_stats', 'okmc_device_bytes', 'okmc_set_profiling', 'okmc_kernel_times', 'okmc_reset_kernel_times',
+    'okmc_launch_shape',
+]
+
+
+class GridDesc(C.Structure):
+    _fields_ = [('n', C.c_int32 * 3), ('k0_mode', C.c_int32), ('precision', C.c_int32), ('reserved', C.c_int32),
+                ('voxel_nm', C.c_double), ('C11', C.c_double), ('C12', C.c_double), ('C44', C.c_double),
+                ('nu0', C.c_double), ('seed', C.c_uint64), ('stream', C.c_void_p), ('hbm_budget', C.c_size_t)]
+
+
+class StepParams(C.Structure):
+    _fields_ = [('T_K', C.c_double), ('mode', C.c_int32), ('reserved', C.c_int32), ('t_end', C.c_double)]
+
+
+class StepStats(C.Structure):
+    _fields_ = [('events', C.c_int64), ('steps', C.c_int64), ('solves', C.c_int64),
+                ('negative_barriers', C.c_int64), ('clock', C.c_double), ('dt_last', C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class OkmcError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__('okmc error %d: %s' % (code, msg))
+        self.code = code
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise OkmcError(-1, 'CUDA library not built: %s (run __graft_entry__.build())' % path)
+    lib = C.CDLL(path)
+    vp, i32, i64, dp = C.c_void_p, C.c_int32, C.c_int64, C.c_void_p
+    sig = {
+        'okmc_grid_create': (C.c_int, [C.POINTER(GridDesc), C.POINTER(vp)]),
+        'okmc_grid_destroy': (C.c_int, [vp]),
+        'okmc_last_error': (C.c_char_p, [vp]),
+        'okmc_set_stream': (C.c_int, [vp, vp]),
+        'okmc_set_defects': (C.c_int, [vp, dp, i32]),
+        'okmc_get_defects': (C.c_int, [vp, dp, i32]),
+        'okmc_set_positions': (C.c_int, [vp, dp, i32, C.c_int]),
+        'okmc_get_positions': (C.c_int, [vp, dp, i32, C.c_int]),
+        'okmc_solve_stress': (C.c_int, [vp, dp, C.c_int]),
+        'okmc_eigenstrain': (C.c_int, [vp, dp, C.c_int]),
+        'okmc_interaction_energies': (C.c_int, [vp, dp, C.c_int]),
+        'okmc_candidate_energies': (C.c_int, [vp, dp, dp, C.c_int]),
+        'okmc_self_terms': (C.c_int, [vp, dp, C.c_int]),
+        'okmc_get_stencil': (C.c_int, [vp, i32, i32, dp, dp, i32, C.POINTER(i32), C.POINTER(C.c_double)]),
+        'okmc_step': (C.c_int, [vp, C.POINTER(StepParams), i64, C.POINTER(StepStats)]),
+        'okmc_get_stats': (C.c_int, [vp, C.POINTER(StepStats)]),
+        'okmc_device_bytes': (C.c_size_t, [vp]),
+        'okmc_set_profiling': (C.c_int, [vp, C.c_int]),
+        'okmc_kernel_times': (C.c_int, [vp, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(i64), C.c_int]),
+        'okmc_reset_kernel_times': (C.c_int, [vp]),
+        'okmc_launch_shape': (C.c_int, [vp, C.POINTER(i32)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """(address, on_device) of a numpy array, a torch tensor or a raw int address."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        assert a.flags['C_CONTIGUOUS']
+        return a.ctypes.data, 0
+    if hasattr(a, 'data_ptr'):
+        assert a.is_contiguous()
+        return a.data_ptr(), int(a.is_cuda)
+    raise TypeError('expected a numpy array or a torch tensor')
+
+
+class Grid:
+    """One okmc_grid handle.  Methods mirror the C calls one to one."""
+
+    def __init__(self, n, voxel_nm, C11, C12, C44, k0_mode=MEAN_STRESS_ZERO, precision=FP32_FIELDS, nu0=0.0,
+                 seed=0, stream=None, hbm_budget=0):
+        self.lib = load()
+        d = GridDesc()
+        n = tuple(int(v) for v in (n if np.ndim(n) else (n, n, n)))
+        d.n[:] = n
+        d.k0_mode, d.precision, d.reserved = k0_mode, precision, 0
+        d.voxel_nm, d.C11, d.C12, d.C44, d.nu0 = voxel_nm, C11, C12, C44, nu0
+        d.seed = seed
+        d.stream = stream
+        d.hbm_budget = hbm_budget
+        h = C.c_void_p()
+        rc = self.lib.okmc_grid_create(C.byref(d), C.byref(h))
+        if rc != OKMC_OK:
+            raise OkmcError(rc, 'okmc_grid_create failed')
+        self.h = h
+        self.n = n
+        self.precision = precision
+        self.nd = 0
+        self.fdtype = np.float64 if precision == FP64_FIELDS else np.float32
+
+    def _chk(self, rc):
+        if rc != OKMC_OK:
+            raise OkmcError(rc, self.lib.okmc_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, 'h', None):
+            self.lib.okmc_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_ptr):
+        self._chk(self.lib.okmc_set_stream(self.h, stream_ptr))
+
+    def set_defects(self, defects):
+        d = np.ascontiguousarray(defects, dtype=DEFECT_DTYPE)
+        self._chk(self.lib.okmc_set_defects(self.h, d.ctypes.data if len(d) else None, len(d)))
+        self.nd = len(d)
+
+    def get_defects(self):
+        out = np.zeros(self.nd, dtype=DEFECT_DTYPE)
+        self._chk(self.lib.okmc_get_defects(self.h, out.ctypes.data if self.nd else None, self.nd))
+        return out
+
+    def set_positions(self, pos):
+        p, dev = _ptr(pos)
+        self._chk(self.lib.okmc_set_positions(self.h, p, self.nd, dev))
+
+    def get_positions(self, out=None):
+        if out is None:
+            out = np.zeros((self.nd, 3), dtype=np.int32)
+        p, dev = _ptr(out)
+        self._chk(self.lib.okmc_get_positions(self.h, p, self.nd, dev))
+        return out
+
+    def solve_stress(self, out=None, copy=True):
+        if out is None and copy:
+            out = np.zeros((6, self.n[2], self.n[1], self.n[0]), dtype=self.fdtype)
+        p, dev = _ptr(out)
+        self._chk(self.lib.okmc_solve_stress(self.h, p, dev))
+        return out
+
+    def eigenstrain(self, out=None):
+        if out is None:
+            out = np.zeros((6, self.n[2], self.n[1], self.n[0]), dtype=self.fdtype)
+        p, dev = _ptr(out)
+        self._chk(self.lib.okmc_eigenstrain(self.h, p, dev))
+        return out
+
+    def interaction_energies(self, out=None):
+        if out is None:
+            out = np.zeros(self.nd)
+        p, dev = _ptr(out)
+        self._chk(self.lib.okmc_interaction_energies(self.h, p, dev))
+        return out
+
+    def candidate_energies(self, out=None, valid=None):
+        if out is None:
+            out = np.zeros((self.nd, 8))
+        if valid is None and isinstance(out, np.ndarray):
+            valid = np.zeros((self.nd, 8), dtype=np.uint8)
+        p, dev = _ptr(out)
+        v, _ = _ptr(valid)
+        self._chk(self.lib.okmc_candidate_energies(self.h, p, v, dev))
+        return out, valid
+
+    def self_terms(self):
+        out = np.zeros((self.nd, 2, 9))
+        self._chk(self.lib.okmc_self_terms(self.h, out.ctypes.data, 0))
+        return out
+
+    def stencil(self, i, c):
+        k = C.c_int32()
+        a = C.c_double()
+        self._chk(self.lib.okmc_get_stencil(self.h, i, c, None, None, 0, C.byref(k), C.byref(a)))
+        offs = np.zeros((k.value, 3), dtype=np.int32)
+        cnt = np.zeros(k.value, dtype=np.int32)
+        self._chk(self.lib.okmc_get_stencil(self.h, i, c, offs.ctypes.data, cnt.ctypes.data, k.value, C.byref(k),
+                                            C.byref(a)))
+        return offs, cnt, a.value
+
+    def step(self, T_K, n_steps=1, mode=RESIDENCE, t_end=0.0):
+        p = StepParams(T_K, mode, 0, t_end)
+        s = StepStats()
+        self._chk(self.lib.okmc_step(self.h, C.byref(p), n_steps, C.byref(s)))
+        return s.as_dict()
+
+    def stats(self):
+        s = StepStats()
+        self._chk(self.lib.okmc_get_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def device_bytes(self):
+        return int(self.lib.okmc_device_bytes(self.h))
+
+    def set_profiling(self, on=True):
+        self._chk(self.lib.okmc_set_profiling(self.h, int(on)))
+
+    def kernel_times(self):
+        cap = 64
+        names = (C.c_char_p * cap)()
+        ms = (C.c_double * cap)()
+        cnt = (C.c_int64 * cap)()
+        k = self.lib.okmc_kernel_times(self.h, names, ms, cnt, cap)
+        return {names[i].decode(): (ms[i], cnt[i]) for i in range(min(k, cap))}
+
+    def reset_kernel_times(self):
+        self._chk(self.lib.okmc_reset_kernel_times(self.h))
+
+    def launch_shape(self):
+        out = (C.c_int32 * 3)()
+        self._chk(self.lib.okmc_launch_shape(self.h, out))
+        return list(out)

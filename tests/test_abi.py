@@ -1,0 +1,95 @@
+"""The C ABI library builds, loads and exports every symbol include/okmc.h declares;
+ctypes structures match the C structure layouts.  No GPU compute is called."""
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+from paper_2403_09158_gb300 import okmc as ok
+from paper_2403_09158_gb300.workload import DEFECT_DTYPE
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, 'include', 'okmc.h')
+
+
+def declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r'/\*.*?\*/', '', txt, flags=re.S)
+    return sorted(set(re.findall(r'\b(okmc_[a-z_]+)\s*\(', txt)))
+
+
+@pytest.fixture(scope='module')
+def lib():
+    __graft_entry__.build()
+    return ok.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared()
+    assert len(names) >= 20
+    out = subprocess.run(['nm', '-D', '--defined-only', ok.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r' T (okmc_\w+)', out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    assert sorted(ok.EXPORTED) == names
+    for n in names:
+        assert hasattr(lib, n)
+
+
+def test_struct_layouts_match_c():
+    src = r'''
+#include <stdio.h>
+#include <stddef.h>
+#include "okmc.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(okmc_grid_desc), sizeof(okmc_defect), sizeof(okmc_step_params),
+         sizeof(okmc_step_stats), offsetof(okmc_grid_desc, voxel_nm), offsetof(okmc_grid_desc, stream),
+         offsetof(okmc_defect, radius_nm));
+  return 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, 'l.c')
+        open(c, 'w').write(src)
+        exe = os.path.join(d, 'l')
+        subprocess.run(['gcc', '-I', os.path.join(ROOT, 'include'), c, '-o', exe], check=True)
+        vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True).stdout.split()]
+    import ctypes as C
+    assert vals[0] == C.sizeof(ok.GridDesc)
+    assert vals[1] == DEFECT_DTYPE.itemsize == 48
+    assert vals[2] == C.sizeof(ok.StepParams)
+    assert vals[3] == C.sizeof(ok.StepStats)
+    assert vals[4] == ok.GridDesc.voxel_nm.offset
+    assert vals[5] == ok.GridDesc.stream.offset
+    assert vals[6] == DEFECT_DTYPE.fields['radius_nm'][1]
+
+
+def test_null_handle_errors_without_gpu(lib):
+    # argument checks run on the host before any CUDA call
+    assert lib.okmc_grid_destroy(None) == ok.OKMC_OK
+    assert lib.okmc_last_error(None) == b'null handle'
+    assert lib.okmc_solve_stress(None, None, 0) == ok.OKMC_EINVAL
+    d = ok.GridDesc()
+    d.n[:] = (20, 32, 32)       # 20 is not a multiple of 16
+    d.voxel_nm, d.C11, d.C12, d.C44 = 0.2855, 243.0, 145.0, 116.0
+    import ctypes as C
+    h = C.c_void_p()
+    assert lib.okmc_grid_create(C.byref(d), C.byref(h)) == ok.OKMC_EINVAL
+    d.n[:] = (32, 32, 32)
+    d.C44 = -1.0
+    assert lib.okmc_grid_create(C.byref(d), C.byref(h)) == ok.OKMC_EINVAL
+    d.C44, d.k0_mode = 116.0, 7
+    assert lib.okmc_grid_create(C.byref(d), C.byref(h)) == ok.OKMC_EINVAL
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, 'paper_2403_09158_gb300')
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith(('.py', '.cu', '.cuh', '.h')):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert 'import oracle' not in txt and 'from oracle' not in txt, f

@@ -1,0 +1,248 @@
+"""GPU (CUDA library through the C ABI) versus the CPU FP64 oracle.
+
+Bars: stencils bit exact; stress relative L2 <= 1e-5 (FP32 fields) or 1e-10 (FP64
+fields); energies within 1e-4 eV (FP32) or 1e-8 eV (FP64); kinetic decisions equal
+given the same energies and Philox counters.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle as O
+from paper_2403_09158_gb300 import okmc as ok
+from paper_2403_09158_gb300.workload import (DEFECT_DTYPE, FE_CUBIC, FE_ISO, config_medium, config_small,
+                                             make_defects, scaled_population)
+
+pytestmark = pytest.mark.gpu
+
+STRESS_TOL = {ok.FP32_FIELDS: 1e-5, ok.FP64_FIELDS: 1e-10}
+ENERGY_TOL = {ok.FP32_FIELDS: 1e-4, ok.FP64_FIELDS: 1e-8}
+
+
+@pytest.fixture(scope='module', autouse=True)
+def _lib():
+    __graft_entry__.build()
+    ok.load()
+
+
+def zyx(a):
+    """oracle (6, nx, ny, nz) -> library layout (6, nz, ny, nx)"""
+    return np.transpose(a, (0, 3, 2, 1))
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+def make_grid(w, precision=ok.FP32_FIELDS, k0=ok.MEAN_STRESS_ZERO, C=None, seed=11):
+    C = C or w.C
+    g = ok.Grid(w.n, w.voxel_nm, *C, k0_mode=k0, precision=precision, seed=seed)
+    g.set_defects(w.defects)
+    return g
+
+
+# ------------------------------------------------------------------ stencils
+def test_stencils_bit_exact():
+    w = config_small()
+    extra = make_defects([0, 0, 1, 1, 2, 2], np.array([[2, 2, 2], [5, 7, 9], [4, 6, 8], [3, 3, 3], [0, 0, 0], [1, 1, 1]]),
+                         [1, 3, 0, 2, 0, 0], [1.37, 0.5, 0.9, 2.2, 0, 0], [0, 0, 0, 0, 1, 37],
+                         [0.1, 0.1, 1, 1, 0.3, 0.3], [1, 1, 0, 0, 2, 1])
+    defs = np.concatenate([w.defects, extra])
+    g = ok.Grid((48, 48, 48), w.voxel_nm, *w.C)
+    g.set_defects(defs)
+    for i, d in enumerate(defs):
+        for c in (0, 1):
+            offs, cnt, alpha = g.stencil(i, c)
+            o2, c2, a2 = O.stencil(d, c, w.voxel_nm)
+            assert np.array_equal(offs, o2), (i, c)
+            assert np.array_equal(cnt, c2), (i, c)
+            assert abs(alpha - a2) <= 1e-15 * a2
+    g.close()
+
+
+# ------------------------------------------------------------------ eigenstrain and stress
+@pytest.mark.parametrize('precision', [ok.FP32_FIELDS, ok.FP64_FIELDS])
+def test_eigenstrain_field(precision):
+    w = config_small()
+    g = make_grid(w, precision)
+    eps = g.eigenstrain()
+    ref = zyx(O.eigenstrain_field(w.defects, w.n, w.voxel_nm))
+    tol = 2e-7 if precision == ok.FP32_FIELDS else 1e-11
+    assert np.abs(eps - ref).max() < tol
+    g.close()
+
+
+CASES = [
+    ((32, 32, 32), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 12),
+    ((32, 32, 32), ok.FP64_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 12),
+    ((32, 32, 32), ok.FP32_FIELDS, ok.MEAN_STRAIN_ZERO, 'iso', 12),
+    ((16, 16, 16), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 3),
+    ((48, 32, 80), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 20),
+    ((80, 48, 32), ok.FP64_FIELDS, ok.MEAN_STRAIN_ZERO, 'cubic', 20),
+    ((96, 64, 160), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 30),
+    ((64, 64, 64), ok.FP64_FIELDS, ok.MEAN_STRESS_ZERO, 'iso', 25),
+]
+
+
+@pytest.mark.parametrize('n,precision,k0,mat,nd', CASES)
+def test_stress_parity(n, precision, k0, mat, nd):
+    w = scaled_population(n, nd, seed=sum(n) + nd, r111=(0.4, 1.0), r100=(0.4, 1.0))
+    C = FE_CUBIC if mat == 'cubic' else O.isotropic_cubic_constants(*FE_ISO)
+    g = make_grid(w, precision, k0, C)
+    sig = g.solve_stress()
+    ref = zyx(O.solve_stress(O.eigenstrain_field(w.defects, w.n, w.voxel_nm), O.stiffness_cubic(*C),
+                             w.voxel_nm, k0))
+    assert rel_l2(sig, ref) <= STRESS_TOL[precision]
+    g.close()
+
+
+# ------------------------------------------------------------------ energies
+@pytest.mark.parametrize('precision', [ok.FP32_FIELDS, ok.FP64_FIELDS])
+def test_energies_bruteforce_small(precision):
+    w = config_small()
+    g = make_grid(w, precision)
+    E = g.interaction_energies()
+    Ec, valid = g.candidate_energies()
+    Eo, Eco = O.energies_bruteforce(w.defects, w.n, w.voxel_nm, O.stiffness_cubic(*w.C))
+    tol = ENERGY_TOL[precision]
+    assert np.abs(E - Eo).max() <= tol, np.abs(E - Eo).max()
+    assert np.abs(Ec - Eco).max() <= tol, np.abs(Ec - Eco).max()
+    for i, d in enumerate(w.defects):
+        assert np.array_equal(valid[i].astype(bool), O.allowed_jumps(d))
+    g.close()
+
+
+def test_self_terms_match_oracle():
+    w = config_small()
+    g = make_grid(w, ok.FP64_FIELDS)
+    W = g.self_terms()
+    C = O.stiffness_cubic(*w.C)
+    for i in (0, 2, 5):
+        Wo = O.self_term_table_fourier(w.defects[i], w.n, w.voxel_nm, C)
+        assert np.abs(W[i] - Wo).max() <= 1e-9 * max(1.0, np.abs(Wo).max())
+    g.close()
+    # FP32 spectra: the table inherits the transform's ~1e-7 relative error; what the
+    # energies need is that error well under the 1e-4 eV bar
+    g = make_grid(w, ok.FP32_FIELDS)
+    W = g.self_terms()
+    for i in (0, 2, 5):
+        Wo = O.self_term_table_fourier(w.defects[i], w.n, w.voxel_nm, C)
+        assert np.abs(W[i] - Wo).max() <= 5e-7 * np.abs(Wo).max() + 1e-6
+        assert np.abs(W[i] - Wo).max() <= 5e-5
+    g.close()
+
+
+# ------------------------------------------------------------------ kinetics
+def test_incremental_field_equals_fresh_voxelisation():
+    w = config_small()
+    g = make_grid(w)
+    g.step(w.T_K, 25)
+    g.step(w.T_K, 5, mode=ok.FIXED_DT)
+    cur = g.get_defects()
+    eps_inc = g.eigenstrain()
+    g2 = make_grid(w)
+    g2.set_defects(cur)
+    eps_new = g2.eigenstrain()
+    assert np.array_equal(eps_inc, eps_new)
+    g.close()
+    g2.close()
+
+
+def test_residence_steps_follow_oracle_decisions():
+    w = config_small()
+    seed = 4242
+    g = make_grid(w, seed=seed)
+    defs = w.defects.copy()
+    clock = 0.0
+    for step in range(20):
+        E = g.interaction_energies()
+        Ec, _ = g.candidate_energies()
+        before = g.get_defects()
+        assert np.array_equal(before['pos'], defs['pos'])
+        i, j, dt, R = O.residence_step(defs, E, Ec, w.T_K, seed, step, w.n)
+        st = g.step(w.T_K, 1)
+        after = g.get_defects()
+        assert np.array_equal(after['pos'], defs['pos']), step
+        clock += dt
+        assert abs(st['clock'] - clock) <= 1e-12 * clock
+    assert g.stats()['events'] == 20
+    g.close()
+
+
+def test_fixed_dt_steps_follow_oracle_decisions():
+    w = config_small()
+    seed = 99
+    g = make_grid(w, seed=seed)
+    defs = w.defects.copy()
+    dt = O.fixed_dt(defs, w.T_K)
+    nev = 0
+    for step in range(10):
+        E = g.interaction_energies()
+        Ec, _ = g.candidate_energies()
+        mv = O.fixed_dt_step(defs, E, Ec, w.T_K, seed, step, w.n, dt)
+        nev += len(mv)
+        st = g.step(w.T_K, 1, mode=ok.FIXED_DT)
+        assert np.array_equal(g.get_defects()['pos'], defs['pos']), step
+        assert st['events'] == nev
+        assert abs(st['dt_last'] - dt) <= 1e-12 * dt
+    g.close()
+
+
+def test_positions_roundtrip_and_update():
+    w = config_small()
+    g = make_grid(w)
+    p = g.get_positions()
+    assert np.array_equal(p, w.defects['pos'])
+    p2 = p.copy()
+    p2[3] = (p2[3] + 2) % 64
+    g.set_positions(p2)
+    assert np.array_equal(g.get_positions(), p2)
+    moved = w.defects.copy()
+    moved['pos'] = p2
+    ref = zyx(O.eigenstrain_field(moved, w.n, w.voxel_nm))
+    assert np.abs(g.eigenstrain() - ref).max() < 2e-7
+    g.close()
+
+
+def test_invalid_inputs_rejected():
+    w = config_small()
+    g = make_grid(w)
+    bad = w.defects.copy()
+    bad['pos'][0] = (1, 2, 3)               # mixed parity: not a bcc site
+    with pytest.raises(ok.OkmcError) as e:
+        g.set_defects(bad)
+    assert e.value.code == ok.OKMC_EINVAL
+    bad = w.defects.copy()
+    bad['radius_nm'][0] = 10.0              # loop wider than half the box
+    with pytest.raises(ok.OkmcError):
+        g.set_defects(bad)
+    bad = make_defects([1], np.array([[0, 0, 0]]), [0], [1.0], [0], [1.0], [ok.ONE_D])
+    with pytest.raises(ok.OkmcError):       # <100> loops are immobile
+        g.set_defects(bad)
+    g.close()
+    with pytest.raises(ok.OkmcError) as e:
+        ok.Grid((64, 64, 64), 0.2855, *FE_CUBIC, hbm_budget=1 << 20)
+    assert e.value.code == ok.OKMC_ENOMEM
+
+
+# ------------------------------------------------------------------ full-size configurations
+def test_medium_128_stress_and_sampled_energies():
+    w = config_medium()
+    g = make_grid(w)
+    sig = g.solve_stress()
+    C = O.stiffness_cubic(*w.C)
+    ref = O.solve_stress(O.eigenstrain_field(w.defects, w.n, w.voxel_nm), C, w.voxel_nm)
+    assert rel_l2(sig, zyx(ref)) <= 1e-5
+    E = g.interaction_energies()
+    Ec, _ = g.candidate_energies()
+    rng = np.random.default_rng(3)
+    for i in rng.choice(len(w.defects), 4, replace=False):
+        d = w.defects[i]
+        W = O.self_term_table_fourier(d, w.n, w.voxel_nm, C)
+        c = O.pos_class(d['pos'])
+        e0 = O.energy_of_stencil(d, d['pos'], ref, w.voxel_nm) - W[c, 0]
+        assert abs(E[i] - e0) <= 1e-4, (i, E[i], e0)
+        for j, Y in enumerate(O.candidate_positions(d['pos'])):
+            ej = O.energy_of_stencil(d, Y, ref, w.voxel_nm) - W[c, 1 + j]
+            assert abs(Ec[i, j] - ej) <= 1e-4, (i, j, Ec[i, j], ej)
+    g.close()
