@@ -205,6 +205,28 @@ int okmc_reset_kernel_times(okmc_grid* g);
  * forward plane pass, CTAs of the pencil pass, cluster size of the inverse pass. */
 int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
 
+/* Allocation-free stress solve (the paper has no counterpart; this is a service for
+ * callers that cannot allocate device memory -- code that runs after its process
+ * has handed all device memory to a pool it does not own, code inside a region
+ * where allocation would synchronise the device or break a caller-owned memory
+ * plan, or embedded callers whose allocator forbids cudaMalloc after start-up).
+ * It does what okmc_solve_stress does for a grid, from an eigenstrain field the
+ * caller provides: eps and sigma are device pointers to 6*nx*ny*nz floats each,
+ * layout [c][z][y][x], both owned by the caller; n = {nx, ny, nz} as for
+ * okmc_grid_create; C11, C12, C44 in GPa; k0_mode as in okmc_grid_desc; stream is
+ * a cudaStream_t (NULL = legacy stream).  It allocates nothing: the half spectrum
+ * and twiddle tables live in one static device array of 6.5 MB (room for
+ * 6*(nx/2+1)*ny*nz <= 6*33*64*64 complex values, e.g. 64^3 voxels) that every GPU
+ * loading this library keeps until the process exits.  Larger grids return
+ * OKMC_EINVAL.  The first call on a device looks up the array's device address
+ * (with that device current), so make that first call outside any stream capture.
+ * All calls share the array and leave their data in it: two calls whose work
+ * overlaps on the GPU (different streams, different host threads) race and give
+ * wrong results; serialise them.  Returns OKMC_OK, OKMC_EINVAL or OKMC_ECUDA
+ * (asynchronous: launch errors only; sync the stream to see execution errors). */
+int okmc_solve_stress_static(const float* eps, float* sigma, const int32_t n[3], double C11, double C12, double C44,
+                             int32_t k0_mode, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

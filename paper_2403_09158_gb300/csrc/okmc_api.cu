@@ -73,43 +73,6 @@ int factor_ok(int n) {
   return n == 1;
 }
 
-LinePlan make_plan(int L) {
-  LinePlan p = {};
-  p.L = L;
-  int m = L, a = 0, b = 0, c = 0;
-  while (m % 2 == 0) m /= 2, ++a;
-  while (m % 3 == 0) m /= 3, ++b;
-  while (m % 5 == 0) m /= 5, ++c;
-  std::vector<int> r;
-  const int q = a / 3, rem = a % 3;
-  if (rem == 0) {
-    for (int i = 0; i < q; ++i) r.push_back(8);
-  } else if (rem == 1) {
-    if (q >= 1) {
-      for (int i = 0; i < q - 1; ++i) r.push_back(8);
-      r.push_back(4);
-      r.push_back(4);
-    } else {
-      r.push_back(2);
-    }
-  } else {
-    for (int i = 0; i < q; ++i) r.push_back(8);
-    r.push_back(4);
-  }
-  for (int i = 0; i < b; ++i) r.push_back(3);
-  for (int i = 0; i < c; ++i) r.push_back(5);
-  if (r.size() == 1) {  // the engine wants two stages at least
-    const int R = r[0];
-    r.clear();
-    if (R == 8) { r.push_back(2); r.push_back(4); }
-    else if (R == 4) { r.push_back(2); r.push_back(2); }
-    else r.push_back(R);
-  }
-  p.nst = (int)r.size();
-  for (int i = 0; i < p.nst; ++i) p.rad[i] = r[i];
-  return p;
-}
-
 template <class T>
 void twiddles(std::vector<C2<T>>& out, int L, int count, double sign) {
   for (int k = 0; k < count; ++k) {

@@ -118,6 +118,46 @@ struct LinePlan {
   int rad[8];
 };
 
+// Radix sequence of a length-L line (L = 2^a 3^b 5^c, L >= 4): radix 8 first, then a
+// 4 or 4,4 for the leftover powers of two, then 3s and 5s; always two stages or more.
+inline LinePlan make_plan(int L) {
+  LinePlan p = {};
+  p.L = L;
+  int m = L, a = 0, b = 0, c = 0;
+  while (m % 2 == 0) m /= 2, ++a;
+  while (m % 3 == 0) m /= 3, ++b;
+  while (m % 5 == 0) m /= 5, ++c;
+  int r[16];
+  int nr = 0;
+  const int q = a / 3, rem = a % 3;
+  if (rem == 0) {
+    for (int i = 0; i < q; ++i) r[nr++] = 8;
+  } else if (rem == 1) {
+    if (q >= 1) {
+      for (int i = 0; i < q - 1; ++i) r[nr++] = 8;
+      r[nr++] = 4;
+      r[nr++] = 4;
+    } else {
+      r[nr++] = 2;
+    }
+  } else {
+    for (int i = 0; i < q; ++i) r[nr++] = 8;
+    r[nr++] = 4;
+  }
+  for (int i = 0; i < b; ++i) r[nr++] = 3;
+  for (int i = 0; i < c; ++i) r[nr++] = 5;
+  if (nr == 1) {  // the engine wants two stages at least
+    const int R = r[0];
+    nr = 0;
+    if (R == 8) { r[nr++] = 2; r[nr++] = 4; }
+    else if (R == 4) { r[nr++] = 2; r[nr++] = 2; }
+    else r[nr++] = R;
+  }
+  p.nst = nr;
+  for (int i = 0; i < p.nst; ++i) p.rad[i] = r[i];
+  return p;
+}
+
 template <class T>
 struct SLine {  // strided line in shared, distributed-shared or global memory
   C2<T>* p;

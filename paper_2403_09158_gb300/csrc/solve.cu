@@ -414,3 +414,106 @@ template cudaError_t launch_pencil<float>(C2<float>*, const PassCfg&, cudaStream
 template cudaError_t launch_pencil<double>(C2<double>*, const PassCfg&, cudaStream_t);
 
 }  // namespace okmc
+
+// ================================================================== allocation-free solve
+// okmc_solve_stress_static: the same three passes, with the half spectrum and the
+// twiddle tables in one file-scope device array instead of handle-owned memory.
+// Every GPU that loads this library keeps the array until the process exits.
+namespace okmc {
+constexpr size_t kStaticSpec = (size_t)6 * 33 * 64 * 64;        // complex values: 6 x (64/2+1) x 64 x 64
+constexpr size_t kStaticTw = 4 * 512 + 8;                       // twiddle tables of the largest line set
+static __device__ __align__(256) C2<float> g_static_scratch[kStaticSpec + kStaticTw];
+
+// RowSrcQ for a plain FP32 eigenstrain row (quantum 1).
+template <>
+struct RowSrcQ<float, float> {
+  const float* p;
+  float q;
+  __device__ __forceinline__ C2<float> ld(int i) const {
+    const float2 v = __ldg(reinterpret_cast<const float2*>(p) + i);
+    return {v.x * q, v.y * q};
+  }
+};
+
+// twH[k] = w_H^k, twY, twZ, untw[k] = exp(-2 pi i k / nx), k <= H, from FP64 sincospi.
+__global__ void k_static_twiddles(C2<float>* tw, int nx, int ny, int nz) {
+  const int H = nx / 2;
+  const int total = H + ny + nz + H + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+    int k = t, L;
+    if (k < H) L = H;
+    else if ((k -= H) < ny) L = ny;
+    else if ((k -= ny) < nz) L = nz;
+    else { k -= nz; L = nx; }
+    double s, c;
+    sincospi(2.0 * (double)k / (double)L, &s, &c);
+    tw[t] = C2<float>{(float)c, (float)-s};
+  }
+}
+
+namespace {
+int g_static_ready[64];
+C2<float>* g_static_ptr[64];
+
+bool edge_ok(int n) {
+  if (n < 16 || n > 512 || n % 16) return false;
+  while (n % 2 == 0) n /= 2;
+  while (n % 3 == 0) n /= 3;
+  while (n % 5 == 0) n /= 5;
+  return n == 1;
+}
+}  // namespace
+}  // namespace okmc
+
+extern "C" int okmc_solve_stress_static(const float* eps, float* sigma, const int32_t n[3], double C11, double C12,
+                                        double C44, int32_t k0_mode, void* stream) {
+  using namespace okmc;
+  if (!eps || !sigma || !n) return OKMC_EINVAL;
+  for (int a = 0; a < 3; ++a)
+    if (!edge_ok(n[a])) return OKMC_EINVAL;
+  const int H = n[0] / 2;
+  if ((size_t)6 * (H + 1) * n[1] * n[2] > kStaticSpec) return OKMC_EINVAL;  // beyond the static scratch
+  if (!(C11 - C12 > 0.0) || !(C11 + 2.0 * C12 > 0.0) || !(C44 > 0.0)) return OKMC_EINVAL;
+  if (k0_mode != OKMC_MEAN_STRESS_ZERO && k0_mode != OKMC_MEAN_STRAIN_ZERO) return OKMC_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return OKMC_ECUDA;
+  if (!g_static_ready[dev]) {
+    // host code cannot use the array's name as a device address: ask the runtime for
+    // it once per device, with that device current
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return OKMC_ECUDA;
+    g_static_ptr[dev] = static_cast<C2<float>*>(p);
+    g_static_ready[dev] = 1;
+  }
+  C2<float>* spec = g_static_ptr[dev];
+  C2<float>* tw = spec + kStaticSpec;
+  cudaStream_t st = (cudaStream_t)stream;
+  PassCfg c = {};
+  c.nx = n[0];
+  c.ny = n[1];
+  c.nz = n[2];
+  c.H = H;
+  c.ncomp = 6;
+  c.cs = pick_cluster<float>(H, n[1], 225 * 1024);
+  c.tw_w = pick_tile<float>(n[1], n[2], 225 * 1024);
+  c.k0_mode = k0_mode;
+  c.forward_only = 0;
+  c.q = 1.0;
+  c.C11 = C11;
+  c.C12 = C12;
+  c.C44 = C44;
+  c.pH = make_plan(H);
+  c.pY = make_plan(n[1]);
+  c.pZ = make_plan(n[2]);
+  c.twH = tw;
+  c.twY = tw + H;
+  c.twZ = tw + H + n[1];
+  c.untw = tw + H + n[1] + n[2];
+  if (!c.cs || !c.tw_w) return OKMC_EINVAL;
+  k_static_twiddles<<<8, 256, 0, st>>>(tw, n[0], n[1], n[2]);
+  if (cudaGetLastError() != cudaSuccess) return OKMC_ECUDA;
+  if (okmc::launch_plane_fwd<float, float>(eps, spec, c, st) != cudaSuccess) return OKMC_ECUDA;
+  if (launch_pencil<float>(spec, c, st) != cudaSuccess) return OKMC_ECUDA;
+  if (launch_plane_inv<float>(spec, sigma, c, st) != cudaSuccess) return OKMC_ECUDA;
+  return OKMC_OK;
+}

@@ -28,7 +28,7 @@ EXPORTED = [
     'okmc_get_defects', 'okmc_set_positions', 'okmc_get_positions', 'okmc_solve_stress', 'okmc_eigenstrain',
     'okmc_interaction_energies', 'okmc_candidate_energies', 'okmc_self_terms', 'okmc_get_stencil', 'okmc_step',
     'okmc_get_stats', 'okmc_device_bytes', 'okmc_set_profiling', 'okmc_kernel_times', 'okmc_reset_kernel_times',
-    'okmc_launch_shape',
+    'okmc_launch_shape', 'okmc_solve_stress_static',
 ]
 
 
@@ -90,6 +90,8 @@ def load(path=LIB_PATH):
         'okmc_kernel_times': (C.c_int, [vp, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(i64), C.c_int]),
         'okmc_reset_kernel_times': (C.c_int, [vp]),
         'okmc_launch_shape': (C.c_int, [vp, C.POINTER(i32)]),
+        'okmc_solve_stress_static': (C.c_int, [dp, dp, C.POINTER(i32), C.c_double, C.c_double, C.c_double, i32,
+                                              vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
