@@ -450,7 +450,7 @@ __global__ void __launch_bounds__(128) k_energies(const T* __restrict__ sig, int
                                                   const int* __restrict__ off, const uint8_t* __restrict__ cnt,
                                                   const double* __restrict__ alpha, const double* __restrict__ W,
                                                   double pref, int want_cand, double* __restrict__ E,
-                                                  double* __restrict__ Ec) {
+                                                  double* __restrict__ Ec, RateArgs ra) {
   __shared__ double sh[32];
   const int i = blockIdx.x;
   const size_t N = (size_t)n.x * n.y * n.z;
@@ -492,19 +492,33 @@ __global__ void __launch_bounds__(128) k_energies(const T* __restrict__ sig, int
       acc[j] += w * (double)dot;
     }
   }
+  double ec[8];
   for (int j = 0; j < 8; ++j) {
     const double t = block_sum_d(acc[j], sh);
-    if (threadIdx.x == 0) Ec[(size_t)i * 8 + j] = pref * alpha[2 * i + cp] * t - W[(size_t)i * 18 + c * 9 + 1 + j];
+    ec[j] = pref * alpha[2 * i + cp] * t - W[(size_t)i * 18 + c * 9 + 1 + j];
+    if (threadIdx.x == 0) Ec[(size_t)i * 8 + j] = ec[j];
   }
+  if (!ra.rates || threadIdx.x != 0) return;
+  // biased jump frequencies nu_j = (nu0/z) exp(-(E_m + (E_j - E_0)/2)/kT) of the
+  // allowed jumps (Eqs. biased_forward/backward_boltzmann, prefactor 1/z)
+  const double e0 = pref * alpha[2 * i + c] * acc0 - W[(size_t)i * 18 + c * 9];
+  double sum = 0.0;
+  int neg = 0;
+  for (int j = 0; j < 8; ++j) {
+    double nu = 0.0;
+    if (g.allowed >> j & 1) {
+      const double barrier = r.Em_eV + 0.5 * (ec[j] - e0);
+      neg += barrier < 0.0;
+      nu = (ra.nu0 / g.z) * exp(-barrier / ra.kT);
+    }
+    ra.rates[(size_t)i * 8 + j] = nu;
+    sum += nu;
+  }
+  ra.rsum[i] = sum;
+  if (neg) atomicAdd(reinterpret_cast<unsigned long long*>(ra.negb), (unsigned long long)neg);
 }
 
 // ---------------------------------------------------------------- events
-__device__ __forceinline__ double jump_rate(double nu0z, double Em, double dE, double kT, long long* negb) {
-  const double barrier = Em + 0.5 * dE;
-  if (barrier < 0.0 && negb) atomicAdd(reinterpret_cast<unsigned long long*>(negb), 1ull);
-  return nu0z * exp(-barrier / kT);
-}
-
 __device__ __forceinline__ void new_position(const int p[3], int j, int3 n, int q[3]) {
   const int L[3] = {2 * n.x, 2 * n.y, 2 * n.z};
   for (int a = 0; a < 3; ++a) {
@@ -516,29 +530,26 @@ __device__ __forceinline__ void new_position(const int p[3], int j, int3 n, int 
 }
 
 // Residence-time event: every allowed jump of every defect on one frequency line
-// (i-major, j-minor), selection of the first entry whose running sum reaches
-// u1 * R_tot (u1 in (0,1]), clock advance -ln(u2)/R_tot.  One block.
+// (i-major, j-minor, rates from the energies kernel), selection of the first entry
+// whose running sum reaches u1 * R_tot (u1 in (0,1], Eq. selection_jump), clock
+// advance -ln(u2)/R_tot.  One block: per-thread sums over a contiguous chunk of
+// defects, a block scan, then the chunk that holds the target is walked.
 constexpr int kEventThreads = 1024;
-__global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __restrict__ d, const DefGeo* __restrict__ G, int nd,
-                                                             const double* __restrict__ E, const double* __restrict__ Ec,
-                                                             double nu0, double kT, int3 n, uint32_t key0, uint32_t key1,
-                                                             Move* __restrict__ moves, DevState* __restrict__ st) {
+__global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __restrict__ d, int nd,
+                                                             const double* __restrict__ rates,
+                                                             const double* __restrict__ rsum, int3 n, uint32_t key0,
+                                                             uint32_t key1, Move* __restrict__ moves,
+                                                             DevState* __restrict__ st) {
   __shared__ double part[kEventThreads];
   __shared__ int sel_t;
   const int t = threadIdx.x;
-  const long long items = (long long)nd * 8;
-  const long long per = (items + blockDim.x - 1) / blockDim.x;
-  const long long k0 = t * per, k1 = min(items, k0 + per);
+  const int per = (nd + blockDim.x - 1) / blockDim.x;
+  const int i0 = min(nd, t * per), i1 = min(nd, i0 + per);
   double s = 0.0;
-  for (long long k = k0; k < k1; ++k) {
-    const int i = (int)(k >> 3), j = (int)(k & 7);
-    const DefGeo& g = G[i];
-    if (g.allowed >> j & 1) s += jump_rate(nu0 / g.z, d[i].Em_eV, Ec[k] - E[i], kT, &st->negative_barriers);
-  }
+  for (int i = i0; i < i1; ++i) s += rsum[i];
   part[t] = s;
   __syncthreads();
-  // inclusive scan (Hillis-Steele), deterministic
-  for (int o = 1; o < blockDim.x; o <<= 1) {
+  for (int o = 1; o < blockDim.x; o <<= 1) {  // inclusive scan, fixed order
     const double v = (t >= o) ? part[t - o] : 0.0;
     __syncthreads();
     part[t] += v;
@@ -557,43 +568,44 @@ __global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __rest
   if (s > 0.0 && part[t] >= target) atomicMin(&sel_t, t);
   __syncthreads();
   if (t == 0 && sel_t == 0x7fffffff) {
-    for (int q = blockDim.x - 1; q >= 0; --q) {
-      const double sq = part[q] - (q > 0 ? part[q - 1] : 0.0);
-      if (sq > 0.0) {
+    for (int q = blockDim.x - 1; q >= 0; --q)
+      if (part[q] - (q > 0 ? part[q - 1] : 0.0) > 0.0) {
         sel_t = q;
         break;
       }
-    }
   }
   __syncthreads();
   if (t != sel_t) return;
   double run = excl;
-  long long pick = -1, last = -1;
-  for (long long k = k0; k < k1; ++k) {
-    const int i = (int)(k >> 3), j = (int)(k & 7);
-    const DefGeo& g = G[i];
-    if (!(g.allowed >> j & 1)) continue;
-    const double r = jump_rate(nu0 / g.z, d[i].Em_eV, Ec[k] - E[i], kT, nullptr);
-    if (r <= 0.0) continue;
-    last = k;
-    run += r;
-    if (run >= target) {
-      pick = k;
-      break;
+  int pi = -1, pj = -1, li = -1, lj = -1;
+  for (int i = i0; i < i1 && pi < 0; ++i) {
+    for (int j = 0; j < 8; ++j) {
+      const double r = rates[(size_t)i * 8 + j];
+      if (r <= 0.0) continue;
+      li = i;
+      lj = j;
+      run += r;
+      if (run >= target) {
+        pi = i;
+        pj = j;
+        break;
+      }
     }
   }
-  if (pick < 0) pick = last;
-  if (pick < 0 || !(R > 0.0)) {
+  if (pi < 0) {
+    pi = li;
+    pj = lj;
+  }
+  if (pi < 0 || !(R > 0.0)) {
     st->err = 5;
     st->nmoves = 0;
     return;
   }
-  const int i = (int)(pick >> 3), j = (int)(pick & 7);
   Move m;
-  m.i = i;
-  for (int a = 0; a < 3; ++a) m.old_pos[a] = d[i].pos[a];
-  new_position(m.old_pos, j, n, m.new_pos);
-  for (int a = 0; a < 3; ++a) d[i].pos[a] = m.new_pos[a];
+  m.i = pi;
+  for (int a = 0; a < 3; ++a) m.old_pos[a] = d[pi].pos[a];
+  new_position(m.old_pos, pj, n, m.new_pos);
+  for (int a = 0; a < 3; ++a) d[pi].pos[a] = m.new_pos[a];
   moves[0] = m;
   st->nmoves = 1;
   st->dt_last = -log(u2) / R;
@@ -606,8 +618,8 @@ __global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __rest
 // defect i fires when its Poisson count is > 0 (u_p > exp(-nu_i delta t)) and then
 // selects a jump on its own biased frequency line with u_s.  One block.
 __global__ void __launch_bounds__(kEventThreads) k_fixed_dt(okmc_defect* __restrict__ d, const DefGeo* __restrict__ G, int nd,
-                                                            const double* __restrict__ E, const double* __restrict__ Ec,
-                                                            double nu0, double kT, int3 n, uint32_t key0, uint32_t key1,
+                                                            const double* __restrict__ rates, double nu0, double kT,
+                                                            int3 n, uint32_t key0, uint32_t key1,
                                                             Move* __restrict__ moves, DevState* __restrict__ st) {
   __shared__ double red[32];
   __shared__ int cnt_s;
@@ -634,7 +646,7 @@ __global__ void __launch_bounds__(kEventThreads) k_fixed_dt(okmc_defect* __restr
     if (up <= exp(-mu)) continue;
     double r[8], tot = 0.0;
     for (int j = 0; j < 8; ++j) {
-      r[j] = (g.allowed >> j & 1) ? jump_rate(nu0 / g.z, d[i].Em_eV, Ec[(size_t)i * 8 + j] - E[i], kT, &st->negative_barriers) : 0.0;
+      r[j] = rates[(size_t)i * 8 + j];
       tot += r[j];
     }
     const double target = us * tot;
@@ -733,19 +745,19 @@ cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
-                            int want_cand, double* E, double* Ec, cudaStream_t st) {
+                            int want_cand, double* E, double* Ec, RateArgs ra, cudaStream_t st) {
   if (nd == 0) return cudaSuccess;
-  k_energies<T><<<nd, 128, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, E, Ec);
+  k_energies<T><<<nd, 128, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, E, Ec, ra);
   return cudaGetLastError();
 }
-cudaError_t launch_residence(okmc_defect* d, const DefGeo* G, int nd, const double* E, const double* Ec, double nu0,
-                             double kT, int3 n, uint64_t seed, Move* moves, DevState* stt, cudaStream_t st) {
-  k_residence<<<1, kEventThreads, 0, st>>>(d, G, nd, E, Ec, nu0, kT, n, (uint32_t)seed, (uint32_t)(seed >> 32), moves, stt);
+cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
+                             Move* moves, DevState* stt, cudaStream_t st) {
+  k_residence<<<1, kEventThreads, 0, st>>>(d, nd, rates, rsum, n, (uint32_t)seed, (uint32_t)(seed >> 32), moves, stt);
   return cudaGetLastError();
 }
-cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* E, const double* Ec, double nu0,
-                            double kT, int3 n, uint64_t seed, Move* moves, DevState* stt, cudaStream_t st) {
-  k_fixed_dt<<<1, kEventThreads, 0, st>>>(d, G, nd, E, Ec, nu0, kT, n, (uint32_t)seed, (uint32_t)(seed >> 32), moves, stt);
+cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* rates, double nu0, double kT, int3 n,
+                            uint64_t seed, Move* moves, DevState* stt, cudaStream_t st) {
+  k_fixed_dt<<<1, kEventThreads, 0, st>>>(d, G, nd, rates, nu0, kT, n, (uint32_t)seed, (uint32_t)(seed >> 32), moves, stt);
   return cudaGetLastError();
 }
 
@@ -767,9 +779,9 @@ template cudaError_t launch_selfterm<double>(const C2<double>*, const PassCfg&, 
                                             const double2*, double*, int, int, const double*, double, double*, cudaStream_t);
 template cudaError_t launch_energies<float>(const float*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
                                            const uint8_t*, const double*, const double*, double, int, double*, double*,
-                                           cudaStream_t);
+                                           RateArgs, cudaStream_t);
 template cudaError_t launch_energies<double>(const double*, int3, const okmc_defect*, const DefGeo*, int, const int*,
                                             const int*, const uint8_t*, const double*, const double*, double, int, double*,
-                                            double*, cudaStream_t);
+                                            double*, RateArgs, cudaStream_t);
 
 }  // namespace okmc

@@ -3,6 +3,7 @@
 // of each call.  All arithmetic of the method runs in the kernels of solve.cu
 // and defects.cu; this file only marshals, validates and sequences.
 #include <cmath>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <map>
@@ -44,11 +45,14 @@ cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
-                            int want_cand, double* E, double* Ec, cudaStream_t st);
-cudaError_t launch_residence(okmc_defect* d, const DefGeo* G, int nd, const double* E, const double* Ec, double nu0,
-                             double kT, int3 n, uint64_t seed, Move* moves, DevState* stt, cudaStream_t st);
-cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* E, const double* Ec, double nu0,
-                            double kT, int3 n, uint64_t seed, Move* moves, DevState* stt, cudaStream_t st);
+                            int want_cand, double* E, double* Ec, RateArgs ra, cudaStream_t st);
+cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
+                             Move* moves, DevState* stt, cudaStream_t st);
+cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* rates, double nu0, double kT, int3 n,
+                            uint64_t seed, Move* moves, DevState* stt, cudaStream_t st);
+bool fast_solve_supported(const PassCfg& c);
+cudaError_t launch_plane_fast(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st);
+cudaError_t launch_pencil_fast(C2<float>* spec, const PassCfg& c, cudaStream_t st);
 }  // namespace okmc
 
 namespace {
@@ -110,6 +114,8 @@ struct okmc_grid {
   double* d_W = nullptr;
   double* d_E = nullptr;
   double* d_Ec = nullptr;
+  double* d_rates = nullptr;
+  double* d_rsum = nullptr;
   Move* d_moves = nullptr;
   DevState* d_state = nullptr;
   int* d_err = nullptr;
@@ -118,6 +124,7 @@ struct okmc_grid {
   std::vector<okmc_defect> h_def;
   bool sigma_valid = false;
   bool any_mobile = false;
+  bool fast = false;  // FP32 register-FFT passes for this grid
   long long solves = 0;
   std::string err;
   bool profiling = false;
@@ -229,6 +236,10 @@ int solve(okmc_grid* g) {
     OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<double, int64_t>((const int64_t*)g->eps, (C2<double>*)g->spec, c, g->st); }));
     OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil<double>((C2<double>*)g->spec, c, g->st); }));
     OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_inv<double>((const C2<double>*)g->spec, (double*)g->sig, c, g->st); }));
+  } else if (g->fast) {
+    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, g->eps, g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil_fast((C2<float>*)g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_fast(true, g->spec, g->sig, c, g->st); }));
   } else {
     OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<float, int32_t>((const int32_t*)g->eps, (C2<float>*)g->spec, c, g->st); }));
     OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil<float>((C2<float>*)g->spec, c, g->st); }));
@@ -239,15 +250,23 @@ int solve(okmc_grid* g) {
   return OKMC_OK;
 }
 
-int energies(okmc_grid* g, int want_cand) {
+int energies(okmc_grid* g, int want_cand, double kT = 0.0) {
   OKMC_TRY(solve(g));
   const double pref = -kKappa * g->h * g->h * g->h;
+  RateArgs ra = {};
+  if (kT > 0.0) {
+    ra.rates = g->d_rates;
+    ra.rsum = g->d_rsum;
+    ra.negb = &g->d_state->negative_barriers;
+    ra.nu0 = g->nu0;
+    ra.kT = kT;
+  }
   return run(g, "energies", [&] {
     if (fp64(g))
       return launch_energies<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
-                                     g->d_alpha, g->d_W, pref, want_cand, g->d_E, g->d_Ec, g->st);
+                                     g->d_alpha, g->d_W, pref, want_cand, g->d_E, g->d_Ec, ra, g->st);
     return launch_energies<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
-                                  g->d_alpha, g->d_W, pref, want_cand, g->d_E, g->d_Ec, g->st);
+                                  g->d_alpha, g->d_W, pref, want_cand, g->d_E, g->d_Ec, ra, g->st);
   });
 }
 
@@ -267,6 +286,7 @@ int check_device_error(okmc_grid* g) {
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(g->st);
   if (ce != cudaSuccess) return cuda_fail(g, ce, "device error check");
   if (e == 4) return fail(g, OKMC_ERANGE, "eigenstrain contribution outside the fixed-point range");
+  if (e == 6) return fail(g, OKMC_ETIMEOUT, "a bounded wait for a bulk copy gave up");
   if (e) return fail(g, OKMC_ECUDA, "stencil construction inconsistency (code " + std::to_string(e) + ")");
   return OKMC_OK;
 }
@@ -336,8 +356,13 @@ int build_self_terms(okmc_grid* g) {
       for (int a = 0; a < 6; ++a) b.e6[d][a] = geo.e6[a];
     }
     OKMC_TRY(run(g, "self_fields", [&] { return launch_wfields<Q>((Q*)g->eps, n, g->d_ptr, g->d_off, g->d_cnt, i0, 2 * b.nb, g->st); }));
-    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)g->spec, c, g->st); }));
-    OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil<T>((C2<T>*)g->spec, c, g->st); }));
+    if (g->fast) {
+      OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, g->eps, g->spec, c, g->st); }));
+      OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast((C2<float>*)g->spec, c, g->st); }));
+    } else {
+      OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)g->spec, c, g->st); }));
+      OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil<T>((C2<T>*)g->spec, c, g->st); }));
+    }
     OKMC_TRY(run(g, "self_terms", [&] {
       return launch_selfterm<T>((const C2<T>*)g->spec, c, b, phx, phy, phz, g->d_partial, kSelfBlocks, i0, g->d_alpha, pref,
                                 g->d_W, g->st);
@@ -364,7 +389,7 @@ int voxelise_all(okmc_grid* g) {
 void free_defects(okmc_grid* g) {
   void** bufs[] = {(void**)&g->d_def, (void**)&g->d_geo, (void**)&g->d_ptr, (void**)&g->d_off, (void**)&g->d_cnt,
                    (void**)&g->d_alpha, (void**)&g->d_sumcnt, (void**)&g->d_nnz, (void**)&g->d_W, (void**)&g->d_E,
-                   (void**)&g->d_Ec, (void**)&g->d_moves, (void**)&g->d_pos};
+                   (void**)&g->d_Ec, (void**)&g->d_rates, (void**)&g->d_rsum, (void**)&g->d_moves, (void**)&g->d_pos};
   for (void** b : bufs) {
     dfree(g, *b);
     *b = nullptr;
@@ -483,6 +508,12 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   c.twY = (const char*)g->tw + off_tw[1];
   c.twZ = (const char*)g->tw + off_tw[2];
   c.untw = (const char*)g->tw + off_tw[3];
+  c.err = g->d_err;
+  // OKMC_GENERIC_FFT=1 keeps the generic passes (diagnostics and cross-checks)
+  {
+    const char* env = std::getenv("OKMC_GENERIC_FFT");
+    g->fast = !f64 && fast_solve_supported(c) && !(env && env[0] == '1');
+  }
   if (cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if (cudaMemsetAsync(g->d_state, 0, sizeof(DevState), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if (cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
@@ -533,6 +564,8 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
     OKMC_TRY(dalloc(g, (void**)&g->d_W, 18 * n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_E, n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_Ec, 8 * n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_rates, 8 * n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_rsum, n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_moves, n1 * sizeof(Move)));
     OKMC_TRY(dalloc(g, (void**)&g->d_pos, 3 * n1 * sizeof(int)));
     cudaError_t e = cudaSuccess;
@@ -725,16 +758,15 @@ int okmc_step(okmc_grid* g, const okmc_step_params* p, int64_t n_steps, okmc_ste
   if (!g->nd || !g->any_mobile) return fail(g, OKMC_ESTATE, "no mobile defect");
   const double kT = kBoltzmann * p->T_K;
   for (int64_t s = 0; s < n_steps; ++s) {
-    OKMC_TRY(energies(g, 1));
+    OKMC_TRY(energies(g, 1, kT));
     if (p->mode == OKMC_RESIDENCE) {
       OKMC_TRY(run(g, "event_residence", [&] {
-        return launch_residence(g->d_def, g->d_geo, g->nd, g->d_E, g->d_Ec, g->nu0, kT, dims(g), g->desc.seed, g->d_moves,
-                                g->d_state, g->st);
+        return launch_residence(g->d_def, g->nd, g->d_rates, g->d_rsum, dims(g), g->desc.seed, g->d_moves, g->d_state, g->st);
       }));
       OKMC_TRY(apply_moves(g, 1));
     } else {
       OKMC_TRY(run(g, "event_fixed_dt", [&] {
-        return launch_fixed_dt(g->d_def, g->d_geo, g->nd, g->d_E, g->d_Ec, g->nu0, kT, dims(g), g->desc.seed, g->d_moves,
+        return launch_fixed_dt(g->d_def, g->d_geo, g->nd, g->d_rates, g->nu0, kT, dims(g), g->desc.seed, g->d_moves,
                                g->d_state, g->st);
       }));
       OKMC_TRY(apply_moves(g, g->nd));
@@ -785,9 +817,9 @@ int okmc_reset_kernel_times(okmc_grid* g) {
 
 int okmc_launch_shape(const okmc_grid* g, int32_t out[3]) {
   if (!g || !out) return OKMC_EINVAL;
-  out[0] = g->cfg.cs;
-  out[1] = (int32_t)(g->P / g->cfg.tw_w);
-  out[2] = g->cfg.cs;
+  out[0] = g->fast ? -1 : g->cfg.cs;  // -1: register-FFT plane passes
+  out[1] = (int32_t)(g->P / (g->fast ? 8 : g->cfg.tw_w));
+  out[2] = g->fast ? -1 : g->cfg.cs;
   return OKMC_OK;
 }
 

@@ -237,6 +237,7 @@ struct PassCfg {
   const void* twY;     // C2<T>[ny]
   const void* twZ;     // C2<T>[nz]
   const void* untw;    // C2<T>[H+1]    exp(-2 pi i k / nx)
+  int* err;            // device error word (bounded waits that gave up set it)
 };
 
 // ---------------------------------------------------------------- defects
@@ -268,6 +269,14 @@ struct DevState {
   int nmoves;
   int err;
   double dt_fixed;
+};
+
+// Optional rate output of the energies kernel (rates == nullptr: energies only).
+struct RateArgs {
+  double* rates;        // [n][8] biased jump frequencies (0 for jumps not allowed)
+  double* rsum;         // [n] sum over j
+  long long* negb;      // count of negative effective barriers
+  double nu0, kT;
 };
 
 // Eigenstrain tensors of the (at most three) defects whose self terms one batch computes.
@@ -316,6 +325,86 @@ __host__ __device__ __forceinline__ void philox4x32_10(const uint32_t ctr_in[4],
 __host__ __device__ __forceinline__ double u53(uint32_t lo, uint32_t hi) {
   const uint64_t k = (((uint64_t)hi << 21) | (lo >> 11)) + 1ull;
   return (double)k * 1.1102230246251565404e-16;
+}
+
+// ---------------------------------------------------------------- Green operator
+template <class T>
+struct GreenC {
+  T C11, C12, C44;
+};
+
+// sigma_hat = C:(sym(q (x) K(q)^-1 (tau q)) - eps*_hat), tau = C:eps*_hat, K_ik = C_ijkl q_j q_l,
+// for cubic C (paper Eqs. EIG_elastic_fourier, basicgammacomplete, summaryEL with the
+// standard index reading of Gamma).  Gamma is homogeneous of degree 0 in the
+// frequency, so q need not be normalised.  The polarisation uses Cs = C/N so that
+// the result comes out already scaled by 1/N; K and the final C:(...) use C.
+template <class T>
+__device__ __forceinline__ void sigma_of(const C2<T>* e, T q0, T q1, T q2, const GreenC<T>& C, const GreenC<T>& Cs,
+                                         C2<T>* s) {
+  const T ds = Cs.C11 - Cs.C12, gs = T(2) * Cs.C44;
+  const C2<T> tr = e[0] + e[1] + e[2];
+  const C2<T> t0 = Cs.C12 * tr + ds * e[0], t1 = Cs.C12 * tr + ds * e[1], t2 = Cs.C12 * tr + ds * e[2];
+  const C2<T> t3 = gs * e[3], t4 = gs * e[4], t5 = gs * e[5];
+  const C2<T> v0 = q0 * t0 + q1 * t5 + q2 * t4;
+  const C2<T> v1 = q0 * t5 + q1 * t1 + q2 * t3;
+  const C2<T> v2 = q0 * t4 + q1 * t3 + q2 * t2;
+  const T A = C.C11 - C.C12 - T(2) * C.C44, B = C.C12 + C.C44;
+  const T a0 = q0 * q0, a1 = q1 * q1, a2 = q2 * q2;
+  const T cq = C.C44 * (a0 + a1 + a2);
+  const T k00 = cq + (A + B) * a0, k11 = cq + (A + B) * a1, k22 = cq + (A + B) * a2;
+  const T k01 = B * q0 * q1, k02 = B * q0 * q2, k12 = B * q1 * q2;
+  const T i00 = k11 * k22 - k12 * k12, i01 = k02 * k12 - k01 * k22, i02 = k01 * k12 - k02 * k11;
+  const T i11 = k00 * k22 - k02 * k02, i12 = k01 * k02 - k00 * k12, i22 = k00 * k11 - k01 * k01;
+  const T rdet = T(1) / (k00 * i00 + k01 * i01 + k02 * i02);
+  const C2<T> w0 = rdet * (i00 * v0 + i01 * v1 + i02 * v2);
+  const C2<T> w1 = rdet * (i01 * v0 + i11 * v1 + i12 * v2);
+  const C2<T> w2 = rdet * (i02 * v0 + i12 * v1 + i22 * v2);
+  const C2<T> qw = q0 * w0 + q1 * w1 + q2 * w2;
+  const T d = C.C11 - C.C12;
+  s[0] = C.C12 * qw + d * (q0 * w0) - t0;
+  s[1] = C.C12 * qw + d * (q1 * w1) - t1;
+  s[2] = C.C12 * qw + d * (q2 * w2) - t2;
+  s[3] = C.C44 * (q1 * w2 + q2 * w1) - t3;
+  s[4] = C.C44 * (q0 * w2 + q2 * w0) - t4;
+  s[5] = C.C44 * (q0 * w1 + q1 * w0) - t5;
+}
+
+// Green operator at half-spectrum index (kx, ky, kz), in place on e[6], scaled by
+// 1/N.  Frequencies follow Eq. frequencies (n = k for k < N/2, k - N otherwise,
+// so the Nyquist index is -N/2); on Nyquist planes the operator is averaged over
+// the sign of the Nyquist components, which is what the real part of the inverse
+// of the full spectrum computes.
+template <class T>
+__device__ __forceinline__ void green_point(C2<T>* e, int kx, int ky, int kz, const PassCfg& c, T scale) {
+  const GreenC<T> C{T(c.C11), T(c.C12), T(c.C44)};
+  const GreenC<T> Cs{T(c.C11 * (double)scale), T(c.C12 * (double)scale), T(c.C44 * (double)scale)};
+  const int fx = kx < c.H ? kx : kx - c.nx;
+  const int fy = ky < c.ny / 2 ? ky : ky - c.ny;
+  const int fz = kz < c.nz / 2 ? kz : kz - c.nz;
+  if (fx == 0 && fy == 0 && fz == 0) {
+    if (c.k0_mode == OKMC_MEAN_STRAIN_ZERO) {
+      const T ds = Cs.C11 - Cs.C12, gs = T(2) * Cs.C44;
+      const C2<T> tr = e[0] + e[1] + e[2];
+      const C2<T> t0 = Cs.C12 * tr + ds * e[0], t1 = Cs.C12 * tr + ds * e[1], t2 = Cs.C12 * tr + ds * e[2];
+      e[0] = T(-1) * t0;
+      e[1] = T(-1) * t1;
+      e[2] = T(-1) * t2;
+      for (int a = 3; a < 6; ++a) e[a] = (-gs) * e[a];
+    } else {
+      for (int a = 0; a < 6; ++a) e[a] = C2<T>{T(0), T(0)};
+    }
+    return;
+  }
+  const T q0 = T(fx) / T(c.nx), q1 = T(fy) / T(c.ny), q2 = T(fz) / T(c.nz);
+  C2<T> s[6];
+  sigma_of<T>(e, q0, q1, q2, C, Cs, s);
+  const bool nx_ = (kx == c.H), ny_ = (2 * ky == c.ny), nz_ = (2 * kz == c.nz);
+  if (nx_ || ny_ || nz_) {
+    C2<T> s2[6];
+    sigma_of<T>(e, nx_ ? -q0 : q0, ny_ ? -q1 : q1, nz_ ? -q2 : q2, C, Cs, s2);
+    for (int a = 0; a < 6; ++a) s[a] = T(0.5) * (s[a] + s2[a]);
+  }
+  for (int a = 0; a < 6; ++a) e[a] = s[a];
 }
 
 }  // namespace okmc

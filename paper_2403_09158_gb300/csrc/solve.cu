@@ -52,84 +52,6 @@ struct RowSrcQ<double, int64_t> {
   }
 };
 
-template <class T>
-struct GreenC {
-  T C11, C12, C44;
-};
-
-// sigma_hat = C:(sym(m (x) K(m)^-1 (tau m)) - eps*_hat), tau = C:eps*_hat, for a unit
-// direction m and cubic C (paper Eqs. EIG_elastic_fourier, basicgammacomplete,
-// summaryEL with the standard index reading of Gamma).
-template <class T>
-__device__ __forceinline__ void sigma_of(const C2<T>* e, T m0, T m1, T m2, const GreenC<T>& C, C2<T>* s) {
-  const T A = C.C11 - C.C12 - T(2) * C.C44;
-  const T B = C.C12 + C.C44;
-  const T k00 = C.C44 + (A + B) * m0 * m0, k11 = C.C44 + (A + B) * m1 * m1, k22 = C.C44 + (A + B) * m2 * m2;
-  const T k01 = B * m0 * m1, k02 = B * m0 * m2, k12 = B * m1 * m2;
-  const T i00 = k11 * k22 - k12 * k12, i01 = k02 * k12 - k01 * k22, i02 = k01 * k12 - k02 * k11;
-  const T i11 = k00 * k22 - k02 * k02, i12 = k01 * k02 - k00 * k12, i22 = k00 * k11 - k01 * k01;
-  const T rdet = T(1) / (k00 * i00 + k01 * i01 + k02 * i02);
-  const T d = C.C11 - C.C12, g = T(2) * C.C44;
-  const C2<T> tr = e[0] + e[1] + e[2];
-  const C2<T> t0 = C.C12 * tr + d * e[0], t1 = C.C12 * tr + d * e[1], t2 = C.C12 * tr + d * e[2];
-  const C2<T> t3 = g * e[3], t4 = g * e[4], t5 = g * e[5];
-  const C2<T> v0 = m0 * t0 + m1 * t5 + m2 * t4;
-  const C2<T> v1 = m0 * t5 + m1 * t1 + m2 * t3;
-  const C2<T> v2 = m0 * t4 + m1 * t3 + m2 * t2;
-  const C2<T> w0 = rdet * (i00 * v0 + i01 * v1 + i02 * v2);
-  const C2<T> w1 = rdet * (i01 * v0 + i11 * v1 + i12 * v2);
-  const C2<T> w2 = rdet * (i02 * v0 + i12 * v1 + i22 * v2);
-  const C2<T> g0 = m0 * w0, g1 = m1 * w1, g2 = m2 * w2;
-  const C2<T> g3 = T(0.5) * (m1 * w2 + m2 * w1), g4 = T(0.5) * (m0 * w2 + m2 * w0), g5 = T(0.5) * (m0 * w1 + m1 * w0);
-  const C2<T> trg = g0 + g1 + g2;
-  s[0] = C.C12 * trg + d * g0 - t0;
-  s[1] = C.C12 * trg + d * g1 - t1;
-  s[2] = C.C12 * trg + d * g2 - t2;
-  s[3] = g * g3 - t3;
-  s[4] = g * g4 - t4;
-  s[5] = g * g5 - t5;
-}
-
-// Green operator at half-spectrum index (kx, ky, kz), in place on e[6], scaled by
-// 1/N.  Frequencies follow Eq. frequencies (n = k for k < N/2, k - N otherwise,
-// so the Nyquist index is -N/2); on Nyquist planes the operator is averaged over
-// the sign of the Nyquist components, which is what the real part of the inverse
-// of the full spectrum computes.
-template <class T>
-__device__ __forceinline__ void green_point(C2<T>* e, int kx, int ky, int kz, const PassCfg& c, T scale) {
-  const GreenC<T> C{T(c.C11), T(c.C12), T(c.C44)};
-  const int fx = kx < c.H ? kx : kx - c.nx;
-  const int fy = ky < c.ny / 2 ? ky : ky - c.ny;
-  const int fz = kz < c.nz / 2 ? kz : kz - c.nz;
-  C2<T> s[6];
-  if (fx == 0 && fy == 0 && fz == 0) {
-    if (c.k0_mode == OKMC_MEAN_STRAIN_ZERO) {
-      const T d = C.C11 - C.C12, g = T(2) * C.C44;
-      const C2<T> tr = e[0] + e[1] + e[2];
-      s[0] = T(-1) * (C.C12 * tr + d * e[0]);
-      s[1] = T(-1) * (C.C12 * tr + d * e[1]);
-      s[2] = T(-1) * (C.C12 * tr + d * e[2]);
-      s[3] = T(-1) * (g * e[3]);
-      s[4] = T(-1) * (g * e[4]);
-      s[5] = T(-1) * (g * e[5]);
-    } else {
-      for (int a = 0; a < 6; ++a) s[a] = C2<T>{T(0), T(0)};
-    }
-  } else {
-    const T qx = T(fx) / T(c.nx), qy = T(fy) / T(c.ny), qz = T(fz) / T(c.nz);
-    const T rn = T(1) / sqrt(qx * qx + qy * qy + qz * qz);
-    const T m0 = qx * rn, m1 = qy * rn, m2 = qz * rn;
-    sigma_of<T>(e, m0, m1, m2, C, s);
-    const bool nx_ = (kx == c.H), ny_ = (2 * ky == c.ny), nz_ = (2 * kz == c.nz);
-    if (nx_ || ny_ || nz_) {
-      C2<T> s2[6];
-      sigma_of<T>(e, nx_ ? -m0 : m0, ny_ ? -m1 : m1, nz_ ? -m2 : m2, C, s2);
-      for (int a = 0; a < 6; ++a) s[a] = T(0.5) * (s[a] + s2[a]);
-    }
-  }
-  for (int a = 0; a < 6; ++a) e[a] = scale * s[a];
-}
-
 // ---------------------------------------------------------------- smem layout
 template <class T>
 struct PlaneSmem {

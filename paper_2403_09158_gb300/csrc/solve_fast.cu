@@ -1,0 +1,373 @@
+// Fast FP32 solve passes for power-of-two edges (nx = ny and nz in 32..256): the same three passes and data layout as solve.cu, with register
+// line FFTs (fft_reg.cuh) instead of the generic shared-memory Stockham engine,
+// loads issued a whole line (or a whole tile) ahead, and clusters sized so that
+// two CTAs share each SM.
+//
+//   plane_fwd_fast : per (component, z) plane; rows of nx reals -> complex rows of
+//                    nx/2 (8 or 4 threads per row, all loads of a row in flight),
+//                    untangling, distributed-shared-memory scatter of the kx
+//                    columns to their owner CTA, cluster barrier, column FFTs of
+//                    length ny (in place, skewed exchange), contiguous stores.
+//   pencil_fast    : per tile of 8 consecutive ky at one kx: the 6 x nz x 8 tile
+//                    arrives by 8-byte cp.async (all in flight at once) into a
+//                    padded layout, forward z FFTs in place, Green operator,
+//                    inverse z FFTs, stores.
+//   plane_inv_fast : inverse of plane_fwd_fast.
+#include <cooperative_groups.h>
+
+#include "fft_reg.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace okmc {
+
+namespace {
+constexpr int kT = 256;  // threads per CTA
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+}  // namespace
+
+__device__ __forceinline__ void load_tw(C2<float>* twH, C2<float>* twY, C2<float>* untw, const PassCfg& c, int H, int NY) {
+  const C2<float>* gH = reinterpret_cast<const C2<float>*>(c.twH);
+  const C2<float>* gY = reinterpret_cast<const C2<float>*>(c.twY);
+  const C2<float>* gU = reinterpret_cast<const C2<float>*>(c.untw);
+  for (int i = threadIdx.x; i < H; i += blockDim.x) twH[i] = gH[i];
+  for (int i = threadIdx.x; i < NY; i += blockDim.x) twY[i] = gY[i];
+  for (int i = threadIdx.x; i <= H; i += blockDim.x) untw[i] = gU[i];
+}
+
+// ---------------------------------------------------------------- plane passes
+// One cluster of CS CTAs (256 threads, two CTAs per SM) per (component, z) plane.
+// Rows: a group of reg_nt<H> threads per row, all of a row's loads in flight,
+// untangling, distributed-shared-memory scatter of every kx value to its column
+// owner; column 0 carries (X[0], X[nx/2]) packed so that every CTA owns exactly
+// H/CS columns.  Columns: in place in shared memory, contiguous stores.
+constexpr int kNT = 256;
+
+template <int H, int NY>
+struct NShape {
+  static constexpr int NTH = reg_nt<H>(), GR = kNT / NTH;
+  static constexpr int NTY = reg_nt<NY>(), GC = kNT / NTY;
+  static constexpr int R2H = RegPlan<H>::R2, R2Y = RegPlan<NY>::R2;
+  static constexpr int XS = RegPlan<H>::R1 * (R2H + 1);       // row exchange slots
+  static constexpr int XSY = RegPlan<NY>::R1 * (R2Y + 1);     // column exchange slots
+  static constexpr int XB = GR * XS > GC * XSY ? GR * XS : GC * XSY;
+  static constexpr int LDC = NY + 1, LDR = H + 1;
+};
+template <int H, int NY>
+__host__ __device__ constexpr size_t nfwd_smem(int cs) {
+  using S = NShape<H, NY>;
+  return sizeof(C2<float>) * ((size_t)(H / cs) * S::LDC + (size_t)S::GR * S::XS + H + NY + H + 1);
+}
+template <int H, int NY>
+__host__ __device__ constexpr size_t ninv_smem(int cs) {
+  using S = NShape<H, NY>;
+  return sizeof(C2<float>) * ((size_t)(NY / cs) * S::LDR + (size_t)S::XB + H + NY + H + 1);
+}
+
+template <int H, int NY, int CS>
+__global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restrict__ eps, C2<float>* __restrict__ spec,
+                                                        PassCfg c) {
+  using S = NShape<H, NY>;
+  constexpr int CPER = H / CS, ROWS = NY / CS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<float>* col = reinterpret_cast<C2<float>*>(smem_raw);  // [CPER][LDC]
+  C2<float>* xb = col + CPER * S::LDC;                       // [GR][XS]
+  C2<float>* twH = xb + S::GR * S::XS;
+  C2<float>* twY = twH + H;
+  C2<float>* untw = twY + NY;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int h = CS > 1 ? (int)cluster.block_rank() : 0;
+  const int plane = blockIdx.y;
+  const int tid = threadIdx.x;
+  const size_t P = (size_t)(H + 1) * NY;
+  const float q = (float)c.q;
+  load_tw(twH, twY, untw, c, H, NY);
+  C2<float>* rcol[CS];
+#pragma unroll
+  for (int r = 0; r < CS; ++r) rcol[r] = (CS > 1 && r != h) ? cluster.map_shared_rank(col, r) : col;
+  __syncthreads();
+  {  // rows along x
+    const int g = tid / S::NTH, t = tid % S::NTH;
+    C2<float>* xg = xb + g * S::XS;
+    for (int r0 = 0; r0 < ROWS; r0 += S::GR) {
+      const bool act = r0 + g < ROWS;
+      const int y = h * ROWS + (act ? r0 + g : 0);
+      const int2* row = reinterpret_cast<const int2*>(eps + ((size_t)plane * NY + y) * (2 * H));
+      auto ld = [&](int i) {
+        const int2 v = __ldg(row + i);
+        return C2<float>{__int2float_rn(v.x) * q, __int2float_rn(v.y) * q};
+      };
+      auto st = [&](int k, C2<float> v) { xg[k] = v; };
+      reg_fft<false, H>(ld, XPad<S::R2H>{xg}, st, twH, t, act);
+      if (act) {
+        for (int k = t; k < H; k += S::NTH) {
+          const C2<float> A = xg[k];
+          C2<float> X;
+          if (k == 0) {
+            X = C2<float>{A.x + A.y, A.x - A.y};  // (X[0], X[nx/2]), both real
+          } else {
+            const C2<float> B = conjg(xg[H - k]);
+            const C2<float> sum = A + B, dif = untw[k] * (A - B);
+            X = C2<float>{0.5f * (sum.x + dif.y), 0.5f * (sum.y - dif.x)};
+          }
+          rcol[k / CPER][(k % CPER) * S::LDC + y] = X;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  if (CS > 1) cluster.sync();
+  else __syncthreads();
+  {  // columns along y
+    const int g = tid / S::NTY, t = tid % S::NTY;
+    for (int c0 = 0; c0 < CPER; c0 += S::GC) {
+      const bool act = c0 + g < CPER;
+      const int cc = act ? c0 + g : 0;
+      const int kx = h * CPER + cc;
+      C2<float>* cp = col + cc * S::LDC;
+      C2<float>* out = spec + (size_t)plane * P + (size_t)kx * NY;
+      const bool packed = (kx == 0);
+      auto ld = [&](int i) { return cp[i]; };
+      auto st = [&](int k, C2<float> v) {
+        if (packed) cp[k] = v;
+        else out[k] = v;
+      };
+      reg_fft<false, NY>(ld, XSkew<S::R2Y>{cp, 1}, st, twY, t, act);
+      if (act && packed) {
+        // P = A + i B, A and B the spectra of the real columns X[0] and X[nx/2]
+        for (int k = t; k < NY; k += S::NTY) {
+          const C2<float> Pk = cp[k], Pm = conjg(cp[(NY - k) & (NY - 1)]);
+          const C2<float> s = Pk + Pm, d = Pk - Pm;
+          out[k] = C2<float>{0.5f * s.x, 0.5f * s.y};
+          out[(size_t)H * NY + k] = C2<float>{0.5f * d.y, -0.5f * d.x};
+        }
+      }
+    }
+  }
+}
+
+template <int H, int NY, int CS>
+__global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restrict__ spec, float* __restrict__ sig,
+                                                        PassCfg c) {
+  using S = NShape<H, NY>;
+  constexpr int CPER = H / CS, ROWS = NY / CS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<float>* rowb = reinterpret_cast<C2<float>*>(smem_raw);  // [ROWS][LDR]
+  C2<float>* xb = rowb + ROWS * S::LDR;
+  C2<float>* twH = xb + S::XB;
+  C2<float>* twY = twH + H;
+  C2<float>* untw = twY + NY;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int h = CS > 1 ? (int)cluster.block_rank() : 0;
+  const int plane = blockIdx.y;
+  const int tid = threadIdx.x;
+  const size_t P = (size_t)(H + 1) * NY;
+  load_tw(twH, twY, untw, c, H, NY);
+  C2<float>* rrow[CS];
+#pragma unroll
+  for (int r = 0; r < CS; ++r) rrow[r] = (CS > 1 && r != h) ? cluster.map_shared_rank(rowb, r) : rowb;
+  __syncthreads();
+  {  // inverse columns along y, scattered to the row owners
+    const int g = tid / S::NTY, t = tid % S::NTY;
+    C2<float>* xg = xb + g * S::XSY;
+    for (int c0 = 0; c0 < CPER; c0 += S::GC) {
+      const bool act = c0 + g < CPER;
+      const int kx = h * CPER + (act ? c0 + g : 0);
+      const C2<float>* in = spec + (size_t)plane * P + (size_t)kx * NY;
+      const C2<float>* nyq = spec + (size_t)plane * P + (size_t)H * NY;
+      const bool packed = (kx == 0);
+      auto ld = [&](int i) {
+        const C2<float> A = in[i];
+        if (!packed) return A;
+        const C2<float> B = nyq[i];
+        return C2<float>{A.x - B.y, A.y + B.x};  // A + i B
+      };
+      auto st = [&](int k, C2<float> v) { rrow[k / ROWS][(k % ROWS) * S::LDR + kx] = v; };
+      reg_fft<true, NY>(ld, XPad<S::R2Y>{xg}, st, twY, t, act);
+    }
+  }
+  if (CS > 1) cluster.sync();
+  else __syncthreads();
+  {  // rows along x
+    const int g = tid / S::NTH, t = tid % S::NTH;
+    for (int r0 = 0; r0 < ROWS; r0 += S::GR) {
+      const bool act = r0 + g < ROWS;
+      const int yl = act ? r0 + g : 0;
+      C2<float>* R = rowb + yl * S::LDR;
+      auto ld = [&](int k) {
+        if (k == 0) {
+          const C2<float> p = R[0];
+          return C2<float>{p.x + p.y, p.x - p.y};
+        }
+        const C2<float> Xk = R[k], Xc = conjg(R[H - k]);
+        const C2<float> E = Xk + Xc;
+        const C2<float> O = conjg(untw[k]) * (Xk - Xc);
+        return C2<float>{E.x - O.y, E.y + O.x};
+      };
+      C2<float>* orow = reinterpret_cast<C2<float>*>(sig + ((size_t)plane * NY + h * ROWS + yl) * (2 * H));
+      auto st = [&](int k, C2<float> v) { orow[k] = v; };
+      reg_fft<true, H>(ld, XSkew<S::R2H>{R, 1}, st, twH, t, act);
+    }
+  }
+}
+
+constexpr int kTW = 8;
+constexpr int kLDT = kTW + 1;  // padded row of a tile: conflict-free strided line access
+
+template <int NZ>
+__host__ __device__ constexpr size_t pencil_fast_smem() {
+  return sizeof(C2<float>) * ((size_t)6 * NZ * kLDT + NZ);
+}
+
+
+template <int NZ>
+__global__ void __launch_bounds__(kT, 2) k_pencil_fast(C2<float>* __restrict__ spec, PassCfg c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw);  // [comp][kz][kLDT]
+  C2<float>* twZ = tile + 6 * NZ * kLDT;
+  const int tid = threadIdx.x;
+  const size_t P = (size_t)(c.H + 1) * c.ny;
+  const size_t p0 = (size_t)blockIdx.x * kTW;
+  const int kx = (int)(p0 / c.ny), ky0 = (int)(p0 % c.ny);
+  for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
+    const int t = idx & (kTW - 1), kz = (idx >> 3) % NZ, comp = idx / (kTW * NZ);
+    cp_async8(tile + (comp * NZ + kz) * kLDT + t, spec + ((size_t)comp * NZ + kz) * P + p0 + t);
+  }
+  {
+    const C2<float>* gZ = reinterpret_cast<const C2<float>*>(c.twZ);
+    for (int i = tid; i < NZ; i += kT) twZ[i] = gZ[i];
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  constexpr int NTZ = reg_nt<NZ>(), GL = kT / NTZ, R2Z = RegPlan<NZ>::R2;
+  const int g = tid / NTZ, t = tid % NTZ;
+  for (int l0 = 0; l0 < 6 * kTW; l0 += GL) {
+    const bool act = l0 + g < 6 * kTW;
+    const int l = act ? l0 + g : 0;
+    C2<float>* base = tile + (l / kTW) * NZ * kLDT + (l % kTW);
+    auto ld = [&](int i) { return base[i * kLDT]; };
+    auto st = [&](int k, C2<float> v) { base[k * kLDT] = v; };
+    reg_fft<false, NZ>(ld, XSkew<R2Z>{base, kLDT}, st, twZ, t, act);
+  }
+  __syncthreads();
+  if (!c.forward_only) {
+    const float scale = 1.0f / ((float)c.nx * (float)c.ny * (float)c.nz);
+    for (int idx = tid; idx < kTW * NZ; idx += kT) {
+      const int t8 = idx & (kTW - 1), kz = idx >> 3;
+      C2<float> e[6];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) e[a] = tile[(a * NZ + kz) * kLDT + t8];
+      green_point<float>(e, kx, ky0 + t8, kz, c, scale);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) tile[(a * NZ + kz) * kLDT + t8] = e[a];
+    }
+    __syncthreads();
+    for (int l0 = 0; l0 < 6 * kTW; l0 += GL) {
+      const bool act = l0 + g < 6 * kTW;
+      const int l = act ? l0 + g : 0;
+      C2<float>* base = tile + (l / kTW) * NZ * kLDT + (l % kTW);
+      auto ld = [&](int i) { return base[i * kLDT]; };
+      auto st = [&](int k, C2<float> v) { base[k * kLDT] = v; };
+      reg_fft<true, NZ>(ld, XSkew<R2Z>{base, kLDT}, st, twZ, t, act);
+    }
+    __syncthreads();
+  }
+  for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
+    const int t8 = idx & (kTW - 1), kz = (idx >> 3) % NZ, comp = idx / (kTW * NZ);
+    spec[((size_t)comp * NZ + kz) * P + p0 + t8] = tile[(comp * NZ + kz) * kLDT + t8];
+  }
+}
+
+// ---------------------------------------------------------------- dispatch
+namespace {
+template <class K, class... Args>
+cudaError_t launch_k(K k, dim3 grid, size_t smem, int cluster, cudaStream_t st, Args... args) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = dim3(kT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  if (cluster > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+  }
+  return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+// smallest cluster that lets two CTAs share an SM
+template <int H, int NY, int CS>
+cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
+  static_assert(H % CS == 0 && NY % CS == 0, "cluster must split rows and columns evenly");
+  const dim3 grid(CS, c.ncomp * c.nz);
+  if (inverse)
+    return launch_k(k_plane_inv_n<H, NY, CS>, grid, ninv_smem<H, NY>(CS), CS, st, static_cast<const C2<float>*>(in),
+                    static_cast<float*>(out), c);
+  return launch_k(k_plane_fwd_n<H, NY, CS>, grid, nfwd_smem<H, NY>(CS), CS, st, static_cast<const int32_t*>(in),
+                  static_cast<C2<float>*>(out), c);
+}
+
+// smallest cluster whose CTAs fit two per SM
+template <int H, int NY>
+constexpr int ncs() {
+  return (nfwd_smem<H, NY>(1) <= 112 * 1024 && ninv_smem<H, NY>(1) <= 112 * 1024) ? 1
+       : (nfwd_smem<H, NY>(2) <= 112 * 1024 && ninv_smem<H, NY>(2) <= 112 * 1024) ? 2 : 4;
+}
+
+template <int H, int NY>
+cudaError_t plane_pair(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
+  return plane_pair_n<H, NY, ncs<H, NY>()>(inverse, in, out, c, st);
+}
+
+template <int NZ>
+cudaError_t pencil_one(C2<float>* spec, const PassCfg& c, cudaStream_t st) {
+  const size_t P = (size_t)(c.H + 1) * c.ny;
+  return launch_k(k_pencil_fast<NZ>, dim3((unsigned)(P / kTW)), pencil_fast_smem<NZ>(), 1, st, spec, c);
+}
+}  // namespace
+
+// The fast path covers nx = ny in {32, 64, 128, 256} with nz in the same set.
+bool fast_solve_supported(const PassCfg& c) {
+  if (c.ncomp != 6) return false;
+  const int key = c.H * 1000 + c.ny;
+  const bool plane = key == 16032 || key == 32064 || key == 64128 || key == 128256;
+  const bool pencil = c.nz == 32 || c.nz == 64 || c.nz == 128 || c.nz == 256;
+  return plane && pencil;
+}
+
+// the planes of cubic power-of-two grids (ny = nx)
+cudaError_t launch_plane_fast(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
+  switch (c.H * 1000 + c.ny) {
+    case 16032: return plane_pair<16, 32>(inverse, in, out, c, st);
+    case 32064: return plane_pair<32, 64>(inverse, in, out, c, st);
+    case 64128: return plane_pair<64, 128>(inverse, in, out, c, st);
+    case 128256: return plane_pair<128, 256>(inverse, in, out, c, st);
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
+
+cudaError_t launch_pencil_fast(C2<float>* spec, const PassCfg& c, cudaStream_t st) {
+  switch (c.nz) {
+    case 32: return pencil_one<32>(spec, c, st);
+    case 64: return pencil_one<64>(spec, c, st);
+    case 128: return pencil_one<128>(spec, c, st);
+    case 256: return pencil_one<256>(spec, c, st);
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
+
+}  // namespace okmc

