@@ -183,8 +183,12 @@ def main():
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--solve-only', type=int, default=0, metavar='N',
+                    help='profiling aid: one stress solve of an N^3 grid holding one SIA cluster, then exit')
     args = ap.parse_args()
     ws, rank = _dist()
+    if args.solve_only:
+        return solve_only(args.solve_only)
     if args.impl == 'reference':
         return run_reference(args, ws, rank)
     import torch
@@ -218,7 +222,8 @@ def main():
         'events_per_s': ws * r['events'] / (r['ms'] / 1e3),
         'setup_s': r['setup_s'],
         'roofline': {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': hbm, 'unit': 'GB/s',
-                     'frac': achieved / hbm, 'traffic': None, 'peak_source': src + ' copy bandwidth'},
+                     'frac': achieved / hbm, 'traffic': measured_traffic(dom),
+                     'algorithmic_bytes': kernel_bytes(dom, r['n']), 'peak_source': src + ' copy bandwidth'},
         'pipeline_roofline': {'solve_ms': solve_ms, 'algorithmic_bytes': 96 * r['N'], 'achieved_gbs': pipe_gbs,
                               'frac': pipe_gbs / hbm},
         'kernel_ms': {k: v[0] / v[1] for k, v in kt.items()},
@@ -233,6 +238,43 @@ def main():
                                'sample': cb['sample']}
     print(json.dumps(out))
     return 0
+
+
+def solve_only(n):
+    """Launch sequence: self-term build (plane_fwd, pencil forward), then one solve
+    (plane_fwd, pencil_green, plane_inv)."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2403_09158_gb300 import okmc as ok
+    from paper_2403_09158_gb300.workload import make_defects
+    g = ok.Grid((n, n, n), 0.2855, 243.0, 145.0, 116.0)
+    g.set_defects(make_defects([2], np.array([[1, 1, 1]]), [0], [0.0], [3], [0.3], [2]))
+    g.solve_stress(copy=False)
+    g.close()
+    print(json.dumps({'solve_only': n}))
+    return 0
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, 'paper_2403_09158_gb300', 'csrc')
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), 'rb').read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from profiles/dram_traffic.json, if that capture
+    was taken on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, 'profiles', 'dram_traffic.json')
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get('sources_hash') != kernel_sources_hash():
+        return None
+    k = d.get('kernels', {}).get(kernel)
+    return None if k is None else k.get('dram_bytes_per_launch')
 
 
 def run_reference(args, ws, rank):
