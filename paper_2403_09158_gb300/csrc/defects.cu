@@ -443,65 +443,126 @@ __global__ void k_selfterm_final(const double* __restrict__ partial, int nblocks
 
 // ---------------------------------------------------------------- energies
 // E_i(Y) = -kappa h^3 alpha sum_v count(v - base(Y)) e_i : sigma(v) - W_i(c, lambda),
-// FP32 (or FP64) loads, FP64 accumulation, for Y = X_i and the eight jumps.
+// for Y = X_i and the eight jumps.  Each product count * (e : sigma) is formed in the
+// field precision and accumulated per thread as a compensated pair (TwoSum), the
+// pairs are combined across the warp by compensated shuffles, and the per-warp
+// results are added in FP64: the sums keep ~48 significant bits without FP64
+// arithmetic in the inner loop.  Blocks visit defects largest stencil first.
+struct CSum {
+  float s, c;
+};
+__device__ __forceinline__ void csum_add(CSum& a, float x) {
+  const float t = a.s + x;
+  const float bp = t - a.s;
+  a.c += (a.s - (t - bp)) + (x - bp);
+  a.s = t;
+}
+__device__ __forceinline__ double csum_value(const CSum& a) { return (double)a.s + (double)a.c; }
+
+constexpr int kEnergyThreads = 256;
+
 template <class T>
-__global__ void __launch_bounds__(128) k_energies(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
-                                                  const DefGeo* __restrict__ G, const int* __restrict__ ptr,
-                                                  const int* __restrict__ off, const uint8_t* __restrict__ cnt,
-                                                  const double* __restrict__ alpha, const double* __restrict__ W,
-                                                  double pref, int want_cand, double* __restrict__ E,
-                                                  double* __restrict__ Ec, RateArgs ra) {
-  __shared__ double sh[32];
-  const int i = blockIdx.x;
+struct EAcc;
+template <>
+struct EAcc<float> {
+  CSum v;
+  __device__ __forceinline__ void zero() { v = CSum{0.f, 0.f}; }
+  __device__ __forceinline__ void add(float x) { csum_add(v, x); }
+  // pairwise TwoSum of (s, c) pairs across the warp
+  __device__ __forceinline__ void warp_reduce() {
+    for (int o = 16; o; o >>= 1) {
+      const float os = __shfl_xor_sync(0xffffffffu, v.s, o), oc = __shfl_xor_sync(0xffffffffu, v.c, o);
+      const float t = v.s + os, bp = t - v.s;
+      const float err = (v.s - (t - bp)) + (os - bp);
+      v.c = v.c + oc + err;
+      v.s = t;
+    }
+  }
+  __device__ __forceinline__ double value() const { return csum_value(v); }
+};
+template <>
+struct EAcc<double> {
+  double v;
+  __device__ __forceinline__ void zero() { v = 0.0; }
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void warp_reduce() {
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+template <class T>
+__global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
+                                                             const DefGeo* __restrict__ G, const int* __restrict__ ptr,
+                                                             const int* __restrict__ off, const uint8_t* __restrict__ cnt,
+                                                             const double* __restrict__ alpha, const double* __restrict__ W,
+                                                             double pref, int want_cand, const int* __restrict__ order,
+                                                             double* __restrict__ E, double* __restrict__ Ec, RateArgs ra) {
+  __shared__ double part[kEnergyThreads / 32][9];
+  const int i = order ? order[blockIdx.x] : blockIdx.x;
   const size_t N = (size_t)n.x * n.y * n.z;
   const okmc_defect r = d[i];
   const DefGeo g = G[i];
-  const int c = r.pos[0] & 1;
+  const int c = r.pos[0] & 1, cp = 1 - c;
   T ew[6];
   for (int a = 0; a < 6; ++a) ew[a] = T(a < 3 ? g.e6[a] : 2.0 * g.e6[a]);
   const int bx = floor_div2(r.pos[0]), by = floor_div2(r.pos[1]), bz = floor_div2(r.pos[2]);
-  double acc0 = 0.0;
+  EAcc<T> acc[9];
+  for (int j = 0; j < 9; ++j) acc[j].zero();
   for (int k = ptr[2 * i + c] + threadIdx.x; k < ptr[2 * i + c + 1]; k += blockDim.x) {
     int dx, dy, dz;
     unpack_off(off[k], dx, dy, dz);
     const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
     T dot = T(0);
+#pragma unroll
     for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
-    acc0 += (double)cnt[k] * (double)dot;
+    acc[0].add(T(cnt[k]) * dot);
   }
-  acc0 = block_sum_d(acc0, sh);
-  if (threadIdx.x == 0) E[i] = pref * alpha[2 * i + c] * acc0 - W[(size_t)i * 18 + c * 9];
-  if (!want_cand) return;
-  const int cp = 1 - c;
-  double acc[8];
-  int jb[8][3];
-  for (int j = 0; j < 8; ++j) {
-    acc[j] = 0.0;
-    jb[j][0] = floor_div2(r.pos[0] + jump_comp(j, 0));
-    jb[j][1] = floor_div2(r.pos[1] + jump_comp(j, 1));
-    jb[j][2] = floor_div2(r.pos[2] + jump_comp(j, 2));
-  }
-  for (int k = ptr[2 * i + cp] + threadIdx.x; k < ptr[2 * i + cp + 1]; k += blockDim.x) {
-    int dx, dy, dz;
-    unpack_off(off[k], dx, dy, dz);
-    const double w = (double)cnt[k];
-    for (int j = 0; j < 8; ++j) {
-      const size_t v = ((size_t)wrap(jb[j][2] + dz, n.z) * n.y + wrap(jb[j][1] + dy, n.y)) * n.x + wrap(jb[j][0] + dx, n.x);
-      T dot = T(0);
-      for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
-      acc[j] += w * (double)dot;
+  if (want_cand) {
+    // candidate j sits at base(X + lambda_j) = base(X) + d_j, d_j in {-1,0}^3 (c = 0)
+    // or {0,1}^3 (c = 1); per axis the shift is (s + 1)/2 - (1 - c) with s = +-1
+    for (int k = ptr[2 * i + cp] + threadIdx.x; k < ptr[2 * i + cp + 1]; k += blockDim.x) {
+      int dx, dy, dz;
+      unpack_off(off[k], dx, dy, dz);
+      const T w = T(cnt[k]);
+      const int x0 = wrap(bx + dx - cp, n.x), x1 = wrap(bx + dx + 1 - cp, n.x);
+      const int y0 = wrap(by + dy - cp, n.y), y1 = wrap(by + dy + 1 - cp, n.y);
+      const int z0 = wrap(bz + dz - cp, n.z), z1 = wrap(bz + dz + 1 - cp, n.z);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const size_t v = ((size_t)((j & 1) ? z1 : z0) * n.y + ((j & 2) ? y1 : y0)) * n.x + ((j & 4) ? x1 : x0);
+        T dot = T(0);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
+        acc[1 + j].add(w * dot);
+      }
     }
   }
+  // warp reduction of the accumulators (compensated pairs stay FP32), FP64 across warps
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    acc[j].warp_reduce();
+    if (lane == 0) part[wid][j] = acc[j].value();
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double tot[9];
+  for (int j = 0; j < 9; ++j) {
+    tot[j] = 0.0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot[j] += part[w2][j];
+  }
+  const double e0 = pref * alpha[2 * i + c] * tot[0] - W[(size_t)i * 18 + c * 9];
+  E[i] = e0;
+  if (!want_cand) return;
   double ec[8];
   for (int j = 0; j < 8; ++j) {
-    const double t = block_sum_d(acc[j], sh);
-    ec[j] = pref * alpha[2 * i + cp] * t - W[(size_t)i * 18 + c * 9 + 1 + j];
-    if (threadIdx.x == 0) Ec[(size_t)i * 8 + j] = ec[j];
+    ec[j] = pref * alpha[2 * i + cp] * tot[1 + j] - W[(size_t)i * 18 + c * 9 + 1 + j];
+    Ec[(size_t)i * 8 + j] = ec[j];
   }
-  if (!ra.rates || threadIdx.x != 0) return;
+  if (!ra.rates) return;
   // biased jump frequencies nu_j = (nu0/z) exp(-(E_m + (E_j - E_0)/2)/kT) of the
   // allowed jumps (Eqs. biased_forward/backward_boltzmann, prefactor 1/z)
-  const double e0 = pref * alpha[2 * i + c] * acc0 - W[(size_t)i * 18 + c * 9];
   double sum = 0.0;
   int neg = 0;
   for (int j = 0; j < 8; ++j) {
@@ -745,9 +806,9 @@ cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
-                            int want_cand, double* E, double* Ec, RateArgs ra, cudaStream_t st) {
+                            int want_cand, const int* order, double* E, double* Ec, RateArgs ra, cudaStream_t st) {
   if (nd == 0) return cudaSuccess;
-  k_energies<T><<<nd, 128, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, E, Ec, ra);
+  k_energies<T><<<nd, kEnergyThreads, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, order, E, Ec, ra);
   return cudaGetLastError();
 }
 cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
@@ -778,10 +839,10 @@ template cudaError_t launch_selfterm<float>(const C2<float>*, const PassCfg&, co
 template cudaError_t launch_selfterm<double>(const C2<double>*, const PassCfg&, const WBatch&, const double2*, const double2*,
                                             const double2*, double*, int, int, const double*, double, double*, cudaStream_t);
 template cudaError_t launch_energies<float>(const float*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
-                                           const uint8_t*, const double*, const double*, double, int, double*, double*,
-                                           RateArgs, cudaStream_t);
+                                           const uint8_t*, const double*, const double*, double, int, const int*, double*,
+                                           double*, RateArgs, cudaStream_t);
 template cudaError_t launch_energies<double>(const double*, int3, const okmc_defect*, const DefGeo*, int, const int*,
-                                            const int*, const uint8_t*, const double*, const double*, double, int, double*,
-                                            double*, RateArgs, cudaStream_t);
+                                            const int*, const uint8_t*, const double*, const double*, double, int, const int*,
+                                            double*, double*, RateArgs, cudaStream_t);
 
 }  // namespace okmc

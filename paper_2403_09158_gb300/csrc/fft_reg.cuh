@@ -102,8 +102,21 @@ struct XSkew {
   }
 };
 
+// Twiddles w_L^(n1*k2) as a padded [R1][R2 + 1] table: a warp's threads (consecutive
+// n1, one k2) then read distinct banks.  tw2 is filled by fill_tw2 from w_L^k.
+template <int L>
+__host__ __device__ constexpr int tw2_size() { return RegPlan<L>::R1 * (RegPlan<L>::R2 + 1); }
+template <int L>
+__device__ __forceinline__ void fill_tw2(C2<float>* tw2, const C2<float>* __restrict__ tw) {
+  constexpr int R2 = RegPlan<L>::R2;
+  for (int i = threadIdx.x; i < tw2_size<L>(); i += blockDim.x) {
+    const int n1 = i / (R2 + 1), k2 = i % (R2 + 1);
+    tw2[i] = k2 < R2 ? tw[n1 * k2] : C2<float>{1.f, 0.f};
+  }
+}
+
 template <bool INV, int L, class Ld, class Xch, class St>
-__device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const C2<float>* __restrict__ tw, int t,
+__device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const C2<float>* __restrict__ tw2, int t,
                                         bool active) {
   constexpr int R1 = RegPlan<L>::R1, R2 = RegPlan<L>::R2, NT = reg_nt<L>();
   constexpr int A = R1 / NT, B = R2 / NT;
@@ -123,7 +136,7 @@ __device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st
       x(n1, 0) = v[a][0];
 #pragma unroll
       for (int k2 = 1; k2 < R2; ++k2) {
-        C2<float> w = tw[n1 * k2];
+        C2<float> w = tw2[n1 * (R2 + 1) + k2];
         if (INV) w.y = -w.y;
         x(n1, k2) = v[a][k2] * w;
       }

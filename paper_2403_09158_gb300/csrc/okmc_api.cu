@@ -2,6 +2,7 @@
 // memory under an optional budget, validation, and the order of kernel launches
 // of each call.  All arithmetic of the method runs in the kernels of solve.cu
 // and defects.cu; this file only marshals, validates and sequences.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstdio>
@@ -45,7 +46,7 @@ cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
-                            int want_cand, double* E, double* Ec, RateArgs ra, cudaStream_t st);
+                            int want_cand, const int* order, double* E, double* Ec, RateArgs ra, cudaStream_t st);
 cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
                              Move* moves, DevState* stt, cudaStream_t st);
 cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* rates, double nu0, double kT, int3 n,
@@ -114,6 +115,7 @@ struct okmc_grid {
   double* d_W = nullptr;
   double* d_E = nullptr;
   double* d_Ec = nullptr;
+  int* d_order = nullptr;  // defects by decreasing stencil size (energy block order)
   double* d_rates = nullptr;
   double* d_rsum = nullptr;
   Move* d_moves = nullptr;
@@ -264,9 +266,9 @@ int energies(okmc_grid* g, int want_cand, double kT = 0.0) {
   return run(g, "energies", [&] {
     if (fp64(g))
       return launch_energies<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
-                                     g->d_alpha, g->d_W, pref, want_cand, g->d_E, g->d_Ec, ra, g->st);
+                                     g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->d_E, g->d_Ec, ra, g->st);
     return launch_energies<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
-                                  g->d_alpha, g->d_W, pref, want_cand, g->d_E, g->d_Ec, ra, g->st);
+                                  g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->d_E, g->d_Ec, ra, g->st);
   });
 }
 
@@ -389,7 +391,7 @@ int voxelise_all(okmc_grid* g) {
 void free_defects(okmc_grid* g) {
   void** bufs[] = {(void**)&g->d_def, (void**)&g->d_geo, (void**)&g->d_ptr, (void**)&g->d_off, (void**)&g->d_cnt,
                    (void**)&g->d_alpha, (void**)&g->d_sumcnt, (void**)&g->d_nnz, (void**)&g->d_W, (void**)&g->d_E,
-                   (void**)&g->d_Ec, (void**)&g->d_rates, (void**)&g->d_rsum, (void**)&g->d_moves, (void**)&g->d_pos};
+                   (void**)&g->d_Ec, (void**)&g->d_order, (void**)&g->d_rates, (void**)&g->d_rsum, (void**)&g->d_moves, (void**)&g->d_pos};
   for (void** b : bufs) {
     dfree(g, *b);
     *b = nullptr;
@@ -565,6 +567,7 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
     OKMC_TRY(dalloc(g, (void**)&g->d_E, n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_Ec, 8 * n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_rates, 8 * n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_order, n1 * sizeof(int)));
     OKMC_TRY(dalloc(g, (void**)&g->d_rsum, n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_moves, n1 * sizeof(Move)));
     OKMC_TRY(dalloc(g, (void**)&g->d_pos, 3 * n1 * sizeof(int)));
@@ -588,6 +591,12 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
         tot += nnz[k];
       }
       ptr[2 * nd] = (int)tot;
+      std::vector<int> order(nd);
+      for (int i = 0; i < nd; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nnz[2 * x] + nnz[2 * x + 1] > nnz[2 * y] + nnz[2 * y + 1]; });
+      e = cudaMemcpyAsync(g->d_order, order.data(), nd * sizeof(int), cudaMemcpyHostToDevice, g->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "energy order");
       if (tot > 0x7fffffffll) return fail(g, OKMC_ENOMEM, "too many stencil entries");
       OKMC_TRY(dalloc(g, (void**)&g->d_off, (size_t)tot * sizeof(int)));
       OKMC_TRY(dalloc(g, (void**)&g->d_cnt, (size_t)tot));

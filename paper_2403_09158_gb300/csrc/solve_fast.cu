@@ -34,12 +34,11 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }
 }  // namespace
 
-__device__ __forceinline__ void load_tw(C2<float>* twH, C2<float>* twY, C2<float>* untw, const PassCfg& c, int H, int NY) {
-  const C2<float>* gH = reinterpret_cast<const C2<float>*>(c.twH);
-  const C2<float>* gY = reinterpret_cast<const C2<float>*>(c.twY);
+template <int H, int NY>
+__device__ __forceinline__ void load_tw(C2<float>* twH, C2<float>* twY, C2<float>* untw, const PassCfg& c) {
+  fill_tw2<H>(twH, reinterpret_cast<const C2<float>*>(c.twH));
+  fill_tw2<NY>(twY, reinterpret_cast<const C2<float>*>(c.twY));
   const C2<float>* gU = reinterpret_cast<const C2<float>*>(c.untw);
-  for (int i = threadIdx.x; i < H; i += blockDim.x) twH[i] = gH[i];
-  for (int i = threadIdx.x; i < NY; i += blockDim.x) twY[i] = gY[i];
   for (int i = threadIdx.x; i <= H; i += blockDim.x) untw[i] = gU[i];
 }
 
@@ -64,12 +63,20 @@ struct NShape {
 template <int H, int NY>
 __host__ __device__ constexpr size_t nfwd_smem(int cs) {
   using S = NShape<H, NY>;
-  return sizeof(C2<float>) * ((size_t)(H / cs) * S::LDC + (size_t)S::GR * S::XS + H + NY + H + 1);
+  return sizeof(C2<float>) * ((size_t)(H / cs) * S::LDC + (size_t)S::GR * S::XS + tw2_size<H>() + tw2_size<NY>() + H + 1);
 }
 template <int H, int NY>
 __host__ __device__ constexpr size_t ninv_smem(int cs) {
   using S = NShape<H, NY>;
-  return sizeof(C2<float>) * ((size_t)(NY / cs) * S::LDR + (size_t)S::XB + H + NY + H + 1);
+  return sizeof(C2<float>) * ((size_t)(NY / cs) * S::LDR + (size_t)S::XB + tw2_size<H>() + tw2_size<NY>() + H + 1);
+}
+
+// store v at column k, row y of the column buffer of the CTA that owns column k
+template <int CS, int CPER, int LDC>
+__device__ __forceinline__ void put_col(cg::cluster_group& cluster, C2<float>* col, int h, int k, int y, C2<float> v) {
+  const int owner = k / CPER;
+  C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(col, owner) : col;
+  base[(k % CPER) * LDC + y] = v;
 }
 
 template <int H, int NY, int CS>
@@ -81,18 +88,15 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
   C2<float>* col = reinterpret_cast<C2<float>*>(smem_raw);  // [CPER][LDC]
   C2<float>* xb = col + CPER * S::LDC;                       // [GR][XS]
   C2<float>* twH = xb + S::GR * S::XS;
-  C2<float>* twY = twH + H;
-  C2<float>* untw = twY + NY;
+  C2<float>* twY = twH + tw2_size<H>();
+  C2<float>* untw = twY + tw2_size<NY>();
   cg::cluster_group cluster = cg::this_cluster();
   const int h = CS > 1 ? (int)cluster.block_rank() : 0;
   const int plane = blockIdx.y;
   const int tid = threadIdx.x;
   const size_t P = (size_t)(H + 1) * NY;
   const float q = (float)c.q;
-  load_tw(twH, twY, untw, c, H, NY);
-  C2<float>* rcol[CS];
-#pragma unroll
-  for (int r = 0; r < CS; ++r) rcol[r] = (CS > 1 && r != h) ? cluster.map_shared_rank(col, r) : col;
+  load_tw<H, NY>(twH, twY, untw, c);
   __syncthreads();
   {  // rows along x
     const int g = tid / S::NTH, t = tid % S::NTH;
@@ -108,17 +112,25 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
       auto st = [&](int k, C2<float> v) { xg[k] = v; };
       reg_fft<false, H>(ld, XPad<S::R2H>{xg}, st, twH, t, act);
       if (act) {
-        for (int k = t; k < H; k += S::NTH) {
+        // X[k] = (A + B)/2 - (i/2) w^k (A - B) and X[H-k] = conj((A + B)/2) - (i/2) w^(H-k) conj(B - A)
+        // from the same A = Z[k], B = conj Z[H-k]; k = 0 packs (X[0], X[nx/2])
+#pragma unroll
+        for (int j = 0; j <= H / 2 / S::NTH; ++j) {
+          const int k = t + S::NTH * j;
+          if (k > H / 2) break;
           const C2<float> A = xg[k];
-          C2<float> X;
           if (k == 0) {
-            X = C2<float>{A.x + A.y, A.x - A.y};  // (X[0], X[nx/2]), both real
-          } else {
-            const C2<float> B = conjg(xg[H - k]);
-            const C2<float> sum = A + B, dif = untw[k] * (A - B);
-            X = C2<float>{0.5f * (sum.x + dif.y), 0.5f * (sum.y - dif.x)};
+            put_col<CS, CPER, S::LDC>(cluster, col, h, 0, y, C2<float>{A.x + A.y, A.x - A.y});
+            continue;
           }
-          rcol[k / CPER][(k % CPER) * S::LDC + y] = X;
+          const C2<float> B = conjg(xg[H - k]);
+          const C2<float> sum = A + B, d1 = untw[k] * (A - B);
+          put_col<CS, CPER, S::LDC>(cluster, col, h, k, y, C2<float>{0.5f * (sum.x + d1.y), 0.5f * (sum.y - d1.x)});
+          if (2 * k != H) {
+            const C2<float> d2 = untw[H - k] * conjg(B - A);
+            put_col<CS, CPER, S::LDC>(cluster, col, h, H - k, y,
+                                      C2<float>{0.5f * (sum.x + d2.y), 0.5f * (-sum.y - d2.x)});
+          }
         }
       }
       __syncwarp();
@@ -163,17 +175,14 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   C2<float>* rowb = reinterpret_cast<C2<float>*>(smem_raw);  // [ROWS][LDR]
   C2<float>* xb = rowb + ROWS * S::LDR;
   C2<float>* twH = xb + S::XB;
-  C2<float>* twY = twH + H;
-  C2<float>* untw = twY + NY;
+  C2<float>* twY = twH + tw2_size<H>();
+  C2<float>* untw = twY + tw2_size<NY>();
   cg::cluster_group cluster = cg::this_cluster();
   const int h = CS > 1 ? (int)cluster.block_rank() : 0;
   const int plane = blockIdx.y;
   const int tid = threadIdx.x;
   const size_t P = (size_t)(H + 1) * NY;
-  load_tw(twH, twY, untw, c, H, NY);
-  C2<float>* rrow[CS];
-#pragma unroll
-  for (int r = 0; r < CS; ++r) rrow[r] = (CS > 1 && r != h) ? cluster.map_shared_rank(rowb, r) : rowb;
+  load_tw<H, NY>(twH, twY, untw, c);
   __syncthreads();
   {  // inverse columns along y, scattered to the row owners
     const int g = tid / S::NTY, t = tid % S::NTY;
@@ -190,7 +199,11 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
         const C2<float> B = nyq[i];
         return C2<float>{A.x - B.y, A.y + B.x};  // A + i B
       };
-      auto st = [&](int k, C2<float> v) { rrow[k / ROWS][(k % ROWS) * S::LDR + kx] = v; };
+      auto st = [&](int k, C2<float> v) {
+        const int owner = k / ROWS;
+        C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
+        base[(k % ROWS) * S::LDR + kx] = v;
+      };
       reg_fft<true, NY>(ld, XPad<S::R2Y>{xg}, st, twY, t, act);
     }
   }
@@ -224,7 +237,7 @@ constexpr int kLDT = kTW + 1;  // padded row of a tile: conflict-free strided li
 
 template <int NZ>
 __host__ __device__ constexpr size_t pencil_fast_smem() {
-  return sizeof(C2<float>) * ((size_t)6 * NZ * kLDT + NZ);
+  return sizeof(C2<float>) * ((size_t)6 * NZ * kLDT + tw2_size<NZ>());
 }
 
 
@@ -241,10 +254,7 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(C2<float>* __restrict__ s
     const int t = idx & (kTW - 1), kz = (idx >> 3) % NZ, comp = idx / (kTW * NZ);
     cp_async8(tile + (comp * NZ + kz) * kLDT + t, spec + ((size_t)comp * NZ + kz) * P + p0 + t);
   }
-  {
-    const C2<float>* gZ = reinterpret_cast<const C2<float>*>(c.twZ);
-    for (int i = tid; i < NZ; i += kT) twZ[i] = gZ[i];
-  }
+  fill_tw2<NZ>(twZ, reinterpret_cast<const C2<float>*>(c.twZ));
   cp_async_wait_all();
   __syncthreads();
   constexpr int NTZ = reg_nt<NZ>(), GL = kT / NTZ, R2Z = RegPlan<NZ>::R2;
