@@ -188,6 +188,27 @@ int okmc_step(okmc_grid* g, const okmc_step_params* p, int64_t n_steps, okmc_ste
 /* Cumulative statistics (host). */
 int okmc_get_stats(okmc_grid* g, okmc_step_stats* out);
 
+/* okmc_step replays a captured CUDA graph of one step (solve, energies and rates,
+ * event, incremental field update), one graph per (mode, T), captured on first use
+ * and dropped by okmc_set_defects.  enable = 0 launches kernel by kernel instead
+ * (kernel timing, see okmc_set_profiling, always does). */
+int okmc_set_graphs(okmc_grid* g, int enable);
+
+/* Batches: many independent replicas (handles of any grid size and defect count on
+ * the same GPU) advanced together.  okmc_batch_step captures every replica's step as
+ * an independent branch of one CUDA graph and launches that graph n_steps times on
+ * the batch stream, so the replicas' kernels overlap on the device.  params[n] and
+ * stats[n] (nullable) are per replica; t_end must be 0.  The graph is re-captured
+ * when a replica's mode or temperature changes or after okmc_set_defects on a
+ * replica.  The handles stay owned by the
+ * caller and must outlive the batch; their own streams are synchronised before the
+ * batch runs.  Results are those of okmc_step on each handle alone. */
+typedef struct okmc_batch okmc_batch;
+int okmc_batch_create(okmc_grid* const* grids, int32_t n, void* stream, okmc_batch** out);
+int okmc_batch_step(okmc_batch* b, const okmc_step_params* params, int64_t n_steps, okmc_step_stats* stats);
+int okmc_batch_destroy(okmc_batch* b);
+const char* okmc_batch_last_error(const okmc_batch* b);
+
 /* Device bytes held by the handle. */
 size_t okmc_device_bytes(const okmc_grid* g);
 
@@ -202,7 +223,9 @@ int okmc_reset_kernel_times(okmc_grid* g);
 
 /* Number of CTAs in each launch of the pass kernels and the cluster size the
  * handle picked for its grid (diagnostics): out[0..2] = cluster size of the
- * forward plane pass, CTAs of the pencil pass, cluster size of the inverse pass. */
+ * forward plane pass, CTAs of the pencil pass, cluster size of the inverse pass.
+ * out[0] = out[2] = -1 when the grid runs the register-FFT passes (FP32 fields,
+ * nx = ny and nx, nz in {32, 48, 64, 96, 128, 160, 192, 256, 320}). */
 int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
 
 /* Allocation-free stress solve (the paper has no counterpart; this is a service for

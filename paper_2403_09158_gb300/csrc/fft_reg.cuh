@@ -1,4 +1,5 @@
-// Register-resident line FFTs for power-of-two lengths 16..256 (FP32).
+// Register-resident line FFTs (FP32) for lengths 16..320 of the form 2^a 3^b 5^c used by
+// the fast passes.
 //
 // A line of length L = R1*R2 is transformed by a group of NT = min(R1, R2)
 // consecutive threads of one warp in two steps (Cooley-Tukey, n = n1 + R1*n2,
@@ -16,12 +17,22 @@
 
 namespace okmc {
 
+// L = R1 * R2 with R1 <= R2; NT = R1 threads per line; each thread does one length-R2
+// DFT in step 1 and ceil(R2 / R1) length-R1 DFTs in step 2 (the last round partial
+// when R1 does not divide R2).
 template <int L> struct RegPlan;
 template <> struct RegPlan<16> { static constexpr int R1 = 4, R2 = 4; };
+template <> struct RegPlan<24> { static constexpr int R1 = 4, R2 = 6; };
 template <> struct RegPlan<32> { static constexpr int R1 = 4, R2 = 8; };
+template <> struct RegPlan<48> { static constexpr int R1 = 4, R2 = 12; };
 template <> struct RegPlan<64> { static constexpr int R1 = 8, R2 = 8; };
+template <> struct RegPlan<80> { static constexpr int R1 = 4, R2 = 20; };
+template <> struct RegPlan<96> { static constexpr int R1 = 8, R2 = 12; };
 template <> struct RegPlan<128> { static constexpr int R1 = 8, R2 = 16; };
+template <> struct RegPlan<160> { static constexpr int R1 = 8, R2 = 20; };
+template <> struct RegPlan<192> { static constexpr int R1 = 8, R2 = 24; };
 template <> struct RegPlan<256> { static constexpr int R1 = 16, R2 = 16; };
+template <> struct RegPlan<320> { static constexpr int R1 = 16, R2 = 20; };
 template <int L> __host__ __device__ constexpr int reg_nt() { return RegPlan<L>::R1 < RegPlan<L>::R2 ? RegPlan<L>::R1 : RegPlan<L>::R2; }
 
 // cos and sin of 2 pi e / 16 for e = 0..15
@@ -78,11 +89,247 @@ __device__ __forceinline__ void dft16(C2<float>* v) {
   }
 }
 
+template <int N> __device__ __forceinline__ float cosN(int e);
+template <int N> __device__ __forceinline__ float sinN(int e);
+// cos and sin of 2 pi e / N for the composite register DFTs (e = 0..N-1)
+template <> __device__ __forceinline__ float cosN<6>(int e) {
+  switch (e) {
+    case 0: return 1.0f;
+    case 1: return 0.5f;
+    case 2: return -0.5f;
+    case 3: return -1.0f;
+    case 4: return -0.5f;
+    default: return 0.5f;
+  }
+}
+template <> __device__ __forceinline__ float sinN<6>(int e) {
+  switch (e) {
+    case 0: return 0.0f;
+    case 1: return 0.8660254037844386f;
+    case 2: return 0.86602540378443871f;
+    case 3: return 0.0f;
+    case 4: return -0.86602540378443837f;
+    default: return -0.8660254037844386f;
+  }
+}
+template <> __device__ __forceinline__ float cosN<10>(int e) {
+  switch (e) {
+    case 0: return 1.0f;
+    case 1: return 0.80901699437494745f;
+    case 2: return 0.30901699437494745f;
+    case 3: return -0.30901699437494734f;
+    case 4: return -0.80901699437494734f;
+    case 5: return -1.0f;
+    case 6: return -0.80901699437494756f;
+    case 7: return -0.30901699437494756f;
+    case 8: return 0.30901699437494723f;
+    default: return 0.80901699437494734f;
+  }
+}
+template <> __device__ __forceinline__ float sinN<10>(int e) {
+  switch (e) {
+    case 0: return 0.0f;
+    case 1: return 0.58778525229247314f;
+    case 2: return 0.95105651629515353f;
+    case 3: return 0.95105651629515364f;
+    case 4: return 0.58778525229247325f;
+    case 5: return 0.0f;
+    case 6: return -0.58778525229247303f;
+    case 7: return -0.95105651629515353f;
+    case 8: return -0.95105651629515364f;
+    default: return -0.58778525229247336f;
+  }
+}
+template <> __device__ __forceinline__ float cosN<12>(int e) {
+  switch (e) {
+    case 0: return 1.0f;
+    case 1: return 0.86602540378443871f;
+    case 2: return 0.5f;
+    case 3: return 0.0f;
+    case 4: return -0.5f;
+    case 5: return -0.86602540378443871f;
+    case 6: return -1.0f;
+    case 7: return -0.86602540378443882f;
+    case 8: return -0.5f;
+    case 9: return 0.0f;
+    case 10: return 0.5f;
+    default: return 0.86602540378443837f;
+  }
+}
+template <> __device__ __forceinline__ float sinN<12>(int e) {
+  switch (e) {
+    case 0: return 0.0f;
+    case 1: return 0.5f;
+    case 2: return 0.8660254037844386f;
+    case 3: return 1.0f;
+    case 4: return 0.86602540378443871f;
+    case 5: return 0.5f;
+    case 6: return 0.0f;
+    case 7: return -0.5f;
+    case 8: return -0.86602540378443837f;
+    case 9: return -1.0f;
+    case 10: return -0.8660254037844386f;
+    default: return -0.5f;
+  }
+}
+template <> __device__ __forceinline__ float cosN<20>(int e) {
+  switch (e) {
+    case 0: return 1.0f;
+    case 1: return 0.95105651629515353f;
+    case 2: return 0.80901699437494745f;
+    case 3: return 0.58778525229247314f;
+    case 4: return 0.30901699437494745f;
+    case 5: return 0.0f;
+    case 6: return -0.30901699437494734f;
+    case 7: return -0.58778525229247303f;
+    case 8: return -0.80901699437494734f;
+    case 9: return -0.95105651629515353f;
+    case 10: return -1.0f;
+    case 11: return -0.95105651629515375f;
+    case 12: return -0.80901699437494756f;
+    case 13: return -0.58778525229247325f;
+    case 14: return -0.30901699437494756f;
+    case 15: return 0.0f;
+    case 16: return 0.30901699437494723f;
+    case 17: return 0.58778525229247292f;
+    case 18: return 0.80901699437494734f;
+    default: return 0.95105651629515353f;
+  }
+}
+template <> __device__ __forceinline__ float sinN<20>(int e) {
+  switch (e) {
+    case 0: return 0.0f;
+    case 1: return 0.3090169943749474f;
+    case 2: return 0.58778525229247314f;
+    case 3: return 0.80901699437494745f;
+    case 4: return 0.95105651629515353f;
+    case 5: return 1.0f;
+    case 6: return 0.95105651629515364f;
+    case 7: return 0.80901699437494745f;
+    case 8: return 0.58778525229247325f;
+    case 9: return 0.30901699437494751f;
+    case 10: return 0.0f;
+    case 11: return -0.3090169943749469f;
+    case 12: return -0.58778525229247303f;
+    case 13: return -0.80901699437494734f;
+    case 14: return -0.95105651629515353f;
+    case 15: return -1.0f;
+    case 16: return -0.95105651629515364f;
+    case 17: return -0.80901699437494756f;
+    case 18: return -0.58778525229247336f;
+    default: return -0.30901699437494762f;
+  }
+}
+template <> __device__ __forceinline__ float cosN<24>(int e) {
+  switch (e) {
+    case 0: return 1.0f;
+    case 1: return 0.96592582628906831f;
+    case 2: return 0.86602540378443871f;
+    case 3: return 0.70710678118654757f;
+    case 4: return 0.5f;
+    case 5: return 0.25881904510252074f;
+    case 6: return 0.0f;
+    case 7: return -0.25881904510252063f;
+    case 8: return -0.5f;
+    case 9: return -0.70710678118654746f;
+    case 10: return -0.86602540378443871f;
+    case 11: return -0.9659258262890682f;
+    case 12: return -1.0f;
+    case 13: return -0.96592582628906831f;
+    case 14: return -0.86602540378443882f;
+    case 15: return -0.70710678118654791f;
+    case 16: return -0.5f;
+    case 17: return -0.25881904510252063f;
+    case 18: return 0.0f;
+    case 19: return 0.2588190451025203f;
+    case 20: return 0.5f;
+    case 21: return 0.70710678118654735f;
+    case 22: return 0.86602540378443837f;
+    default: return 0.96592582628906809f;
+  }
+}
+template <> __device__ __forceinline__ float sinN<24>(int e) {
+  switch (e) {
+    case 0: return 0.0f;
+    case 1: return 0.25881904510252074f;
+    case 2: return 0.5f;
+    case 3: return 0.70710678118654746f;
+    case 4: return 0.8660254037844386f;
+    case 5: return 0.96592582628906831f;
+    case 6: return 1.0f;
+    case 7: return 0.96592582628906831f;
+    case 8: return 0.86602540378443871f;
+    case 9: return 0.70710678118654757f;
+    case 10: return 0.5f;
+    case 11: return 0.25881904510252102f;
+    case 12: return 0.0f;
+    case 13: return -0.25881904510252079f;
+    case 14: return -0.5f;
+    case 15: return -0.70710678118654713f;
+    case 16: return -0.86602540378443837f;
+    case 17: return -0.96592582628906831f;
+    case 18: return -1.0f;
+    case 19: return -0.96592582628906842f;
+    case 20: return -0.8660254037844386f;
+    case 21: return -0.70710678118654768f;
+    case 22: return -0.5f;
+    default: return -0.25881904510252157f;
+  }
+}
+
+// Composite register DFT of size R = P * Q (Cooley-Tukey in registers):
+// n = n1 + P n2, k = k2 + Q k1; twiddles exp(-+2 pi i n1 k2 / R) from the tables above.
+template <int R> struct Split;
+template <> struct Split<6> { static constexpr int P = 2, Q = 3; };
+template <> struct Split<10> { static constexpr int P = 2, Q = 5; };
+template <> struct Split<12> { static constexpr int P = 4, Q = 3; };
+template <> struct Split<20> { static constexpr int P = 4, Q = 5; };
+template <> struct Split<24> { static constexpr int P = 8, Q = 3; };
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_reg(C2<float>* v);
+
+template <int R, bool INV>
+__device__ __forceinline__ void dft_composite(C2<float>* v) {
+  constexpr int P = Split<R>::P, Q = Split<R>::Q;
+  C2<float> y[R];
+#pragma unroll
+  for (int n1 = 0; n1 < P; ++n1) {
+    C2<float> a[Q];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) a[n2] = v[n1 + P * n2];
+    dft_reg<Q, INV>(a);
+#pragma unroll
+    for (int k2 = 0; k2 < Q; ++k2) {
+      const int e = (n1 * k2) % R;
+      if (e == 0) {
+        y[n1 * Q + k2] = a[k2];
+      } else {
+        const float c = cosN<R>(e), s = INV ? sinN<R>(e) : -sinN<R>(e);
+        y[n1 * Q + k2] = C2<float>{a[k2].x * c - a[k2].y * s, a[k2].x * s + a[k2].y * c};
+      }
+    }
+  }
+#pragma unroll
+  for (int k2 = 0; k2 < Q; ++k2) {
+    C2<float> b[P];
+#pragma unroll
+    for (int n1 = 0; n1 < P; ++n1) b[n1] = y[n1 * Q + k2];
+    dft_reg<P, INV>(b);
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) v[k2 + Q * k1] = b[k1];
+  }
+}
+
 template <int R, bool INV>
 __device__ __forceinline__ void dft_reg(C2<float>* v) {
-  if constexpr (R == 4) dft4<float, INV>(v);
+  if constexpr (R == 2) dft2<float, INV>(v);
+  else if constexpr (R == 3) dft3<float, INV>(v);
+  else if constexpr (R == 4) dft4<float, INV>(v);
+  else if constexpr (R == 5) dft5<float, INV>(v);
   else if constexpr (R == 8) dft8<float, INV>(v);
-  else dft16<INV>(v);
+  else if constexpr (R == 16) dft16<INV>(v);
+  else dft_composite<R, INV>(v);
 }
 
 // exchange slots: padded [R1][R2 + 1] rows
@@ -97,8 +344,10 @@ template <int R2>
 struct XSkew {
   C2<float>* p;
   int s;
-  __device__ __forceinline__ C2<float>& operator()(int n1, int k2) const {
-    return p[s * (n1 * R2 + ((k2 + n1) & (R2 - 1)))];
+  __device__ __forceinline__ C2<float>& operator()(int n1, int k2) const {  // n1 < R2
+    int m = k2 + n1;
+    if (m >= R2) m -= R2;
+    return p[s * (n1 * R2 + m)];
   }
 };
 
@@ -119,7 +368,8 @@ template <bool INV, int L, class Ld, class Xch, class St>
 __device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const C2<float>* __restrict__ tw2, int t,
                                         bool active) {
   constexpr int R1 = RegPlan<L>::R1, R2 = RegPlan<L>::R2, NT = reg_nt<L>();
-  constexpr int A = R1 / NT, B = R2 / NT;
+  constexpr int A = R1 / NT, B = (R2 + NT - 1) / NT;
+  static_assert(R1 % NT == 0, "step 1 needs whole DFTs per thread");
   C2<float> v[A][R2];
   if (active) {
 #pragma unroll
@@ -147,17 +397,20 @@ __device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st
   if (active) {
 #pragma unroll
     for (int b = 0; b < B; ++b)
+      if (R2 % NT == 0 || t + NT * b < R2) {
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) u[b][n1] = x(n1, t + NT * b);
+        for (int n1 = 0; n1 < R1; ++n1) u[b][n1] = x(n1, t + NT * b);
+      }
   }
   __syncwarp();
   if (active) {
 #pragma unroll
-    for (int b = 0; b < B; ++b) {
-      dft_reg<R1, INV>(u[b]);
+    for (int b = 0; b < B; ++b)
+      if (R2 % NT == 0 || t + NT * b < R2) {
+        dft_reg<R1, INV>(u[b]);
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) st(t + NT * b + R2 * k1, u[b][k1]);
-    }
+        for (int k1 = 0; k1 < R1; ++k1) st(t + NT * b + R2 * k1, u[b][k1]);
+      }
   }
   __syncwarp();
 }

@@ -134,6 +134,26 @@ struct okmc_grid {
   std::vector<cudaEvent_t> free_events;
   std::map<std::string, std::pair<double, long long>> prof;
   std::vector<std::string> prof_names;
+  // captured step graphs, one per (mode, temperature)
+  struct StepGraph {
+    int mode;
+    double T;
+    cudaGraphExec_t exec;
+  };
+  std::vector<StepGraph> graphs;
+  bool use_graphs = true;
+  long long gen = 0;  // bumped by okmc_set_defects (device buffers may move)
+};
+
+struct okmc_batch {
+  std::vector<okmc_grid*> grids;
+  std::vector<long long> gens;
+  std::vector<okmc_step_params> params;
+  cudaStream_t st = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> ev;
+  std::string err;
 };
 
 namespace {
@@ -399,6 +419,60 @@ void free_defects(okmc_grid* g) {
   g->nd = 0;
 }
 
+// Kernels of one step (solve, energies + rates, event, incremental field update)
+// on g->st.  With capture set the solve is always included.
+int step_body(okmc_grid* g, int mode, double kT, bool capture) {
+  if (capture) g->sigma_valid = false;
+  OKMC_TRY(energies(g, 1, kT));
+  if (mode == OKMC_RESIDENCE) {
+    OKMC_TRY(run(g, "event_residence", [&] {
+      return launch_residence(g->d_def, g->nd, g->d_rates, g->d_rsum, dims(g), g->desc.seed, g->d_moves, g->d_state, g->st);
+    }));
+    OKMC_TRY(apply_moves(g, 1));
+  } else {
+    OKMC_TRY(run(g, "event_fixed_dt", [&] {
+      return launch_fixed_dt(g->d_def, g->d_geo, g->nd, g->d_rates, g->nu0, kT, dims(g), g->desc.seed, g->d_moves,
+                             g->d_state, g->st);
+    }));
+    OKMC_TRY(apply_moves(g, g->nd));
+  }
+  g->sigma_valid = false;
+  return OKMC_OK;
+}
+
+void drop_graphs(okmc_grid* g) {
+  for (auto& s : g->graphs) cudaGraphExecDestroy(s.exec);
+  g->graphs.clear();
+}
+
+// Capture one step of g into a graph on a private stream (the handle's stream may be
+// the legacy stream, which cannot be captured); the graph is launched on g->st.
+int capture_step(okmc_grid* g, int mode, double T, cudaGraphExec_t* out) {
+  cudaStream_t cs;
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(g, e, "capture stream");
+  cudaStream_t keep = g->st;
+  const bool prof = g->profiling;
+  g->profiling = false;
+  g->st = cs;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  int rc = (e == cudaSuccess) ? step_body(g, mode, kBoltzmann * T, true) : cuda_fail(g, e, "begin capture");
+  cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+  g->st = keep;
+  g->profiling = prof;
+  cudaStreamDestroy(cs);
+  if (rc != OKMC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e2 != cudaSuccess) return cuda_fail(g, e2, "end capture");
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
+  return OKMC_OK;
+}
+
 }  // namespace
 
 // ================================================================== C ABI
@@ -532,6 +606,7 @@ int okmc_grid_destroy(okmc_grid* g) {
     cudaEventDestroy(p.b);
   }
   for (auto ev : g->free_events) cudaEventDestroy(ev);
+  drop_graphs(g);
   for (auto& a : g->allocs) cudaFree(a.first);
   delete g;
   return OKMC_OK;
@@ -551,6 +626,8 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
   try {
     OKMC_TRY(validate_defects(g, defs, nd));
     cudaStreamSynchronize(g->st);
+    drop_graphs(g);
+    g->gen += 1;
     free_defects(g);
     g->h_def.assign(defs, defs + nd);
     g->nd = nd;
@@ -766,21 +843,26 @@ int okmc_step(okmc_grid* g, const okmc_step_params* p, int64_t n_steps, okmc_ste
   if (n_steps < 0) return fail(g, OKMC_EINVAL, "negative step count");
   if (!g->nd || !g->any_mobile) return fail(g, OKMC_ESTATE, "no mobile defect");
   const double kT = kBoltzmann * p->T_K;
-  for (int64_t s = 0; s < n_steps; ++s) {
-    OKMC_TRY(energies(g, 1, kT));
-    if (p->mode == OKMC_RESIDENCE) {
-      OKMC_TRY(run(g, "event_residence", [&] {
-        return launch_residence(g->d_def, g->nd, g->d_rates, g->d_rsum, dims(g), g->desc.seed, g->d_moves, g->d_state, g->st);
-      }));
-      OKMC_TRY(apply_moves(g, 1));
-    } else {
-      OKMC_TRY(run(g, "event_fixed_dt", [&] {
-        return launch_fixed_dt(g->d_def, g->d_geo, g->nd, g->d_rates, g->nu0, kT, dims(g), g->desc.seed, g->d_moves,
-                               g->d_state, g->st);
-      }));
-      OKMC_TRY(apply_moves(g, g->nd));
+  // Steady state: replay a captured graph of the step (one launch per step).  With
+  // kernel timing on, launch kernel by kernel so that each one can be timed.
+  cudaGraphExec_t exec = nullptr;
+  if (g->use_graphs && !g->profiling && n_steps > 0) {
+    for (auto& s : g->graphs)
+      if (s.mode == p->mode && s.T == p->T_K) exec = s.exec;
+    if (!exec) {
+      OKMC_TRY(capture_step(g, p->mode, p->T_K, &exec));
+      g->graphs.push_back({p->mode, p->T_K, exec});
     }
-    g->sigma_valid = false;
+  }
+  for (int64_t s = 0; s < n_steps; ++s) {
+    if (exec) {
+      cudaError_t e = cudaGraphLaunch(exec, g->st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "graph launch");
+      g->solves += 1;
+      g->sigma_valid = false;
+    } else {
+      OKMC_TRY(step_body(g, p->mode, kT, false));
+    }
     if (p->t_end > 0.0) {
       okmc_step_stats tmp;
       OKMC_TRY(okmc_get_stats(g, &tmp));
@@ -788,6 +870,140 @@ int okmc_step(okmc_grid* g, const okmc_step_params* p, int64_t n_steps, okmc_ste
     }
   }
   if (out) OKMC_TRY(okmc_get_stats(g, out));
+  return OKMC_OK;
+}
+
+int okmc_set_graphs(okmc_grid* g, int enable) {
+  if (!g) return OKMC_EINVAL;
+  g->use_graphs = enable != 0;
+  return OKMC_OK;
+}
+
+// ---------------------------------------------------------------- batches
+int okmc_batch_create(okmc_grid* const* grids, int32_t n, void* stream, okmc_batch** out) {
+  if (!grids || n <= 0 || !out) return OKMC_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!grids[i]) return OKMC_EINVAL;
+  okmc_batch* b = new (std::nothrow) okmc_batch();
+  if (!b) return OKMC_ENOMEM;
+  b->grids.assign(grids, grids + n);
+  b->st = (cudaStream_t)stream;
+  *out = b;
+  return OKMC_OK;
+}
+
+int okmc_batch_destroy(okmc_batch* b) {
+  if (!b) return OKMC_OK;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (auto s : b->side) cudaStreamDestroy(s);
+  for (auto e : b->ev) cudaEventDestroy(e);
+  delete b;
+  return OKMC_OK;
+}
+
+const char* okmc_batch_last_error(const okmc_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+// One graph holds every replica's step as an independent branch (fork/join on
+// private streams); each launch advances all replicas by one step, and their
+// kernels overlap on the GPU.
+static int batch_build(okmc_batch* b) {
+  const int n = (int)b->grids.size();
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  while ((int)b->side.size() < n + 1) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return OKMC_ECUDA;
+    b->side.push_back(s);
+  }
+  while ((int)b->ev.size() < 2 * n + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return OKMC_ECUDA;
+    b->ev.push_back(e);
+  }
+  cudaStream_t root = b->side[n];
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return OKMC_ECUDA;
+  int rc = OKMC_OK;
+  if (cudaEventRecord(b->ev[2 * n], root) != cudaSuccess) rc = OKMC_ECUDA;
+  for (int i = 0; i < n && rc == OKMC_OK; ++i) {
+    okmc_grid* g = b->grids[i];
+    const okmc_step_params& p = b->params[i];
+    if (cudaStreamWaitEvent(b->side[i], b->ev[2 * n], 0) != cudaSuccess) { rc = OKMC_ECUDA; break; }
+    cudaStream_t keep = g->st;
+    const bool prof = g->profiling;
+    g->st = b->side[i];
+    g->profiling = false;
+    rc = step_body(g, p.mode, kBoltzmann * p.T_K, true);
+    g->st = keep;
+    g->profiling = prof;
+    if (rc != OKMC_OK) {
+      b->err = "replica " + std::to_string(i) + ": " + g->err;
+      break;
+    }
+    if (cudaEventRecord(b->ev[i], b->side[i]) != cudaSuccess || cudaStreamWaitEvent(root, b->ev[i], 0) != cudaSuccess)
+      rc = OKMC_ECUDA;
+  }
+  cudaError_t e = cudaStreamEndCapture(root, &graph);
+  if (rc != OKMC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return OKMC_ECUDA;
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  return e == cudaSuccess ? OKMC_OK : OKMC_ECUDA;
+}
+
+int okmc_batch_step(okmc_batch* b, const okmc_step_params* params, int64_t n_steps, okmc_step_stats* stats) {
+  if (!b || !params || n_steps < 0) return OKMC_EINVAL;
+  const int n = (int)b->grids.size();
+  bool same = (int)b->params.size() == n;
+  for (int i = 0; i < n; ++i) {
+    const okmc_step_params& p = params[i];
+    okmc_grid* g = b->grids[i];
+    if (!(p.T_K > 0.0) || (p.mode != OKMC_RESIDENCE && p.mode != OKMC_FIXED_DT) || p.t_end != 0.0) {
+      b->err = "replica " + std::to_string(i) + ": bad step parameters (t_end must be 0 in a batch)";
+      return OKMC_EINVAL;
+    }
+    if (!g->nd || !g->any_mobile) {
+      b->err = "replica " + std::to_string(i) + ": no mobile defect";
+      return OKMC_ESTATE;
+    }
+    if (same && (b->params[i].mode != p.mode || b->params[i].T_K != p.T_K)) same = false;
+    if ((int)b->gens.size() != n || b->gens[i] != g->gen) same = false;
+  }
+  if (!same || !b->exec) {
+    b->params.assign(params, params + n);
+    b->gens.resize(n);
+    for (int i = 0; i < n; ++i) b->gens[i] = b->grids[i]->gen;
+    const int rc = batch_build(b);
+    if (rc != OKMC_OK) {
+      if (b->err.empty()) b->err = "batch graph capture failed";
+      return rc;
+    }
+  }
+  // the replicas' own streams must not have work in flight that the batch could race
+  for (auto* g : b->grids) cudaStreamSynchronize(g->st);
+  for (int64_t s = 0; s < n_steps; ++s) {
+    cudaError_t e = cudaGraphLaunch(b->exec, b->st);
+    if (e != cudaSuccess) {
+      b->err = std::string("graph launch: ") + cudaGetErrorString(e);
+      return OKMC_ECUDA;
+    }
+  }
+  if (cudaStreamSynchronize(b->st) != cudaSuccess) return OKMC_ECUDA;
+  for (int i = 0; i < n; ++i) {
+    okmc_grid* g = b->grids[i];
+    g->solves += n_steps;
+    g->sigma_valid = false;
+    if (stats) {
+      const int rc = okmc_get_stats(g, &stats[i]);
+      if (rc != OKMC_OK) return rc;
+    }
+  }
   return OKMC_OK;
 }
 

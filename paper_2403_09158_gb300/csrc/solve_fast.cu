@@ -1,4 +1,4 @@
-// Fast FP32 solve passes for power-of-two edges (nx = ny and nz in 32..256): the same three passes and data layout as solve.cu, with register
+// Fast FP32 solve passes for nx = ny and nz in {32, 48, 64, 96, 128, 160, 192, 256, 320}: the same three passes and data layout as solve.cu, with register
 // line FFTs (fft_reg.cuh) instead of the generic shared-memory Stockham engine,
 // loads issued a whole line (or a whole tile) ahead, and clusters sized so that
 // two CTAs share each SM.
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
       if (act && packed) {
         // P = A + i B, A and B the spectra of the real columns X[0] and X[nx/2]
         for (int k = t; k < NY; k += S::NTY) {
-          const C2<float> Pk = cp[k], Pm = conjg(cp[(NY - k) & (NY - 1)]);
+          const C2<float> Pk = cp[k], Pm = conjg(cp[k == 0 ? 0 : NY - k]);
           const C2<float> s = Pk + Pm, d = Pk - Pm;
           out[k] = C2<float>{0.5f * s.x, 0.5f * s.y};
           out[(size_t)H * NY + k] = C2<float>{0.5f * d.y, -0.5f * d.x};
@@ -333,9 +333,12 @@ cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg&
 
 // smallest cluster whose CTAs fit two per SM
 template <int H, int NY>
+constexpr bool ncs_fits(int cs) {
+  return H % cs == 0 && NY % cs == 0 && nfwd_smem<H, NY>(cs) <= 112 * 1024 && ninv_smem<H, NY>(cs) <= 112 * 1024;
+}
+template <int H, int NY>
 constexpr int ncs() {
-  return (nfwd_smem<H, NY>(1) <= 112 * 1024 && ninv_smem<H, NY>(1) <= 112 * 1024) ? 1
-       : (nfwd_smem<H, NY>(2) <= 112 * 1024 && ninv_smem<H, NY>(2) <= 112 * 1024) ? 2 : 4;
+  return ncs_fits<H, NY>(1) ? 1 : ncs_fits<H, NY>(2) ? 2 : ncs_fits<H, NY>(4) ? 4 : 8;
 }
 
 template <int H, int NY>
@@ -350,22 +353,27 @@ cudaError_t pencil_one(C2<float>* spec, const PassCfg& c, cudaStream_t st) {
 }
 }  // namespace
 
-// The fast path covers nx = ny in {32, 64, 128, 256} with nz in the same set.
+// The fast path covers nx = ny in {32, 48, 64, 96, 128, 160, 192, 256, 320} and nz
+// in the same set.
 bool fast_solve_supported(const PassCfg& c) {
-  if (c.ncomp != 6) return false;
-  const int key = c.H * 1000 + c.ny;
-  const bool plane = key == 16032 || key == 32064 || key == 64128 || key == 128256;
-  const bool pencil = c.nz == 32 || c.nz == 64 || c.nz == 128 || c.nz == 256;
-  return plane && pencil;
+  if (c.ncomp != 6 || c.nx != c.ny) return false;
+  auto ok = [](int n) {
+    return n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 160 || n == 192 || n == 256 || n == 320;
+  };
+  return ok(c.nx) && ok(c.nz);
 }
 
-// the planes of cubic power-of-two grids (ny = nx)
 cudaError_t launch_plane_fast(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
-  switch (c.H * 1000 + c.ny) {
-    case 16032: return plane_pair<16, 32>(inverse, in, out, c, st);
-    case 32064: return plane_pair<32, 64>(inverse, in, out, c, st);
-    case 64128: return plane_pair<64, 128>(inverse, in, out, c, st);
-    case 128256: return plane_pair<128, 256>(inverse, in, out, c, st);
+  switch (c.ny) {
+    case 32: return plane_pair<16, 32>(inverse, in, out, c, st);
+    case 48: return plane_pair<24, 48>(inverse, in, out, c, st);
+    case 64: return plane_pair<32, 64>(inverse, in, out, c, st);
+    case 96: return plane_pair<48, 96>(inverse, in, out, c, st);
+    case 128: return plane_pair<64, 128>(inverse, in, out, c, st);
+    case 160: return plane_pair<80, 160>(inverse, in, out, c, st);
+    case 192: return plane_pair<96, 192>(inverse, in, out, c, st);
+    case 256: return plane_pair<128, 256>(inverse, in, out, c, st);
+    case 320: return plane_pair<160, 320>(inverse, in, out, c, st);
     default: return cudaErrorInvalidConfiguration;
   }
 }
@@ -373,9 +381,14 @@ cudaError_t launch_plane_fast(bool inverse, const void* in, void* out, const Pas
 cudaError_t launch_pencil_fast(C2<float>* spec, const PassCfg& c, cudaStream_t st) {
   switch (c.nz) {
     case 32: return pencil_one<32>(spec, c, st);
+    case 48: return pencil_one<48>(spec, c, st);
     case 64: return pencil_one<64>(spec, c, st);
+    case 96: return pencil_one<96>(spec, c, st);
     case 128: return pencil_one<128>(spec, c, st);
+    case 160: return pencil_one<160>(spec, c, st);
+    case 192: return pencil_one<192>(spec, c, st);
     case 256: return pencil_one<256>(spec, c, st);
+    case 320: return pencil_one<320>(spec, c, st);
     default: return cudaErrorInvalidConfiguration;
   }
 }

@@ -28,7 +28,8 @@ EXPORTED = [
     'okmc_get_defects', 'okmc_set_positions', 'okmc_get_positions', 'okmc_solve_stress', 'okmc_eigenstrain',
     'okmc_interaction_energies', 'okmc_candidate_energies', 'okmc_self_terms', 'okmc_get_stencil', 'okmc_step',
     'okmc_get_stats', 'okmc_device_bytes', 'okmc_set_profiling', 'okmc_kernel_times', 'okmc_reset_kernel_times',
-    'okmc_launch_shape', 'okmc_solve_stress_static',
+    'okmc_launch_shape', 'okmc_solve_stress_static', 'okmc_set_graphs', 'okmc_batch_create', 'okmc_batch_step',
+    'okmc_batch_destroy', 'okmc_batch_last_error',
 ]
 
 
@@ -92,6 +93,11 @@ def load(path=LIB_PATH):
         'okmc_launch_shape': (C.c_int, [vp, C.POINTER(i32)]),
         'okmc_solve_stress_static': (C.c_int, [dp, dp, C.POINTER(i32), C.c_double, C.c_double, C.c_double, i32,
                                               vp]),
+        'okmc_set_graphs': (C.c_int, [vp, C.c_int]),
+        'okmc_batch_create': (C.c_int, [C.POINTER(vp), i32, vp, C.POINTER(vp)]),
+        'okmc_batch_step': (C.c_int, [vp, C.POINTER(StepParams), i64, C.POINTER(StepStats)]),
+        'okmc_batch_destroy': (C.c_int, [vp]),
+        'okmc_batch_last_error': (C.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -251,7 +257,46 @@ class Grid:
     def reset_kernel_times(self):
         self._chk(self.lib.okmc_reset_kernel_times(self.h))
 
+    def set_graphs(self, on=True):
+        self._chk(self.lib.okmc_set_graphs(self.h, int(on)))
+
     def launch_shape(self):
         out = (C.c_int32 * 3)()
         self._chk(self.lib.okmc_launch_shape(self.h, out))
         return list(out)
+
+
+class Batch:
+    """Replicas advanced together by one CUDA graph launch per step (okmc_batch_*)."""
+
+    def __init__(self, grids, stream=None):
+        self.lib = load()
+        self.grids = list(grids)
+        arr = (C.c_void_p * len(self.grids))(*[g.h.value for g in self.grids])
+        h = C.c_void_p()
+        rc = self.lib.okmc_batch_create(arr, len(self.grids), stream, C.byref(h))
+        if rc != OKMC_OK:
+            raise OkmcError(rc, 'okmc_batch_create failed')
+        self.h = h
+
+    def step(self, T_K, n_steps=1, mode=RESIDENCE):
+        n = len(self.grids)
+        Ts = list(T_K) if np.ndim(T_K) else [T_K] * n
+        modes = list(mode) if np.ndim(mode) else [mode] * n
+        params = (StepParams * n)(*[StepParams(float(t), int(m), 0, 0.0) for t, m in zip(Ts, modes)])
+        stats = (StepStats * n)()
+        rc = self.lib.okmc_batch_step(self.h, params, n_steps, stats)
+        if rc != OKMC_OK:
+            raise OkmcError(rc, self.lib.okmc_batch_last_error(self.h).decode())
+        return [s.as_dict() for s in stats]
+
+    def close(self):
+        if getattr(self, 'h', None):
+            self.lib.okmc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

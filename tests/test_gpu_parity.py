@@ -81,7 +81,16 @@ CASES = [
     ((80, 48, 32), ok.FP64_FIELDS, ok.MEAN_STRAIN_ZERO, 'cubic', 20),
     ((96, 64, 160), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 30),
     ((64, 64, 64), ok.FP64_FIELDS, ok.MEAN_STRESS_ZERO, 'iso', 25),
+    # register-FFT passes with mixed-radix lines (2^a 3^b 5^c)
+    ((48, 48, 48), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 15),
+    ((96, 96, 96), ok.FP32_FIELDS, ok.MEAN_STRAIN_ZERO, 'iso', 30),
+    ((160, 160, 32), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 30),
+    ((192, 192, 48), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 30),
+    ((320, 320, 32), ok.FP32_FIELDS, ok.MEAN_STRAIN_ZERO, 'cubic', 30),
+    ((32, 32, 320), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 20),
+    ((64, 64, 192), ok.FP32_FIELDS, ok.MEAN_STRESS_ZERO, 'cubic', 20),
 ]
+FAST_EDGES = {32, 48, 64, 96, 128, 160, 192, 256, 320}
 
 
 @pytest.mark.parametrize('n,precision,k0,mat,nd', CASES)
@@ -89,6 +98,8 @@ def test_stress_parity(n, precision, k0, mat, nd):
     w = scaled_population(n, nd, seed=sum(n) + nd, r111=(0.4, 1.0), r100=(0.4, 1.0))
     C = FE_CUBIC if mat == 'cubic' else O.isotropic_cubic_constants(*FE_ISO)
     g = make_grid(w, precision, k0, C)
+    fast = precision == ok.FP32_FIELDS and n[0] == n[1] and n[0] in FAST_EDGES and n[2] in FAST_EDGES
+    assert (g.launch_shape()[0] == -1) == fast
     sig = g.solve_stress()
     ref = zyx(O.solve_stress(O.eigenstrain_field(w.defects, w.n, w.voxel_nm), O.stiffness_cubic(*C),
                              w.voxel_nm, k0))
@@ -309,3 +320,49 @@ def test_large_256_stress_and_sampled_energies(large_oracle, precision):
     for i, (e0, ej) in picks.items():
         assert abs(E[i] - e0) <= tol, (i, E[i], e0)
         assert np.abs(Ec[i] - ej).max() <= tol, (i, Ec[i], ej)
+
+
+# ------------------------------------------------------------------ graphs and batches
+def test_graph_replay_equals_kernel_by_kernel():
+    w = config_small()
+    a = make_grid(w, seed=5)
+    b = make_grid(w, seed=5)
+    b.set_graphs(False)
+    for mode in (ok.RESIDENCE, ok.FIXED_DT):
+        sa = a.step(w.T_K, 15, mode=mode)
+        sb = b.step(w.T_K, 15, mode=mode)
+        assert np.array_equal(a.get_positions(), b.get_positions())
+        assert sa['clock'] == sb['clock'] and sa['events'] == sb['events']
+    a.close()
+    b.close()
+
+
+def test_batch_replicas_equal_alone():
+    """Replicas of uneven size (fast and generic passes) advanced by one graph per
+    step give the same trajectory as each replica stepped alone."""
+    small = dict(r111=(0.4, 1.0), r100=(0.4, 1.0))
+    cases = [scaled_population((32, 32, 32), 12, seed=1, **small), scaled_population((64, 64, 64), 40, seed=2, **small),
+             scaled_population((48, 32, 80), 20, seed=3, r111=(0.4, 1.0), r100=(0.4, 1.0))]
+    Ts = [300.0, 450.0, 600.0]
+    alone, mixed = [], []
+    for w, T in zip(cases, Ts):
+        g = ok.Grid(w.n, w.voxel_nm, *w.C, seed=77)
+        g.set_defects(w.defects)
+        st = g.step(T, 12)
+        alone.append((g.get_positions(), st, g.interaction_energies()))
+        g.close()
+    grids = []
+    for w in cases:
+        g = ok.Grid(w.n, w.voxel_nm, *w.C, seed=77)
+        g.set_defects(w.defects)
+        grids.append(g)
+    batch = ok.Batch(grids)
+    batch.step(Ts, 5)
+    stats = batch.step(Ts, 7)
+    for (pos, st, E), g, s in zip(alone, grids, stats):
+        assert np.array_equal(g.get_positions(), pos)
+        assert s['clock'] == st['clock'] and s['events'] == st['events'] == 12
+        assert np.array_equal(g.interaction_energies(), E)
+    batch.close()
+    for g in grids:
+        g.close()
