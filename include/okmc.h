@@ -228,6 +228,18 @@ int okmc_reset_kernel_times(okmc_grid* g);
  * nx = ny and nx, nz in {32, 48, 64, 96, 128, 160, 192, 256, 320}). */
 int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
 
+/* Launch variants of the three FFT passes (forward plane pass = 0, pencil pass = 1,
+ * inverse plane pass = 2), for diagnostics and tests.  okmc_grid_create times every
+ * variant that exists for the grid's shape and keeps the fastest (set the
+ * environment variable OKMC_TUNE=0 to keep variant 0); the variants differ in
+ * cluster size, threads per CTA and how data reaches shared memory, not in
+ * arithmetic, so results are bitwise the same under every variant.
+ * okmc_get_variants: current[p] = variant in use, available[p] = bit mask of the
+ * variants that exist.  okmc_set_variant: OKMC_EINVAL if the variant does not exist
+ * for this grid; drops captured step graphs. */
+int okmc_get_variants(const okmc_grid* g, int32_t current[3], int32_t available[3]);
+int okmc_set_variant(okmc_grid* g, int32_t pass, int32_t variant);
+
 /* Allocation-free stress solve (the paper has no counterpart; this is a service for
  * callers that cannot allocate device memory -- code that runs after its process
  * has handed all device memory to a pool it does not own, code inside a region

@@ -213,7 +213,7 @@ __device__ __forceinline__ int wrap(int x, int n) { return x < 0 ? x + n : (x >=
 template <class Q>
 __device__ void scatter_stencil(Q* __restrict__ eps, int3 n, size_t N, const DefGeo& g, const int* __restrict__ ptr,
                                 const int* __restrict__ off, const uint8_t* __restrict__ cnt, const double* __restrict__ alpha,
-                                int i, const int pos[3], int sign, double rq, double lim, int* err) {
+                                int i, const int pos[3], int sign, double rq, double lim, int* err, int* dirty) {
   const int c = pos[0] & 1;
   const int bx = floor_div2(pos[0]), by = floor_div2(pos[1]), bz = floor_div2(pos[2]);
   const int s = ptr[2 * i + c], e = ptr[2 * i + c + 1];
@@ -221,13 +221,17 @@ __device__ void scatter_stencil(Q* __restrict__ eps, int3 n, size_t N, const Def
   for (int k = s + threadIdx.x; k < e; k += blockDim.x) {
     int dx, dy, dz;
     unpack_off(off[k], dx, dy, dz);
-    const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
+    const int zz = wrap(bz + dz, n.z);
+    const size_t v = ((size_t)zz * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
     const double w = (double)cnt[k] * a;
     for (int comp = 0; comp < 6; ++comp) {
       const double val = w * g.e6[comp] * rq;
       if (fabs(val) > lim) atomicExch(err, 4);
       const long long iv = __double2ll_rn(val);
-      if (iv) fixed_add<Q>(eps + comp * N + v, sign * iv);
+      if (iv) {
+        fixed_add<Q>(eps + comp * N + v, sign * iv);
+        if (dirty) dirty[comp * n.z + zz] = 1;  // same value from every writer
+      }
     }
   }
 }
@@ -239,19 +243,20 @@ __global__ void k_voxelise(Q* __restrict__ eps, int3 n, const okmc_defect* __res
   const int i = blockIdx.x;
   const size_t N = (size_t)n.x * n.y * n.z;
   const int pos[3] = {d[i].pos[0], d[i].pos[1], d[i].pos[2]};
-  scatter_stencil<Q>(eps, n, N, G[i], ptr, off, cnt, alpha, i, pos, +1, rq, lim, err);
+  scatter_stencil<Q>(eps, n, N, G[i], ptr, off, cnt, alpha, i, pos, +1, rq, lim, err, nullptr);
 }
 
 // One block per move: remove the old stencil, add the new one (exact in fixed point).
 template <class Q>
 __global__ void k_apply_moves(Q* __restrict__ eps, int3 n, const DefGeo* __restrict__ G, const int* __restrict__ ptr,
                               const int* __restrict__ off, const uint8_t* __restrict__ cnt, const double* __restrict__ alpha,
-                              const Move* __restrict__ moves, const DevState* __restrict__ st, double rq, double lim, int* err) {
+                              const Move* __restrict__ moves, const DevState* __restrict__ st, double rq, double lim, int* err,
+                              int* dirty) {
   if ((int)blockIdx.x >= st->nmoves) return;
   const Move m = moves[blockIdx.x];
   const size_t N = (size_t)n.x * n.y * n.z;
-  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.old_pos, -1, rq, lim, err);
-  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.new_pos, +1, rq, lim, err);
+  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.old_pos, -1, rq, lim, err, dirty);
+  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.new_pos, +1, rq, lim, err, dirty);
 }
 
 // Moves recorded from a host-side position update.
@@ -770,9 +775,9 @@ cudaError_t launch_voxelise(Q* eps, int3 n, const okmc_defect* d, const DefGeo* 
 template <class Q>
 cudaError_t launch_apply_moves(Q* eps, int3 n, const DefGeo* G, int maxmoves, const int* ptr, const int* off,
                                const uint8_t* cnt, const double* alpha, const Move* moves, const DevState* stt, double rq,
-                               double lim, int* err, cudaStream_t st) {
+                               double lim, int* err, int* dirty, cudaStream_t st) {
   if (maxmoves == 0) return cudaSuccess;
-  k_apply_moves<Q><<<maxmoves, 256, 0, st>>>(eps, n, G, ptr, off, cnt, alpha, moves, stt, rq, lim, err);
+  k_apply_moves<Q><<<maxmoves, 256, 0, st>>>(eps, n, G, ptr, off, cnt, alpha, moves, stt, rq, lim, err, dirty);
   return cudaGetLastError();
 }
 cudaError_t launch_diff_positions(okmc_defect* d, const int* pos, int nd, Move* moves, DevState* stt, cudaStream_t st) {
@@ -827,9 +832,9 @@ template cudaError_t launch_voxelise<int32_t>(int32_t*, int3, const okmc_defect*
 template cudaError_t launch_voxelise<int64_t>(int64_t*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
                                               const uint8_t*, const double*, double, double, int*, cudaStream_t);
 template cudaError_t launch_apply_moves<int32_t>(int32_t*, int3, const DefGeo*, int, const int*, const int*, const uint8_t*,
-                                                 const double*, const Move*, const DevState*, double, double, int*, cudaStream_t);
+                                                 const double*, const Move*, const DevState*, double, double, int*, int*, cudaStream_t);
 template cudaError_t launch_apply_moves<int64_t>(int64_t*, int3, const DefGeo*, int, const int*, const int*, const uint8_t*,
-                                                 const double*, const Move*, const DevState*, double, double, int*, cudaStream_t);
+                                                 const double*, const Move*, const DevState*, double, double, int*, int*, cudaStream_t);
 template cudaError_t launch_fixed_to_real<int32_t, float>(const int32_t*, float*, size_t, double, cudaStream_t);
 template cudaError_t launch_fixed_to_real<int64_t, double>(const int64_t*, double*, size_t, double, cudaStream_t);
 template cudaError_t launch_wfields<int32_t>(int32_t*, int3, const int*, const int*, const uint8_t*, int, int, cudaStream_t);

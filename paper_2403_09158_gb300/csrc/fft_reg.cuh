@@ -35,6 +35,92 @@ template <> struct RegPlan<256> { static constexpr int R1 = 16, R2 = 16; };
 template <> struct RegPlan<320> { static constexpr int R1 = 16, R2 = 20; };
 template <int L> __host__ __device__ constexpr int reg_nt() { return RegPlan<L>::R1 < RegPlan<L>::R2 ? RegPlan<L>::R1 : RegPlan<L>::R2; }
 
+// ---------------------------------------------------------------- packed FP32 pairs
+// The sm_100 family executes add, multiply and fma on a pair of FP32 values in one
+// instruction (round to nearest, each lane exactly as the scalar operation), so a
+// complex add, subtract or real scaling costs one instruction instead of two.  A
+// multiplication by -i or +i swaps the lanes; such terms are added in scalar form.
+__device__ __forceinline__ float2 pk(C2<float> a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ C2<float> un(float2 a) { return C2<float>{a.x, a.y}; }
+__device__ __forceinline__ C2<float> padd(C2<float> a, C2<float> b) { return un(__fadd2_rn(pk(a), pk(b))); }
+// a - b as fma(b, -1, a): b * -1 is exact, so this is the correctly rounded difference
+__device__ __forceinline__ C2<float> psub(C2<float> a, C2<float> b) {
+  return un(__ffma2_rn(pk(b), make_float2(-1.f, -1.f), pk(a)));
+}
+__device__ __forceinline__ C2<float> pscale(float s, C2<float> a) { return un(__fmul2_rn(make_float2(s, s), pk(a))); }
+// s * a + c
+__device__ __forceinline__ C2<float> pfma(float s, C2<float> a, C2<float> c) {
+  return un(__ffma2_rn(make_float2(s, s), pk(a), pk(c)));
+}
+// b + rot(e) and b - rot(e), rot = multiply by -i (forward) or +i (inverse)
+template <bool INV> __device__ __forceinline__ C2<float> add_rot(C2<float> b, C2<float> e) {
+  return INV ? C2<float>{b.x - e.y, b.y + e.x} : C2<float>{b.x + e.y, b.y - e.x};
+}
+template <bool INV> __device__ __forceinline__ C2<float> sub_rot(C2<float> b, C2<float> e) {
+  return INV ? C2<float>{b.x + e.y, b.y - e.x} : C2<float>{b.x - e.y, b.y + e.x};
+}
+// b + s * rot(e) and b - s * rot(e)
+template <bool INV> __device__ __forceinline__ C2<float> add_srot(C2<float> b, float s, C2<float> e) {
+  return INV ? C2<float>{fmaf(-s, e.y, b.x), fmaf(s, e.x, b.y)} : C2<float>{fmaf(s, e.y, b.x), fmaf(-s, e.x, b.y)};
+}
+template <bool INV> __device__ __forceinline__ C2<float> sub_srot(C2<float> b, float s, C2<float> e) {
+  return INV ? C2<float>{fmaf(s, e.y, b.x), fmaf(-s, e.x, b.y)} : C2<float>{fmaf(-s, e.y, b.x), fmaf(s, e.x, b.y)};
+}
+
+// Small DFTs on packed pairs; X_k = sum_n x_n exp(-+2 pi i n k / R), minus sign forward.
+template <bool INV> __device__ __forceinline__ void pdft2(C2<float>* v) {
+  const C2<float> a = v[0];
+  v[0] = padd(a, v[1]);
+  v[1] = psub(a, v[1]);
+}
+template <bool INV> __device__ __forceinline__ void pdft3(C2<float>* v) {
+  const float s = 0.86602540378443864676f;  // sin(2 pi / 3)
+  const C2<float> t1 = padd(v[1], v[2]), t2 = psub(v[1], v[2]);
+  const C2<float> m = pfma(-0.5f, t1, v[0]);
+  v[0] = padd(v[0], t1);
+  v[1] = add_srot<INV>(m, s, t2);
+  v[2] = sub_srot<INV>(m, s, t2);
+}
+template <bool INV> __device__ __forceinline__ void pdft4(C2<float>* v) {
+  const C2<float> a = padd(v[0], v[2]), b = psub(v[0], v[2]), c = padd(v[1], v[3]), e = psub(v[1], v[3]);
+  v[0] = padd(a, c);
+  v[2] = psub(a, c);
+  v[1] = add_rot<INV>(b, e);
+  v[3] = sub_rot<INV>(b, e);
+}
+template <bool INV> __device__ __forceinline__ void pdft5(C2<float>* v) {
+  const float c1 = 0.30901699437494742410f, c2 = -0.80901699437494742410f;  // cos(2pi/5), cos(4pi/5)
+  const float s1 = 0.95105651629515357212f, s2 = 0.58778525229247312917f;   // sin(2pi/5), sin(4pi/5)
+  const C2<float> a1 = padd(v[1], v[4]), b1 = psub(v[1], v[4]), a2 = padd(v[2], v[3]), b2 = psub(v[2], v[3]);
+  const C2<float> m1 = pfma(c2, a2, pfma(c1, a1, v[0]));
+  const C2<float> m2 = pfma(c1, a2, pfma(c2, a1, v[0]));
+  const C2<float> n1 = pfma(s2, b2, pscale(s1, b1));
+  const C2<float> n2 = pfma(-s1, b2, pscale(s2, b1));
+  v[0] = padd(v[0], padd(a1, a2));
+  v[1] = add_rot<INV>(m1, n1);
+  v[4] = sub_rot<INV>(m1, n1);
+  v[2] = add_rot<INV>(m2, n2);
+  v[3] = sub_rot<INV>(m2, n2);
+}
+template <bool INV> __device__ __forceinline__ void pdft8(C2<float>* v) {
+  const float h = 0.70710678118654752440f;  // sqrt(1/2)
+  C2<float> e[4] = {v[0], v[2], v[4], v[6]};
+  C2<float> o[4] = {v[1], v[3], v[5], v[7]};
+  pdft4<INV>(e);
+  pdft4<INV>(o);
+  // w8 o1 = h * t1 and w8^3 o3 = h * t3 with w8 = exp(-+ i pi / 4)
+  const C2<float> t1 = INV ? C2<float>{o[1].x - o[1].y, o[1].x + o[1].y} : C2<float>{o[1].x + o[1].y, o[1].y - o[1].x};
+  const C2<float> t3 = INV ? C2<float>{-o[3].x - o[3].y, o[3].x - o[3].y} : C2<float>{o[3].y - o[3].x, -o[3].x - o[3].y};
+  v[0] = padd(e[0], o[0]);
+  v[4] = psub(e[0], o[0]);
+  v[1] = pfma(h, t1, e[1]);
+  v[5] = pfma(-h, t1, e[1]);
+  v[2] = add_rot<INV>(e[2], o[2]);
+  v[6] = sub_rot<INV>(e[2], o[2]);
+  v[3] = pfma(h, t3, e[3]);
+  v[7] = pfma(-h, t3, e[3]);
+}
+
 // cos and sin of 2 pi e / 16 for e = 0..15
 __device__ __forceinline__ float cos16(int e) {
   switch (e & 15) {
@@ -76,14 +162,14 @@ __device__ __forceinline__ void dft16(C2<float>* v) {
 #pragma unroll
   for (int n1 = 0; n1 < 4; ++n1) {
     C2<float> a[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
-    dft4<float, INV>(a);
+    pdft4<INV>(a);
 #pragma unroll
     for (int k2 = 0; k2 < 4; ++k2) y[n1 * 4 + k2] = tw16<INV>(a[k2], n1 * k2);
   }
 #pragma unroll
   for (int k2 = 0; k2 < 4; ++k2) {
     C2<float> b[4] = {y[k2], y[4 + k2], y[8 + k2], y[12 + k2]};
-    dft4<float, INV>(b);
+    pdft4<INV>(b);
 #pragma unroll
     for (int k1 = 0; k1 < 4; ++k1) v[k2 + 4 * k1] = b[k1];
   }
@@ -323,11 +409,11 @@ __device__ __forceinline__ void dft_composite(C2<float>* v) {
 
 template <int R, bool INV>
 __device__ __forceinline__ void dft_reg(C2<float>* v) {
-  if constexpr (R == 2) dft2<float, INV>(v);
-  else if constexpr (R == 3) dft3<float, INV>(v);
-  else if constexpr (R == 4) dft4<float, INV>(v);
-  else if constexpr (R == 5) dft5<float, INV>(v);
-  else if constexpr (R == 8) dft8<float, INV>(v);
+  if constexpr (R == 2) pdft2<INV>(v);
+  else if constexpr (R == 3) pdft3<INV>(v);
+  else if constexpr (R == 4) pdft4<INV>(v);
+  else if constexpr (R == 5) pdft5<INV>(v);
+  else if constexpr (R == 8) pdft8<INV>(v);
   else if constexpr (R == 16) dft16<INV>(v);
   else dft_composite<R, INV>(v);
 }

@@ -8,6 +8,8 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
+#include <tuple>
 #include <new>
 #include <string>
 #include <utility>
@@ -33,7 +35,7 @@ cudaError_t launch_voxelise(Q* eps, int3 n, const okmc_defect* d, const DefGeo* 
 template <class Q>
 cudaError_t launch_apply_moves(Q* eps, int3 n, const DefGeo* G, int maxmoves, const int* ptr, const int* off,
                                const uint8_t* cnt, const double* alpha, const Move* moves, const DevState* stt, double rq,
-                               double lim, int* err, cudaStream_t st);
+                               double lim, int* err, int* dirty, cudaStream_t st);
 cudaError_t launch_diff_positions(okmc_defect* d, const int* pos, int nd, Move* moves, DevState* stt, cudaStream_t st);
 cudaError_t launch_gather_positions(const okmc_defect* d, int* pos, int nd, cudaStream_t st);
 template <class Q, class T> cudaError_t launch_fixed_to_real(const Q* eps, T* out, size_t total, double q, cudaStream_t st);
@@ -52,8 +54,9 @@ cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const 
 cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* rates, double nu0, double kT, int3 n,
                             uint64_t seed, Move* moves, DevState* stt, cudaStream_t st);
 bool fast_solve_supported(const PassCfg& c);
-cudaError_t launch_plane_fast(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st);
-cudaError_t launch_pencil_fast(C2<float>* spec, const PassCfg& c, cudaStream_t st);
+cudaError_t launch_plane_fast(bool inverse, int variant, const void* in, void* out, const PassCfg& c, cudaStream_t st);
+int plane_inv_variant_mask(const PassCfg& c);
+cudaError_t launch_pencil_fast(const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st);
 }  // namespace okmc
 
 namespace {
@@ -100,6 +103,8 @@ struct okmc_grid {
   void* eps = nullptr;
   void* sig = nullptr;
   void* spec = nullptr;
+  void* spec2 = nullptr;  // fast path: Green operator output (spec keeps the plane transforms)
+  int* d_dirty = nullptr;  // [6][nz] planes whose eigenstrain changed since their last transform
   void* tw = nullptr;
   double2* ph = nullptr;
   PassCfg cfg{};
@@ -127,6 +132,8 @@ struct okmc_grid {
   bool sigma_valid = false;
   bool any_mobile = false;
   bool fast = false;  // FP32 register-FFT passes for this grid
+  int variant[3] = {0, 0, 0};  // launch variant of the forward plane, pencil and inverse plane passes
+  int avail[3] = {1, 1, 1};    // bit v: variant v exists for this grid
   long long solves = 0;
   std::string err;
   bool profiling = false;
@@ -259,9 +266,15 @@ int solve(okmc_grid* g) {
     OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil<double>((C2<double>*)g->spec, c, g->st); }));
     OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_inv<double>((const C2<double>*)g->spec, (double*)g->sig, c, g->st); }));
   } else if (g->fast) {
-    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, g->eps, g->spec, c, g->st); }));
-    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil_fast((C2<float>*)g->spec, c, g->st); }));
-    OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_fast(true, g->spec, g->sig, c, g->st); }));
+    // spec keeps the plane transforms of the eigenstrain between solves: only planes
+    // whose eigenstrain changed are transformed again (bitwise the same result as a
+    // full pass, since a clean plane's input is unchanged); the Green operator's
+    // output goes to spec2
+    c.dirty = g->d_dirty;
+    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, 0, g->eps, g->spec, c, g->st); }));
+    c.dirty = nullptr;
+    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil_fast((const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st); }));
+    OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_fast(true, g->variant[2], g->spec2, g->sig, c, g->st); }));
   } else {
     OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<float, int32_t>((const int32_t*)g->eps, (C2<float>*)g->spec, c, g->st); }));
     OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil<float>((C2<float>*)g->spec, c, g->st); }));
@@ -296,9 +309,9 @@ int apply_moves(okmc_grid* g, int maxmoves) {
   return run(g, "apply_moves", [&] {
     if (fp64(g))
       return launch_apply_moves<int64_t>((int64_t*)g->eps, dims(g), g->d_geo, maxmoves, g->d_ptr, g->d_off, g->d_cnt,
-                                         g->d_alpha, g->d_moves, g->d_state, 1.0 / quantum(g), qlimit(g), g->d_err, g->st);
+                                         g->d_alpha, g->d_moves, g->d_state, 1.0 / quantum(g), qlimit(g), g->d_err, g->d_dirty, g->st);
     return launch_apply_moves<int32_t>((int32_t*)g->eps, dims(g), g->d_geo, maxmoves, g->d_ptr, g->d_off, g->d_cnt,
-                                       g->d_alpha, g->d_moves, g->d_state, 1.0 / quantum(g), qlimit(g), g->d_err, g->st);
+                                       g->d_alpha, g->d_moves, g->d_state, 1.0 / quantum(g), qlimit(g), g->d_err, g->d_dirty, g->st);
   });
 }
 
@@ -379,8 +392,8 @@ int build_self_terms(okmc_grid* g) {
     }
     OKMC_TRY(run(g, "self_fields", [&] { return launch_wfields<Q>((Q*)g->eps, n, g->d_ptr, g->d_off, g->d_cnt, i0, 2 * b.nb, g->st); }));
     if (g->fast) {
-      OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, g->eps, g->spec, c, g->st); }));
-      OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast((C2<float>*)g->spec, c, g->st); }));
+      OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, 0, g->eps, g->spec, c, g->st); }));
+      OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast((const C2<float>*)g->spec, (C2<float>*)g->spec, c, g->st); }));
     } else {
       OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)g->spec, c, g->st); }));
       OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil<T>((C2<T>*)g->spec, c, g->st); }));
@@ -397,6 +410,8 @@ int build_self_terms(okmc_grid* g) {
 
 int voxelise_all(okmc_grid* g) {
   cudaError_t e = cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st);
+  // every plane transform is stale (the self-term build also used spec as scratch)
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->d_dirty, 1, sizeof(int) * 6 * g->n[2], g->st);
   if (e != cudaSuccess) return cuda_fail(g, e, "memset");
   g->sigma_valid = false;
   return run(g, "voxelise", [&] {
@@ -470,6 +485,63 @@ int capture_step(okmc_grid* g, int mode, double T, cudaGraphExec_t* out) {
   e = cudaGraphInstantiate(out, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return cuda_fail(g, e, "graph instantiate");
+  return OKMC_OK;
+}
+
+// Launch-variant autotuner of the fast passes: each variant that exists for the grid
+// is timed on the grid's own buffers (one warm-up launch, then three launches
+// between events) and the fastest is kept.  Every variant computes each line with
+// the same arithmetic, so the choice changes the time and not the result.  Choices
+// are cached per grid shape for the life of the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune_cache;
+
+int autotune(okmc_grid* g) {
+  if (!g->fast) return OKMC_OK;
+  const char* env = std::getenv("OKMC_TUNE");
+  if (env && env[0] == '0') return OKMC_OK;
+  const auto key = std::make_tuple(g->n[0], g->n[1], g->n[2]);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      g->variant[2] = it->second;
+      return OKMC_OK;
+    }
+  }
+  cudaError_t e = cudaMemsetAsync(g->spec2, 0, 6 * g->n[2] * g->P * 2 * tsize(g), g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "tune");
+  PassCfg c = g->cfg;
+  c.dirty = nullptr;
+  cudaEvent_t a, b;
+  if (cudaEventCreate(&a) != cudaSuccess) return cuda_fail(g, cudaGetLastError(), "tune event");
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return cuda_fail(g, cudaGetLastError(), "tune event");
+  }
+  float best = 0.f;
+  int pick = 0;
+  for (int v = 0; v < 8; ++v) {
+    if (!((g->avail[2] >> v) & 1)) continue;
+    e = launch_plane_fast(true, v, g->spec2, g->sig, c, g->st);
+    if (e == cudaSuccess) e = cudaEventRecord(a, g->st);
+    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_plane_fast(true, v, g->spec2, g->sig, c, g->st);
+    if (e == cudaSuccess) e = cudaEventRecord(b, g->st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) break;
+    if (v == 0 || ms < best) {
+      best = ms;
+      pick = v;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (e != cudaSuccess) return cuda_fail(g, e, "tune");
+  g->variant[2] = pick;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = pick;
   return OKMC_OK;
 }
 
@@ -590,10 +662,15 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
     const char* env = std::getenv("OKMC_GENERIC_FFT");
     g->fast = !f64 && fast_solve_supported(c) && !(env && env[0] == '1');
   }
+  if (g->fast && (rc = dalloc(g, &g->spec2, 6 * g->n[2] * g->P * 2 * tsize(g)))) return cleanup(rc);
+  if (g->fast) g->avail[2] = plane_inv_variant_mask(c);
+  if ((rc = dalloc(g, (void**)&g->d_dirty, sizeof(int) * 6 * g->n[2]))) return cleanup(rc);
+  if (cudaMemsetAsync(g->d_dirty, 1, sizeof(int) * 6 * g->n[2], g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if (cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if (cudaMemsetAsync(g->d_state, 0, sizeof(DevState), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if (cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if (cudaStreamSynchronize(g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
+  if ((rc = autotune(g))) return cleanup(rc);
   *out = g;
   return OKMC_OK;
 }
@@ -1037,6 +1114,26 @@ int okmc_reset_kernel_times(okmc_grid* g) {
   if (!g) return OKMC_EINVAL;
   drain_profile(g);
   g->prof.clear();
+  return OKMC_OK;
+}
+
+int okmc_get_variants(const okmc_grid* g, int32_t current[3], int32_t available[3]) {
+  if (!g || !current || !available) return OKMC_EINVAL;
+  for (int p = 0; p < 3; ++p) {
+    current[p] = g->variant[p];
+    available[p] = g->avail[p];
+  }
+  return OKMC_OK;
+}
+
+int okmc_set_variant(okmc_grid* g, int32_t pass, int32_t variant) {
+  if (!g) return OKMC_EINVAL;
+  if (pass < 0 || pass > 2 || variant < 0 || variant > 30 || !((g->avail[pass] >> variant) & 1))
+    return fail(g, OKMC_EINVAL, "no such launch variant for this grid");
+  cudaStreamSynchronize(g->st);
+  drop_graphs(g);
+  g->variant[pass] = variant;
+  g->sigma_valid = false;
   return OKMC_OK;
 }
 

@@ -238,6 +238,9 @@ struct PassCfg {
   const void* twZ;     // C2<T>[nz]
   const void* untw;    // C2<T>[H+1]    exp(-2 pi i k / nx)
   int* err;            // device error word (bounded waits that gave up set it)
+  int* dirty;          // fast forward plane pass: per plane (c*nz + z) flag, nonzero when the
+                       // plane's eigenstrain changed since its last transform (the pass skips
+                       // clean planes and clears the flags it consumed); nullptr: every plane
 };
 
 // ---------------------------------------------------------------- defects

@@ -28,6 +28,10 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -93,6 +97,9 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
   cg::cluster_group cluster = cg::this_cluster();
   const int h = CS > 1 ? (int)cluster.block_rank() : 0;
   const int plane = blockIdx.y;
+  // a plane whose eigenstrain has not changed keeps its transform from the last pass
+  // (every CTA of the cluster reads the same flag, so the whole cluster leaves)
+  if (c.dirty && c.dirty[plane] == 0) return;
   const int tid = threadIdx.x;
   const size_t P = (size_t)(H + 1) * NY;
   const float q = (float)c.q;
@@ -138,6 +145,8 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
   }
   if (CS > 1) cluster.sync();
   else __syncthreads();
+  // every CTA of the cluster has read the flag before the barrier above
+  if (c.dirty && h == 0 && tid == 0) c.dirty[plane] = 0;
   {  // columns along y
     const int g = tid / S::NTY, t = tid % S::NTY;
     for (int c0 = 0; c0 < CPER; c0 += S::GC) {
@@ -232,6 +241,92 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   }
 }
 
+// Staged variant of the inverse plane pass: the CTA's CPER columns are one contiguous
+// block of the kx-major spectrum plane, so they arrive by 16-byte cp.async at the
+// start (no registers held while the copies fly; the owner of column 0 also fetches
+// the Nyquist column), and each column is transformed in place in the staging
+// buffer, with no separate exchange buffer.  The row phase is the same as above.
+template <int H, int NY>
+__host__ __device__ constexpr size_t sinv_smem(int cs) {
+  return sizeof(C2<float>) * ((size_t)(H / cs + 1) * NY + (size_t)(NY / cs) * (H + 1) + tw2_size<H>() + tw2_size<NY>() + H + 1);
+}
+
+template <int H, int NY, int CS, int NTHR, int MINB>
+__global__ void __launch_bounds__(NTHR, MINB) k_plane_inv_s(const C2<float>* __restrict__ spec, float* __restrict__ sig,
+                                                         PassCfg c) {
+  constexpr int CPER = H / CS, ROWS = NY / CS, LDR = H + 1;
+  constexpr int NTY = reg_nt<NY>(), GC = NTHR / NTY, NTH = reg_nt<H>(), GR = NTHR / NTH;
+  constexpr int R2Y = RegPlan<NY>::R2, R2H = RegPlan<H>::R2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C2<float>* stg = reinterpret_cast<C2<float>*>(smem_raw);  // [CPER][NY] own columns, then [NY] Nyquist
+  C2<float>* nyq = stg + CPER * NY;
+  C2<float>* rowb = nyq + NY;                                 // [ROWS][LDR]
+  C2<float>* twH = rowb + ROWS * LDR;
+  C2<float>* twY = twH + tw2_size<H>();
+  C2<float>* untw = twY + tw2_size<NY>();
+  cg::cluster_group cluster = cg::this_cluster();
+  const int h = CS > 1 ? (int)cluster.block_rank() : 0;
+  const int plane = blockIdx.y;
+  const int tid = threadIdx.x;
+  const size_t P = (size_t)(H + 1) * NY;
+  {
+    const C2<float>* src = spec + (size_t)plane * P + (size_t)h * CPER * NY;
+    for (int i = tid; i < CPER * NY / 2; i += NTHR) cp_async16(stg + 2 * i, src + 2 * i);
+    if (h == 0) {
+      const C2<float>* sn = spec + (size_t)plane * P + (size_t)H * NY;
+      for (int i = tid; i < NY / 2; i += NTHR) cp_async16(nyq + 2 * i, sn + 2 * i);
+    }
+  }
+  load_tw<H, NY>(twH, twY, untw, c);
+  cp_async_wait_all();
+  __syncthreads();
+  {  // inverse columns along y, in place, scattered to the row owners
+    const int g = tid / NTY, t = tid % NTY;
+    for (int c0 = 0; c0 < CPER; c0 += GC) {
+      const bool act = c0 + g < CPER;
+      const int cc = act ? c0 + g : 0;
+      const int kx = h * CPER + cc;
+      C2<float>* col = stg + cc * NY;
+      const bool packed = (kx == 0);
+      auto ld = [&](int i) {
+        const C2<float> A = col[i];
+        if (!packed) return A;
+        const C2<float> B = nyq[i];
+        return C2<float>{A.x - B.y, A.y + B.x};  // A + i B
+      };
+      auto st = [&](int k, C2<float> v) {
+        const int owner = k / ROWS;
+        C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
+        base[(k % ROWS) * LDR + kx] = v;
+      };
+      reg_fft<true, NY>(ld, XSkew<R2Y>{col, 1}, st, twY, t, act);
+    }
+  }
+  if (CS > 1) cluster.sync();
+  else __syncthreads();
+  {  // rows along x
+    const int g = tid / NTH, t = tid % NTH;
+    for (int r0 = 0; r0 < ROWS; r0 += GR) {
+      const bool act = r0 + g < ROWS;
+      const int yl = act ? r0 + g : 0;
+      C2<float>* R = rowb + yl * LDR;
+      auto ld = [&](int k) {
+        if (k == 0) {
+          const C2<float> p = R[0];
+          return C2<float>{p.x + p.y, p.x - p.y};
+        }
+        const C2<float> Xk = R[k], Xc = conjg(R[H - k]);
+        const C2<float> E = Xk + Xc;
+        const C2<float> O = conjg(untw[k]) * (Xk - Xc);
+        return C2<float>{E.x - O.y, E.y + O.x};
+      };
+      C2<float>* orow = reinterpret_cast<C2<float>*>(sig + ((size_t)plane * NY + h * ROWS + yl) * (2 * H));
+      auto st = [&](int k, C2<float> v) { orow[k] = v; };
+      reg_fft<true, H>(ld, XSkew<R2H>{R, 1}, st, twH, t, act);
+    }
+  }
+}
+
 constexpr int kTW = 8;
 constexpr int kLDT = kTW + 1;  // padded row of a tile: conflict-free strided line access
 
@@ -241,8 +336,9 @@ __host__ __device__ constexpr size_t pencil_fast_smem() {
 }
 
 
+// in and out may be the same buffer: every CTA reads its whole tile before it writes.
 template <int NZ>
-__global__ void __launch_bounds__(kT, 2) k_pencil_fast(C2<float>* __restrict__ spec, PassCfg c) {
+__global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<float>* out, PassCfg c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw);  // [comp][kz][kLDT]
   C2<float>* twZ = tile + 6 * NZ * kLDT;
@@ -252,7 +348,7 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(C2<float>* __restrict__ s
   const int kx = (int)(p0 / c.ny), ky0 = (int)(p0 % c.ny);
   for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
     const int t = idx & (kTW - 1), kz = (idx >> 3) % NZ, comp = idx / (kTW * NZ);
-    cp_async8(tile + (comp * NZ + kz) * kLDT + t, spec + ((size_t)comp * NZ + kz) * P + p0 + t);
+    cp_async8(tile + (comp * NZ + kz) * kLDT + t, in + ((size_t)comp * NZ + kz) * P + p0 + t);
   }
   fill_tw2<NZ>(twZ, reinterpret_cast<const C2<float>*>(c.twZ));
   cp_async_wait_all();
@@ -292,19 +388,19 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(C2<float>* __restrict__ s
   }
   for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
     const int t8 = idx & (kTW - 1), kz = (idx >> 3) % NZ, comp = idx / (kTW * NZ);
-    spec[((size_t)comp * NZ + kz) * P + p0 + t8] = tile[(comp * NZ + kz) * kLDT + t8];
+    out[((size_t)comp * NZ + kz) * P + p0 + t8] = tile[(comp * NZ + kz) * kLDT + t8];
   }
 }
 
 // ---------------------------------------------------------------- dispatch
 namespace {
 template <class K, class... Args>
-cudaError_t launch_k(K k, dim3 grid, size_t smem, int cluster, cudaStream_t st, Args... args) {
+cudaError_t launch_kb(K k, dim3 grid, int nthr, size_t smem, int cluster, cudaStream_t st, Args... args) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
-  cfg.blockDim = dim3(kT);
+  cfg.blockDim = dim3(nthr);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -317,6 +413,11 @@ cudaError_t launch_k(K k, dim3 grid, size_t smem, int cluster, cudaStream_t st, 
     cfg.numAttrs = 1;
   }
   return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <class K, class... Args>
+cudaError_t launch_k(K k, dim3 grid, size_t smem, int cluster, cudaStream_t st, Args... args) {
+  return launch_kb(k, grid, kT, smem, cluster, st, args...);
 }
 
 // smallest cluster that lets two CTAs share an SM
@@ -341,15 +442,46 @@ constexpr int ncs() {
   return ncs_fits<H, NY>(1) ? 1 : ncs_fits<H, NY>(2) ? 2 : ncs_fits<H, NY>(4) ? 4 : 8;
 }
 
+// staged inverse pass: smallest cluster (<= 8) whose CTAs need at most `limit` bytes
 template <int H, int NY>
-cudaError_t plane_pair(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
+constexpr int stage_cs(size_t limit) {
+  for (int cs = 1; cs <= 8; cs *= 2)
+    if (H % cs == 0 && NY % cs == 0 && sinv_smem<H, NY>(cs) <= limit) return cs;
+  return 0;
+}
+constexpr size_t kTwoPerSM = 112 * 1024, kThreePerSM = 74 * 1024;
+
+template <int H, int NY, int CS, int NTHR, int MINB>
+cudaError_t plane_inv_staged(const void* in, void* out, const PassCfg& c, cudaStream_t st) {
+  if constexpr (CS == 0) {
+    return cudaErrorInvalidConfiguration;
+  } else {
+    const dim3 grid(CS, c.ncomp * c.nz);
+    return launch_kb(k_plane_inv_s<H, NY, CS, NTHR, MINB>, grid, NTHR, sinv_smem<H, NY>(CS), CS, st,
+                     static_cast<const C2<float>*>(in), static_cast<float*>(out), c);
+  }
+}
+
+// Inverse-pass variants: 0 register-loaded columns (cluster of ncs CTAs, 256 threads);
+// staged: 1 with 256 threads and two CTAs per SM, 2 with 128 threads and three CTAs
+// per SM, 3 with 256 threads and three CTAs per SM (registers capped at 85).
+template <int H, int NY>
+int plane_inv_variants() {
+  return 1 | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0);
+}
+
+template <int H, int NY>
+cudaError_t plane_pair(bool inverse, int variant, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
+  if (inverse && variant == 1) return plane_inv_staged<H, NY, stage_cs<H, NY>(kTwoPerSM), 256, 2>(in, out, c, st);
+  if (inverse && variant == 2) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 128, 3>(in, out, c, st);
+  if (inverse && variant == 3) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 256, 3>(in, out, c, st);
   return plane_pair_n<H, NY, ncs<H, NY>()>(inverse, in, out, c, st);
 }
 
 template <int NZ>
-cudaError_t pencil_one(C2<float>* spec, const PassCfg& c, cudaStream_t st) {
+cudaError_t pencil_one(const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st) {
   const size_t P = (size_t)(c.H + 1) * c.ny;
-  return launch_k(k_pencil_fast<NZ>, dim3((unsigned)(P / kTW)), pencil_fast_smem<NZ>(), 1, st, spec, c);
+  return launch_k(k_pencil_fast<NZ>, dim3((unsigned)(P / kTW)), pencil_fast_smem<NZ>(), 1, st, in, out, c);
 }
 }  // namespace
 
@@ -363,32 +495,40 @@ bool fast_solve_supported(const PassCfg& c) {
   return ok(c.nx) && ok(c.nz);
 }
 
-cudaError_t launch_plane_fast(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
+#define OKMC_FAST_EDGES(X) X(32, 16) X(48, 24) X(64, 32) X(96, 48) X(128, 64) X(160, 80) X(192, 96) X(256, 128) X(320, 160)
+
+cudaError_t launch_plane_fast(bool inverse, int variant, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
   switch (c.ny) {
-    case 32: return plane_pair<16, 32>(inverse, in, out, c, st);
-    case 48: return plane_pair<24, 48>(inverse, in, out, c, st);
-    case 64: return plane_pair<32, 64>(inverse, in, out, c, st);
-    case 96: return plane_pair<48, 96>(inverse, in, out, c, st);
-    case 128: return plane_pair<64, 128>(inverse, in, out, c, st);
-    case 160: return plane_pair<80, 160>(inverse, in, out, c, st);
-    case 192: return plane_pair<96, 192>(inverse, in, out, c, st);
-    case 256: return plane_pair<128, 256>(inverse, in, out, c, st);
-    case 320: return plane_pair<160, 320>(inverse, in, out, c, st);
+#define OKMC_CASE(n, h) \
+  case n: return plane_pair<h, n>(inverse, variant, in, out, c, st);
+    OKMC_FAST_EDGES(OKMC_CASE)
+#undef OKMC_CASE
     default: return cudaErrorInvalidConfiguration;
   }
 }
 
-cudaError_t launch_pencil_fast(C2<float>* spec, const PassCfg& c, cudaStream_t st) {
+// bit v set: inverse-pass variant v exists for this grid
+int plane_inv_variant_mask(const PassCfg& c) {
+  switch (c.ny) {
+#define OKMC_CASE(n, h) \
+  case n: return plane_inv_variants<h, n>();
+    OKMC_FAST_EDGES(OKMC_CASE)
+#undef OKMC_CASE
+    default: return 0;
+  }
+}
+
+cudaError_t launch_pencil_fast(const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st) {
   switch (c.nz) {
-    case 32: return pencil_one<32>(spec, c, st);
-    case 48: return pencil_one<48>(spec, c, st);
-    case 64: return pencil_one<64>(spec, c, st);
-    case 96: return pencil_one<96>(spec, c, st);
-    case 128: return pencil_one<128>(spec, c, st);
-    case 160: return pencil_one<160>(spec, c, st);
-    case 192: return pencil_one<192>(spec, c, st);
-    case 256: return pencil_one<256>(spec, c, st);
-    case 320: return pencil_one<320>(spec, c, st);
+    case 32: return pencil_one<32>(in, out, c, st);
+    case 48: return pencil_one<48>(in, out, c, st);
+    case 64: return pencil_one<64>(in, out, c, st);
+    case 96: return pencil_one<96>(in, out, c, st);
+    case 128: return pencil_one<128>(in, out, c, st);
+    case 160: return pencil_one<160>(in, out, c, st);
+    case 192: return pencil_one<192>(in, out, c, st);
+    case 256: return pencil_one<256>(in, out, c, st);
+    case 320: return pencil_one<320>(in, out, c, st);
     default: return cudaErrorInvalidConfiguration;
   }
 }

@@ -29,7 +29,7 @@ EXPORTED = [
     'okmc_interaction_energies', 'okmc_candidate_energies', 'okmc_self_terms', 'okmc_get_stencil', 'okmc_step',
     'okmc_get_stats', 'okmc_device_bytes', 'okmc_set_profiling', 'okmc_kernel_times', 'okmc_reset_kernel_times',
     'okmc_launch_shape', 'okmc_solve_stress_static', 'okmc_set_graphs', 'okmc_batch_create', 'okmc_batch_step',
-    'okmc_batch_destroy', 'okmc_batch_last_error',
+    'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_get_variants', 'okmc_set_variant',
 ]
 
 
@@ -98,6 +98,8 @@ def load(path=LIB_PATH):
         'okmc_batch_step': (C.c_int, [vp, C.POINTER(StepParams), i64, C.POINTER(StepStats)]),
         'okmc_batch_destroy': (C.c_int, [vp]),
         'okmc_batch_last_error': (C.c_char_p, [vp]),
+        'okmc_get_variants': (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32)]),
+        'okmc_set_variant': (C.c_int, [vp, i32, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -259,6 +261,17 @@ class Grid:
 
     def set_graphs(self, on=True):
         self._chk(self.lib.okmc_set_graphs(self.h, int(on)))
+
+    def variants(self):
+        """(current, available): per pass (forward plane, pencil, inverse plane) the
+        launch variant in use and the bit mask of variants that exist."""
+        cur = (C.c_int32 * 3)()
+        av = (C.c_int32 * 3)()
+        self._chk(self.lib.okmc_get_variants(self.h, cur, av))
+        return list(cur), list(av)
+
+    def set_variant(self, pass_, variant):
+        self._chk(self.lib.okmc_set_variant(self.h, pass_, variant))
 
     def launch_shape(self):
         out = (C.c_int32 * 3)()

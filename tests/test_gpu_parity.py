@@ -322,6 +322,53 @@ def test_large_256_stress_and_sampled_energies(large_oracle, precision):
         assert np.abs(Ec[i] - ej).max() <= tol, (i, Ec[i], ej)
 
 
+# ------------------------------------------------------------------ incremental plane transforms
+@pytest.mark.parametrize('mode', [ok.RESIDENCE, ok.FIXED_DT])
+def test_incremental_plane_transforms_equal_fresh_solve(mode):
+    """After steps that move defects, only the z-planes whose eigenstrain changed are
+    transformed again; the stress equals, bit for bit, a fresh solve of the same
+    configuration on a new grid (the fixed-point eigenstrain is exact, so every clean
+    plane's input is the same)."""
+    w = scaled_population((64, 64, 64), 40, seed=9, r111=(0.4, 1.2), r100=(0.4, 1.2))
+    a = make_grid(w, seed=3)
+    assert a.launch_shape()[0] == -1
+    a.step(w.T_K, 25, mode=mode)
+    moved = a.get_defects()
+    assert not np.array_equal(moved['pos'], w.defects['pos'])
+    sa = a.solve_stress()
+    b = ok.Grid(w.n, w.voxel_nm, *w.C)
+    b.set_defects(moved)
+    sb = b.solve_stress()
+    assert np.array_equal(sa, sb)
+    assert np.array_equal(a.interaction_energies(), b.interaction_energies())
+    a.close()
+    b.close()
+
+
+# ------------------------------------------------------------------ launch variants
+@pytest.mark.parametrize('n', [(48, 48, 48), (96, 96, 64), (128, 128, 32), (160, 160, 32), (320, 320, 32)])
+def test_pass_variants_bitwise_equal(n):
+    """Every launch variant of the FFT passes gives the same stress, bit for bit."""
+    w = scaled_population(n, 20, seed=n[0], r111=(0.4, 1.0), r100=(0.4, 1.0))
+    g = make_grid(w)
+    cur, avail = g.variants()
+    assert all((avail[p] >> cur[p]) & 1 for p in range(3))
+    ref = None
+    for p in range(3):
+        for v in range(31):
+            if not (avail[p] >> v) & 1:
+                continue
+            g.set_variant(p, v)
+            s = g.solve_stress()
+            if ref is None:
+                ref = s
+            assert np.array_equal(s, ref), (p, v)
+        g.set_variant(p, cur[p])
+    with pytest.raises(ok.OkmcError):
+        g.set_variant(2, 30)
+    g.close()
+
+
 # ------------------------------------------------------------------ graphs and batches
 def test_graph_replay_equals_kernel_by_kernel():
     w = config_small()
