@@ -297,15 +297,15 @@ __global__ void k_fixed_to_real(const Q* __restrict__ eps, T* __restrict__ out, 
 }
 
 // ---------------------------------------------------------------- self-term table
-// Scalar count fields of up to six stencils (defect i0 + f/2, class f%2), each
+// Scalar count fields of up to six stencils (defect b.idx[f/2], class f%2), each
 // placed with its base voxel at the origin.
 template <class Q>
 __global__ void k_wfields(Q* __restrict__ f, int3 n, const int* __restrict__ ptr, const int* __restrict__ off,
-                          const uint8_t* __restrict__ cnt, int i0, int nf) {
+                          const uint8_t* __restrict__ cnt, WBatch b) {
   const int fi = blockIdx.x;
-  if (fi >= nf) return;
+  if (fi >= 2 * b.nb) return;
   const size_t N = (size_t)n.x * n.y * n.z;
-  const int i = i0 + fi / 2, c = fi & 1;
+  const int i = b.idx[fi / 2], c = fi & 1;
   for (int k = ptr[2 * i + c] + threadIdx.x; k < ptr[2 * i + c + 1]; k += blockDim.x) {
     int dx, dy, dz;
     unpack_off(off[k], dx, dy, dz);
@@ -334,95 +334,131 @@ __device__ __forceinline__ T q_of(const T* tau, T te, T m0, T m1, T m2, T C11, T
 }
 
 
-// q(xi) is evaluated in FP64 whatever the field precision: it is a difference of two
-// terms of similar size, and an FP32 evaluation biases the self terms by ~2e-7
-// relative (tens of micro-eV on a 100 eV self energy).
-template <class T>
-__global__ void __launch_bounds__(256) k_selfterm_partial(const C2<T>* __restrict__ spec, PassCfg c, WBatch b,
-                                                          const double2* __restrict__ phx, const double2* __restrict__ phy,
-                                                          const double2* __restrict__ phz, double* __restrict__ partial) {
-  __shared__ double sh[32];
+// Frequency of half-spectrum index (kx, ky, kz) as a unit vector (signed frequencies,
+// Nyquist index -N/2); false at xi = 0.
+__device__ __forceinline__ bool unit_freq(const PassCfg& c, int kx, int ky, int kz, double& m0, double& m1, double& m2) {
+  const int fx = kx < c.H ? kx : kx - c.nx;
+  const int fy = ky < c.ny / 2 ? ky : ky - c.ny;
+  const int fz = kz < c.nz / 2 ? kz : kz - c.nz;
+  if (fx == 0 && fy == 0 && fz == 0) return false;
+  const double qx = (double)fx / c.nx, qy = (double)fy / c.ny, qz = (double)fz / c.nz;
+  const double rn = 1.0 / sqrt(qx * qx + qy * qy + qz * qz);
+  m0 = qx * rn;
+  m1 = qy * rn;
+  m2 = qz * rn;
+  return true;
+}
+
+// Q_t(xi) = E_t : M(xi) : E_t for each defect type present, [t][kz][p].  It is
+// evaluated in FP64 whatever the field precision (a difference of two terms of
+// similar size; an FP32 evaluation biases the self terms by ~2e-7 relative) and
+// stored in QT.  A defect's q is s^2 Q_t with e = s E_t.
+template <class QT>
+__global__ void __launch_bounds__(256) k_qtable(QT* __restrict__ out, PassCfg c, QTypes qt) {
   const size_t P = (size_t)(c.H + 1) * c.ny;
   const size_t total = P * c.nz;
-  double tau[3][6], te[3];
-  for (int d = 0; d < 3; ++d) {
-    const double* e = b.e6[d];
-    const double tr = e[0] + e[1] + e[2];
-    for (int a = 0; a < 3; ++a) tau[d][a] = c.C12 * tr + (c.C11 - c.C12) * e[a];
-    for (int a = 3; a < 6; ++a) tau[d][a] = 2.0 * c.C44 * e[a];
-    te[d] = tau[d][0] * e[0] + tau[d][1] * e[1] + tau[d][2] * e[2] +
-            2.0 * (tau[d][3] * e[3] + tau[d][4] * e[4] + tau[d][5] * e[5]);
-  }
-  double acc[3][10];
-  for (int d = 0; d < 3; ++d)
-    for (int k = 0; k < 10; ++k) acc[d][k] = 0.0;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
     const int kz = (int)(idx / P);
     const int p = (int)(idx % P);
     const int kx = p / c.ny, ky = p % c.ny;
-    const int fx = kx < c.H ? kx : kx - c.nx;
-    const int fy = ky < c.ny / 2 ? ky : ky - c.ny;
-    const int fz = kz < c.nz / 2 ? kz : kz - c.nz;
-    const double wgt = (kx == 0 || kx == c.H) ? 1.0 : 2.0;
-    double qd[3];
-    if (fx == 0 && fy == 0 && fz == 0) {
-      for (int d = 0; d < 3; ++d) qd[d] = (c.k0_mode == OKMC_MEAN_STRAIN_ZERO) ? -te[d] : 0.0;
-    } else {
-      const double qx = (double)fx / c.nx, qy = (double)fy / c.ny, qz = (double)fz / c.nz;
-      const double rn = 1.0 / sqrt(qx * qx + qy * qy + qz * qz);
-      const double m0 = qx * rn, m1 = qy * rn, m2 = qz * rn;
-      const bool nx_ = (kx == c.H), ny_ = (2 * ky == c.ny), nz_ = (2 * kz == c.nz);
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        double v = q_of<double>(tau[d], te[d], m0, m1, m2, c.C11, c.C12, c.C44);
+    double m0, m1, m2;
+    const bool nz0 = unit_freq(c, kx, ky, kz, m0, m1, m2);
+    const bool nx_ = (kx == c.H), ny_ = (2 * ky == c.ny), nz_ = (2 * kz == c.nz);
+    for (int t = 0; t < qt.nt; ++t) {
+      const double* e = qt.e6[t];
+      const double tr = e[0] + e[1] + e[2];
+      double tau[6];
+      for (int a = 0; a < 3; ++a) tau[a] = c.C12 * tr + (c.C11 - c.C12) * e[a];
+      for (int a = 3; a < 6; ++a) tau[a] = 2.0 * c.C44 * e[a];
+      const double te = tau[0] * e[0] + tau[1] * e[1] + tau[2] * e[2] + 2.0 * (tau[3] * e[3] + tau[4] * e[4] + tau[5] * e[5]);
+      double v;
+      if (!nz0) {
+        v = (c.k0_mode == OKMC_MEAN_STRAIN_ZERO) ? -te : 0.0;
+      } else {
+        v = q_of<double>(tau, te, m0, m1, m2, c.C11, c.C12, c.C44);
         if (nx_ || ny_ || nz_)
-          v = 0.5 * (v + q_of<double>(tau[d], te[d], nx_ ? -m0 : m0, ny_ ? -m1 : m1, nz_ ? -m2 : m2, c.C11, c.C12, c.C44));
-        qd[d] = v;
+          v = 0.5 * (v + q_of<double>(tau, te, nx_ ? -m0 : m0, ny_ ? -m1 : m1, nz_ ? -m2 : m2, c.C11, c.C12, c.C44));
       }
+      out[(size_t)t * total + idx] = (QT)v;
     }
+  }
+}
+
+// Per-thread accumulators of the self-term sums: compensated FP32 pairs for FP32
+// spectra, plain FP64 for FP64 spectra.
+template <class T> struct WAcc;
+template <> struct WAcc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+template <> struct WAcc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+// Sums over the half spectrum (weight 2 off the kx = 0 and kx = nx/2 planes) of
+// Q_t(xi) |w0|^2, Q_t |w1|^2 and Q_t Re(conj(w1) w0 exp(i xi.d)) for the eight
+// d in {-1, 0}^3, per defect of the batch; the products are formed in the
+// spectrum precision.
+template <class T, class QT>
+__global__ void __launch_bounds__(256) k_selfterm_partial(const C2<T>* __restrict__ spec, PassCfg c, WBatch b,
+                                                          const QT* __restrict__ qtab, const double2* __restrict__ phx,
+                                                          const double2* __restrict__ phy, const double2* __restrict__ phz,
+                                                          double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const size_t P = (size_t)(c.H + 1) * c.ny;
+  const size_t total = P * c.nz;
+  WAcc<T> acc[3][10];
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int kz = (int)(idx / P);
+    const int p = (int)(idx % P);
+    const int kx = p / c.ny, ky = p % c.ny;
+    const T wgt = (kx == 0 || kx == c.H) ? T(1) : T(2);
+    // phase factors: bit 2 (x), 1 (y), 0 (z) clear means d = -1 on that axis, i.e. a
+    // factor conj(e_axis)
     const double2 ex = phx[kx], ey = phy[ky], ez = phz[kz];
+    const C2<T> ax{(T)ex.x, (T)-ex.y}, ay{(T)ey.x, (T)-ey.y}, az{(T)ez.x, (T)-ez.y};
+    C2<T> ph[8];
+    ph[7] = C2<T>{T(1), T(0)};
+    ph[6] = az;
+    ph[5] = ay;
+    ph[4] = ay * az;
+    ph[3] = ax;
+    ph[2] = ax * az;
+    ph[1] = ax * ay;
+    ph[0] = ph[1] * az;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
+      if (d >= b.nb) break;
       const C2<T> w0 = spec[((size_t)(2 * d) * c.nz + kz) * P + p];
       const C2<T> w1 = spec[((size_t)(2 * d + 1) * c.nz + kz) * P + p];
-      const double q = wgt * qd[d];
-      const double a0r = w0.x, a0i = w0.y, a1r = w1.x, a1i = w1.y;
-      acc[d][0] += q * (a0r * a0r + a0i * a0i);
-      acc[d][1] += q * (a1r * a1r + a1i * a1i);
+      const T q = wgt * (T)qtab[(size_t)b.type[d] * total + idx];
+      acc[d][0].add(q * (w0.x * w0.x + w0.y * w0.y));
+      acc[d][1].add(q * (w1.x * w1.x + w1.y * w1.y));
       // conj(w1) * w0
-      const double cr = a1r * a0r + a1i * a0i, ci = a1r * a0i - a1i * a0r;
-      // d = (dx, dy, dz) in {-1, 0}^3, index 4(dx==0) + 2(dy==0) + (dz==0) ... times exp(i xi.d)
-      for (int s = 0; s < 8; ++s) {
-        double pr = cr, pi = ci;
-        if (!(s & 4)) {  // dx = -1: multiply by conj(ex)
-          const double r = pr * ex.x + pi * ex.y, im = pi * ex.x - pr * ex.y;
-          pr = r;
-          pi = im;
-        }
-        if (!(s & 2)) {
-          const double r = pr * ey.x + pi * ey.y, im = pi * ey.x - pr * ey.y;
-          pr = r;
-          pi = im;
-        }
-        if (!(s & 1)) {
-          const double r = pr * ez.x + pi * ez.y, im = pi * ez.x - pr * ez.y;
-          pr = r;
-          pi = im;
-        }
-        acc[d][2 + s] += q * pr;
-      }
+      const T cr = w1.x * w0.x + w1.y * w0.y, ci = w1.x * w0.y - w1.y * w0.x;
+      const T qr = q * cr, qi = q * ci;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) acc[d][2 + s].add(qr * ph[s].x - qi * ph[s].y);
     }
   }
   for (int d = 0; d < 3; ++d)
     for (int k = 0; k < 10; ++k) {
-      const double t = block_sum_d(acc[d][k], sh);
+      const double t = block_sum_d(acc[d][k].value(), sh);
       if (threadIdx.x == 0) partial[(size_t)blockIdx.x * 30 + d * 10 + k] = t;
     }
 }
 
-// W[i][c][0] = pref a_c^2 S_cc;  W[i][0][1+j] = pref a_0 a_1 X[d0(lambda_j)],
+// W[i][c][0] = pref a_c^2 s^2 S_cc;  W[i][0][1+j] = pref a_0 a_1 s^2 X[d0(lambda_j)],
 // d0 = (lambda - 1)/2 in {-1,0}^3;  W[i][1][1+j] = W[i][0][1+(7-j)] (the reverse jump).
-__global__ void k_selfterm_final(const double* __restrict__ partial, int nblocks, int i0, int nb,
+__global__ void k_selfterm_final(const double* __restrict__ partial, int nblocks, WBatch b,
                                  const double* __restrict__ alpha, double pref, double* __restrict__ W) {
   const int d = threadIdx.x / 10, k = threadIdx.x % 10;
   __shared__ double S[30];
@@ -432,17 +468,16 @@ __global__ void k_selfterm_final(const double* __restrict__ partial, int nblocks
     S[threadIdx.x] = t;
   }
   __syncthreads();
-  if (threadIdx.x >= 30 || d >= nb || k) return;
-  const int i = i0 + d;
+  if (threadIdx.x >= 30 || d >= b.nb || k) return;
+  const int i = b.idx[d];
   const double a0 = alpha[2 * i], a1 = alpha[2 * i + 1];
+  const double ps = pref * b.s2[d];
   double* w = W + (size_t)i * 18;
-  w[0] = pref * a0 * a0 * S[d * 10 + 0];
-  w[9] = pref * a1 * a1 * S[d * 10 + 1];
-  for (int j = 0; j < 8; ++j) {
-    // lambda_j components sx = +-1 -> d0 = 0 (sx = +1) or -1 (sx = -1); s bit set means d = 0
-    const int s = j;  // bit 2: sx > 0, bit 1: sy > 0, bit 0: sz > 0 -- same encoding as s
-    w[1 + j] = pref * a0 * a1 * S[d * 10 + 2 + s];
-  }
+  w[0] = ps * a0 * a0 * S[d * 10 + 0];
+  w[9] = ps * a1 * a1 * S[d * 10 + 1];
+  // lambda_j components sx = +-1 -> d0 = 0 (sx = +1) or -1 (sx = -1); bit set means d = 0,
+  // the same encoding as j (bit 2: sx > 0, bit 1: sy > 0, bit 0: sz > 0)
+  for (int j = 0; j < 8; ++j) w[1 + j] = ps * a0 * a1 * S[d * 10 + 2 + j];
   for (int j = 0; j < 8; ++j) w[10 + j] = w[1 + (7 - j)];
 }
 
@@ -794,18 +829,23 @@ cudaError_t launch_fixed_to_real(const Q* eps, T* out, size_t total, double q, c
   return cudaGetLastError();
 }
 template <class Q>
-cudaError_t launch_wfields(Q* f, int3 n, const int* ptr, const int* off, const uint8_t* cnt, int i0, int nf, cudaStream_t st) {
-  k_wfields<Q><<<nf, 256, 0, st>>>(f, n, ptr, off, cnt, i0, nf);
+cudaError_t launch_wfields(Q* f, int3 n, const int* ptr, const int* off, const uint8_t* cnt, const WBatch& b, cudaStream_t st) {
+  k_wfields<Q><<<2 * b.nb, 256, 0, st>>>(f, n, ptr, off, cnt, b);
+  return cudaGetLastError();
+}
+template <class QT>
+cudaError_t launch_qtable(QT* out, const PassCfg& c, const QTypes& qt, cudaStream_t st) {
+  k_qtable<QT><<<1216, 256, 0, st>>>(out, c, qt);
   return cudaGetLastError();
 }
 template <class T>
-cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b, const double2* phx, const double2* phy,
-                            const double2* phz, double* partial, int nblocks, int i0, const double* alpha, double pref,
-                            double* W, cudaStream_t st) {
-  k_selfterm_partial<T><<<nblocks, 256, 0, st>>>(spec, c, b, phx, phy, phz, partial);
+cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b, const T* qtab, const double2* phx,
+                            const double2* phy, const double2* phz, double* partial, int nblocks, const double* alpha,
+                            double pref, double* W, cudaStream_t st) {
+  k_selfterm_partial<T, T><<<nblocks, 256, 0, st>>>(spec, c, b, qtab, phx, phy, phz, partial);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_selfterm_final<<<1, 32, 0, st>>>(partial, nblocks, i0, b.nb, alpha, pref, W);
+  k_selfterm_final<<<1, 32, 0, st>>>(partial, nblocks, b, alpha, pref, W);
   return cudaGetLastError();
 }
 template <class T>
@@ -837,12 +877,16 @@ template cudaError_t launch_apply_moves<int64_t>(int64_t*, int3, const DefGeo*, 
                                                  const double*, const Move*, const DevState*, double, double, int*, int*, cudaStream_t);
 template cudaError_t launch_fixed_to_real<int32_t, float>(const int32_t*, float*, size_t, double, cudaStream_t);
 template cudaError_t launch_fixed_to_real<int64_t, double>(const int64_t*, double*, size_t, double, cudaStream_t);
-template cudaError_t launch_wfields<int32_t>(int32_t*, int3, const int*, const int*, const uint8_t*, int, int, cudaStream_t);
-template cudaError_t launch_wfields<int64_t>(int64_t*, int3, const int*, const int*, const uint8_t*, int, int, cudaStream_t);
-template cudaError_t launch_selfterm<float>(const C2<float>*, const PassCfg&, const WBatch&, const double2*, const double2*,
-                                           const double2*, double*, int, int, const double*, double, double*, cudaStream_t);
-template cudaError_t launch_selfterm<double>(const C2<double>*, const PassCfg&, const WBatch&, const double2*, const double2*,
-                                            const double2*, double*, int, int, const double*, double, double*, cudaStream_t);
+template cudaError_t launch_wfields<int32_t>(int32_t*, int3, const int*, const int*, const uint8_t*, const WBatch&, cudaStream_t);
+template cudaError_t launch_wfields<int64_t>(int64_t*, int3, const int*, const int*, const uint8_t*, const WBatch&, cudaStream_t);
+template cudaError_t launch_qtable<float>(float*, const PassCfg&, const QTypes&, cudaStream_t);
+template cudaError_t launch_qtable<double>(double*, const PassCfg&, const QTypes&, cudaStream_t);
+template cudaError_t launch_selfterm<float>(const C2<float>*, const PassCfg&, const WBatch&, const float*, const double2*,
+                                           const double2*, const double2*, double*, int, const double*, double, double*,
+                                           cudaStream_t);
+template cudaError_t launch_selfterm<double>(const C2<double>*, const PassCfg&, const WBatch&, const double*, const double2*,
+                                            const double2*, const double2*, double*, int, const double*, double, double*,
+                                            cudaStream_t);
 template cudaError_t launch_energies<float>(const float*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
                                            const uint8_t*, const double*, const double*, double, int, const int*, double*,
                                            double*, RateArgs, cudaStream_t);

@@ -40,11 +40,13 @@ cudaError_t launch_diff_positions(okmc_defect* d, const int* pos, int nd, Move* 
 cudaError_t launch_gather_positions(const okmc_defect* d, int* pos, int nd, cudaStream_t st);
 template <class Q, class T> cudaError_t launch_fixed_to_real(const Q* eps, T* out, size_t total, double q, cudaStream_t st);
 template <class Q>
-cudaError_t launch_wfields(Q* f, int3 n, const int* ptr, const int* off, const uint8_t* cnt, int i0, int nf, cudaStream_t st);
+cudaError_t launch_wfields(Q* f, int3 n, const int* ptr, const int* off, const uint8_t* cnt, const WBatch& b, cudaStream_t st);
+template <class QT>
+cudaError_t launch_qtable(QT* out, const PassCfg& c, const QTypes& qt, cudaStream_t st);
 template <class T>
-cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b, const double2* phx, const double2* phy,
-                            const double2* phz, double* partial, int nblocks, int i0, const double* alpha, double pref,
-                            double* W, cudaStream_t st);
+cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b, const T* qtab, const double2* phx,
+                            const double2* phy, const double2* phz, double* partial, int nblocks, const double* alpha,
+                            double pref, double* W, cudaStream_t st);
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
@@ -365,32 +367,86 @@ int validate_defects(okmc_grid* g, const okmc_defect* d, int nd) {
   return OKMC_OK;
 }
 
+// Self-term table W (translation invariant, so computed once per distinct shape):
+// the scalar count fields of three defects' stencils (both classes) are transformed
+// with the forward plane and pencil passes, and k_selfterm_partial sums them against
+// the type tables Q_t, which k_qtable leaves in the (idle) stress buffer.
 template <class T, class Q>
 int build_self_terms(okmc_grid* g) {
   const size_t N = g->N;
   const int3 n = dims(g);
-  cudaError_t e = cudaMemsetAsync(g->eps, 0, 6 * N * sizeof(Q), g->st);
-  if (e != cudaSuccess) return cuda_fail(g, e, "memset");
+  const int nd = g->nd;
+  std::vector<DefGeo> geo(nd);
+  cudaError_t e = cudaMemcpyAsync(geo.data(), g->d_geo, nd * sizeof(DefGeo), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "geometry read back");
+  // types: 1/2<111> axes 0-3, <100> axes 4-6, SIA cluster 7; e = s E_t
+  QTypes qt{};
+  int slot[8];
+  for (int t = 0; t < 8; ++t) slot[t] = -1;
+  std::vector<int> ty(nd);
+  std::vector<double> s2(nd);
+  for (int i = 0; i < nd; ++i) {
+    const okmc_defect& r = g->h_def[i];
+    const int t = r.type == OKMC_LOOP_111 ? r.axis : r.type == OKMC_LOOP_100 ? 4 + r.axis : 7;
+    if (slot[t] < 0) {
+      slot[t] = qt.nt++;
+      double nrm = 0.0;
+      for (int a = 0; a < 6; ++a) nrm = std::max(nrm, std::fabs(geo[i].e6[a]));
+      for (int a = 0; a < 6; ++a) qt.e6[slot[t]][a] = geo[i].e6[a] / nrm;
+    }
+    const double* E = qt.e6[slot[t]];
+    double num = 0.0, den = 0.0;
+    for (int a = 0; a < 6; ++a) {
+      num += geo[i].e6[a] * E[a];
+      den += E[a] * E[a];
+    }
+    const double sc = num / den;
+    for (int a = 0; a < 6; ++a)
+      if (std::fabs(geo[i].e6[a] - sc * E[a]) > 1e-12 * std::fabs(sc))
+        return fail(g, OKMC_ECUDA, "eigenstrain tensor not proportional to its type's");
+    ty[i] = slot[t];
+    s2[i] = sc * sc;
+  }
+  // one computation per distinct shape: loops by (type, axis, radius), clusters by size
+  std::map<std::tuple<int, int, int64_t>, int> first;
+  std::vector<int> rep(nd), reps;
+  for (int i = 0; i < nd; ++i) {
+    const okmc_defect& r = g->h_def[i];
+    int64_t rb;
+    std::memcpy(&rb, &r.radius_nm, sizeof(rb));
+    const auto key = r.type == OKMC_SIA_CLUSTER ? std::make_tuple(r.type, 0, (int64_t)r.size) : std::make_tuple(r.type, r.axis, rb);
+    auto it = first.find(key);
+    if (it == first.end()) {
+      first.emplace(key, i);
+      rep[i] = i;
+      reps.push_back(i);
+    } else {
+      rep[i] = it->second;
+    }
+  }
+  T* qtab = (T*)g->sig;
+  if ((size_t)qt.nt * g->P * g->n[2] > 6 * N) return fail(g, OKMC_EINVAL, "grid too small for the self-term tables");
   PassCfg c = g->cfg;
   c.q = 1.0;
   c.ncomp = 6;
   c.forward_only = 1;
+  OKMC_TRY(run(g, "self_qtable", [&] { return launch_qtable<T>(qtab, c, qt, g->st); }));
+  e = cudaMemsetAsync(g->eps, 0, 6 * N * sizeof(Q), g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "memset");
   const double pref = -kKappa * g->h * g->h * g->h / (double)N;
   const double2* phx = g->ph;
   const double2* phy = g->ph + (g->H + 1);
   const double2* phz = phy + g->n[1];
-  for (int i0 = 0; i0 < g->nd; i0 += 3) {
+  for (size_t r0 = 0; r0 < reps.size(); r0 += 3) {
     WBatch b{};
-    b.nb = std::min(3, g->nd - i0);
+    b.nb = (int)std::min<size_t>(3, reps.size() - r0);
     for (int d = 0; d < b.nb; ++d) {
-      // the eigenstrain tensor of each defect is read back from the setup kernel's output
-      DefGeo geo;
-      e = cudaMemcpyAsync(&geo, g->d_geo + i0 + d, sizeof(DefGeo), cudaMemcpyDeviceToHost, g->st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
-      if (e != cudaSuccess) return cuda_fail(g, e, "geometry read back");
-      for (int a = 0; a < 6; ++a) b.e6[d][a] = geo.e6[a];
+      b.idx[d] = reps[r0 + d];
+      b.type[d] = ty[b.idx[d]];
+      b.s2[d] = s2[b.idx[d]];
     }
-    OKMC_TRY(run(g, "self_fields", [&] { return launch_wfields<Q>((Q*)g->eps, n, g->d_ptr, g->d_off, g->d_cnt, i0, 2 * b.nb, g->st); }));
+    OKMC_TRY(run(g, "self_fields", [&] { return launch_wfields<Q>((Q*)g->eps, n, g->d_ptr, g->d_off, g->d_cnt, b, g->st); }));
     if (g->fast) {
       OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, 0, g->eps, g->spec, c, g->st); }));
       OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast((const C2<float>*)g->spec, (C2<float>*)g->spec, c, g->st); }));
@@ -399,12 +455,23 @@ int build_self_terms(okmc_grid* g) {
       OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil<T>((C2<T>*)g->spec, c, g->st); }));
     }
     OKMC_TRY(run(g, "self_terms", [&] {
-      return launch_selfterm<T>((const C2<T>*)g->spec, c, b, phx, phy, phz, g->d_partial, kSelfBlocks, i0, g->d_alpha, pref,
+      return launch_selfterm<T>((const C2<T>*)g->spec, c, b, qtab, phx, phy, phz, g->d_partial, kSelfBlocks, g->d_alpha, pref,
                                 g->d_W, g->st);
     }));
     e = cudaMemsetAsync(g->eps, 0, 6 * N * sizeof(Q), g->st);
     if (e != cudaSuccess) return cuda_fail(g, e, "memset");
   }
+  if (reps.size() < (size_t)nd) {  // copy each shape's row to the defects that share it
+    std::vector<double> W((size_t)nd * 18);
+    e = cudaMemcpyAsync(W.data(), g->d_W, W.size() * sizeof(double), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    for (int i = 0; i < nd && e == cudaSuccess; ++i)
+      if (rep[i] != i) std::copy(W.begin() + (size_t)rep[i] * 18, W.begin() + (size_t)rep[i] * 18 + 18, W.begin() + (size_t)i * 18);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_W, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+    if (e != cudaSuccess) return cuda_fail(g, e, "self-term copy");
+  }
+  g->sigma_valid = false;
   return OKMC_OK;
 }
 

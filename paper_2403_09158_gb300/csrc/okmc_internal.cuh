@@ -283,9 +283,21 @@ struct RateArgs {
 };
 
 // Eigenstrain tensors of the (at most three) defects whose self terms one batch computes.
+// One batch of the self-term build: up to three defects (the stencils of defect
+// idx[d] in classes 0 and 1 occupy fields 2d and 2d+1), the type table row of each
+// and the square of its eigenstrain scale relative to the type's unit tensor.
 struct WBatch {
-  double e6[3][6];
+  int idx[3];
+  int type[3];
+  double s2[3];
   int nb;
+};
+
+// Unit eigenstrain tensors of the defect types present (at most eight: four
+// 1/2<111> loop axes, three <100> loop axes, the dilatational SIA cluster).
+struct QTypes {
+  double e6[8][6];
+  int nt;
 };
 
 __host__ __device__ __forceinline__ int pack_off(int dx, int dy, int dz) {

@@ -55,29 +55,25 @@ def place(rng, n, h, kinds, radii, sizes, max_tries=20000):
     rejecting a site closer than R_i + R_j + 2h (minimum image) to an earlier one."""
     n = np.asarray(n)
     L = n * h
-    pos = np.zeros((len(kinds), 3), dtype=np.int64)
-    centres = []
-    rr = []
+    m = len(kinds)
+    pos = np.zeros((m, 3), dtype=np.int64)
+    centres = np.zeros((m, 3))
+    rr = np.zeros(m)
     for i, (k, R, s) in enumerate(zip(kinds, radii, sizes)):
         Ri = _shape_radius_nm(k, R, s, h)
         for _ in range(max_tries):
             c = int(rng.integers(0, 2))
             p = 2 * rng.integers(0, n) + c
             x = p * (h / 2.0)
-            ok = True
-            for xc, Rj in zip(centres, rr):
-                dvec = x - xc
-                dvec -= L * np.round(dvec / L)
-                if np.sqrt(dvec @ dvec) < Ri + Rj + 2.0 * h:
-                    ok = False
-                    break
-            if ok:
+            dvec = x - centres[:i]
+            dvec -= L * np.round(dvec / L)
+            if not np.any(np.sqrt(np.einsum('ij,ij->i', dvec, dvec)) < Ri + rr[:i] + 2.0 * h):
                 break
         else:
             raise RuntimeError('could not place defect %d' % i)
         pos[i] = p
-        centres.append(x)
-        rr.append(Ri)
+        centres[i] = x
+        rr[i] = Ri
     return pos
 
 
@@ -187,3 +183,39 @@ def scaled_population(n, n_defects, seed, T_K=500.0, r111=(0.5, 4.0), r100=(0.5,
     n = tuple(int(v) for v in (n if np.ndim(n) else (n, n, n)))
     d = mixed_population(n, n_defects, seed, r111=r111, r100=r100)
     return Workload('mix_%dx%dx%d_%d' % (n + (n_defects,)), n, VOXEL_NM, d, T_K, FE_CUBIC, seed, 0)
+
+
+def density_cap(n):
+    """Largest defect count drawn for an n^3 box in the ensemble and serving workloads:
+    150 per 64^3 box scaled by volume.  With the config-2 radii and the
+    R_i + R_j + 2h exclusion of ``place``, larger counts do not fit a small box
+    (64^3 with 300 defects already fails)."""
+    return max(1, int(150 * (n / 64.0) ** 3))
+
+
+def _placed_population(n, nd, seed, r111, r100):
+    """mixed_population with the count lowered by 10 % until placement succeeds
+    (deterministic for a given seed)."""
+    while True:
+        try:
+            return mixed_population((n, n, n), nd, seed, r111=r111, r100=r100)
+        except RuntimeError:
+            if nd <= 1:
+                raise
+            nd = max(1, int(nd * 0.9))
+
+
+def config_batch(seed=1004, n_replicas=64, edges=(64, 96, 128, 160, 192), nd_range=(50, 800),
+                 T_range=(300.0, 600.0)):
+    """Ensemble of independent replicas: edge ~ U(edges), defect count ~ U{50..800}
+    capped by ``density_cap``, config-2 mix and radii, T ~ U(300, 600) K."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_replicas):
+        n = int(rng.choice(edges))
+        nd = min(int(rng.integers(nd_range[0], nd_range[1] + 1)), density_cap(n))
+        T = float(rng.uniform(*T_range))
+        d = _placed_population(n, nd, seed * 1000 + r, (0.5, 2.5), (1.0, 3.0))
+        out.append(Workload('replica%02d_%dcubed_%d' % (r, n, len(d)), (n, n, n), VOXEL_NM, d, T, FE_CUBIC,
+                            seed * 1000 + r, 1000))
+    return out
