@@ -240,6 +240,82 @@ def run_batch(args):
     return 0
 
 
+def run_serve(args):
+    """Serving: a pool of 32 resident replicas (edges 48-320) behind the request server
+    (4 lanes, 120 GB admission budget); Poisson request streams at each offered rate,
+    half solves (stress + site energies) and half steps of 1-10 events.  Latency is
+    completion minus submission on the server's clock."""
+    import torch
+
+    from paper_2403_09158_gb300 import okmc as ok
+    from paper_2403_09158_gb300.workload import config_serve, request_stream
+
+    pool = config_serve()
+    budget = 120 * 10 ** 9
+    srv = ok.Server(hbm_budget=budget, lanes=4)
+    ids = [srv.add_replica(w.n, w.voxel_nm, *w.C, w.defects, seed=w.seed) for w in pool]
+    vox = [int(np.prod(w.n)) for w in pool]
+    # admission of every replica (cold start), measured on its own
+    t0 = time.perf_counter()
+    cold = [srv.submit_solve(i) for i in ids]
+    cold_lat = []
+    solves = {}  # per replica: solves done so far (the work of a request is the solves it ran)
+    for r, t in enumerate(cold):
+        res, _ = srv.wait(t)
+        assert res['status'] == 0, res
+        cold_lat.append(res['t_end'] - res['t_submit'])
+        solves[r] = res['stats']['solves']
+    cold_s = time.perf_counter() - t0
+    rates = [float(x) for x in args.rates.split(',')]
+    per_rate = []
+    clk = Clocks(torch.cuda.current_device())
+    for k, rate in enumerate(rates):
+        n_req = int(min(args.max_requests, max(40, rate * args.seconds)))
+        reqs = request_stream(1005 + k, rate, n_req, len(ids))
+        tickets = []
+        start = time.perf_counter()
+        for (ta, r, kind, kk) in reqs:
+            while True:
+                dt = start + ta - time.perf_counter()
+                if dt <= 0:
+                    break
+                time.sleep(min(dt, 0.002))
+            if kind == 'solve':
+                tickets.append((srv.submit_solve(ids[r]), r))
+            else:
+                tickets.append((srv.submit_step(ids[r], pool[r].T_K, kk, positions=True), r))
+        lat, t_first, t_last, work = [], None, None, 0
+        for t, r in tickets:  # one replica's requests complete in submission order
+            res, _ = srv.wait(t)
+            assert res['status'] == 0, res
+            lat.append(res['t_end'] - res['t_submit'])
+            t_first = res['t_submit'] if t_first is None else min(t_first, res['t_submit'])
+            t_last = res['t_end'] if t_last is None else max(t_last, res['t_end'])
+            work += vox[r] * (res['stats']['solves'] - solves[r])
+            solves[r] = res['stats']['solves']
+        span = t_last - t_first
+        lat = np.array(lat) * 1e3
+        per_rate.append({'offered_req_per_s': rate, 'requests': n_req, 'achieved_req_per_s': n_req / span,
+                         'voxel_updates_per_s': work / span, 'p50_ms': float(np.percentile(lat, 50)),
+                         'p99_ms': float(np.percentile(lat, 99)), 'max_ms': float(lat.max())})
+    clocks = clk.stop()
+    st = srv.stats()
+    srv.close()
+    best = max(per_rate, key=lambda x: x['voxel_updates_per_s'])
+    out = {'metric': 'served voxel stress+energy updates/s', 'value': best['voxel_updates_per_s'],
+           'unit': 'voxel updates/s', 'n_gpus': 1, 'steps': None, 'warmup': None, 'higher_is_better': True,
+           'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32 fields / f64 energies', 'data': 'synthetic',
+           'config': {'workload': 'serving: 32 replicas (edge ~ U{48,64,128,256,320}, 20-3000 defects capped at the '
+                                  '256^3 density), Poisson arrivals, half solves and half steps of 1-10 events, '
+                                  '4 lanes, 120 GB admission budget',
+                      'replica_voxels': int(sum(vox)), 'defects': int(sum(len(w.defects) for w in pool))},
+           'rates': per_rate, 'cold_start': {'seconds': cold_s, 'p50_ms': float(np.percentile(cold_lat, 50) * 1e3),
+                                              'max_ms': float(max(cold_lat) * 1e3)},
+           'server': st, 'clocks': clocks}
+    print(json.dumps(out))
+    return 0
+
+
 def cpu_sample(seconds_hint=True):
     """The oracle as it stands on a bounded sample: one FP64 stress solve and the
     site + candidate energies of 4 defects on a 96^3 grid at the 256^3 workload's
@@ -268,8 +344,12 @@ def main():
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--workload', default='large', choices=['large', 'batch'],
-                    help='large: the 256^3 single-replica step (default); batch: the 64-replica ensemble')
+    ap.add_argument('--workload', default='large', choices=['large', 'batch', 'serve'],
+                    help='large: the 256^3 single-replica step (default); batch: the 64-replica ensemble; '
+                         'serve: the request server under Poisson load')
+    ap.add_argument('--rates', default='10,30,100,300,1000,2000', help='serve: offered request rates (1/s)')
+    ap.add_argument('--seconds', type=float, default=4.0, help='serve: length of each rate\'s request stream')
+    ap.add_argument('--max-requests', type=int, default=600, help='serve: cap on requests per rate')
     ap.add_argument('--solve-only', type=int, default=0, metavar='N',
                     help='profiling aid: one stress solve of an N^3 grid holding one SIA cluster, then exit')
     args = ap.parse_args()
@@ -285,6 +365,8 @@ def main():
     __graft_entry__.build()
     if args.workload == 'batch':
         return run_batch(args) if rank == 0 else 0
+    if args.workload == 'serve':
+        return run_serve(args) if rank == 0 else 0
     r = run_ours(args, ws, rank)
     if ws > 1:
         torch.distributed.destroy_process_group()

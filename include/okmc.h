@@ -188,6 +188,13 @@ int okmc_step(okmc_grid* g, const okmc_step_params* p, int64_t n_steps, okmc_ste
 /* Cumulative statistics (host). */
 int okmc_get_stats(okmc_grid* g, okmc_step_stats* out);
 
+/* Restores the kinetic state (clock, step counter, events, negative-barrier count,
+ * last time step, solve count) saved by okmc_get_stats, e.g. after re-creating a
+ * handle from defects saved with okmc_get_defects: the step counter drives the
+ * Philox counters, so the trajectory then continues exactly as it would have.
+ * s is read (host); OKMC_EINVAL for negative counts or non-finite times. */
+int okmc_set_kinetic_state(okmc_grid* g, const okmc_step_stats* s);
+
 /* okmc_step replays a captured CUDA graph of one step (solve, energies and rates,
  * event, incremental field update), one graph per (mode, T), captured on first use
  * and dropped by okmc_set_defects.  enable = 0 launches kernel by kernel instead
@@ -211,6 +218,10 @@ const char* okmc_batch_last_error(const okmc_batch* b);
 
 /* Device bytes held by the handle. */
 size_t okmc_device_bytes(const okmc_grid* g);
+
+/* Device bytes okmc_grid_create allocates for a description (fields, spectra and
+ * tables; defect data come on top with okmc_set_defects); 0 for a bad description. */
+size_t okmc_estimate_field_bytes(const okmc_grid_desc* d);
 
 /* Kernel timing: when enabled, every kernel launch of the handle is bracketed
  * with CUDA events on the handle's stream and its time is accumulated per
@@ -239,6 +250,73 @@ int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
  * for this grid; drops captured step graphs. */
 int okmc_get_variants(const okmc_grid* g, int32_t current[3], int32_t available[3]);
 int okmc_set_variant(okmc_grid* g, int32_t pass, int32_t variant);
+
+/* ---------------------------------------------------------------- serving
+ * Request server over resident replicas (the paper runs one simulation at a time;
+ * this is the library's serving loop: continuous batching of solve and step
+ * requests for many independent replicas on one GPU).
+ *
+ * okmc_server_create starts `lanes` worker threads, each with its own non-blocking
+ * CUDA stream on the device current at the call; a lane takes the oldest runnable
+ * request, runs it on its stream and waits for it, so requests for different
+ * replicas overlap on the device.  Replicas are registered with a grid description
+ * and defects (both copied; the description's stream and hbm_budget are ignored)
+ * and become resident (a live handle) at the first request that needs them.
+ * Requests for one replica run in submission order, one at a time.  Admission: a
+ * replica becomes resident only while the device bytes of all resident replicas
+ * stay within hbm_budget (0 = no limit); idle replicas are evicted least recently
+ * used first to make room, their defects and kinetic state kept on the host and
+ * restored on re-admission, so every replica's trajectory is the one it would
+ * follow alone.  While the oldest request that needs memory waits, no other replica
+ * is admitted ahead of it.
+ *
+ * Requests: OKMC_REQ_SOLVE computes the stress and the site energies (energies:
+ * host array of the replica's defect count, required); OKMC_REQ_STEP runs n_events
+ * steps with params (positions: nullable host array of 3 x defect count, filled
+ * after the steps).  The arrays must stay valid until the request completes.
+ * okmc_server_wait returns the result of a ticket once (timeout_ms < 0 waits
+ * without limit; OKMC_ETIMEOUT if not done in time); times are seconds since
+ * okmc_server_create on the host's steady clock.  okmc_server_destroy stops the
+ * lanes after their current request (queued requests are dropped) and frees every
+ * replica; no other call on the server may be in progress. */
+typedef struct okmc_server okmc_server;
+
+typedef struct {
+  size_t hbm_budget;  /* bytes the resident replicas may hold, 0 = no limit */
+  int32_t lanes;      /* worker threads and streams, 1..64 */
+  int32_t reserved;   /* must be 0 */
+} okmc_server_desc;
+
+enum okmc_request_kind { OKMC_REQ_SOLVE = 0, OKMC_REQ_STEP = 1 };
+
+typedef struct {
+  int32_t replica;          /* id from okmc_server_add_replica */
+  int32_t kind;             /* okmc_request_kind */
+  int64_t n_events;         /* STEP: number of steps */
+  okmc_step_params params;  /* STEP: temperature, mode, t_end */
+  double* energies;         /* SOLVE: host, defect count */
+  int32_t* positions;       /* STEP: host, 3 x defect count, nullable */
+} okmc_request;
+
+typedef struct {
+  int32_t status;           /* OKMC_OK or the error of the failing call */
+  int32_t admitted;         /* 1 if this request made its replica resident */
+  double t_submit, t_start, t_end;
+  okmc_step_stats stats;    /* the replica's statistics after the request */
+} okmc_result;
+
+typedef struct {
+  int64_t submitted, completed, failed, admissions, evictions, resident, queued;
+  size_t device_bytes;      /* bytes held or reserved by resident replicas */
+} okmc_server_stats;
+
+int okmc_server_create(const okmc_server_desc* d, okmc_server** out);
+int okmc_server_add_replica(okmc_server* s, const okmc_grid_desc* d, const okmc_defect* defs, int32_t nd, int32_t* id);
+int okmc_server_submit(okmc_server* s, const okmc_request* r, uint64_t* ticket);
+int okmc_server_wait(okmc_server* s, uint64_t ticket, int32_t timeout_ms, okmc_result* out);
+int okmc_server_get_stats(okmc_server* s, okmc_server_stats* out);
+const char* okmc_server_last_error(const okmc_server* s);
+int okmc_server_destroy(okmc_server* s);
 
 /* Allocation-free stress solve (the paper has no counterpart; this is a service for
  * callers that cannot allocate device memory -- code that runs after its process

@@ -527,9 +527,15 @@ void drop_graphs(okmc_grid* g) {
   g->graphs.clear();
 }
 
+// Held while a step graph is captured and while device memory is allocated or freed
+// by handle creation, defect setup and destruction, so that threads driving different
+// handles (the request server's lanes) never allocate during another's capture.
+std::recursive_mutex g_capture_mu;
+
 // Capture one step of g into a graph on a private stream (the handle's stream may be
 // the legacy stream, which cannot be captured); the graph is launched on g->st.
 int capture_step(okmc_grid* g, int mode, double T, cudaGraphExec_t* out) {
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);
   cudaStream_t cs;
   cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(g, e, "capture stream");
@@ -623,6 +629,7 @@ const char* okmc_last_error(const okmc_grid* g) {
 }
 
 int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);
   if (!d || !out) return OKMC_EINVAL;
   *out = nullptr;
   for (int a = 0; a < 3; ++a)
@@ -742,8 +749,27 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   return OKMC_OK;
 }
 
+size_t okmc_estimate_field_bytes(const okmc_grid_desc* d) {
+  if (!d || d->n[0] < 1 || d->n[1] < 1 || d->n[2] < 1) return 0;
+  const bool f64 = d->precision == OKMC_FP64_FIELDS;
+  const size_t N = (size_t)d->n[0] * d->n[1] * d->n[2];
+  const size_t H = d->n[0] / 2, P = (H + 1) * d->n[1], w = f64 ? 8 : 4;
+  PassCfg c{};
+  c.nx = d->n[0];
+  c.ny = d->n[1];
+  c.nz = d->n[2];
+  c.ncomp = 6;
+  const char* env = std::getenv("OKMC_GENERIC_FFT");
+  const bool fast = !f64 && fast_solve_supported(c) && !(env && env[0] == '1');
+  size_t b = 6 * N * w * 2 + 6 * d->n[2] * P * 2 * w * (fast ? 2 : 1);
+  b += sizeof(DevState) + sizeof(int) + sizeof(double) * 30 * kSelfBlocks + sizeof(int) * 6 * d->n[2];
+  b += (2 * H + 1 + d->n[1] + d->n[2]) * 2 * w + (H + 1 + d->n[1] + d->n[2]) * sizeof(double2);
+  return b;
+}
+
 int okmc_grid_destroy(okmc_grid* g) {
   if (!g) return OKMC_OK;
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);
   if (g->st || true) cudaStreamSynchronize(g->st);
   for (auto& p : g->pending) {
     cudaEventDestroy(p.a);
@@ -766,6 +792,7 @@ int okmc_set_stream(okmc_grid* g, void* stream) {
 
 int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
   if (!g) return OKMC_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);
   if (nd < 0 || (nd > 0 && !defs)) return fail(g, OKMC_EINVAL, "bad defect array");
   try {
     OKMC_TRY(validate_defects(g, defs, nd));
@@ -980,6 +1007,27 @@ int okmc_get_stats(okmc_grid* g, okmc_step_stats* out) {
   return OKMC_OK;
 }
 
+int okmc_set_kinetic_state(okmc_grid* g, const okmc_step_stats* s) {
+  if (!g || !s) return OKMC_EINVAL;
+  if (s->events < 0 || s->steps < 0 || s->solves < 0 || s->negative_barriers < 0 || !std::isfinite(s->clock) ||
+      !std::isfinite(s->dt_last))
+    return fail(g, OKMC_EINVAL, "bad kinetic state");
+  DevState st;
+  cudaError_t e = cudaMemcpyAsync(&st, g->d_state, sizeof(st), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "state read");
+  st.clock = s->clock;
+  st.dt_last = s->dt_last;
+  st.events = s->events;
+  st.negative_barriers = s->negative_barriers;
+  st.step = s->steps;
+  e = cudaMemcpyAsync(g->d_state, &st, sizeof(st), cudaMemcpyHostToDevice, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "state write");
+  g->solves = s->solves;
+  return OKMC_OK;
+}
+
 int okmc_step(okmc_grid* g, const okmc_step_params* p, int64_t n_steps, okmc_step_stats* out) {
   if (!g || !p) return OKMC_EINVAL;
   if (!(p->T_K > 0.0) || !std::isfinite(p->T_K)) return fail(g, OKMC_EINVAL, "temperature must be > 0");
@@ -1052,6 +1100,7 @@ const char* okmc_batch_last_error(const okmc_batch* b) { return b ? b->err.c_str
 // private streams); each launch advances all replicas by one step, and their
 // kernels overlap on the GPU.
 static int batch_build(okmc_batch* b) {
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);
   const int n = (int)b->grids.size();
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);

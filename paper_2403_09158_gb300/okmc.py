@@ -30,6 +30,8 @@ EXPORTED = [
     'okmc_get_stats', 'okmc_device_bytes', 'okmc_set_profiling', 'okmc_kernel_times', 'okmc_reset_kernel_times',
     'okmc_launch_shape', 'okmc_solve_stress_static', 'okmc_set_graphs', 'okmc_batch_create', 'okmc_batch_step',
     'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_get_variants', 'okmc_set_variant',
+    'okmc_set_kinetic_state', 'okmc_estimate_field_bytes', 'okmc_server_create', 'okmc_server_add_replica',
+    'okmc_server_submit', 'okmc_server_wait', 'okmc_server_get_stats', 'okmc_server_last_error', 'okmc_server_destroy',
 ]
 
 
@@ -46,6 +48,28 @@ class StepParams(C.Structure):
 class StepStats(C.Structure):
     _fields_ = [('events', C.c_int64), ('steps', C.c_int64), ('solves', C.c_int64),
                 ('negative_barriers', C.c_int64), ('clock', C.c_double), ('dt_last', C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerDesc(C.Structure):
+    _fields_ = [('hbm_budget', C.c_size_t), ('lanes', C.c_int32), ('reserved', C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [('replica', C.c_int32), ('kind', C.c_int32), ('n_events', C.c_int64), ('params', StepParams),
+                ('energies', C.c_void_p), ('positions', C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [('status', C.c_int32), ('admitted', C.c_int32), ('t_submit', C.c_double), ('t_start', C.c_double),
+                ('t_end', C.c_double), ('stats', StepStats)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [('submitted', C.c_int64), ('completed', C.c_int64), ('failed', C.c_int64), ('admissions', C.c_int64),
+                ('evictions', C.c_int64), ('resident', C.c_int64), ('queued', C.c_int64), ('device_bytes', C.c_size_t)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -99,6 +123,15 @@ def load(path=LIB_PATH):
         'okmc_batch_destroy': (C.c_int, [vp]),
         'okmc_batch_last_error': (C.c_char_p, [vp]),
         'okmc_get_variants': (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32)]),
+        'okmc_set_kinetic_state': (C.c_int, [vp, C.POINTER(StepStats)]),
+        'okmc_estimate_field_bytes': (C.c_size_t, [C.POINTER(GridDesc)]),
+        'okmc_server_create': (C.c_int, [C.POINTER(ServerDesc), C.POINTER(vp)]),
+        'okmc_server_add_replica': (C.c_int, [vp, C.POINTER(GridDesc), dp, i32, C.POINTER(i32)]),
+        'okmc_server_submit': (C.c_int, [vp, C.POINTER(Request), C.POINTER(C.c_uint64)]),
+        'okmc_server_wait': (C.c_int, [vp, C.c_uint64, i32, C.POINTER(Result)]),
+        'okmc_server_get_stats': (C.c_int, [vp, C.POINTER(ServerStats)]),
+        'okmc_server_last_error': (C.c_char_p, [vp]),
+        'okmc_server_destroy': (C.c_int, [vp]),
         'okmc_set_variant': (C.c_int, [vp, i32, i32]),
     }
     for name, (res, args) in sig.items():
@@ -237,6 +270,10 @@ class Grid:
         self._chk(self.lib.okmc_step(self.h, C.byref(p), n_steps, C.byref(s)))
         return s.as_dict()
 
+    def set_kinetic_state(self, st):
+        s = StepStats(**{k: st[k] for k, _ in StepStats._fields_})
+        self._chk(self.lib.okmc_set_kinetic_state(self.h, C.byref(s)))
+
     def stats(self):
         s = StepStats()
         self._chk(self.lib.okmc_get_stats(self.h, C.byref(s)))
@@ -306,6 +343,94 @@ class Batch:
     def close(self):
         if getattr(self, 'h', None):
             self.lib.okmc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+SOLVE, STEP = 0, 1
+
+
+def _grid_desc(n, voxel_nm, C11, C12, C44, k0_mode=MEAN_STRESS_ZERO, precision=FP32_FIELDS, nu0=0.0, seed=0):
+    d = GridDesc()
+    d.n[:] = tuple(int(v) for v in (n if np.ndim(n) else (n, n, n)))
+    d.k0_mode, d.precision, d.reserved = k0_mode, precision, 0
+    d.voxel_nm, d.C11, d.C12, d.C44, d.nu0 = voxel_nm, C11, C12, C44, nu0
+    d.seed = seed
+    return d
+
+
+def estimate_field_bytes(n, voxel_nm, C11, C12, C44, **kw):
+    return int(load().okmc_estimate_field_bytes(C.byref(_grid_desc(n, voxel_nm, C11, C12, C44, **kw))))
+
+
+class Server:
+    """okmc_server_*: request server over resident replicas.  submit() returns a
+    ticket; the output arrays handed to the library are kept alive here until the
+    ticket's result has been fetched with wait()."""
+
+    def __init__(self, hbm_budget=0, lanes=4):
+        self.lib = load()
+        d = ServerDesc(hbm_budget, lanes, 0)
+        h = C.c_void_p()
+        rc = self.lib.okmc_server_create(C.byref(d), C.byref(h))
+        if rc != OKMC_OK:
+            raise OkmcError(rc, 'okmc_server_create failed')
+        self.h = h
+        self.nd = []
+        self._keep = {}
+
+    def _chk(self, rc):
+        if rc != OKMC_OK:
+            raise OkmcError(rc, self.lib.okmc_server_last_error(self.h).decode())
+
+    def add_replica(self, n, voxel_nm, C11, C12, C44, defects, **kw):
+        d = _grid_desc(n, voxel_nm, C11, C12, C44, **kw)
+        defs = np.ascontiguousarray(defects, dtype=DEFECT_DTYPE)
+        rid = C.c_int32()
+        self._chk(self.lib.okmc_server_add_replica(self.h, C.byref(d), defs.ctypes.data if len(defs) else None,
+                                                   len(defs), C.byref(rid)))
+        self.nd.append(len(defs))
+        return rid.value
+
+    def submit_solve(self, replica):
+        E = np.zeros(self.nd[replica], dtype=np.float64)
+        r = Request(replica, SOLVE, 0, StepParams(0.0, RESIDENCE, 0, 0.0), E.ctypes.data, None)
+        return self._submit(r, E)
+
+    def submit_step(self, replica, T_K, n_events, mode=RESIDENCE, positions=True):
+        P = np.zeros((self.nd[replica], 3), dtype=np.int32) if positions else None
+        r = Request(replica, STEP, n_events, StepParams(float(T_K), mode, 0, 0.0), None,
+                    P.ctypes.data if P is not None else None)
+        return self._submit(r, P)
+
+    def _submit(self, r, out):
+        t = C.c_uint64()
+        self._chk(self.lib.okmc_server_submit(self.h, C.byref(r), C.byref(t)))
+        self._keep[t.value] = out
+        return t.value
+
+    def wait(self, ticket, timeout_ms=-1):
+        """(result dict, output array) of a ticket; raises OkmcError on timeout."""
+        res = Result()
+        self._chk(self.lib.okmc_server_wait(self.h, ticket, timeout_ms, C.byref(res)))
+        out = self._keep.pop(ticket)
+        d = {k: getattr(res, k) for k, _ in Result._fields_ if k != 'stats'}
+        d['stats'] = res.stats.as_dict()
+        return d, out
+
+    def stats(self):
+        st = ServerStats()
+        self._chk(self.lib.okmc_server_get_stats(self.h, C.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, 'h', None):
+            self.lib.okmc_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -219,3 +219,38 @@ def config_batch(seed=1004, n_replicas=64, edges=(64, 96, 128, 160, 192), nd_ran
         out.append(Workload('replica%02d_%dcubed_%d' % (r, n, len(d)), (n, n, n), VOXEL_NM, d, T, FE_CUBIC,
                             seed * 1000 + r, 1000))
     return out
+
+
+def config_serve(seed=1005, n_replicas=32, edges=(48, 64, 128, 256, 320), nd_range=(20, 3000),
+                 T_range=(300.0, 600.0)):
+    """Replica pool of the serving workload: edge ~ U(edges), defect count ~ U{20..3000}
+    capped at the 256^3 workload's density (2000 per 256^3 box, at least 20), the
+    large-config mix (loop radii U(0.5, 4) nm, at most a quarter of the box),
+    T ~ U(300, 600) K."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in range(n_replicas):
+        n = int(rng.choice(edges))
+        cap = max(nd_range[0], int(2000 * (n / 256.0) ** 3))
+        nd = min(int(rng.integers(nd_range[0], nd_range[1] + 1)), cap)
+        T = float(rng.uniform(*T_range))
+        rmax = min(4.0, 0.25 * n * VOXEL_NM)
+        d = _placed_population(n, nd, seed * 1000 + r, (0.5, rmax), (0.5, rmax))
+        out.append(Workload('serve%02d_%dcubed_%d' % (r, n, len(d)), (n, n, n), VOXEL_NM, d, T, FE_CUBIC,
+                            seed * 1000 + r, 0))
+    return out
+
+
+def request_stream(seed, rate, n_requests, n_replicas, p_solve=0.5, k_range=(1, 10)):
+    """Poisson arrivals at `rate` per second: (arrival time s, replica, kind, k) with kind
+    'solve' or 'step' (k steps, k ~ U{1..10})."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_requests))
+    reqs = []
+    for i in range(n_requests):
+        r = int(rng.integers(0, n_replicas))
+        if rng.random() < p_solve:
+            reqs.append((float(t[i]), r, 'solve', 1))
+        else:
+            reqs.append((float(t[i]), r, 'step', int(rng.integers(k_range[0], k_range[1] + 1))))
+    return reqs

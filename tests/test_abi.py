@@ -49,6 +49,9 @@ int main(void) {
   printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(okmc_grid_desc), sizeof(okmc_defect), sizeof(okmc_step_params),
          sizeof(okmc_step_stats), offsetof(okmc_grid_desc, voxel_nm), offsetof(okmc_grid_desc, stream),
          offsetof(okmc_defect, radius_nm));
+  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(okmc_server_desc), sizeof(okmc_request), sizeof(okmc_result),
+         sizeof(okmc_server_stats), offsetof(okmc_request, params), offsetof(okmc_request, positions),
+         offsetof(okmc_result, stats));
   return 0;
 }
 '''
@@ -66,6 +69,13 @@ int main(void) {
     assert vals[4] == ok.GridDesc.voxel_nm.offset
     assert vals[5] == ok.GridDesc.stream.offset
     assert vals[6] == DEFECT_DTYPE.fields['radius_nm'][1]
+    assert vals[7] == C.sizeof(ok.ServerDesc)
+    assert vals[8] == C.sizeof(ok.Request)
+    assert vals[9] == C.sizeof(ok.Result)
+    assert vals[10] == C.sizeof(ok.ServerStats)
+    assert vals[11] == ok.Request.params.offset
+    assert vals[12] == ok.Request.positions.offset
+    assert vals[13] == ok.Result.stats.offset
 
 
 def test_null_handle_errors_without_gpu(lib):
@@ -84,6 +94,28 @@ def test_null_handle_errors_without_gpu(lib):
     assert lib.okmc_grid_create(C.byref(d), C.byref(h)) == ok.OKMC_EINVAL
     d.C44, d.k0_mode = 116.0, 7
     assert lib.okmc_grid_create(C.byref(d), C.byref(h)) == ok.OKMC_EINVAL
+
+
+def test_server_and_estimate_argument_checks_without_gpu(lib):
+    import ctypes as C
+    assert lib.okmc_server_destroy(None) == ok.OKMC_OK
+    assert lib.okmc_server_last_error(None) == b'null server'
+    assert lib.okmc_server_create(None, None) == ok.OKMC_EINVAL
+    d = ok.ServerDesc(0, 0, 0)  # no lanes
+    h = C.c_void_p()
+    assert lib.okmc_server_create(C.byref(d), C.byref(h)) == ok.OKMC_EINVAL
+    assert lib.okmc_server_submit(None, None, None) == ok.OKMC_EINVAL
+    assert lib.okmc_server_wait(None, 1, 0, None) == ok.OKMC_EINVAL
+    assert lib.okmc_set_kinetic_state(None, None) == ok.OKMC_EINVAL
+    # field bytes of a 256^3 FP32 grid on the register-FFT path: int32 eigenstrain,
+    # FP32 stress, two half spectra, plus small tables
+    n = 256
+    b = ok.estimate_field_bytes((n, n, n), 0.2855, 243.0, 145.0, 116.0)
+    fields = 6 * n ** 3 * 4 * 2 + 2 * 6 * n * (n // 2 + 1) * n * 8
+    assert fields <= b <= fields + (1 << 20)
+    bd = ok.estimate_field_bytes((n, n, n), 0.2855, 243.0, 145.0, 116.0, precision=ok.FP64_FIELDS)
+    assert 6 * n ** 3 * 8 * 2 + 6 * n * (n // 2 + 1) * n * 16 <= bd
+    assert ok.estimate_field_bytes((0, 8, 8), 0.2855, 243.0, 145.0, 116.0) == 0
 
 
 def test_product_path_does_not_import_oracle():
