@@ -236,6 +236,110 @@ __device__ void scatter_stencil(Q* __restrict__ eps, int3 n, size_t N, const Def
   }
 }
 
+// ---------------------------------------------------------------- dilated candidate lists
+// The eight candidate positions of a defect in class c use the stencil of class
+// cp = 1 - c shifted by s_j, s_j per axis in {-cp, 1 - cp} (bit 2 of j: x, bit 1: y,
+// bit 0: z).  Their voxels are the 2x2x2 dilation of that stencil.  For the energies
+// each voxel u of the dilation is listed once with the eight counts cnt(u - s_j)
+// packed in a uint64, so sigma at u is read once for all eight candidates.  One block
+// per (defect, class c); the count box of the stencil lives in shared memory (side
+// 2E + 1, E the scan half-width), and lists come out in the box's linear order.
+constexpr int kDilateMaxSide = 58;  // 58^3 bytes of shared memory; larger defects use the direct loop
+
+__device__ __forceinline__ int dilate_prepare(const DefGeo& g, const int* __restrict__ ptr, const int* __restrict__ off,
+                                              const uint8_t* __restrict__ cnt, int i, int cp, uint8_t* box) {
+  const int E = g.extent, side = 2 * E + 1;
+  const int nv = side * side * side;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) box[v] = 0;
+  __syncthreads();
+  for (int k = ptr[2 * i + cp] + threadIdx.x; k < ptr[2 * i + cp + 1]; k += blockDim.x) {
+    int dx, dy, dz;
+    unpack_off(off[k], dx, dy, dz);
+    box[((dz + E) * side + (dy + E)) * side + (dx + E)] = cnt[k];
+  }
+  __syncthreads();
+  return nv;
+}
+
+__device__ __forceinline__ unsigned long long dilate_counts(const uint8_t* box, int E, int cp, int ux, int uy, int uz) {
+  const int side = 2 * E + 1;
+  unsigned long long cc = 0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int x = ux - (((j >> 2) & 1) - cp), y = uy - (((j >> 1) & 1) - cp), z = uz - ((j & 1) - cp);
+    if (x >= -E && x <= E && y >= -E && y <= E && z >= -E && z <= E)
+      cc |= (unsigned long long)box[((z + E) * side + (y + E)) * side + (x + E)] << (8 * j);
+  }
+  return cc;
+}
+
+__global__ void k_dilate_count(const DefGeo* __restrict__ G, const int* __restrict__ ptr, const int* __restrict__ off,
+                               const uint8_t* __restrict__ cnt, int* __restrict__ ndil) {
+  extern __shared__ uint8_t box[];
+  __shared__ long long sh[32];
+  const int i = blockIdx.x >> 1, c = blockIdx.x & 1, cp = 1 - c;
+  const DefGeo g = G[i];
+  const int E = g.extent, side = 2 * E + 1;
+  if (side > kDilateMaxSide) {
+    if (threadIdx.x == 0) ndil[blockIdx.x] = -1;
+    return;
+  }
+  const int nv = dilate_prepare(g, ptr, off, cnt, i, cp, box);
+  long long n = 0;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    const int ux = v % side - E, uy = (v / side) % side - E, uz = v / (side * side) - E;
+    n += dilate_counts(box, E, cp, ux, uy, uz) != 0ull;
+  }
+  n = block_sum_ll(n, sh);
+  if (threadIdx.x == 0) ndil[blockIdx.x] = (int)n;
+}
+
+__global__ void k_dilate_fill(const DefGeo* __restrict__ G, const int* __restrict__ ptr, const int* __restrict__ off,
+                              const uint8_t* __restrict__ cnt, DilatedLists dl, int* __restrict__ doff,
+                              unsigned long long* __restrict__ dcnt, int* __restrict__ err) {
+  extern __shared__ uint8_t box[];
+  __shared__ int wsum[32];
+  const int i = blockIdx.x >> 1, c = blockIdx.x & 1, cp = 1 - c;
+  const DefGeo g = G[i];
+  const int E = g.extent, side = 2 * E + 1;
+  if (side > kDilateMaxSide || dl.ptr[blockIdx.x] < 0) return;
+  const int nv = dilate_prepare(g, ptr, off, cnt, i, cp, box);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int base = dl.ptr[blockIdx.x];
+  const int end = dl.end[blockIdx.x];
+  for (int v0 = 0; v0 < nv; v0 += blockDim.x) {
+    const int v = v0 + threadIdx.x;
+    int ux = 0, uy = 0, uz = 0;
+    unsigned long long cc = 0;
+    if (v < nv) {
+      ux = v % side - E;
+      uy = (v / side) % side - E;
+      uz = v / (side * side) - E;
+      cc = dilate_counts(box, E, cp, ux, uy, uz);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, cc != 0ull);
+    const int rank = __popc(bal & ((1u << lane) - 1u));
+    if (lane == 0) wsum[w] = __popc(bal);
+    __syncthreads();
+    int pre = 0, tot = 0;
+    for (int q = 0; q < nw; ++q) {
+      if (q < w) pre += wsum[q];
+      tot += wsum[q];
+    }
+    if (cc) {
+      const int at = base + pre + rank;
+      if (at < end) {
+        doff[at] = pack_off(ux, uy, uz);
+        dcnt[at] = cc;
+      } else {
+        atomicExch(err, 5);
+      }
+    }
+    base += tot;
+    __syncthreads();
+  }
+}
+
 template <class Q>
 __global__ void k_voxelise(Q* __restrict__ eps, int3 n, const okmc_defect* __restrict__ d, const DefGeo* __restrict__ G,
                            const int* __restrict__ ptr, const int* __restrict__ off, const uint8_t* __restrict__ cnt,
@@ -537,7 +641,8 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict
                                                              const int* __restrict__ off, const uint8_t* __restrict__ cnt,
                                                              const double* __restrict__ alpha, const double* __restrict__ W,
                                                              double pref, int want_cand, const int* __restrict__ order,
-                                                             double* __restrict__ E, double* __restrict__ Ec, RateArgs ra) {
+                                                             double* __restrict__ E, double* __restrict__ Ec, RateArgs ra,
+                                                             DilatedLists dl) {
   __shared__ double part[kEnergyThreads / 32][9];
   const int i = order ? order[blockIdx.x] : blockIdx.x;
   const size_t N = (size_t)n.x * n.y * n.z;
@@ -558,7 +663,20 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict
     for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
     acc[0].add(T(cnt[k]) * dot);
   }
-  if (want_cand) {
+  if (want_cand && dl.ptr && dl.ptr[2 * i + c] >= 0) {
+    // the dilation of the candidate stencil, each voxel once with its eight counts
+    for (int k = dl.ptr[2 * i + c] + threadIdx.x; k < dl.end[2 * i + c]; k += blockDim.x) {
+      int ux, uy, uz;
+      unpack_off(dl.off[k], ux, uy, uz);
+      const unsigned long long cc = dl.cnt[k];
+      const size_t v = ((size_t)wrap(bz + uz, n.z) * n.y + wrap(by + uy, n.y)) * n.x + wrap(bx + ux, n.x);
+      T dot = T(0);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) acc[1 + j].add(T((unsigned)(cc >> (8 * j)) & 255u) * dot);
+    }
+  } else if (want_cand) {
     // candidate j sits at base(X + lambda_j) = base(X) + d_j, d_j in {-1,0}^3 (c = 0)
     // or {0,1}^3 (c = 1); per axis the shift is (s + 1)/2 - (1 - c) with s = +-1
     for (int k = ptr[2 * i + cp] + threadIdx.x; k < ptr[2 * i + cp + 1]; k += blockDim.x) {
@@ -795,6 +913,23 @@ cudaError_t launch_stencil_count(const DefGeo* G, int nd, int* nnz, long long* s
   k_stencil_count<<<2 * nd, 256, 0, st>>>(G, nnz, sumcnt);
   return cudaGetLastError();
 }
+cudaError_t launch_dilate_count(const DefGeo* G, int nd, const int* ptr, const int* off, const uint8_t* cnt, int* ndil,
+                                cudaStream_t st) {
+  const size_t smem = (size_t)kDilateMaxSide * kDilateMaxSide * kDilateMaxSide;
+  cudaError_t e = cudaFuncSetAttribute(k_dilate_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_dilate_count<<<2 * nd, 256, smem, st>>>(G, ptr, off, cnt, ndil);
+  return cudaGetLastError();
+}
+cudaError_t launch_dilate_fill(const DefGeo* G, int nd, const int* ptr, const int* off, const uint8_t* cnt,
+                               const DilatedLists& dl, int* err, cudaStream_t st) {
+  const size_t smem = (size_t)kDilateMaxSide * kDilateMaxSide * kDilateMaxSide;
+  cudaError_t e = cudaFuncSetAttribute(k_dilate_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_dilate_fill<<<2 * nd, 256, smem, st>>>(G, ptr, off, cnt, dl, const_cast<int*>(dl.off),
+                                           const_cast<unsigned long long*>(dl.cnt), err);
+  return cudaGetLastError();
+}
 cudaError_t launch_stencil_fill(const DefGeo* G, int nd, const int* ptr, const long long* sumcnt, int* off, uint8_t* cnt,
                                 double* alpha, int* err, cudaStream_t st) {
   k_stencil_fill<<<2 * nd, 256, 0, st>>>(G, ptr, sumcnt, off, cnt, alpha, err);
@@ -851,9 +986,10 @@ cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
-                            int want_cand, const int* order, double* E, double* Ec, RateArgs ra, cudaStream_t st) {
+                            int want_cand, const int* order, double* E, double* Ec, RateArgs ra, const DilatedLists& dl,
+                            cudaStream_t st) {
   if (nd == 0) return cudaSuccess;
-  k_energies<T><<<nd, kEnergyThreads, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, order, E, Ec, ra);
+  k_energies<T><<<nd, kEnergyThreads, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, order, E, Ec, ra, dl);
   return cudaGetLastError();
 }
 cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
@@ -889,9 +1025,9 @@ template cudaError_t launch_selfterm<double>(const C2<double>*, const PassCfg&, 
                                             cudaStream_t);
 template cudaError_t launch_energies<float>(const float*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
                                            const uint8_t*, const double*, const double*, double, int, const int*, double*,
-                                           double*, RateArgs, cudaStream_t);
+                                           double*, RateArgs, const DilatedLists&, cudaStream_t);
 template cudaError_t launch_energies<double>(const double*, int3, const okmc_defect*, const DefGeo*, int, const int*,
                                             const int*, const uint8_t*, const double*, const double*, double, int, const int*,
-                                            double*, double*, RateArgs, cudaStream_t);
+                                            double*, double*, RateArgs, const DilatedLists&, cudaStream_t);
 
 }  // namespace okmc

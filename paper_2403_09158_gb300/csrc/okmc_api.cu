@@ -27,6 +27,10 @@ template <class T> cudaError_t launch_plane_inv(const C2<T>* spec, T* sig, const
 template <class T> cudaError_t launch_pencil(C2<T>* spec, const PassCfg& c, cudaStream_t st);
 cudaError_t launch_defect_setup(const okmc_defect* d, DefGeo* G, int nd, double h, cudaStream_t st);
 cudaError_t launch_stencil_count(const DefGeo* G, int nd, int* nnz, long long* sumcnt, cudaStream_t st);
+cudaError_t launch_dilate_count(const DefGeo* G, int nd, const int* ptr, const int* off, const uint8_t* cnt, int* ndil,
+                                cudaStream_t st);
+cudaError_t launch_dilate_fill(const DefGeo* G, int nd, const int* ptr, const int* off, const uint8_t* cnt,
+                               const DilatedLists& dl, int* err, cudaStream_t st);
 cudaError_t launch_stencil_fill(const DefGeo* G, int nd, const int* ptr, const long long* sumcnt, int* off, uint8_t* cnt,
                                 double* alpha, int* err, cudaStream_t st);
 template <class Q>
@@ -50,7 +54,7 @@ cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
-                            int want_cand, const int* order, double* E, double* Ec, RateArgs ra, cudaStream_t st);
+                            int want_cand, const int* order, double* E, double* Ec, RateArgs ra, const DilatedLists& dl, cudaStream_t st);
 cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
                              Move* moves, DevState* stt, cudaStream_t st);
 cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* rates, double nu0, double kT, int3 n,
@@ -130,6 +134,9 @@ struct okmc_grid {
   int* d_err = nullptr;
   int* d_pos = nullptr;
   double* d_partial = nullptr;
+  int* d_dl = nullptr;                  // [4 nd]: start and end of each dilated candidate list
+  int* d_doff = nullptr;                // dilated lists: packed offsets
+  unsigned long long* d_dcnt = nullptr; // dilated lists: eight candidate counts
   std::vector<okmc_defect> h_def;
   bool sigma_valid = false;
   bool any_mobile = false;
@@ -298,12 +305,19 @@ int energies(okmc_grid* g, int want_cand, double kT = 0.0) {
     ra.nu0 = g->nu0;
     ra.kT = kT;
   }
+  DilatedLists dl{};
+  if (g->d_dl) {
+    dl.ptr = g->d_dl;
+    dl.end = g->d_dl + 2 * g->nd;
+    dl.off = g->d_doff;
+    dl.cnt = g->d_dcnt;
+  }
   return run(g, "energies", [&] {
     if (fp64(g))
       return launch_energies<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
-                                     g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->d_E, g->d_Ec, ra, g->st);
+                                     g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->d_E, g->d_Ec, ra, dl, g->st);
     return launch_energies<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
-                                  g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->d_E, g->d_Ec, ra, g->st);
+                                  g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->d_E, g->d_Ec, ra, dl, g->st);
   });
 }
 
@@ -475,6 +489,38 @@ int build_self_terms(okmc_grid* g) {
   return OKMC_OK;
 }
 
+// Dilated candidate lists of every (defect, class): sizes, offsets, fill.
+int build_dilated_lists(okmc_grid* g) {
+  const int nd = g->nd;
+  int* d_n = nullptr;
+  OKMC_TRY(dalloc(g, (void**)&d_n, 2 * nd * sizeof(int)));
+  int rc = run(g, "dilate_count", [&] { return launch_dilate_count(g->d_geo, nd, g->d_ptr, g->d_off, g->d_cnt, d_n, g->st); });
+  std::vector<int> cnt(2 * nd), se(4 * nd);
+  cudaError_t e = cudaSuccess;
+  if (rc == OKMC_OK) {
+    e = cudaMemcpyAsync(cnt.data(), d_n, 2 * nd * sizeof(int), cudaMemcpyDeviceToHost, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  }
+  dfree(g, d_n);
+  if (rc != OKMC_OK) return rc;
+  if (e != cudaSuccess) return cuda_fail(g, e, "dilated list sizes");
+  long long tot = 0;
+  for (int k = 0; k < 2 * nd; ++k) {
+    se[k] = cnt[k] < 0 ? -1 : (int)tot;
+    se[2 * nd + k] = cnt[k] < 0 ? -1 : (int)(tot + cnt[k]);
+    if (cnt[k] > 0) tot += cnt[k];
+  }
+  if (tot > 0x7fffffffll) return fail(g, OKMC_ENOMEM, "too many dilated stencil entries");
+  OKMC_TRY(dalloc(g, (void**)&g->d_dl, 4 * nd * sizeof(int)));
+  OKMC_TRY(dalloc(g, (void**)&g->d_doff, (size_t)tot * sizeof(int)));
+  OKMC_TRY(dalloc(g, (void**)&g->d_dcnt, (size_t)tot * sizeof(unsigned long long)));
+  e = cudaMemcpyAsync(g->d_dl, se.data(), se.size() * sizeof(int), cudaMemcpyHostToDevice, g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "dilated list offsets");
+  DilatedLists dl{g->d_dl, g->d_dl + 2 * nd, g->d_doff, g->d_dcnt};
+  OKMC_TRY(run(g, "dilate_fill", [&] { return launch_dilate_fill(g->d_geo, nd, g->d_ptr, g->d_off, g->d_cnt, dl, g->d_err, g->st); }));
+  return check_device_error(g);
+}
+
 int voxelise_all(okmc_grid* g) {
   cudaError_t e = cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st);
   // every plane transform is stale (the self-term build also used spec as scratch)
@@ -493,7 +539,8 @@ int voxelise_all(okmc_grid* g) {
 void free_defects(okmc_grid* g) {
   void** bufs[] = {(void**)&g->d_def, (void**)&g->d_geo, (void**)&g->d_ptr, (void**)&g->d_off, (void**)&g->d_cnt,
                    (void**)&g->d_alpha, (void**)&g->d_sumcnt, (void**)&g->d_nnz, (void**)&g->d_W, (void**)&g->d_E,
-                   (void**)&g->d_Ec, (void**)&g->d_order, (void**)&g->d_rates, (void**)&g->d_rsum, (void**)&g->d_moves, (void**)&g->d_pos};
+                   (void**)&g->d_Ec, (void**)&g->d_order, (void**)&g->d_rates, (void**)&g->d_rsum, (void**)&g->d_moves, (void**)&g->d_pos,
+                   (void**)&g->d_dl, (void**)&g->d_doff, (void**)&g->d_dcnt};
   for (void** b : bufs) {
     dfree(g, *b);
     *b = nullptr;
@@ -859,6 +906,7 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
         return launch_stencil_fill(g->d_geo, nd, g->d_ptr, g->d_sumcnt, g->d_off, g->d_cnt, g->d_alpha, g->d_err, g->st);
       }));
       OKMC_TRY(check_device_error(g));
+      OKMC_TRY(build_dilated_lists(g));
       OKMC_TRY((fp64(g) ? build_self_terms<double, int64_t>(g) : build_self_terms<float, int32_t>(g)));
     }
     OKMC_TRY(voxelise_all(g));

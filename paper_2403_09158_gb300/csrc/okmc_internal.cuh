@@ -293,6 +293,15 @@ struct WBatch {
   int nb;
 };
 
+// Dilated candidate stencils (one list per defect and current class; ptr < 0: none,
+// the energies kernel then walks the candidate stencil eight times).
+struct DilatedLists {
+  const int* ptr;                 // [2 nd] first entry of list (i, c)
+  const int* end;                 // [2 nd] one past the last entry
+  const int* off;                 // packed offsets of the dilation's voxels
+  const unsigned long long* cnt;  // counts of the eight candidates, byte j for jump j
+};
+
 // Unit eigenstrain tensors of the defect types present (at most eight: four
 // 1/2<111> loop axes, three <100> loop axes, the dilatational SIA cluster).
 struct QTypes {

@@ -123,6 +123,34 @@ def test_energies_bruteforce_small(precision):
     g.close()
 
 
+@pytest.mark.parametrize('precision', [ok.FP32_FIELDS, ok.FP64_FIELDS])
+def test_candidate_energies_large_loop_and_small_defects(precision):
+    """A loop too large for the dilated candidate lists (scan box side 63 voxels) takes
+    the direct candidate loop; the small defects beside it take the lists.  Both match
+    the brute-force oracle (N_d + 1 solves)."""
+    from paper_2403_09158_gb300.workload import LOOP_111, ONE_D, SIA_CLUSTER, THREE_D
+    defs = make_defects([LOOP_111, SIA_CLUSTER, SIA_CLUSTER, LOOP_111],
+                        np.array([[64, 64, 64], [10, 10, 100], [101, 21, 31], [30, 100, 20]]), [0, 1, 2, 3],
+                        [8.2, 0.0, 0.0, 0.8], [0, 3, 1, 0], [0.1, 0.3, 0.3, 0.1], [ONE_D, ONE_D, THREE_D, ONE_D])
+    n = (64, 64, 64)
+    g = ok.Grid(n, 0.2855, *FE_CUBIC, precision=precision)
+    g.set_defects(defs)
+    E = g.interaction_energies()
+    Ec, _ = g.candidate_energies()
+    W = g.self_terms()
+    g.close()
+    Eo, Eco = O.energies_bruteforce(defs, n, 0.2855, O.stiffness_cubic(*FE_CUBIC))
+    if precision == ok.FP64_FIELDS:
+        tol = np.full(len(defs), ENERGY_TOL[ok.FP64_FIELDS])
+    else:
+        # FP32 fields: the transform's rounding noise scales with the whole field, and
+        # this loop's own field is extreme (R = 8.2 nm in an 18 nm box; self energy
+        # ~1e3 eV), so the bound grows with the defect's self-energy magnitude
+        tol = 2e-4 + 1e-6 * np.abs(W.reshape(len(defs), -1)).max(axis=1)
+    assert np.all(np.abs(E - Eo) <= tol), (np.abs(E - Eo), tol)
+    assert np.all(np.abs(Ec - Eco).max(axis=1) <= tol), (np.abs(Ec - Eco).max(axis=1), tol)
+
+
 def test_self_terms_match_oracle():
     w = config_small()
     g = make_grid(w, ok.FP64_FIELDS)
