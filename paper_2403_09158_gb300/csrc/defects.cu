@@ -213,12 +213,13 @@ __device__ __forceinline__ int wrap(int x, int n) { return x < 0 ? x + n : (x >=
 template <class Q>
 __device__ void scatter_stencil(Q* __restrict__ eps, int3 n, size_t N, const DefGeo& g, const int* __restrict__ ptr,
                                 const int* __restrict__ off, const uint8_t* __restrict__ cnt, const double* __restrict__ alpha,
-                                int i, const int pos[3], int sign, double rq, double lim, int* err, int* dirty) {
+                                int i, const int pos[3], int sign, double rq, double lim, int* err, int* dirty,
+                                int slice = 0, int nslices = 1) {
   const int c = pos[0] & 1;
   const int bx = floor_div2(pos[0]), by = floor_div2(pos[1]), bz = floor_div2(pos[2]);
   const int s = ptr[2 * i + c], e = ptr[2 * i + c + 1];
   const double a = alpha[2 * i + c];
-  for (int k = s + threadIdx.x; k < e; k += blockDim.x) {
+  for (int k = s + slice * blockDim.x + threadIdx.x; k < e; k += nslices * blockDim.x) {
     int dx, dy, dz;
     unpack_off(off[k], dx, dy, dz);
     const int zz = wrap(bz + dz, n.z);
@@ -350,7 +351,10 @@ __global__ void k_voxelise(Q* __restrict__ eps, int3 n, const okmc_defect* __res
   scatter_stencil<Q>(eps, n, N, G[i], ptr, off, cnt, alpha, i, pos, +1, rq, lim, err, nullptr);
 }
 
-// One block per move: remove the old stencil, add the new one (exact in fixed point).
+// Blocks (move, slice): each slice of a move removes its share of the old stencil and
+// adds its share of the new one (exact in fixed point, in any order).  Several slices
+// per move spread the FP64 fixed-point conversions over several SMs.
+constexpr int kMoveSlices = 16;
 template <class Q>
 __global__ void k_apply_moves(Q* __restrict__ eps, int3 n, const DefGeo* __restrict__ G, const int* __restrict__ ptr,
                               const int* __restrict__ off, const uint8_t* __restrict__ cnt, const double* __restrict__ alpha,
@@ -359,8 +363,10 @@ __global__ void k_apply_moves(Q* __restrict__ eps, int3 n, const DefGeo* __restr
   if ((int)blockIdx.x >= st->nmoves) return;
   const Move m = moves[blockIdx.x];
   const size_t N = (size_t)n.x * n.y * n.z;
-  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.old_pos, -1, rq, lim, err, dirty);
-  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.new_pos, +1, rq, lim, err, dirty);
+  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.old_pos, -1, rq, lim, err, dirty, blockIdx.y,
+                     gridDim.y);
+  scatter_stencil<Q>(eps, n, N, G[m.i], ptr, off, cnt, alpha, m.i, m.new_pos, +1, rq, lim, err, dirty, blockIdx.y,
+                     gridDim.y);
 }
 
 // Moves recorded from a host-side position update.
@@ -654,27 +660,65 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict
   const int bx = floor_div2(r.pos[0]), by = floor_div2(r.pos[1]), bz = floor_div2(r.pos[2]);
   EAcc<T> acc[9];
   for (int j = 0; j < 9; ++j) acc[j].zero();
-  for (int k = ptr[2 * i + c] + threadIdx.x; k < ptr[2 * i + c + 1]; k += blockDim.x) {
-    int dx, dy, dz;
-    unpack_off(off[k], dx, dy, dz);
-    const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
-    T dot = T(0);
+  // Each thread takes the entries k = first + tid + m * blockDim in order; U of them at
+  // a time, with every load of the group issued before the first use, so that U
+  // gathers are in flight per thread (the accumulation order is that of the plain loop).
+  constexpr int U = 4;
+  {
+    const int k_end = ptr[2 * i + c + 1];
+    for (int k0 = ptr[2 * i + c] + threadIdx.x; k0 < k_end; k0 += U * blockDim.x) {
+      T sv[U][6], w[U];
 #pragma unroll
-    for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
-    acc[0].add(T(cnt[k]) * dot);
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + u * blockDim.x;
+        w[u] = T(0);
+        if (k < k_end) {
+          int dx, dy, dz;
+          unpack_off(off[k], dx, dy, dz);
+          w[u] = T(cnt[k]);
+          const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
+#pragma unroll
+          for (int a = 0; a < 6; ++a) sv[u][a] = __ldg(sig + a * N + v);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (k0 + u * (int)blockDim.x >= k_end) break;
+        T dot = T(0);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) dot += ew[a] * sv[u][a];
+        acc[0].add(w[u] * dot);
+      }
+    }
   }
   if (want_cand && dl.ptr && dl.ptr[2 * i + c] >= 0) {
     // the dilation of the candidate stencil, each voxel once with its eight counts
-    for (int k = dl.ptr[2 * i + c] + threadIdx.x; k < dl.end[2 * i + c]; k += blockDim.x) {
-      int ux, uy, uz;
-      unpack_off(dl.off[k], ux, uy, uz);
-      const unsigned long long cc = dl.cnt[k];
-      const size_t v = ((size_t)wrap(bz + uz, n.z) * n.y + wrap(by + uy, n.y)) * n.x + wrap(bx + ux, n.x);
-      T dot = T(0);
+    const int k_end = dl.end[2 * i + c];
+    for (int k0 = dl.ptr[2 * i + c] + threadIdx.x; k0 < k_end; k0 += U * blockDim.x) {
+      T sv[U][6];
+      unsigned long long cc[U];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + u * blockDim.x;
+        cc[u] = 0ull;
+        if (k < k_end) {
+          int ux, uy, uz;
+          unpack_off(dl.off[k], ux, uy, uz);
+          cc[u] = dl.cnt[k];
+          const size_t v = ((size_t)wrap(bz + uz, n.z) * n.y + wrap(by + uy, n.y)) * n.x + wrap(bx + ux, n.x);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) acc[1 + j].add(T((unsigned)(cc >> (8 * j)) & 255u) * dot);
+          for (int a = 0; a < 6; ++a) sv[u][a] = __ldg(sig + a * N + v);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        if (k0 + u * (int)blockDim.x >= k_end) break;
+        T dot = T(0);
+#pragma unroll
+        for (int a = 0; a < 6; ++a) dot += ew[a] * sv[u][a];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[1 + j].add(T((unsigned)(cc[u] >> (8 * j)) & 255u) * dot);
+      }
     }
   } else if (want_cand) {
     // candidate j sits at base(X + lambda_j) = base(X) + d_j, d_j in {-1,0}^3 (c = 0)
@@ -704,37 +748,40 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict
     if (lane == 0) part[wid][j] = acc[j].value();
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  double tot[9];
-  for (int j = 0; j < 9; ++j) {
-    tot[j] = 0.0;
-    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot[j] += part[w2][j];
-  }
-  const double e0 = pref * alpha[2 * i + c] * tot[0] - W[(size_t)i * 18 + c * 9];
-  E[i] = e0;
+  // epilogue on warp 0, one lane per position (lane 0: the site, lane 1 + j: jump j),
+  // so the FP64 work (sums, energies, Boltzmann factors) runs side by side
+  if (threadIdx.x >= 32) return;
+  double tot = 0.0;
+  if (lane < 9)
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += part[w2][lane];
+  double ej = 0.0;
+  if (lane == 0) ej = pref * alpha[2 * i + c] * tot - W[(size_t)i * 18 + c * 9];
+  else if (lane < 9) ej = pref * alpha[2 * i + cp] * tot - W[(size_t)i * 18 + c * 9 + lane];
+  const double e0 = __shfl_sync(0xffffffffu, ej, 0);
+  if (lane == 0) E[i] = e0;
   if (!want_cand) return;
-  double ec[8];
-  for (int j = 0; j < 8; ++j) {
-    ec[j] = pref * alpha[2 * i + cp] * tot[1 + j] - W[(size_t)i * 18 + c * 9 + 1 + j];
-    Ec[(size_t)i * 8 + j] = ec[j];
-  }
+  if (lane >= 1 && lane < 9) Ec[(size_t)i * 8 + lane - 1] = ej;
   if (!ra.rates) return;
   // biased jump frequencies nu_j = (nu0/z) exp(-(E_m + (E_j - E_0)/2)/kT) of the
   // allowed jumps (Eqs. biased_forward/backward_boltzmann, prefactor 1/z)
-  double sum = 0.0;
+  double nu = 0.0;
   int neg = 0;
-  for (int j = 0; j < 8; ++j) {
-    double nu = 0.0;
+  if (lane >= 1 && lane < 9) {
+    const int j = lane - 1;
     if (g.allowed >> j & 1) {
-      const double barrier = r.Em_eV + 0.5 * (ec[j] - e0);
-      neg += barrier < 0.0;
-      nu = (ra.nu0 / g.z) * exp(-barrier / ra.kT);
+      const double barrier = r.Em_eV + 0.5 * (ej - e0);
+      neg = barrier < 0.0;
+      nu = (ra.nu0 / g.z) * exp(-barrier * ra.rkT);
     }
     ra.rates[(size_t)i * 8 + j] = nu;
-    sum += nu;
   }
-  ra.rsum[i] = sum;
-  if (neg) atomicAdd(reinterpret_cast<unsigned long long*>(ra.negb), (unsigned long long)neg);
+  double sum = 0.0;  // in jump order, as the frequency line walks them
+  for (int j = 0; j < 8; ++j) sum += __shfl_sync(0xffffffffu, nu, 1 + j);
+  neg = __reduce_add_sync(0xffffffffu, neg);
+  if (lane == 0) {
+    ra.rsum[i] = sum;
+    if (neg) atomicAdd(reinterpret_cast<unsigned long long*>(ra.negb), (unsigned long long)neg);
+  }
 }
 
 // ---------------------------------------------------------------- events
@@ -947,7 +994,8 @@ cudaError_t launch_apply_moves(Q* eps, int3 n, const DefGeo* G, int maxmoves, co
                                const uint8_t* cnt, const double* alpha, const Move* moves, const DevState* stt, double rq,
                                double lim, int* err, int* dirty, cudaStream_t st) {
   if (maxmoves == 0) return cudaSuccess;
-  k_apply_moves<Q><<<maxmoves, 256, 0, st>>>(eps, n, G, ptr, off, cnt, alpha, moves, stt, rq, lim, err, dirty);
+  k_apply_moves<Q><<<dim3(maxmoves, kMoveSlices), 256, 0, st>>>(eps, n, G, ptr, off, cnt, alpha, moves, stt, rq, lim, err,
+                                                                 dirty);
   return cudaGetLastError();
 }
 cudaError_t launch_diff_positions(okmc_defect* d, const int* pos, int nd, Move* moves, DevState* stt, cudaStream_t st) {

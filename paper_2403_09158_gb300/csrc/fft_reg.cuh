@@ -35,38 +35,6 @@ template <> struct RegPlan<256> { static constexpr int R1 = 16, R2 = 16; };
 template <> struct RegPlan<320> { static constexpr int R1 = 16, R2 = 20; };
 template <int L> __host__ __device__ constexpr int reg_nt() { return RegPlan<L>::R1 < RegPlan<L>::R2 ? RegPlan<L>::R1 : RegPlan<L>::R2; }
 
-// ---------------------------------------------------------------- packed FP32 pairs
-// The sm_100 family executes add, multiply and fma on a pair of FP32 values in one
-// instruction (round to nearest, each lane exactly as the scalar operation), so a
-// complex add, subtract or real scaling costs one instruction instead of two.  A
-// multiplication by -i or +i swaps the lanes; such terms are added in scalar form.
-__device__ __forceinline__ float2 pk(C2<float> a) { return make_float2(a.x, a.y); }
-__device__ __forceinline__ C2<float> un(float2 a) { return C2<float>{a.x, a.y}; }
-__device__ __forceinline__ C2<float> padd(C2<float> a, C2<float> b) { return un(__fadd2_rn(pk(a), pk(b))); }
-// a - b as fma(b, -1, a): b * -1 is exact, so this is the correctly rounded difference
-__device__ __forceinline__ C2<float> psub(C2<float> a, C2<float> b) {
-  return un(__ffma2_rn(pk(b), make_float2(-1.f, -1.f), pk(a)));
-}
-__device__ __forceinline__ C2<float> pscale(float s, C2<float> a) { return un(__fmul2_rn(make_float2(s, s), pk(a))); }
-// s * a + c
-__device__ __forceinline__ C2<float> pfma(float s, C2<float> a, C2<float> c) {
-  return un(__ffma2_rn(make_float2(s, s), pk(a), pk(c)));
-}
-// b + rot(e) and b - rot(e), rot = multiply by -i (forward) or +i (inverse)
-template <bool INV> __device__ __forceinline__ C2<float> add_rot(C2<float> b, C2<float> e) {
-  return INV ? C2<float>{b.x - e.y, b.y + e.x} : C2<float>{b.x + e.y, b.y - e.x};
-}
-template <bool INV> __device__ __forceinline__ C2<float> sub_rot(C2<float> b, C2<float> e) {
-  return INV ? C2<float>{b.x + e.y, b.y - e.x} : C2<float>{b.x - e.y, b.y + e.x};
-}
-// b + s * rot(e) and b - s * rot(e)
-template <bool INV> __device__ __forceinline__ C2<float> add_srot(C2<float> b, float s, C2<float> e) {
-  return INV ? C2<float>{fmaf(-s, e.y, b.x), fmaf(s, e.x, b.y)} : C2<float>{fmaf(s, e.y, b.x), fmaf(-s, e.x, b.y)};
-}
-template <bool INV> __device__ __forceinline__ C2<float> sub_srot(C2<float> b, float s, C2<float> e) {
-  return INV ? C2<float>{fmaf(s, e.y, b.x), fmaf(-s, e.x, b.y)} : C2<float>{fmaf(-s, e.y, b.x), fmaf(s, e.x, b.y)};
-}
-
 // Small DFTs on packed pairs; X_k = sum_n x_n exp(-+2 pi i n k / R), minus sign forward.
 template <bool INV> __device__ __forceinline__ void pdft2(C2<float>* v) {
   const C2<float> a = v[0];

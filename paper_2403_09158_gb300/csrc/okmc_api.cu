@@ -62,7 +62,8 @@ cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const doubl
 bool fast_solve_supported(const PassCfg& c);
 cudaError_t launch_plane_fast(bool inverse, int variant, const void* in, void* out, const PassCfg& c, cudaStream_t st);
 int plane_inv_variant_mask(const PassCfg& c);
-cudaError_t launch_pencil_fast(const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st);
+cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st);
+int pencil_variant_mask(const PassCfg& c);
 }  // namespace okmc
 
 namespace {
@@ -282,7 +283,7 @@ int solve(okmc_grid* g) {
     c.dirty = g->d_dirty;
     OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, 0, g->eps, g->spec, c, g->st); }));
     c.dirty = nullptr;
-    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil_fast((const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st); }));
+    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st); }));
     OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_fast(true, g->variant[2], g->spec2, g->sig, c, g->st); }));
   } else {
     OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<float, int32_t>((const int32_t*)g->eps, (C2<float>*)g->spec, c, g->st); }));
@@ -304,6 +305,7 @@ int energies(okmc_grid* g, int want_cand, double kT = 0.0) {
     ra.negb = &g->d_state->negative_barriers;
     ra.nu0 = g->nu0;
     ra.kT = kT;
+    ra.rkT = 1.0 / kT;
   }
   DilatedLists dl{};
   if (g->d_dl) {
@@ -463,7 +465,7 @@ int build_self_terms(okmc_grid* g) {
     OKMC_TRY(run(g, "self_fields", [&] { return launch_wfields<Q>((Q*)g->eps, n, g->d_ptr, g->d_off, g->d_cnt, b, g->st); }));
     if (g->fast) {
       OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, 0, g->eps, g->spec, c, g->st); }));
-      OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast((const C2<float>*)g->spec, (C2<float>*)g->spec, c, g->st); }));
+      OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec, c, g->st); }));
     } else {
       OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)g->spec, c, g->st); }));
       OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil<T>((C2<T>*)g->spec, c, g->st); }));
@@ -614,7 +616,7 @@ int capture_step(okmc_grid* g, int mode, double T, cudaGraphExec_t* out) {
 // the same arithmetic, so the choice changes the time and not the result.  Choices
 // are cached per grid shape for the life of the process.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune_cache;  // shape -> (pencil, inverse plane)
 
 int autotune(okmc_grid* g) {
   if (!g->fast) return OKMC_OK;
@@ -625,11 +627,14 @@ int autotune(okmc_grid* g) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      g->variant[2] = it->second;
+      g->variant[1] = it->second.first;
+      g->variant[2] = it->second.second;
       return OKMC_OK;
     }
   }
-  cudaError_t e = cudaMemsetAsync(g->spec2, 0, 6 * g->n[2] * g->P * 2 * tsize(g), g->st);
+  const size_t sbytes = 6 * g->n[2] * g->P * 2 * tsize(g);
+  cudaError_t e = cudaMemsetAsync(g->spec, 0, sbytes, g->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->spec2, 0, sbytes, g->st);
   if (e != cudaSuccess) return cuda_fail(g, e, "tune");
   PassCfg c = g->cfg;
   c.dirty = nullptr;
@@ -639,29 +644,35 @@ int autotune(okmc_grid* g) {
     cudaEventDestroy(a);
     return cuda_fail(g, cudaGetLastError(), "tune event");
   }
-  float best = 0.f;
-  int pick = 0;
-  for (int v = 0; v < 8; ++v) {
-    if (!((g->avail[2] >> v) & 1)) continue;
-    e = launch_plane_fast(true, v, g->spec2, g->sig, c, g->st);
-    if (e == cudaSuccess) e = cudaEventRecord(a, g->st);
-    for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_plane_fast(true, v, g->spec2, g->sig, c, g->st);
-    if (e == cudaSuccess) e = cudaEventRecord(b, g->st);
-    if (e == cudaSuccess) e = cudaEventSynchronize(b);
-    float ms = 0.f;
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-    if (e != cudaSuccess) break;
-    if (v == 0 || ms < best) {
-      best = ms;
-      pick = v;
+  for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass) {
+    auto launch = [&](int v) {
+      return pass == 1 ? launch_pencil_fast(v, (const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st)
+                       : launch_plane_fast(true, v, g->spec2, g->sig, c, g->st);
+    };
+    float best = 0.f;
+    int pick = 0;
+    for (int v = 0; v < 8; ++v) {
+      if (!((g->avail[pass] >> v) & 1)) continue;
+      e = launch(v);
+      if (e == cudaSuccess) e = cudaEventRecord(a, g->st);
+      for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch(v);
+      if (e == cudaSuccess) e = cudaEventRecord(b, g->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess) break;
+      if (v == 0 || ms < best) {
+        best = ms;
+        pick = v;
+      }
     }
+    g->variant[pass] = pick;
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   if (e != cudaSuccess) return cuda_fail(g, e, "tune");
-  g->variant[2] = pick;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = pick;
+  g_tune_cache[key] = std::make_pair(g->variant[1], g->variant[2]);
   return OKMC_OK;
 }
 
@@ -770,6 +781,7 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   c.C11 = d->C11;
   c.C12 = d->C12;
   c.C44 = d->C44;
+  for (int a = 0; a < 3; ++a) c.rn[a] = (float)(1.0 / g->n[a]);
   c.pH = make_plan(g->H);
   c.pY = make_plan(g->n[1]);
   c.pZ = make_plan(g->n[2]);
@@ -784,7 +796,10 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
     g->fast = !f64 && fast_solve_supported(c) && !(env && env[0] == '1');
   }
   if (g->fast && (rc = dalloc(g, &g->spec2, 6 * g->n[2] * g->P * 2 * tsize(g)))) return cleanup(rc);
-  if (g->fast) g->avail[2] = plane_inv_variant_mask(c);
+  if (g->fast) {
+    g->avail[1] = pencil_variant_mask(c);
+    g->avail[2] = plane_inv_variant_mask(c);
+  }
   if ((rc = dalloc(g, (void**)&g->d_dirty, sizeof(int) * 6 * g->n[2]))) return cleanup(rc);
   if (cudaMemsetAsync(g->d_dirty, 1, sizeof(int) * 6 * g->n[2], g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if (cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);

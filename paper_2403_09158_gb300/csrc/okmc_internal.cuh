@@ -40,6 +40,38 @@ template <class T, bool INV> __device__ __forceinline__ C2<T> rot(C2<T> v) {
   return INV ? C2<T>{-v.y, v.x} : C2<T>{v.y, -v.x};
 }
 
+// ---------------------------------------------------------------- packed FP32 pairs
+// The sm_100 family executes add, multiply and fma on a pair of FP32 values in one
+// instruction (round to nearest, each lane exactly as the scalar operation), so a
+// complex add, subtract or real scaling costs one instruction instead of two.  A
+// multiplication by -i or +i swaps the lanes; such terms are added in scalar form.
+__device__ __forceinline__ float2 pk(C2<float> a) { return make_float2(a.x, a.y); }
+__device__ __forceinline__ C2<float> un(float2 a) { return C2<float>{a.x, a.y}; }
+__device__ __forceinline__ C2<float> padd(C2<float> a, C2<float> b) { return un(__fadd2_rn(pk(a), pk(b))); }
+// a - b as fma(b, -1, a): b * -1 is exact, so this is the correctly rounded difference
+__device__ __forceinline__ C2<float> psub(C2<float> a, C2<float> b) {
+  return un(__ffma2_rn(pk(b), make_float2(-1.f, -1.f), pk(a)));
+}
+__device__ __forceinline__ C2<float> pscale(float s, C2<float> a) { return un(__fmul2_rn(make_float2(s, s), pk(a))); }
+// s * a + c
+__device__ __forceinline__ C2<float> pfma(float s, C2<float> a, C2<float> c) {
+  return un(__ffma2_rn(make_float2(s, s), pk(a), pk(c)));
+}
+// b + rot(e) and b - rot(e), rot = multiply by -i (forward) or +i (inverse)
+template <bool INV> __device__ __forceinline__ C2<float> add_rot(C2<float> b, C2<float> e) {
+  return INV ? C2<float>{b.x - e.y, b.y + e.x} : C2<float>{b.x + e.y, b.y - e.x};
+}
+template <bool INV> __device__ __forceinline__ C2<float> sub_rot(C2<float> b, C2<float> e) {
+  return INV ? C2<float>{b.x + e.y, b.y - e.x} : C2<float>{b.x - e.y, b.y + e.x};
+}
+// b + s * rot(e) and b - s * rot(e)
+template <bool INV> __device__ __forceinline__ C2<float> add_srot(C2<float> b, float s, C2<float> e) {
+  return INV ? C2<float>{fmaf(-s, e.y, b.x), fmaf(s, e.x, b.y)} : C2<float>{fmaf(s, e.y, b.x), fmaf(-s, e.x, b.y)};
+}
+template <bool INV> __device__ __forceinline__ C2<float> sub_srot(C2<float> b, float s, C2<float> e) {
+  return INV ? C2<float>{fmaf(s, e.y, b.x), fmaf(-s, e.x, b.y)} : C2<float>{fmaf(-s, e.y, b.x), fmaf(s, e.x, b.y)};
+}
+
 // ---------------------------------------------------------------- small DFTs
 // X_k = sum_n x_n exp(-+2 pi i n k / R): minus sign forward, plus sign inverse.
 template <class T, bool INV> __device__ __forceinline__ void dft2(C2<T>* v) {
@@ -238,6 +270,7 @@ struct PassCfg {
   const void* twZ;     // C2<T>[nz]
   const void* untw;    // C2<T>[H+1]    exp(-2 pi i k / nx)
   int* err;            // device error word (bounded waits that gave up set it)
+  float rn[3];         // 1/nx, 1/ny, 1/nz (rounded from FP64)
   int* dirty;          // fast forward plane pass: per plane (c*nz + z) flag, nonzero when the
                        // plane's eigenstrain changed since its last transform (the pass skips
                        // clean planes and clears the flags it consumed); nullptr: every plane
@@ -280,6 +313,7 @@ struct RateArgs {
   double* rsum;         // [n] sum over j
   long long* negb;      // count of negative effective barriers
   double nu0, kT;
+  double rkT;           // 1 / kT
 };
 
 // Eigenstrain tensors of the (at most three) defects whose self terms one batch computes.
@@ -393,6 +427,40 @@ __device__ __forceinline__ void sigma_of(const C2<T>* e, T q0, T q1, T q2, const
   s[5] = C.C44 * (q0 * w1 + q1 * w0) - t5;
 }
 
+// The same for FP32 on paired instructions: every complex-times-real term is one
+// packed fma; the adjugate and the determinant stay scalar.
+__device__ __forceinline__ void sigma_of(const C2<float>* e, float q0, float q1, float q2, const GreenC<float>& C,
+                                         const GreenC<float>& Cs, C2<float>* s) {
+  const float ds = Cs.C11 - Cs.C12, gs = 2.f * Cs.C44;
+  const C2<float> tr = padd(padd(e[0], e[1]), e[2]);
+  const C2<float> c12tr = pscale(Cs.C12, tr);
+  const C2<float> t0 = pfma(ds, e[0], c12tr), t1 = pfma(ds, e[1], c12tr), t2 = pfma(ds, e[2], c12tr);
+  const C2<float> t3 = pscale(gs, e[3]), t4 = pscale(gs, e[4]), t5 = pscale(gs, e[5]);
+  const C2<float> v0 = pfma(q2, t4, pfma(q1, t5, pscale(q0, t0)));
+  const C2<float> v1 = pfma(q2, t3, pfma(q1, t1, pscale(q0, t5)));
+  const C2<float> v2 = pfma(q2, t2, pfma(q1, t3, pscale(q0, t4)));
+  const float A = C.C11 - C.C12 - 2.f * C.C44, B = C.C12 + C.C44;
+  const float a0 = q0 * q0, a1 = q1 * q1, a2 = q2 * q2;
+  const float cq = C.C44 * (a0 + a1 + a2);
+  const float k00 = cq + (A + B) * a0, k11 = cq + (A + B) * a1, k22 = cq + (A + B) * a2;
+  const float k01 = B * q0 * q1, k02 = B * q0 * q2, k12 = B * q1 * q2;
+  const float i00 = k11 * k22 - k12 * k12, i01 = k02 * k12 - k01 * k22, i02 = k01 * k12 - k02 * k11;
+  const float i11 = k00 * k22 - k02 * k02, i12 = k01 * k02 - k00 * k12, i22 = k00 * k11 - k01 * k01;
+  const float rdet = __frcp_rn(k00 * i00 + k01 * i01 + k02 * i02);
+  const C2<float> w0 = pscale(rdet, pfma(i02, v2, pfma(i01, v1, pscale(i00, v0))));
+  const C2<float> w1 = pscale(rdet, pfma(i12, v2, pfma(i11, v1, pscale(i01, v0))));
+  const C2<float> w2 = pscale(rdet, pfma(i22, v2, pfma(i12, v1, pscale(i02, v0))));
+  const C2<float> qw = pfma(q2, w2, pfma(q1, w1, pscale(q0, w0)));
+  const float d = C.C11 - C.C12;
+  const C2<float> c12qw = pscale(C.C12, qw);
+  s[0] = pfma(d * q0, w0, psub(c12qw, t0));
+  s[1] = pfma(d * q1, w1, psub(c12qw, t1));
+  s[2] = pfma(d * q2, w2, psub(c12qw, t2));
+  s[3] = psub(pscale(C.C44, pfma(q1, w2, pscale(q2, w1))), t3);
+  s[4] = psub(pscale(C.C44, pfma(q0, w2, pscale(q2, w0))), t4);
+  s[5] = psub(pscale(C.C44, pfma(q0, w1, pscale(q1, w0))), t5);
+}
+
 // Green operator at half-spectrum index (kx, ky, kz), in place on e[6], scaled by
 // 1/N.  Frequencies follow Eq. frequencies (n = k for k < N/2, k - N otherwise,
 // so the Nyquist index is -N/2); on Nyquist planes the operator is averaged over
@@ -419,13 +487,23 @@ __device__ __forceinline__ void green_point(C2<T>* e, int kx, int ky, int kz, co
     }
     return;
   }
-  const T q0 = T(fx) / T(c.nx), q1 = T(fy) / T(c.ny), q2 = T(fz) / T(c.nz);
+  // FP32: multiply by the reciprocal edge; FP64: divide (the reciprocals are FP32)
+  T q0, q1, q2;
+  if constexpr (sizeof(T) == 4) {
+    q0 = T(fx) * c.rn[0];
+    q1 = T(fy) * c.rn[1];
+    q2 = T(fz) * c.rn[2];
+  } else {
+    q0 = T(fx) / T(c.nx);
+    q1 = T(fy) / T(c.ny);
+    q2 = T(fz) / T(c.nz);
+  }
   C2<T> s[6];
-  sigma_of<T>(e, q0, q1, q2, C, Cs, s);
+  sigma_of(e, q0, q1, q2, C, Cs, s);
   const bool nx_ = (kx == c.H), ny_ = (2 * ky == c.ny), nz_ = (2 * kz == c.nz);
   if (nx_ || ny_ || nz_) {
     C2<T> s2[6];
-    sigma_of<T>(e, nx_ ? -q0 : q0, ny_ ? -q1 : q1, nz_ ? -q2 : q2, C, Cs, s2);
+    sigma_of(e, nx_ ? -q0 : q0, ny_ ? -q1 : q1, nz_ ? -q2 : q2, C, Cs, s2);
     for (int a = 0; a < 6; ++a) s[a] = T(0.5) * (s[a] + s2[a]);
   }
   for (int a = 0; a < 6; ++a) e[a] = s[a];

@@ -424,6 +424,7 @@ extern "C" int okmc_solve_stress_static(const float* eps, float* sigma, const in
   c.C11 = C11;
   c.C12 = C12;
   c.C44 = C44;
+  for (int a = 0; a < 3; ++a) c.rn[a] = (float)(1.0 / n[a]);
   c.pH = make_plan(H);
   c.pY = make_plan(n[1]);
   c.pZ = make_plan(n[2]);
