@@ -47,6 +47,18 @@ __device__ __forceinline__ void load_tw(C2<float>* twH, C2<float>* twY, C2<float
   for (int i = threadIdx.x; i <= H; i += blockDim.x) untw[i] = gU[i];
 }
 
+// Row of a plane handled by row group g in the row phases of the inverse pass.  A row
+// buffer stride of H + 1 complex puts adjacent rows 2 banks apart, so two groups of
+// one half-warp on adjacent rows collide; groups of one half-warp take rows NTH apart
+// instead (their 64-bit accesses then cover the 32 banks once).  A bijection on each
+// block of 16 rows.
+template <int NTH>
+__device__ __forceinline__ int row_of_group(int g) {
+  constexpr int q = 16 / NTH;  // groups per half-warp
+  const int hw = g / q, i = g % q;
+  return (hw / NTH) * 16 + (hw % NTH) + i * NTH;
+}
+
 // ---------------------------------------------------------------- plane passes
 // One cluster of CS CTAs (256 threads, two CTAs per SM) per (component, z) plane.
 // Rows: a group of reg_nt<H> threads per row, all of a row's loads in flight,
@@ -222,8 +234,9 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   {  // rows along x
     const int g = tid / S::NTH, t = tid % S::NTH;
     for (int r0 = 0; r0 < ROWS; r0 += S::GR) {
-      const bool act = r0 + g < ROWS;
-      const int yl = act ? r0 + g : 0;
+      const int yr = r0 + row_of_group<S::NTH>(g);
+      const bool act = yr < ROWS;
+      const int yl = act ? yr : 0;
       C2<float>* R = rowb + yl * S::LDR;
       auto ld = [&](int k) {
         if (k == 0) {
@@ -308,8 +321,9 @@ __global__ void __launch_bounds__(NTHR, MINB) k_plane_inv_s(const C2<float>* __r
   {  // rows along x
     const int g = tid / NTH, t = tid % NTH;
     for (int r0 = 0; r0 < ROWS; r0 += GR) {
-      const bool act = r0 + g < ROWS;
-      const int yl = act ? r0 + g : 0;
+      const int yr = r0 + row_of_group<NTH>(g);
+      const bool act = yr < ROWS;
+      const int yl = act ? yr : 0;
       C2<float>* R = rowb + yl * LDR;
       auto ld = [&](int k) {
         if (k == 0) {
