@@ -351,6 +351,12 @@ __host__ __device__ constexpr size_t pencil_fast_smem() {
 }
 
 
+// Tile row handled by row counter r in the load, Green and store loops: lanes 0-7 and
+// 8-15 of a half-warp take rows 8 apart, whose 18-word stride puts them 16 banks apart
+// (adjacent rows would wrap onto the same banks).  A bijection on each block of 16
+// rows; NZ is a multiple of 16, so a block never straddles two components.
+__device__ __forceinline__ int tile_row(int r) { return (r & ~15) + ((r & 1) << 3) + ((r >> 1) & 7); }
+
 // in and out may be the same buffer: every CTA reads its whole tile before it writes.
 template <int NZ>
 __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<float>* out, PassCfg c) {
@@ -362,8 +368,8 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<f
   const size_t p0 = (size_t)blockIdx.x * kTW;
   const int kx = (int)(p0 / c.ny), ky0 = (int)(p0 % c.ny);
   for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
-    const int t = idx & (kTW - 1), kz = (idx >> 3) % NZ, comp = idx / (kTW * NZ);
-    cp_async8(tile + (comp * NZ + kz) * kLDT + t, in + ((size_t)comp * NZ + kz) * P + p0 + t);
+    const int t = idx & (kTW - 1), row = tile_row(idx >> 3);  // row = comp * NZ + kz
+    cp_async8(tile + row * kLDT + t, in + (size_t)row * P + p0 + t);
   }
   fill_tw2<NZ>(twZ, reinterpret_cast<const C2<float>*>(c.twZ));
   cp_async_wait_all();
@@ -382,7 +388,7 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<f
   if (!c.forward_only) {
     const float scale = 1.0f / ((float)c.nx * (float)c.ny * (float)c.nz);
     for (int idx = tid; idx < kTW * NZ; idx += kT) {
-      const int t8 = idx & (kTW - 1), kz = idx >> 3;
+      const int t8 = idx & (kTW - 1), kz = tile_row(idx >> 3);
       C2<float> e[6];
 #pragma unroll
       for (int a = 0; a < 6; ++a) e[a] = tile[(a * NZ + kz) * kLDT + t8];
@@ -402,8 +408,8 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<f
     __syncthreads();
   }
   for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
-    const int t8 = idx & (kTW - 1), kz = (idx >> 3) % NZ, comp = idx / (kTW * NZ);
-    out[((size_t)comp * NZ + kz) * P + p0 + t8] = tile[(comp * NZ + kz) * kLDT + t8];
+    const int t8 = idx & (kTW - 1), row = tile_row(idx >> 3);
+    out[(size_t)row * P + p0 + t8] = tile[row * kLDT + t8];
   }
 }
 
