@@ -806,42 +806,65 @@ __global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __rest
                                                              const double* __restrict__ rsum, int3 n, uint32_t key0,
                                                              uint32_t key1, Move* __restrict__ moves,
                                                              DevState* __restrict__ st) {
-  __shared__ double part[kEventThreads];
-  __shared__ int sel_t;
-  const int t = threadIdx.x;
+  __shared__ double wsum[kEventThreads / 32];
+  __shared__ int sel_t, last_t;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int per = (nd + blockDim.x - 1) / blockDim.x;
   const int i0 = min(nd, t * per), i1 = min(nd, i0 + per);
   double s = 0.0;
   for (int i = i0; i < i1; ++i) s += rsum[i];
-  part[t] = s;
-  __syncthreads();
-  for (int o = 1; o < blockDim.x; o <<= 1) {  // inclusive scan, fixed order
-    const double v = (t >= o) ? part[t - o] : 0.0;
-    __syncthreads();
-    part[t] += v;
-    __syncthreads();
+  // inclusive scan of the chunk sums: within each warp by shuffles, then over the
+  // warp totals (fixed order, so the line is the same on every run)
+  double v = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += y;
   }
-  const double R = part[blockDim.x - 1];
+  double ex = __shfl_up_sync(0xffffffffu, v, 1);
+  if (lane == 0) ex = 0.0;
+  if (lane == 31) wsum[w] = v;
+  if (t == 0) {
+    sel_t = 0x7fffffff;
+    last_t = -1;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    double x = lane < nw ? wsum[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const double y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < nw) wsum[lane] = x;
+  }
+  __syncthreads();
+  const double base = w > 0 ? wsum[w - 1] : 0.0;
+  const double incl = base + v, excl = base + ex;
+  const double R = wsum[(blockDim.x >> 5) - 1];
   const long long step = st->step;
   const uint32_t ctr[4] = {(uint32_t)step, (uint32_t)(step >> 32), 0xFFFFFFFFu, 0u};
   uint32_t x[4];
   philox4x32_10(ctr, key0, key1, x);
   const double u1 = u53(x[0], x[1]), u2 = u53(x[2], x[3]);
   const double target = u1 * R;
-  if (t == 0) sel_t = 0x7fffffff;
-  __syncthreads();
-  const double excl = (t > 0) ? part[t - 1] : 0.0;
-  if (s > 0.0 && part[t] >= target) atomicMin(&sel_t, t);
-  __syncthreads();
-  if (t == 0 && sel_t == 0x7fffffff) {
-    for (int q = blockDim.x - 1; q >= 0; --q)
-      if (part[q] - (q > 0 ? part[q - 1] : 0.0) > 0.0) {
-        sel_t = q;
-        break;
-      }
+  // the first chunk whose running sum reaches the target (else the last nonzero one)
+  const unsigned hit = __ballot_sync(0xffffffffu, s > 0.0 && incl >= target);
+  const unsigned nz = __ballot_sync(0xffffffffu, s > 0.0);
+  if (lane == 0) {
+    if (hit) atomicMin(&sel_t, (w << 5) + __ffs(hit) - 1);
+    if (nz) atomicMax(&last_t, (w << 5) + 31 - __clz(nz));
   }
   __syncthreads();
-  if (t != sel_t) return;
+  const int pick_t = sel_t != 0x7fffffff ? sel_t : last_t;
+  if (t != pick_t) {
+    if (t == 0 && pick_t < 0) {  // no positive rate anywhere
+      st->err = 5;
+      st->nmoves = 0;
+    }
+    return;
+  }
   double run = excl;
   int pi = -1, pj = -1, li = -1, lj = -1;
   for (int i = i0; i < i1 && pi < 0; ++i) {
