@@ -41,6 +41,16 @@ def _peaks():
     return 6800.0, 'fallback'
 
 
+def max_over_ranks(x, ws):
+    """The largest value of x over the ranks (the job takes as long as its slowest
+    replica); x itself when there is one rank."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get('WORLD_SIZE', '1'))
     rank = int(os.environ.get('RANK', '0'))
@@ -157,10 +167,9 @@ def run_ours(args, ws, rank):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / k_e2e
     g.close()
-    t = torch.tensor([ms], dtype=torch.float64)
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    return dict(ms=float(t.item()), N=N, events=events, kt=kt, clocks=clocks, setup_s=setup_s, e2e_s=e2e_s,
+    ms = max_over_ranks(ms, ws)
+    e2e_s = max_over_ranks(e2e_s, ws)
+    return dict(ms=ms, N=N, events=events, kt=kt, clocks=clocks, setup_s=setup_s, e2e_s=e2e_s,
                 nd=len(w.defects), n=w.n, T=w.T_K, stats_bytes=C.sizeof(ok.StepStats))
 
 
@@ -409,7 +418,7 @@ def main():
         'kernel_ms': {k: v[0] / v[1] for k, v in kt.items()},
         'gpu_launches': int(launches),
         'clocks': r['clocks'],
-        'e2e': {'value': r['N'] / r['e2e_s'], 'unit': UNIT, 'h2d_bytes_per_step': r['nd'] * 12,
+        'e2e': {'value': ws * r['N'] / r['e2e_s'], 'unit': UNIT, 'h2d_bytes_per_step': r['nd'] * 12,
                 'd2h_bytes_per_step': r['nd'] * 12 + r['stats_bytes']},
     }
     if not args.no_cpu_baseline:
