@@ -241,8 +241,10 @@ int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
 
 /* Launch variants of the three FFT passes (forward plane pass = 0, pencil pass = 1,
  * inverse plane pass = 2), for diagnostics and tests.  okmc_grid_create times every
- * variant that exists for the grid's shape and keeps the fastest (set the
- * environment variable OKMC_TUNE=0 to keep variant 0); the variants differ in
+ * variant that exists for the grid's shape (three interleaved rounds, best of each)
+ * and keeps variant 0 unless another is more than 3% faster; the choice is cached per
+ * grid shape for the life of the process (the environment variable OKMC_TUNE=0 keeps
+ * variant 0 without timing, e.g. under a profiler); the variants differ in
  * cluster size, threads per CTA and how data reaches shared memory, not in
  * arithmetic, so results are bitwise the same under every variant.
  * okmc_get_variants: current[p] = variant in use, available[p] = bit mask of the
