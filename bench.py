@@ -173,6 +173,78 @@ def run_ours(args, ws, rank):
                 nd=len(w.defects), n=w.n, T=w.T_K, stats_bytes=C.sizeof(ok.StepStats))
 
 
+def _time_steps(g, T, steps, stream):
+    """Device time (ms) of `steps` residence steps (graph replays) and the events they ran."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ev = g.stats()['events']
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        g.step(T, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), g.stats()['events'] - ev
+
+
+def run_config(args, which):
+    """The small (32^3, FP64 fields) and medium (128^3, FP32 fields beside the FP64 GPU
+    path) workloads: residence-time steps per second and the latency of one
+    request-level solve through the C ABI (move one defect from the host, then the
+    stress solve and the site energies copied back)."""
+    import torch
+
+    from paper_2403_09158_gb300 import okmc as ok
+    from paper_2403_09158_gb300.workload import config_medium, config_small
+
+    w = config_small() if which == 'small' else config_medium()
+    stream = torch.cuda.current_stream()
+    N = int(np.prod(w.n))
+    precs = [('f64', ok.FP64_FIELDS)] if which == 'small' else [('f32', ok.FP32_FIELDS), ('f64', ok.FP64_FIELDS)]
+    out_paths = {}
+    clk = Clocks(torch.cuda.current_device())
+    for tag, prec in precs:
+        g = ok.Grid(w.n, w.voxel_nm, *w.C, precision=prec, seed=w.seed, stream=stream.cuda_stream)
+        g.set_defects(w.defects)
+        for _ in range(args.warmup):
+            g.step(w.T_K, 1)
+        ms, events = _time_steps(g, w.T_K, args.steps, stream)
+        # request-level solve latency: one defect moves (host positions in), then the
+        # solve and the site energies (host array out)
+        pos = g.get_positions()
+        moved = pos.copy()
+        E = np.zeros(g.nd)
+        lat = []
+        for k in range(max(5, args.steps // 2)):
+            moved[:] = pos
+            j = int(np.flatnonzero(w.defects['mobility'] != 0)[k % int((w.defects['mobility'] != 0).sum())])
+            moved[j] = (moved[j] + (1 if k % 2 == 0 else -1)) % (2 * np.asarray(w.n))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g.set_positions(moved)
+            g.interaction_energies(E)
+            lat.append(time.perf_counter() - t0)
+        g.set_positions(pos)
+        g.close()
+        out_paths[tag] = {'ms_per_step': ms / args.steps, 'voxel_updates_per_s': N * args.steps / (ms / 1e3),
+                          'events_per_s': events / (ms / 1e3), 'steps_per_s': args.steps / (ms / 1e3),
+                          'solve_latency_ms_p50': float(np.percentile(np.array(lat) * 1e3, 50)),
+                          'solve_latency_ms_max': float(max(lat) * 1e3)}
+    clocks = clk.stop()
+    head = out_paths[precs[0][0]]
+    desc = ('small_32cubed (32^3, 2 1/2<111> loops R = 1 nm + 8 SIA clusters, 300 K, FP64 fields)' if which == 'small'
+            else 'medium_128cubed_200defects (128^3, 200 defects, config-2 mix, 400 K)')
+    out = {'metric': 'voxel stress+energy updates/s', 'value': head['voxel_updates_per_s'], 'unit': 'voxel updates/s',
+           'n_gpus': 1, 'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': head['ms_per_step'],
+           'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None,
+           'dtype': 'f64' if which == 'small' else 'f32 fields / f64 energies', 'data': 'synthetic',
+           'config': {'workload': desc, 'grid': list(w.n), 'defects': len(w.defects), 'mode': 'residence'},
+           'paths': out_paths, 'clocks': clocks}
+    print(json.dumps(out))
+    return 0
+
+
 def run_batch(args):
     """Ensemble of 64 independent replicas (edges 64-192, 50-800 defects capped by box
     volume, 300-600 K) advanced together: one CUDA graph launch per step runs every
@@ -360,9 +432,10 @@ def main():
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--workload', default='large', choices=['large', 'batch', 'serve'],
+    ap.add_argument('--workload', default='large', choices=['large', 'batch', 'serve', 'small', 'medium'],
                     help='large: the 256^3 single-replica step (default); batch: the 64-replica ensemble; '
-                         'serve: the request server under Poisson load')
+                         'serve: the request server under Poisson load; small / medium: the 32^3 FP64 and '
+                         'the 128^3 workloads')
     ap.add_argument('--rates', default='10,30,100,300,1000,2000', help='serve: offered request rates (1/s)')
     ap.add_argument('--seconds', type=float, default=4.0, help='serve: length of each rate\'s request stream')
     ap.add_argument('--max-requests', type=int, default=600, help='serve: cap on requests per rate')
@@ -383,6 +456,8 @@ def main():
         return run_batch(args) if rank == 0 else 0
     if args.workload == 'serve':
         return run_serve(args) if rank == 0 else 0
+    if args.workload in ('small', 'medium'):
+        return run_config(args, args.workload) if rank == 0 else 0
     r = run_ours(args, ws, rank)
     if ws > 1:
         torch.distributed.destroy_process_group()
