@@ -740,7 +740,10 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
     off_tw[2] = t.size(); twiddles(t, g->n[2], g->n[2], -1.0);
     off_tw[3] = t.size(); twiddles(t, g->n[0], g->H + 1, -1.0);
     if ((rc = dalloc(g, &g->tw, t.size() * sizeof(t[0])))) return cleanup(rc);
-    e = cudaMemcpy(g->tw, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice);
+    // on the handle's stream (which may be non-blocking, so unordered with the legacy
+    // stream), then waited for: the host table must outlive the copy
+    e = cudaMemcpyAsync(g->tw, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     for (int k = 0; k < 4; ++k) off_tw[k] *= sizeof(C2<double>);
   } else {
     std::vector<C2<float>> t;
@@ -749,7 +752,10 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
     off_tw[2] = t.size(); twiddles(t, g->n[2], g->n[2], -1.0);
     off_tw[3] = t.size(); twiddles(t, g->n[0], g->H + 1, -1.0);
     if ((rc = dalloc(g, &g->tw, t.size() * sizeof(t[0])))) return cleanup(rc);
-    e = cudaMemcpy(g->tw, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice);
+    // on the handle's stream (which may be non-blocking, so unordered with the legacy
+    // stream), then waited for: the host table must outlive the copy
+    e = cudaMemcpyAsync(g->tw, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     for (int k = 0; k < 4; ++k) off_tw[k] *= sizeof(C2<float>);
   }
   if (e != cudaSuccess) return cleanup(OKMC_ECUDA);
@@ -767,7 +773,8 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
     add(g->n[1], g->n[1], 0);
     add(g->n[2], g->n[2], 0);
     if ((rc = dalloc(g, (void**)&g->ph, ph.size() * sizeof(double2)))) return cleanup(rc);
-    e = cudaMemcpy(g->ph, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(g->ph, ph.data(), ph.size() * sizeof(double2), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     if (e != cudaSuccess) return cleanup(OKMC_ECUDA);
   }
   PassCfg& c = g->cfg;
@@ -835,7 +842,7 @@ size_t okmc_estimate_field_bytes(const okmc_grid_desc* d) {
 int okmc_grid_destroy(okmc_grid* g) {
   if (!g) return OKMC_OK;
   std::lock_guard<std::recursive_mutex> lk(g_capture_mu);
-  if (g->st || true) cudaStreamSynchronize(g->st);
+  cudaStreamSynchronize(g->st);
   for (auto& p : g->pending) {
     cudaEventDestroy(p.a);
     cudaEventDestroy(p.b);
@@ -982,6 +989,7 @@ int okmc_solve_stress(okmc_grid* g, void* sigma_out, int out_on_device) {
 
 int okmc_eigenstrain(okmc_grid* g, void* eps_out, int out_on_device) {
   if (!g || !eps_out) return OKMC_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);  // allocates: not during another thread's capture
   void* tmp = nullptr;
   OKMC_TRY(dalloc(g, &tmp, 6 * g->N * tsize(g)));
   int rc = run(g, "fixed_to_real", [&] {
