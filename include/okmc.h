@@ -216,6 +216,12 @@ int okmc_batch_step(okmc_batch* b, const okmc_step_params* params, int64_t n_ste
 int okmc_batch_destroy(okmc_batch* b);
 const char* okmc_batch_last_error(const okmc_batch* b);
 
+/* Cubic constants of an isotropic solid, for okmc_grid_desc: C[0] = C11 =
+ * lambda + 2 mu, C[1] = C12 = lambda, C[2] = C44 = mu, with the Lame constant
+ * lambda = 2 mu nu / (1 - 2 nu) (so C44 = (C11 - C12)/2).  mu_GPa > 0 and
+ * -1 < nu < 1/2, else OKMC_EINVAL.  Host only; C (host, 3 doubles) is written. */
+int okmc_isotropic_stiffness(double mu_GPa, double nu, double C[3]);
+
 /* Device bytes held by the handle. */
 size_t okmc_device_bytes(const okmc_grid* g);
 

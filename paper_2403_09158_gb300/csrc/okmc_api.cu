@@ -821,6 +821,15 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   return OKMC_OK;
 }
 
+int okmc_isotropic_stiffness(double mu_GPa, double nu, double C[3]) {
+  if (!C || !(mu_GPa > 0.0) || !std::isfinite(mu_GPa) || !(nu > -1.0) || !(nu < 0.5)) return OKMC_EINVAL;
+  const double lam = 2.0 * mu_GPa * nu / (1.0 - 2.0 * nu);
+  C[0] = lam + 2.0 * mu_GPa;
+  C[1] = lam;
+  C[2] = mu_GPa;
+  return OKMC_OK;
+}
+
 size_t okmc_estimate_field_bytes(const okmc_grid_desc* d) {
   if (!d || d->n[0] < 1 || d->n[1] < 1 || d->n[2] < 1) return 0;
   const bool f64 = d->precision == OKMC_FP64_FIELDS;

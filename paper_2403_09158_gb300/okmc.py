@@ -32,6 +32,7 @@ EXPORTED = [
     'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_get_variants', 'okmc_set_variant',
     'okmc_set_kinetic_state', 'okmc_estimate_field_bytes', 'okmc_server_create', 'okmc_server_add_replica',
     'okmc_server_submit', 'okmc_server_wait', 'okmc_server_get_stats', 'okmc_server_last_error', 'okmc_server_destroy',
+    'okmc_isotropic_stiffness',
 ]
 
 
@@ -132,6 +133,7 @@ def load(path=LIB_PATH):
         'okmc_server_get_stats': (C.c_int, [vp, C.POINTER(ServerStats)]),
         'okmc_server_last_error': (C.c_char_p, [vp]),
         'okmc_server_destroy': (C.c_int, [vp]),
+        'okmc_isotropic_stiffness': (C.c_int, [C.c_double, C.c_double, C.POINTER(C.c_double)]),
         'okmc_set_variant': (C.c_int, [vp, i32, i32]),
     }
     for name, (res, args) in sig.items():
@@ -362,6 +364,15 @@ def _grid_desc(n, voxel_nm, C11, C12, C44, k0_mode=MEAN_STRESS_ZERO, precision=F
     d.voxel_nm, d.C11, d.C12, d.C44, d.nu0 = voxel_nm, C11, C12, C44, nu0
     d.seed = seed
     return d
+
+
+def isotropic_stiffness(mu_GPa, nu):
+    """(C11, C12, C44) of an isotropic solid (okmc_isotropic_stiffness)."""
+    out = (C.c_double * 3)()
+    rc = load().okmc_isotropic_stiffness(mu_GPa, nu, out)
+    if rc != OKMC_OK:
+        raise OkmcError(rc, 'okmc_isotropic_stiffness: mu must be > 0 and -1 < nu < 1/2')
+    return tuple(out)
 
 
 def estimate_field_bytes(n, voxel_nm, C11, C12, C44, **kw):

@@ -125,3 +125,15 @@ def test_product_path_does_not_import_oracle():
             if f.endswith(('.py', '.cu', '.cuh', '.h')):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert 'import oracle' not in txt and 'from oracle' not in txt, f
+
+
+def test_isotropic_stiffness_matches_the_lame_relations(lib):
+    import oracle as O
+    for mu, nu in ((82.0, 0.29), (100.0, 0.0), (50.0, -0.4), (30.0, 0.49)):
+        got = ok.isotropic_stiffness(mu, nu)
+        ref = O.isotropic_cubic_constants(mu, nu)
+        assert np.allclose(got, ref, rtol=1e-15, atol=0)
+        assert abs(got[2] - 0.5 * (got[0] - got[1])) <= 1e-12 * got[0]
+    for mu, nu in ((0.0, 0.3), (-1.0, 0.3), (80.0, 0.5), (80.0, -1.0), (float('nan'), 0.3)):
+        with pytest.raises(ok.OkmcError):
+            ok.isotropic_stiffness(mu, nu)
