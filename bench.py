@@ -102,6 +102,28 @@ def kernel_bytes(name, n):
     return {'plane_fwd': 6 * N * 4 + spec, 'pencil_green': 2 * spec, 'plane_inv': spec + 6 * N * 4}.get(name)
 
 
+def cufft_reference(n, stream, reps):
+    """Device time (ms) of cuFFT (through torch.fft) on the same transform sizes: a
+    forward R2C and an inverse C2R of six components of an n grid, without the Green
+    operator.  A reference point for the solve passes; the library does not use it."""
+    import torch
+    x = torch.randn((6, n[2], n[1], n[0]), device='cuda', dtype=torch.float32)
+    for _ in range(2):
+        y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=(n[2], n[1], n[0]), dim=(1, 2, 3))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        y = torch.fft.irfftn(torch.fft.rfftn(x, dim=(1, 2, 3)), s=(n[2], n[1], n[0]), dim=(1, 2, 3))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    del x, y
+    torch.cuda.empty_cache()
+    return ms
+
+
 def run_ours(args, ws, rank):
     import ctypes as C
 
@@ -167,9 +189,10 @@ def run_ours(args, ws, rank):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / k_e2e
     g.close()
+    cufft = cufft_reference(w.n, stream, max(3, args.steps // 3))
     ms = max_over_ranks(ms, ws)
     e2e_s = max_over_ranks(e2e_s, ws)
-    return dict(ms=ms, N=N, events=events, kt=kt, clocks=clocks, setup_s=setup_s, e2e_s=e2e_s,
+    return dict(ms=ms, N=N, events=events, kt=kt, clocks=clocks, setup_s=setup_s, e2e_s=e2e_s, cufft=cufft,
                 nd=len(w.defects), n=w.n, T=w.T_K, stats_bytes=C.sizeof(ok.StepStats))
 
 
@@ -491,6 +514,10 @@ def main():
         'pipeline_roofline': {'solve_ms': solve_ms, 'algorithmic_bytes': 96 * r['N'], 'achieved_gbs': pipe_gbs,
                               'frac': pipe_gbs / hbm},
         'kernel_ms': {k: v[0] / v[1] for k, v in kt.items()},
+        'cufft_reference': {'fwd_inv_ms': r['cufft'], 'solve_ms': solve_ms,
+                            'note': 'torch.fft (cuFFT) R2C + C2R of the six components on the same grid, no Green '
+                                    'operator, on fresh input (no clean-plane reuse); solve_ms is the three solve '
+                                    'kernels of one step here'},
         'gpu_launches': int(launches),
         'clocks': r['clocks'],
         'e2e': {'value': ws * r['N'] / r['e2e_s'], 'unit': UNIT, 'h2d_bytes_per_step': r['nd'] * 12,

@@ -248,7 +248,7 @@ int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
 /* Launch variants of the three FFT passes (forward plane pass = 0, pencil pass = 1,
  * inverse plane pass = 2), for diagnostics and tests.  okmc_grid_create times every
  * variant that exists for the grid's shape (three interleaved rounds, best of each)
- * and keeps variant 0 unless another is more than 3% faster; the choice is cached per
+ * and keeps variant 0 unless another is more than 2% faster; the choice is cached per
  * grid shape for the life of the process (the environment variable OKMC_TUNE=0 keeps
  * variant 0 without timing, e.g. under a profiler); the variants differ in
  * cluster size, threads per CTA and how data reaches shared memory, not in

@@ -121,7 +121,7 @@ __device__ __forceinline__ C2<float> tw16(C2<float> v, int e) {
   if (e == 8) return C2<float>{-v.x, -v.y};
   if (e == 12) return rot<float, !INV>(v);
   const float c = cos16(e), s = INV ? sin16(e) : -sin16(e);
-  return C2<float>{v.x * c - v.y * s, v.x * s + v.y * c};
+  return cmul_rn(v, C2<float>{c, s});
 }
 
 template <bool INV>
@@ -360,7 +360,7 @@ __device__ __forceinline__ void dft_composite(C2<float>* v) {
         y[n1 * Q + k2] = a[k2];
       } else {
         const float c = cosN<R>(e), s = INV ? sinN<R>(e) : -sinN<R>(e);
-        y[n1 * Q + k2] = C2<float>{a[k2].x * c - a[k2].y * s, a[k2].x * s + a[k2].y * c};
+        y[n1 * Q + k2] = cmul_rn(a[k2], C2<float>{c, s});
       }
     }
   }
@@ -442,7 +442,7 @@ __device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st
       for (int k2 = 1; k2 < R2; ++k2) {
         C2<float> w = tw2[n1 * (R2 + 1) + k2];
         if (INV) w.y = -w.y;
-        x(n1, k2) = v[a][k2] * w;
+        x(n1, k2) = cmul_rn(v[a][k2], w);
       }
     }
   }

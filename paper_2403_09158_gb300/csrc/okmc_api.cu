@@ -645,7 +645,7 @@ int autotune(okmc_grid* g) {
     return cuda_fail(g, cudaGetLastError(), "tune event");
   }
   // three interleaved rounds, the best of each variant, and variant 0 kept unless
-  // another is more than 3% faster (robust against a noisy or shared device)
+  // another is more than 2% faster (robust against a noisy or shared device)
   for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass) {
     auto launch = [&](int v) {
       return pass == 1 ? launch_pencil_fast(v, (const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st)
@@ -668,7 +668,7 @@ int autotune(okmc_grid* g) {
     }
     int pick = 0;
     for (int v = 1; v < 8; ++v)
-      if (best[v] < 0.97f * best[0] && best[v] < best[pick]) pick = v;
+      if (best[v] < 0.98f * best[0] && best[v] < best[pick]) pick = v;
     g->variant[pass] = pick;
   }
   cudaEventDestroy(a);

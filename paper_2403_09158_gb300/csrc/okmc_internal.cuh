@@ -46,6 +46,11 @@ template <class T, bool INV> __device__ __forceinline__ C2<T> rot(C2<T> v) {
 // complex add, subtract or real scaling costs one instruction instead of two.  A
 // multiplication by -i or +i swaps the lanes; such terms are added in scalar form.
 __device__ __forceinline__ float2 pk(C2<float> a) { return make_float2(a.x, a.y); }
+// a * b with explicit roundings (re = fma(a.x, b.x, -(a.y b.y)), im = fma(a.x, b.y, a.y b.x)),
+// so the result does not depend on how the compiler contracts where this is inlined
+__device__ __forceinline__ C2<float> cmul_rn(C2<float> a, C2<float> b) {
+  return C2<float>{__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x))};
+}
 __device__ __forceinline__ C2<float> un(float2 a) { return C2<float>{a.x, a.y}; }
 __device__ __forceinline__ C2<float> padd(C2<float> a, C2<float> b) { return un(__fadd2_rn(pk(a), pk(b))); }
 // a - b as fma(b, -1, a): b * -1 is exact, so this is the correctly rounded difference
@@ -428,10 +433,12 @@ __device__ __forceinline__ void sigma_of(const C2<T>* e, T q0, T q1, T q2, const
 }
 
 // The same for FP32 on paired instructions: every complex-times-real term is one
-// packed fma; the adjugate and the determinant stay scalar.
+// packed fma; the adjugate and the determinant stay scalar.  Every operation is an
+// explicit intrinsic, so the rounding does not depend on how the compiler contracts
+// products and sums where this is inlined (launch variants agree bit for bit).
 __device__ __forceinline__ void sigma_of(const C2<float>* e, float q0, float q1, float q2, const GreenC<float>& C,
                                          const GreenC<float>& Cs, C2<float>* s) {
-  const float ds = Cs.C11 - Cs.C12, gs = 2.f * Cs.C44;
+  const float ds = __fsub_rn(Cs.C11, Cs.C12), gs = __fmul_rn(2.f, Cs.C44);
   const C2<float> tr = padd(padd(e[0], e[1]), e[2]);
   const C2<float> c12tr = pscale(Cs.C12, tr);
   const C2<float> t0 = pfma(ds, e[0], c12tr), t1 = pfma(ds, e[1], c12tr), t2 = pfma(ds, e[2], c12tr);
@@ -439,23 +446,27 @@ __device__ __forceinline__ void sigma_of(const C2<float>* e, float q0, float q1,
   const C2<float> v0 = pfma(q2, t4, pfma(q1, t5, pscale(q0, t0)));
   const C2<float> v1 = pfma(q2, t3, pfma(q1, t1, pscale(q0, t5)));
   const C2<float> v2 = pfma(q2, t2, pfma(q1, t3, pscale(q0, t4)));
-  const float A = C.C11 - C.C12 - 2.f * C.C44, B = C.C12 + C.C44;
-  const float a0 = q0 * q0, a1 = q1 * q1, a2 = q2 * q2;
-  const float cq = C.C44 * (a0 + a1 + a2);
-  const float k00 = cq + (A + B) * a0, k11 = cq + (A + B) * a1, k22 = cq + (A + B) * a2;
-  const float k01 = B * q0 * q1, k02 = B * q0 * q2, k12 = B * q1 * q2;
-  const float i00 = k11 * k22 - k12 * k12, i01 = k02 * k12 - k01 * k22, i02 = k01 * k12 - k02 * k11;
-  const float i11 = k00 * k22 - k02 * k02, i12 = k01 * k02 - k00 * k12, i22 = k00 * k11 - k01 * k01;
-  const float rdet = __frcp_rn(k00 * i00 + k01 * i01 + k02 * i02);
+  const float B = __fadd_rn(C.C12, C.C44);
+  const float AB = __fsub_rn(C.C11, C.C44);  // A + B with A = C11 - C12 - 2 C44
+  const float a0 = __fmul_rn(q0, q0), a1 = __fmul_rn(q1, q1), a2 = __fmul_rn(q2, q2);
+  const float cq = __fmul_rn(C.C44, __fadd_rn(__fadd_rn(a0, a1), a2));
+  const float k00 = __fmaf_rn(AB, a0, cq), k11 = __fmaf_rn(AB, a1, cq), k22 = __fmaf_rn(AB, a2, cq);
+  const float Bq0 = __fmul_rn(B, q0);
+  const float k01 = __fmul_rn(Bq0, q1), k02 = __fmul_rn(Bq0, q2), k12 = __fmul_rn(__fmul_rn(B, q1), q2);
+  // a*b - c*d as fma(a, b, -(c*d))
+  auto dif = [](float a, float b, float c, float d) { return __fmaf_rn(a, b, -__fmul_rn(c, d)); };
+  const float i00 = dif(k11, k22, k12, k12), i01 = dif(k02, k12, k01, k22), i02 = dif(k01, k12, k02, k11);
+  const float i11 = dif(k00, k22, k02, k02), i12 = dif(k01, k02, k00, k12), i22 = dif(k00, k11, k01, k01);
+  const float rdet = __frcp_rn(__fmaf_rn(k02, i02, __fmaf_rn(k01, i01, __fmul_rn(k00, i00))));
   const C2<float> w0 = pscale(rdet, pfma(i02, v2, pfma(i01, v1, pscale(i00, v0))));
   const C2<float> w1 = pscale(rdet, pfma(i12, v2, pfma(i11, v1, pscale(i01, v0))));
   const C2<float> w2 = pscale(rdet, pfma(i22, v2, pfma(i12, v1, pscale(i02, v0))));
   const C2<float> qw = pfma(q2, w2, pfma(q1, w1, pscale(q0, w0)));
-  const float d = C.C11 - C.C12;
+  const float d = __fsub_rn(C.C11, C.C12);
   const C2<float> c12qw = pscale(C.C12, qw);
-  s[0] = pfma(d * q0, w0, psub(c12qw, t0));
-  s[1] = pfma(d * q1, w1, psub(c12qw, t1));
-  s[2] = pfma(d * q2, w2, psub(c12qw, t2));
+  s[0] = pfma(__fmul_rn(d, q0), w0, psub(c12qw, t0));
+  s[1] = pfma(__fmul_rn(d, q1), w1, psub(c12qw, t1));
+  s[2] = pfma(__fmul_rn(d, q2), w2, psub(c12qw, t2));
   s[3] = psub(pscale(C.C44, pfma(q1, w2, pscale(q2, w1))), t3);
   s[4] = psub(pscale(C.C44, pfma(q0, w2, pscale(q2, w0))), t4);
   s[5] = psub(pscale(C.C44, pfma(q0, w1, pscale(q1, w0))), t5);
@@ -475,13 +486,23 @@ __device__ __forceinline__ void green_point(C2<T>* e, int kx, int ky, int kz, co
   const int fz = kz < c.nz / 2 ? kz : kz - c.nz;
   if (fx == 0 && fy == 0 && fz == 0) {
     if (c.k0_mode == OKMC_MEAN_STRAIN_ZERO) {
-      const T ds = Cs.C11 - Cs.C12, gs = T(2) * Cs.C44;
-      const C2<T> tr = e[0] + e[1] + e[2];
-      const C2<T> t0 = Cs.C12 * tr + ds * e[0], t1 = Cs.C12 * tr + ds * e[1], t2 = Cs.C12 * tr + ds * e[2];
-      e[0] = T(-1) * t0;
-      e[1] = T(-1) * t1;
-      e[2] = T(-1) * t2;
-      for (int a = 3; a < 6; ++a) e[a] = (-gs) * e[a];
+      if constexpr (sizeof(T) == 4) {  // explicit roundings, as in sigma_of
+        const float ds = __fsub_rn(Cs.C11, Cs.C12), gs = __fmul_rn(2.f, Cs.C44);
+        const C2<float> c12tr = pscale(Cs.C12, padd(padd(e[0], e[1]), e[2]));
+        const C2<float> t0 = pfma(ds, e[0], c12tr), t1 = pfma(ds, e[1], c12tr), t2 = pfma(ds, e[2], c12tr);
+        e[0] = pscale(-1.f, t0);
+        e[1] = pscale(-1.f, t1);
+        e[2] = pscale(-1.f, t2);
+        for (int a = 3; a < 6; ++a) e[a] = pscale(-gs, e[a]);
+      } else {
+        const T ds = Cs.C11 - Cs.C12, gs = T(2) * Cs.C44;
+        const C2<T> tr = e[0] + e[1] + e[2];
+        const C2<T> t0 = Cs.C12 * tr + ds * e[0], t1 = Cs.C12 * tr + ds * e[1], t2 = Cs.C12 * tr + ds * e[2];
+        e[0] = T(-1) * t0;
+        e[1] = T(-1) * t1;
+        e[2] = T(-1) * t2;
+        for (int a = 3; a < 6; ++a) e[a] = (-gs) * e[a];
+      }
     } else {
       for (int a = 0; a < 6; ++a) e[a] = C2<T>{T(0), T(0)};
     }

@@ -9,12 +9,13 @@
 //                    columns to their owner CTA, cluster barrier, column FFTs of
 //                    length ny (in place, skewed exchange), contiguous stores.
 //   pencil_fast    : per tile of 8 consecutive ky at one kx: the 6 x nz x 8 tile
-//                    arrives by 8-byte cp.async (all in flight at once) into a
-//                    padded layout, forward z FFTs in place, Green operator,
-//                    inverse z FFTs, stores.
+//                    arrives by 16-byte cp.async that bypass L1 (all in flight at
+//                    once) into a swizzled layout, forward z FFTs in place, Green
+//                    operator, inverse z FFTs, stores.
 //   plane_inv_fast : inverse of plane_fwd_fast.
 #include <algorithm>
 #include <cooperative_groups.h>
+#include <type_traits>
 
 #include "fft_reg.cuh"
 
@@ -33,6 +34,8 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// hint: bring the 128-byte line holding p into L2 (no effect on results)
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
@@ -144,10 +147,10 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
             continue;
           }
           const C2<float> B = conjg(xg[H - k]);
-          const C2<float> sum = A + B, d1 = untw[k] * (A - B);
+          const C2<float> sum = A + B, d1 = cmul_rn(untw[k], A - B);
           put_col<CS, CPER, S::LDC>(cluster, col, h, k, y, C2<float>{0.5f * (sum.x + d1.y), 0.5f * (sum.y - d1.x)});
           if (2 * k != H) {
-            const C2<float> d2 = untw[H - k] * conjg(B - A);
+            const C2<float> d2 = cmul_rn(untw[H - k], conjg(B - A));
             put_col<CS, CPER, S::LDC>(cluster, col, h, H - k, y,
                                       C2<float>{0.5f * (sum.x + d2.y), 0.5f * (-sum.y - d2.x)});
           }
@@ -188,9 +191,12 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
   }
 }
 
+// pf > 0: first bring into L2 this CTA's columns of plane + pf, the plane whose
+// cluster will most likely take this one's place one wave later (pf = clusters
+// resident at once), so that the next wave's loads hit L2 while this wave transforms.
 template <int H, int NY, int CS>
 __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restrict__ spec, float* __restrict__ sig,
-                                                        PassCfg c) {
+                                                        PassCfg c, int pf) {
   using S = NShape<H, NY>;
   constexpr int CPER = H / CS, ROWS = NY / CS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -204,6 +210,14 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   const int plane = blockIdx.y;
   const int tid = threadIdx.x;
   const size_t P = (size_t)(H + 1) * NY;
+  if (pf > 0 && plane + pf < (int)gridDim.y) {
+    const char* nx = reinterpret_cast<const char*>(spec + (size_t)(plane + pf) * P + (size_t)h * CPER * NY);
+    for (int i = tid; i < CPER * NY * 8 / 128; i += kNT) prefetch_l2(nx + (size_t)i * 128);
+    if (h == 0) {
+      const char* nq = reinterpret_cast<const char*>(spec + (size_t)(plane + pf) * P + (size_t)H * NY);
+      for (int i = tid; i < NY * 8 / 128; i += kNT) prefetch_l2(nq + (size_t)i * 128);
+    }
+  }
   load_tw<H, NY>(twH, twY, untw, c);
   __syncthreads();
   {  // inverse columns along y, scattered to the row owners
@@ -245,7 +259,7 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
         }
         const C2<float> Xk = R[k], Xc = conjg(R[H - k]);
         const C2<float> E = Xk + Xc;
-        const C2<float> O = conjg(untw[k]) * (Xk - Xc);
+        const C2<float> O = cmul_rn(conjg(untw[k]), Xk - Xc);
         return C2<float>{E.x - O.y, E.y + O.x};
       };
       C2<float>* orow = reinterpret_cast<C2<float>*>(sig + ((size_t)plane * NY + h * ROWS + yl) * (2 * H));
@@ -332,7 +346,7 @@ __global__ void __launch_bounds__(NTHR, MINB) k_plane_inv_s(const C2<float>* __r
         }
         const C2<float> Xk = R[k], Xc = conjg(R[H - k]);
         const C2<float> E = Xk + Xc;
-        const C2<float> O = conjg(untw[k]) * (Xk - Xc);
+        const C2<float> O = cmul_rn(conjg(untw[k]), Xk - Xc);
         return C2<float>{E.x - O.y, E.y + O.x};
       };
       C2<float>* orow = reinterpret_cast<C2<float>*>(sig + ((size_t)plane * NY + h * ROWS + yl) * (2 * H));
@@ -345,71 +359,115 @@ __global__ void __launch_bounds__(NTHR, MINB) k_plane_inv_s(const C2<float>* __r
 constexpr int kTW = 8;
 constexpr int kLDT = kTW + 1;  // padded row of a tile: conflict-free strided line access
 
-template <int NZ>
+// Tile layouts.  Padded: rows of kLDT complex, element (row, col) at row * kLDT + col.
+// Swizzled: dense rows of kTW = 8 complex (64 bytes, so every row starts on a 16-byte
+// boundary and arrives by 16-byte copies that bypass L1), with the 16-byte pieces of a
+// row permuted by bits 1-2 of the row: element (row, col) at row * 8 + (col ^ (row & 6)).
+// A half-warp then reads 8 consecutive rows of each of two lines of opposite column
+// parity without bank conflicts.
+template <int NZ, bool SWZ>
 __host__ __device__ constexpr size_t pencil_fast_smem() {
-  return sizeof(C2<float>) * ((size_t)6 * NZ * kLDT + tw2_size<NZ>());
+  return sizeof(C2<float>) * ((size_t)6 * NZ * (SWZ ? kTW : kLDT) + tw2_size<NZ>());
+}
+template <bool SWZ>
+__device__ __forceinline__ int tile_at(int row, int col) {
+  return SWZ ? row * kTW + (col ^ (row & 6)) : row * kLDT + col;
 }
 
+// Exchange slots of a line of the swizzled tile (the skew of XSkew, rows r0 + n1 * R2 + m)
+template <int R2>
+struct XSwz {
+  C2<float>* tile;
+  int r0, col;
+  __device__ __forceinline__ C2<float>& operator()(int n1, int k2) const {  // n1 < R2
+    int m = k2 + n1;
+    if (m >= R2) m -= R2;
+    return tile[tile_at<true>(r0 + n1 * R2 + m, col)];
+  }
+};
 
-// Tile row handled by row counter r in the load, Green and store loops: lanes 0-7 and
-// 8-15 of a half-warp take rows 8 apart, whose 18-word stride puts them 16 banks apart
-// (adjacent rows would wrap onto the same banks).  A bijection on each block of 16
-// rows; NZ is a multiple of 16, so a block never straddles two components.
+// Tile row handled by row counter r in the load, Green and store loops of the padded
+// tile: lanes 0-7 and 8-15 of a half-warp take rows 8 apart, whose 18-word stride puts
+// them 16 banks apart (adjacent rows would wrap onto the same banks).  A bijection on
+// each block of 16 rows; NZ is a multiple of 16, so a block never straddles two
+// components.  The swizzled tile takes adjacent rows (row & 1 selects the bank half).
 __device__ __forceinline__ int tile_row(int r) { return (r & ~15) + ((r & 1) << 3) + ((r >> 1) & 7); }
 
 // in and out may be the same buffer: every CTA reads its whole tile before it writes.
-template <int NZ>
+// SWZ false: padded tile, 8-byte copies (through L1).  SWZ true: swizzled tile, every
+// row by 16-byte copies that bypass L1; with lines of 16 threads the groups of a warp
+// are paired so that each half-warp holds 8 threads of each of two adjacent lines.  The
+// two layouts give the same arithmetic.  (8-byte copies allocate in L1, which two CTAs'
+// shared memory leave small, and so limit the loads in flight on the SM.)
+template <int NZ, bool SWZ>
 __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<float>* out, PassCfg c) {
+  constexpr int PITCH = SWZ ? kTW : kLDT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw);  // [comp][kz][kLDT]
-  C2<float>* twZ = tile + 6 * NZ * kLDT;
+  C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw);  // [comp * NZ + kz][PITCH]
+  C2<float>* twZ = tile + 6 * NZ * PITCH;
   const int tid = threadIdx.x;
   const size_t P = (size_t)(c.H + 1) * c.ny;
   const size_t p0 = (size_t)blockIdx.x * kTW;
   const int kx = (int)(p0 / c.ny), ky0 = (int)(p0 % c.ny);
-  for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
-    const int t = idx & (kTW - 1), row = tile_row(idx >> 3);  // row = comp * NZ + kz
-    cp_async8(tile + row * kLDT + t, in + (size_t)row * P + p0 + t);
+  if constexpr (SWZ) {
+    for (int idx = tid; idx < 6 * NZ * 4; idx += kT) {  // four 16-byte pieces per row
+      const int row = idx >> 2, t = 2 * (idx & 3);
+      cp_async16(tile + tile_at<true>(row, t), in + (size_t)row * P + p0 + t);
+    }
+  } else {
+    for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
+      const int t = idx & (kTW - 1), row = tile_row(idx >> 3);  // row = comp * NZ + kz
+      cp_async8(tile + row * kLDT + t, in + (size_t)row * P + p0 + t);
+    }
   }
   fill_tw2<NZ>(twZ, reinterpret_cast<const C2<float>*>(c.twZ));
   cp_async_wait_all();
   __syncthreads();
   constexpr int NTZ = reg_nt<NZ>(), GL = kT / NTZ, R2Z = RegPlan<NZ>::R2;
-  const int g = tid / NTZ, t = tid % NTZ;
-  for (int l0 = 0; l0 < 6 * kTW; l0 += GL) {
-    const bool act = l0 + g < 6 * kTW;
-    const int l = act ? l0 + g : 0;
-    C2<float>* base = tile + (l / kTW) * NZ * kLDT + (l % kTW);
-    auto ld = [&](int i) { return base[i * kLDT]; };
-    auto st = [&](int k, C2<float> v) { base[k * kLDT] = v; };
-    reg_fft<false, NZ>(ld, XSkew<R2Z>{base, kLDT}, st, twZ, t, act);
+  int g = tid / NTZ, t = tid % NTZ;
+  if (SWZ && NTZ == 16) {  // group 2w + b of warp w: lanes 8b + {0-7, 16-23}
+    g = 2 * (tid >> 5) + ((tid >> 3) & 1);
+    t = (tid & 7) | (((tid >> 4) & 1) << 3);
   }
+  auto lines = [&](auto inv) {
+    constexpr bool INV = decltype(inv)::value;
+    for (int l0 = 0; l0 < 6 * kTW; l0 += GL) {
+      const bool act = l0 + g < 6 * kTW;
+      const int l = act ? l0 + g : 0;
+      const int r0 = (l / kTW) * NZ, col = l % kTW;
+      if constexpr (SWZ) {
+        auto ld = [&](int i) { return tile[tile_at<true>(r0 + i, col)]; };
+        auto st = [&](int k, C2<float> v) { tile[tile_at<true>(r0 + k, col)] = v; };
+        reg_fft<INV, NZ>(ld, XSwz<R2Z>{tile, r0, col}, st, twZ, t, act);
+      } else {
+        C2<float>* base = tile + r0 * kLDT + col;
+        auto ld = [&](int i) { return base[i * kLDT]; };
+        auto st = [&](int k, C2<float> v) { base[k * kLDT] = v; };
+        reg_fft<INV, NZ>(ld, XSkew<R2Z>{base, kLDT}, st, twZ, t, act);
+      }
+    }
+  };
+  auto row_of = [](int r) { return SWZ ? r : tile_row(r); };
+  lines(std::false_type{});
   __syncthreads();
   if (!c.forward_only) {
     const float scale = 1.0f / ((float)c.nx * (float)c.ny * (float)c.nz);
     for (int idx = tid; idx < kTW * NZ; idx += kT) {
-      const int t8 = idx & (kTW - 1), kz = tile_row(idx >> 3);
+      const int t8 = idx & (kTW - 1), kz = row_of(idx >> 3);
       C2<float> e[6];
 #pragma unroll
-      for (int a = 0; a < 6; ++a) e[a] = tile[(a * NZ + kz) * kLDT + t8];
+      for (int a = 0; a < 6; ++a) e[a] = tile[tile_at<SWZ>(a * NZ + kz, t8)];
       green_point<float>(e, kx, ky0 + t8, kz, c, scale);
 #pragma unroll
-      for (int a = 0; a < 6; ++a) tile[(a * NZ + kz) * kLDT + t8] = e[a];
+      for (int a = 0; a < 6; ++a) tile[tile_at<SWZ>(a * NZ + kz, t8)] = e[a];
     }
     __syncthreads();
-    for (int l0 = 0; l0 < 6 * kTW; l0 += GL) {
-      const bool act = l0 + g < 6 * kTW;
-      const int l = act ? l0 + g : 0;
-      C2<float>* base = tile + (l / kTW) * NZ * kLDT + (l % kTW);
-      auto ld = [&](int i) { return base[i * kLDT]; };
-      auto st = [&](int k, C2<float> v) { base[k * kLDT] = v; };
-      reg_fft<true, NZ>(ld, XSkew<R2Z>{base, kLDT}, st, twZ, t, act);
-    }
+    lines(std::true_type{});
     __syncthreads();
   }
   for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
-    const int t8 = idx & (kTW - 1), row = tile_row(idx >> 3);
-    out[(size_t)row * P + p0 + t8] = tile[row * kLDT + t8];
+    const int t8 = idx & (kTW - 1), row = row_of(idx >> 3);
+    out[(size_t)row * P + p0 + t8] = tile[tile_at<SWZ>(row, t8)];
   }
 }
 
@@ -442,13 +500,52 @@ cudaError_t launch_k(K k, dim3 grid, size_t smem, int cluster, cudaStream_t st, 
 }
 
 // smallest cluster that lets two CTAs share an SM
+// clusters of cs CTAs (kT threads, smem bytes each) of kernel k resident at once on the
+// device; 0 if the query fails
+template <class K>
+int resident_clusters(K k, int cs, size_t smem) {
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(cs, 1024);
+  cfg.blockDim = dim3(kT);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  cudaError_t e;
+  if (cs > 1) {
+    e = cudaOccupancyMaxActiveClusters(&n, k, &cfg);
+  } else {
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kT, smem);
+    n *= sms;
+  }
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    n = 0;
+  }
+  return n;
+}
+
 template <int H, int NY, int CS>
-cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st) {
+cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st, bool prefetch = false) {
   static_assert(H % CS == 0 && NY % CS == 0, "cluster must split rows and columns evenly");
   const dim3 grid(CS, c.ncomp * c.nz);
-  if (inverse)
+  if (inverse) {
+    static const int wave = resident_clusters(k_plane_inv_n<H, NY, CS>, CS, ninv_smem<H, NY>(CS));
     return launch_k(k_plane_inv_n<H, NY, CS>, grid, ninv_smem<H, NY>(CS), CS, st, static_cast<const C2<float>*>(in),
-                    static_cast<float*>(out), c);
+                    static_cast<float*>(out), c, prefetch ? wave : 0);
+  }
   return launch_k(k_plane_fwd_n<H, NY, CS>, grid, nfwd_smem<H, NY>(CS), CS, st, static_cast<const int32_t*>(in),
                   static_cast<C2<float>*>(out), c);
 }
@@ -485,10 +582,11 @@ cudaError_t plane_inv_staged(const void* in, void* out, const PassCfg& c, cudaSt
 
 // Inverse-pass variants: 0 register-loaded columns (cluster of ncs CTAs, 256 threads);
 // staged: 1 with 256 threads and two CTAs per SM, 2 with 128 threads and three CTAs
-// per SM, 3 with 256 threads and three CTAs per SM (registers capped at 85).
+// per SM, 3 with 256 threads and three CTAs per SM (registers capped at 85); 4 as 0,
+// with the next wave's columns prefetched into L2.
 template <int H, int NY>
 int plane_inv_variants() {
-  return 1 | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0);
+  return 1 | 16 | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0);
 }
 
 template <int H, int NY>
@@ -496,22 +594,24 @@ cudaError_t plane_pair(bool inverse, int variant, const void* in, void* out, con
   if (inverse && variant == 1) return plane_inv_staged<H, NY, stage_cs<H, NY>(kTwoPerSM), 256, 2>(in, out, c, st);
   if (inverse && variant == 2) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 128, 3>(in, out, c, st);
   if (inverse && variant == 3) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 256, 3>(in, out, c, st);
-  return plane_pair_n<H, NY, ncs<H, NY>()>(inverse, in, out, c, st);
+  return plane_pair_n<H, NY, ncs<H, NY>()>(inverse, in, out, c, st, inverse && variant == 4);
 }
 
 template <int NZ>
 cudaError_t pencil_one(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st) {
-  (void)variant;
   const size_t P = (size_t)(c.H + 1) * c.ny;
-  return launch_k(k_pencil_fast<NZ>, dim3((unsigned)(P / kTW)), pencil_fast_smem<NZ>(), 1, st, in, out, c);
+  const dim3 grid((unsigned)(P / kTW));
+  if (variant == 1)
+    return launch_k(k_pencil_fast<NZ, false>, grid, pencil_fast_smem<NZ, false>(), 1, st, in, out, c);
+  return launch_k(k_pencil_fast<NZ, true>, grid, pencil_fast_smem<NZ, true>(), 1, st, in, out, c);
 }
 
-// Pencil variants: only 0 (one tile per CTA, two CTAs per SM).  A persistent,
-// double-buffered form (one CTA of 384 threads per SM) measured 1.3-1.6x slower: the
-// transform phase needs the warps more than the loads need hiding.
+// Pencil variants (one tile per CTA, two CTAs per SM): 0 swizzled tile, 1 padded tile.
+// A persistent, double-buffered form (one CTA of 384 threads per SM) measured
+// 1.3-1.6x slower: the transform phase needs the warps more than the loads need hiding.
 template <int NZ>
 int pencil_variants() {
-  return 1;
+  return 3;
 }
 }  // namespace
 
