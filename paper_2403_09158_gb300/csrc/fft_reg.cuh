@@ -418,19 +418,33 @@ __device__ __forceinline__ void fill_tw2(C2<float>* tw2, const C2<float>* __rest
   }
 }
 
-template <bool INV, int L, class Ld, class Xch, class St>
-__device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const C2<float>* __restrict__ tw2, int t,
-                                        bool active) {
-  constexpr int R1 = RegPlan<L>::R1, R2 = RegPlan<L>::R2, NT = reg_nt<L>();
-  constexpr int A = R1 / NT, B = (R2 + NT - 1) / NT;
-  static_assert(R1 % NT == 0, "step 1 needs whole DFTs per thread");
+// The inputs one thread of a line group holds: reg_load fills them, reg_fft_loaded
+// transforms them (reg_fft does both; split, a caller can issue the loads of its first
+// line before other setup work and its barrier).
+template <int L>
+struct RegLine {
+  static constexpr int R1 = RegPlan<L>::R1, R2 = RegPlan<L>::R2, NT = reg_nt<L>();
+  static constexpr int A = R1 / NT;
   C2<float> v[A][R2];
+};
+template <int L, class Ld>
+__device__ __forceinline__ void reg_load(RegLine<L>& in, const Ld& ld, int t, bool active) {
+  constexpr int R1 = RegPlan<L>::R1, R2 = RegPlan<L>::R2, NT = reg_nt<L>(), A = R1 / NT;
   if (active) {
 #pragma unroll
     for (int a = 0; a < A; ++a)
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) v[a][n2] = ld(t + NT * a + R1 * n2);
+      for (int n2 = 0; n2 < R2; ++n2) in.v[a][n2] = ld(t + NT * a + R1 * n2);
   }
+}
+
+template <bool INV, int L, class Xch, class St>
+__device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, const St& st, const C2<float>* __restrict__ tw2,
+                                               int t, bool active) {
+  constexpr int R1 = RegPlan<L>::R1, R2 = RegPlan<L>::R2, NT = reg_nt<L>();
+  constexpr int A = R1 / NT, B = (R2 + NT - 1) / NT;
+  static_assert(R1 % NT == 0, "step 1 needs whole DFTs per thread");
+  auto& v = in.v;
   __syncwarp();
   if (active) {
 #pragma unroll
@@ -467,6 +481,14 @@ __device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st
       }
   }
   __syncwarp();
+}
+
+template <bool INV, int L, class Ld, class Xch, class St>
+__device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const C2<float>* __restrict__ tw2, int t,
+                                        bool active) {
+  RegLine<L> in;
+  reg_load<L>(in, ld, t, active);
+  reg_fft_loaded<INV, L>(in, x, st, tw2, t, active);
 }
 
 }  // namespace okmc

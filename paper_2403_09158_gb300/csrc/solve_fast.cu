@@ -34,6 +34,12 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// Split cluster barrier.  Every thread arrives once at its CTA's start and waits before
+// its first store into another CTA's shared memory, which must be running by then (the
+// CTAs of a cluster are launched together, so the wait ends at once); the closing
+// cluster.sync() is the barrier's next phase.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
 // hint: bring the 128-byte line holding p into L2 (no effect on results)
 __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 __device__ __forceinline__ void cp_async_wait_all() {
@@ -49,6 +55,47 @@ __device__ __forceinline__ void load_tw(C2<float>* twH, C2<float>* twY, C2<float
   const C2<float>* gU = reinterpret_cast<const C2<float>*>(c.untw);
   for (int i = threadIdx.x; i <= H; i += blockDim.x) untw[i] = gU[i];
 }
+
+// The twiddle tables of a plane pass staged through registers (at most a few values per
+// thread): load() first, so that these L2 hits are not queued behind the pass's first
+// DRAM loads, store() once those are in flight.
+template <int H, int NY, int NTHR>
+struct TwStage {
+  static constexpr int NH = (tw2_size<H>() + NTHR - 1) / NTHR, NYs = (tw2_size<NY>() + NTHR - 1) / NTHR;
+  static constexpr int NU = (H + 1 + NTHR - 1) / NTHR;
+  C2<float> h[NH], y[NYs], u[NU];
+  template <int L>
+  __device__ __forceinline__ static C2<float> tw2_entry(const C2<float>* tw, int i) {
+    constexpr int R2 = RegPlan<L>::R2;
+    const int n1 = i / (R2 + 1), k2 = i % (R2 + 1);
+    return k2 < R2 ? tw[n1 * k2] : C2<float>{1.f, 0.f};
+  }
+  __device__ __forceinline__ void load(const PassCfg& c, int tid) {
+    const C2<float>* gH = reinterpret_cast<const C2<float>*>(c.twH);
+    const C2<float>* gY = reinterpret_cast<const C2<float>*>(c.twY);
+    const C2<float>* gU = reinterpret_cast<const C2<float>*>(c.untw);
+#pragma unroll
+    for (int j = 0; j < NH; ++j)
+      if (tid + NTHR * j < tw2_size<H>()) h[j] = tw2_entry<H>(gH, tid + NTHR * j);
+#pragma unroll
+    for (int j = 0; j < NYs; ++j)
+      if (tid + NTHR * j < tw2_size<NY>()) y[j] = tw2_entry<NY>(gY, tid + NTHR * j);
+#pragma unroll
+    for (int j = 0; j < NU; ++j)
+      if (tid + NTHR * j <= H) u[j] = gU[tid + NTHR * j];
+  }
+  __device__ __forceinline__ void store(C2<float>* twH, C2<float>* twY, C2<float>* untw, int tid) const {
+#pragma unroll
+    for (int j = 0; j < NH; ++j)
+      if (tid + NTHR * j < tw2_size<H>()) twH[tid + NTHR * j] = h[j];
+#pragma unroll
+    for (int j = 0; j < NYs; ++j)
+      if (tid + NTHR * j < tw2_size<NY>()) twY[tid + NTHR * j] = y[j];
+#pragma unroll
+    for (int j = 0; j < NU; ++j)
+      if (tid + NTHR * j <= H) untw[tid + NTHR * j] = u[j];
+  }
+};
 
 // Row of a plane handled by row group g in the row phases of the inverse pass.  A row
 // buffer stride of H + 1 complex puts adjacent rows 2 banks apart, so two groups of
@@ -116,24 +163,36 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
   // a plane whose eigenstrain has not changed keeps its transform from the last pass
   // (every CTA of the cluster reads the same flag, so the whole cluster leaves)
   if (c.dirty && c.dirty[plane] == 0) return;
+  if (CS > 1) cluster_arrive();
   const int tid = threadIdx.x;
   const size_t P = (size_t)(H + 1) * NY;
   const float q = (float)c.q;
-  load_tw<H, NY>(twH, twY, untw, c);
+  const int g = tid / S::NTH, t = tid % S::NTH;
+  // loads of row group r0 (the first group's loads fly while the twiddles are filled)
+  RegLine<H> line;
+  auto load_rows = [&](int r0) {
+    const bool act = r0 + g < ROWS;
+    const int y = h * ROWS + (act ? r0 + g : 0);
+    const int2* row = reinterpret_cast<const int2*>(eps + ((size_t)plane * NY + y) * (2 * H));
+    reg_load<H>(line, [&](int i) {
+      const int2 v = __ldg(row + i);
+      return C2<float>{__int2float_rn(v.x) * q, __int2float_rn(v.y) * q};
+    }, t, act);
+  };
+  TwStage<H, NY, kNT> tws;
+  tws.load(c, tid);
+  load_rows(0);
+  tws.store(twH, twY, untw, tid);
   __syncthreads();
   {  // rows along x
-    const int g = tid / S::NTH, t = tid % S::NTH;
     C2<float>* xg = xb + g * S::XS;
     for (int r0 = 0; r0 < ROWS; r0 += S::GR) {
       const bool act = r0 + g < ROWS;
       const int y = h * ROWS + (act ? r0 + g : 0);
-      const int2* row = reinterpret_cast<const int2*>(eps + ((size_t)plane * NY + y) * (2 * H));
-      auto ld = [&](int i) {
-        const int2 v = __ldg(row + i);
-        return C2<float>{__int2float_rn(v.x) * q, __int2float_rn(v.y) * q};
-      };
+      if (r0 > 0) load_rows(r0);
       auto st = [&](int k, C2<float> v) { xg[k] = v; };
-      reg_fft<false, H>(ld, XPad<S::R2H>{xg}, st, twH, t, act);
+      reg_fft_loaded<false, H>(line, XPad<S::R2H>{xg}, st, twH, t, act);
+      if (CS > 1 && r0 == 0) cluster_wait();
       if (act) {
         // X[k] = (A + B)/2 - (i/2) w^k (A - B) and X[H-k] = conj((A + B)/2) - (i/2) w^(H-k) conj(B - A)
         // from the same A = Z[k], B = conj Z[H-k]; k = 0 packs (X[0], X[nx/2])
@@ -210,6 +269,7 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   const int plane = blockIdx.y;
   const int tid = threadIdx.x;
   const size_t P = (size_t)(H + 1) * NY;
+  if (CS > 1) cluster_arrive();
   if (pf > 0 && plane + pf < (int)gridDim.y) {
     const char* nx = reinterpret_cast<const char*>(spec + (size_t)(plane + pf) * P + (size_t)h * CPER * NY);
     for (int i = tid; i < CPER * NY * 8 / 128; i += kNT) prefetch_l2(nx + (size_t)i * 128);
@@ -218,29 +278,40 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
       for (int i = tid; i < NY * 8 / 128; i += kNT) prefetch_l2(nq + (size_t)i * 128);
     }
   }
-  load_tw<H, NY>(twH, twY, untw, c);
-  __syncthreads();
   {  // inverse columns along y, scattered to the row owners
     const int g = tid / S::NTY, t = tid % S::NTY;
-    C2<float>* xg = xb + g * S::XSY;
-    for (int c0 = 0; c0 < CPER; c0 += S::GC) {
+    // loads of column group c0 (the first group's loads fly while the twiddles are filled)
+    RegLine<NY> line;
+    auto load_cols = [&](int c0) {
       const bool act = c0 + g < CPER;
       const int kx = h * CPER + (act ? c0 + g : 0);
       const C2<float>* in = spec + (size_t)plane * P + (size_t)kx * NY;
       const C2<float>* nyq = spec + (size_t)plane * P + (size_t)H * NY;
       const bool packed = (kx == 0);
-      auto ld = [&](int i) {
+      reg_load<NY>(line, [&](int i) {
         const C2<float> A = in[i];
         if (!packed) return A;
         const C2<float> B = nyq[i];
         return C2<float>{A.x - B.y, A.y + B.x};  // A + i B
-      };
+      }, t, act);
+    };
+    TwStage<H, NY, kNT> tws;
+    tws.load(c, tid);
+    load_cols(0);
+    tws.store(twH, twY, untw, tid);
+    __syncthreads();
+    C2<float>* xg = xb + g * S::XSY;
+    for (int c0 = 0; c0 < CPER; c0 += S::GC) {
+      const bool act = c0 + g < CPER;
+      const int kx = h * CPER + (act ? c0 + g : 0);
+      if (c0 > 0) load_cols(c0);
       auto st = [&](int k, C2<float> v) {
         const int owner = k / ROWS;
         C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
         base[(k % ROWS) * S::LDR + kx] = v;
       };
-      reg_fft<true, NY>(ld, XPad<S::R2Y>{xg}, st, twY, t, act);
+      if (CS > 1 && c0 == 0) cluster_wait();
+      reg_fft_loaded<true, NY>(line, XPad<S::R2Y>{xg}, st, twY, t, act);
     }
   }
   if (CS > 1) cluster.sync();
@@ -296,6 +367,7 @@ __global__ void __launch_bounds__(NTHR, MINB) k_plane_inv_s(const C2<float>* __r
   const int h = CS > 1 ? (int)cluster.block_rank() : 0;
   const int plane = blockIdx.y;
   const int tid = threadIdx.x;
+  if (CS > 1) cluster_arrive();
   const size_t P = (size_t)(H + 1) * NY;
   {
     const C2<float>* src = spec + (size_t)plane * P + (size_t)h * CPER * NY;
@@ -308,6 +380,7 @@ __global__ void __launch_bounds__(NTHR, MINB) k_plane_inv_s(const C2<float>* __r
   load_tw<H, NY>(twH, twY, untw, c);
   cp_async_wait_all();
   __syncthreads();
+  if (CS > 1) cluster_wait();
   {  // inverse columns along y, in place, scattered to the row owners
     const int g = tid / NTY, t = tid % NTY;
     for (int c0 = 0; c0 < CPER; c0 += GC) {
