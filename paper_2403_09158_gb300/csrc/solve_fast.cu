@@ -125,6 +125,10 @@ struct NShape {
   static constexpr int XS = RegPlan<H>::R1 * (R2H + 1);       // row exchange slots
   static constexpr int XSY = RegPlan<NY>::R1 * (R2Y + 1);     // column exchange slots
   static constexpr int XB = GR * XS > GC * XSY ? GR * XS : GC * XSY;
+  // inverse pass: column groups XSY + 1 apart (odd, so that a row of the staged column
+  // outputs, one element per group, is read without bank conflicts)
+  static constexpr int XSYP = XSY + 1;
+  static constexpr int XBI = GR * XS > GC * XSYP ? GR * XS : GC * XSYP;
   static constexpr int LDC = NY + 1, LDR = H + 1;
 };
 template <int H, int NY>
@@ -135,7 +139,7 @@ __host__ __device__ constexpr size_t nfwd_smem(int cs) {
 template <int H, int NY>
 __host__ __device__ constexpr size_t ninv_smem(int cs) {
   using S = NShape<H, NY>;
-  return sizeof(C2<float>) * ((size_t)(NY / cs) * S::LDR + (size_t)S::XB + tw2_size<H>() + tw2_size<NY>() + H + 1);
+  return sizeof(C2<float>) * ((size_t)(NY / cs) * S::LDR + (size_t)S::XBI + tw2_size<H>() + tw2_size<NY>() + H + 1);
 }
 
 // store v at column k, row y of the column buffer of the CTA that owns column k
@@ -253,7 +257,12 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
 // pf > 0: first bring into L2 this CTA's columns of plane + pf, the plane whose
 // cluster will most likely take this one's place one wave later (pf = clusters
 // resident at once), so that the next wave's loads hit L2 while this wave transforms.
-template <int H, int NY, int CS>
+// WIDE: each column group's transform output is staged in the group's own exchange
+// slots, and after a barrier the CTA copies it out by rows: a warp then writes 16 or
+// more consecutive kx of one row of the owner's buffer (128 contiguous bytes or more)
+// instead of two kx of 16 rows.  Remote stores into another CTA's shared memory cost
+// by the write pattern: the wide copy-out makes the scatter far cheaper.
+template <int H, int NY, int CS, bool WIDE>
 __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restrict__ spec, float* __restrict__ sig,
                                                         PassCfg c, int pf) {
   using S = NShape<H, NY>;
@@ -261,7 +270,7 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<float>* rowb = reinterpret_cast<C2<float>*>(smem_raw);  // [ROWS][LDR]
   C2<float>* xb = rowb + ROWS * S::LDR;
-  C2<float>* twH = xb + S::XB;
+  C2<float>* twH = xb + S::XBI;
   C2<float>* twY = twH + tw2_size<H>();
   C2<float>* untw = twY + tw2_size<NY>();
   cg::cluster_group cluster = cg::this_cluster();
@@ -300,18 +309,36 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
     load_cols(0);
     tws.store(twH, twY, untw, tid);
     __syncthreads();
-    C2<float>* xg = xb + g * S::XSY;
+    C2<float>* xg = xb + g * (WIDE ? S::XSYP : S::XSY);
     for (int c0 = 0; c0 < CPER; c0 += S::GC) {
       const bool act = c0 + g < CPER;
       const int kx = h * CPER + (act ? c0 + g : 0);
       if (c0 > 0) load_cols(c0);
-      auto st = [&](int k, C2<float> v) {
-        const int owner = k / ROWS;
-        C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
-        base[(k % ROWS) * S::LDR + kx] = v;
-      };
-      if (CS > 1 && c0 == 0) cluster_wait();
-      reg_fft_loaded<true, NY>(line, XPad<S::R2Y>{xg}, st, twY, t, act);
+      if constexpr (WIDE) {
+        auto st = [&](int k, C2<float> v) { xg[k] = v; };
+        reg_fft_loaded<true, NY>(line, XPad<S::R2Y>{xg}, st, twY, t, act);
+        __syncthreads();
+        if (CS > 1 && c0 == 0) cluster_wait();
+        constexpr int GC = S::GC;
+        const int ncol = CPER - c0 < GC ? CPER - c0 : GC;
+        for (int e = tid; e < NY * GC; e += kNT) {  // element (row k, column j)
+          const int j = e % GC, k = e / GC;
+          if (j < ncol) {
+            const int owner = k / ROWS;
+            C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
+            base[(k % ROWS) * S::LDR + h * CPER + c0 + j] = xb[j * S::XSYP + k];
+          }
+        }
+        __syncthreads();
+      } else {
+        auto st = [&](int k, C2<float> v) {
+          const int owner = k / ROWS;
+          C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
+          base[(k % ROWS) * S::LDR + kx] = v;
+        };
+        if (CS > 1 && c0 == 0) cluster_wait();
+        reg_fft_loaded<true, NY>(line, XPad<S::R2Y>{xg}, st, twY, t, act);
+      }
     }
   }
   if (CS > 1) cluster.sync();
@@ -611,13 +638,17 @@ int resident_clusters(K k, int cs, size_t smem) {
 }
 
 template <int H, int NY, int CS>
-cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st, bool prefetch = false) {
+cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st, bool prefetch = false,
+                         bool wide = false) {
   static_assert(H % CS == 0 && NY % CS == 0, "cluster must split rows and columns evenly");
   const dim3 grid(CS, c.ncomp * c.nz);
   if (inverse) {
-    static const int wave = resident_clusters(k_plane_inv_n<H, NY, CS>, CS, ninv_smem<H, NY>(CS));
-    return launch_k(k_plane_inv_n<H, NY, CS>, grid, ninv_smem<H, NY>(CS), CS, st, static_cast<const C2<float>*>(in),
-                    static_cast<float*>(out), c, prefetch ? wave : 0);
+    static const int wave = resident_clusters(k_plane_inv_n<H, NY, CS, false>, CS, ninv_smem<H, NY>(CS));
+    if (wide)
+      return launch_k(k_plane_inv_n<H, NY, CS, true>, grid, ninv_smem<H, NY>(CS), CS, st,
+                      static_cast<const C2<float>*>(in), static_cast<float*>(out), c, prefetch ? wave : 0);
+    return launch_k(k_plane_inv_n<H, NY, CS, false>, grid, ninv_smem<H, NY>(CS), CS, st,
+                    static_cast<const C2<float>*>(in), static_cast<float*>(out), c, prefetch ? wave : 0);
   }
   return launch_k(k_plane_fwd_n<H, NY, CS>, grid, nfwd_smem<H, NY>(CS), CS, st, static_cast<const int32_t*>(in),
                   static_cast<C2<float>*>(out), c);
@@ -656,10 +687,11 @@ cudaError_t plane_inv_staged(const void* in, void* out, const PassCfg& c, cudaSt
 // Inverse-pass variants: 0 register-loaded columns (cluster of ncs CTAs, 256 threads);
 // staged: 1 with 256 threads and two CTAs per SM, 2 with 128 threads and three CTAs
 // per SM, 3 with 256 threads and three CTAs per SM (registers capped at 85); 4 as 0,
-// with the next wave's columns prefetched into L2.
+// with the next wave's columns prefetched into L2; 5 and 6 as 0 and 4 with the wide
+// copy-out of the column outputs.
 template <int H, int NY>
 int plane_inv_variants() {
-  return 1 | 16 | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0);
+  return 1 | 16 | 32 | 64 | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0);
 }
 
 template <int H, int NY>
@@ -667,7 +699,8 @@ cudaError_t plane_pair(bool inverse, int variant, const void* in, void* out, con
   if (inverse && variant == 1) return plane_inv_staged<H, NY, stage_cs<H, NY>(kTwoPerSM), 256, 2>(in, out, c, st);
   if (inverse && variant == 2) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 128, 3>(in, out, c, st);
   if (inverse && variant == 3) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 256, 3>(in, out, c, st);
-  return plane_pair_n<H, NY, ncs<H, NY>()>(inverse, in, out, c, st, inverse && variant == 4);
+  return plane_pair_n<H, NY, ncs<H, NY>()>(inverse, in, out, c, st, inverse && (variant == 4 || variant == 6),
+                                          inverse && (variant == 5 || variant == 6));
 }
 
 template <int NZ>
