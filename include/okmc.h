@@ -250,7 +250,8 @@ int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
  * variant that exists for the grid's shape (three interleaved rounds, best of each)
  * and keeps variant 0 unless another is more than 2% faster; the choice is cached per
  * grid shape for the life of the process (the environment variable OKMC_TUNE=0 keeps
- * variant 0 without timing, e.g. under a profiler); the variants differ in
+ * variant 0 without timing, e.g. under a profiler, and OKMC_VARIANTS=a,b,c pins
+ * variants a, b and c of the three passes, each where it exists); the variants differ in
  * cluster size, threads per CTA and how data reaches shared memory, not in
  * arithmetic, so results are bitwise the same under every variant.
  * okmc_get_variants: current[p] = variant in use, available[p] = bit mask of the

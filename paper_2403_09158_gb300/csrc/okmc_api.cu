@@ -7,6 +7,7 @@
 #include <cstdlib>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -281,7 +282,7 @@ int solve(okmc_grid* g) {
     // full pass, since a clean plane's input is unchanged); the Green operator's
     // output goes to spec2
     c.dirty = g->d_dirty;
-    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, 0, g->eps, g->spec, c, g->st); }));
+    OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, g->variant[0], g->eps, g->spec, c, g->st); }));
     c.dirty = nullptr;
     OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st); }));
     OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_fast(true, g->variant[2], g->spec2, g->sig, c, g->st); }));
@@ -464,7 +465,7 @@ int build_self_terms(okmc_grid* g) {
     }
     OKMC_TRY(run(g, "self_fields", [&] { return launch_wfields<Q>((Q*)g->eps, n, g->d_ptr, g->d_off, g->d_cnt, b, g->st); }));
     if (g->fast) {
-      OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, 0, g->eps, g->spec, c, g->st); }));
+      OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, g->variant[0], g->eps, g->spec, c, g->st); }));
       OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec, c, g->st); }));
     } else {
       OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)g->spec, c, g->st); }));
@@ -616,10 +617,19 @@ int capture_step(okmc_grid* g, int mode, double T, cudaGraphExec_t* out) {
 // the same arithmetic, so the choice changes the time and not the result.  Choices
 // are cached per grid shape for the life of the process.
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune_cache;  // shape -> (pencil, inverse plane)
+std::map<std::tuple<int, int, int>, std::array<int, 3>> g_tune_cache;  // shape -> variant of each pass
 
 int autotune(okmc_grid* g) {
   if (!g->fast) return OKMC_OK;
+  // OKMC_VARIANTS=a,b,c pins the variant of each pass (where it exists) without timing,
+  // e.g. under a profiler; OKMC_TUNE=0 keeps variant 0 of every pass
+  if (const char* pin = std::getenv("OKMC_VARIANTS")) {
+    int v[3] = {0, 0, 0};
+    if (std::sscanf(pin, "%d,%d,%d", &v[0], &v[1], &v[2]) == 3)
+      for (int p = 0; p < 3; ++p)
+        if (v[p] >= 0 && v[p] < 31 && ((g->avail[p] >> v[p]) & 1)) g->variant[p] = v[p];
+    return OKMC_OK;
+  }
   const char* env = std::getenv("OKMC_TUNE");
   if (env && env[0] == '0') return OKMC_OK;
   const auto key = std::make_tuple(g->n[0], g->n[1], g->n[2]);
@@ -627,8 +637,7 @@ int autotune(okmc_grid* g) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      g->variant[1] = it->second.first;
-      g->variant[2] = it->second.second;
+      for (int p = 0; p < 3; ++p) g->variant[p] = it->second[p];
       return OKMC_OK;
     }
   }
@@ -646,8 +655,13 @@ int autotune(okmc_grid* g) {
   }
   // three interleaved rounds, the best of each variant, and variant 0 kept unless
   // another is more than 2% faster (robust against a noisy or shared device)
-  for (int pass = 1; pass <= 2 && e == cudaSuccess; ++pass) {
+  // (the forward pass runs on every plane here, and on the zero field the grid starts
+  // with, so the plane transforms it leaves in spec stay those of the field); a pass
+  // with a single variant is not timed
+  for (int pass = 0; pass <= 2 && e == cudaSuccess; ++pass) {
+    if (g->avail[pass] == 1) continue;
     auto launch = [&](int v) {
+      if (pass == 0) return launch_plane_fast(false, v, g->eps, g->spec, c, g->st);
       return pass == 1 ? launch_pencil_fast(v, (const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st)
                        : launch_plane_fast(true, v, g->spec2, g->sig, c, g->st);
     };
@@ -675,7 +689,7 @@ int autotune(okmc_grid* g) {
   cudaEventDestroy(b);
   if (e != cudaSuccess) return cuda_fail(g, e, "tune");
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune_cache[key] = std::make_pair(g->variant[1], g->variant[2]);
+  g_tune_cache[key] = {g->variant[0], g->variant[1], g->variant[2]};
   return OKMC_OK;
 }
 

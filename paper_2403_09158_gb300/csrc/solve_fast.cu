@@ -699,8 +699,8 @@ cudaError_t plane_pair(bool inverse, int variant, const void* in, void* out, con
   if (inverse && variant == 1) return plane_inv_staged<H, NY, stage_cs<H, NY>(kTwoPerSM), 256, 2>(in, out, c, st);
   if (inverse && variant == 2) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 128, 3>(in, out, c, st);
   if (inverse && variant == 3) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 256, 3>(in, out, c, st);
-  return plane_pair_n<H, NY, ncs<H, NY>()>(inverse, in, out, c, st, inverse && (variant == 4 || variant == 6),
-                                          inverse && (variant == 5 || variant == 6));
+  if (!inverse) return plane_pair_n<H, NY, ncs<H, NY>()>(false, in, out, c, st);
+  return plane_pair_n<H, NY, ncs<H, NY>()>(true, in, out, c, st, variant == 4 || variant == 6, variant == 5 || variant == 6);
 }
 
 template <int NZ>

@@ -374,7 +374,8 @@ def test_incremental_plane_transforms_equal_fresh_solve(mode):
 
 
 # ------------------------------------------------------------------ launch variants
-@pytest.mark.parametrize('n', [(48, 48, 48), (96, 96, 64), (128, 128, 32), (160, 160, 32), (320, 320, 32)])
+@pytest.mark.parametrize('n', [(48, 48, 48), (96, 96, 64), (128, 128, 32), (160, 160, 32), (192, 192, 32),
+                               (256, 256, 32), (320, 320, 32)])
 def test_pass_variants_bitwise_equal(n):
     """Every launch variant of the FFT passes gives the same stress, bit for bit."""
     w = scaled_population(n, 20, seed=n[0], r111=(0.4, 1.0), r100=(0.4, 1.0))
@@ -387,6 +388,8 @@ def test_pass_variants_bitwise_equal(n):
             if not (avail[p] >> v) & 1:
                 continue
             g.set_variant(p, v)
+            if p == 0:
+                g.set_defects(w.defects)  # every plane dirty, so the forward pass runs in full
             s = g.solve_stress()
             if ref is None:
                 ref = s
@@ -394,6 +397,20 @@ def test_pass_variants_bitwise_equal(n):
         g.set_variant(p, cur[p])
     with pytest.raises(ok.OkmcError):
         g.set_variant(2, 30)
+    g.close()
+
+
+def test_variants_pinned_by_environment(monkeypatch):
+    """OKMC_VARIANTS=a,b,c pins each pass's variant where it exists (no timing)."""
+    w = scaled_population((64, 64, 64), 8, seed=3, r111=(0.4, 1.0), r100=(0.4, 1.0))
+    monkeypatch.setenv('OKMC_VARIANTS', '1,1,4')
+    g = make_grid(w)
+    cur, avail = g.variants()
+    assert cur == [v if (avail[p] >> v) & 1 else 0 for p, v in enumerate((1, 1, 4))]
+    g.close()
+    monkeypatch.setenv('OKMC_VARIANTS', '0,0,30')  # variant 30 exists for no pass
+    g = make_grid(w)
+    assert g.variants()[0] == [0, 0, 0]
     g.close()
 
 
