@@ -546,31 +546,36 @@ def solve_only(n):
     return 0
 
 
-KERNEL_SOURCES = ('defects.cu', 'fft_reg.cuh', 'okmc_internal.cuh', 'solve.cu', 'solve_fast.cu')
+# the source files that hold each timed kernel's device code
+KERNEL_SOURCES = {
+    'plane_fwd': ('solve_fast.cu', 'fft_reg.cuh', 'okmc_internal.cuh'),
+    'pencil_green': ('solve_fast.cu', 'fft_reg.cuh', 'okmc_internal.cuh'),
+    'plane_inv': ('solve_fast.cu', 'fft_reg.cuh', 'okmc_internal.cuh'),
+    'energies': ('defects.cu', 'okmc_internal.cuh'),
+}
 
 
-def kernel_sources_hash():
-    """Hash of the files that hold device code (host-only files such as the C ABI
-    layer do not change a kernel's DRAM traffic)."""
+def kernel_sources_hash(kernel):
+    """Hash of the files that hold `kernel`'s device code (a change elsewhere, e.g. in
+    the C ABI layer or another kernel's file, does not change its DRAM traffic)."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, 'paper_2403_09158_gb300', 'csrc')
-    for f in KERNEL_SOURCES:
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(d, f), 'rb').read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(kernel):
     """DRAM bytes per launch of `kernel` from profiles/dram_traffic.json, if that capture
-    was taken on the current kernel sources (else None)."""
+    was taken on the kernel's current sources (else None)."""
     p = os.path.join(ROOT, 'profiles', 'dram_traffic.json')
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
-    d = json.load(open(p))
-    if d.get('sources_hash') != kernel_sources_hash():
+    k = json.load(open(p)).get('kernels', {}).get(kernel)
+    if k is None or k.get('sources_hash') != kernel_sources_hash(kernel):
         return None
-    k = d.get('kernels', {}).get(kernel)
-    return None if k is None else k.get('dram_bytes_per_launch')
+    return k.get('dram_bytes_per_launch')
 
 
 def run_reference(args, ws, rank):

@@ -657,6 +657,10 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict
   const int c = r.pos[0] & 1, cp = 1 - c;
   T ew[6];
   for (int a = 0; a < 6; ++a) ew[a] = T(a < 3 ? g.e6[a] : 2.0 * g.e6[a]);
+  // components with zero weight (a <100> loop needs sigma_xx only, a dilatation the
+  // trace) are not gathered; adding their zero products would not change any sum
+  bool use[6];
+  for (int a = 0; a < 6; ++a) use[a] = ew[a] != T(0);
   const int bx = floor_div2(r.pos[0]), by = floor_div2(r.pos[1]), bz = floor_div2(r.pos[2]);
   EAcc<T> acc[9];
   for (int j = 0; j < 9; ++j) acc[j].zero();
@@ -678,7 +682,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict
           w[u] = T(cnt[k]);
           const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
 #pragma unroll
-          for (int a = 0; a < 6; ++a) sv[u][a] = __ldg(sig + a * N + v);
+          for (int a = 0; a < 6; ++a) sv[u][a] = use[a] ? __ldg(sig + a * N + v) : T(0);
         }
       }
 #pragma unroll
@@ -707,7 +711,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict
           cc[u] = dl.cnt[k];
           const size_t v = ((size_t)wrap(bz + uz, n.z) * n.y + wrap(by + uy, n.y)) * n.x + wrap(bx + ux, n.x);
 #pragma unroll
-          for (int a = 0; a < 6; ++a) sv[u][a] = __ldg(sig + a * N + v);
+          for (int a = 0; a < 6; ++a) sv[u][a] = use[a] ? __ldg(sig + a * N + v) : T(0);
         }
       }
 #pragma unroll
@@ -735,7 +739,7 @@ __global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict
         const size_t v = ((size_t)((j & 1) ? z1 : z0) * n.y + ((j & 2) ? y1 : y0)) * n.x + ((j & 4) ? x1 : x0);
         T dot = T(0);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) dot += ew[a] * __ldg(sig + a * N + v);
+        for (int a = 0; a < 6; ++a) dot += ew[a] * (use[a] ? __ldg(sig + a * N + v) : T(0));
         acc[1 + j].add(w * dot);
       }
     }
