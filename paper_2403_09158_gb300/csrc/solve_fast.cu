@@ -137,9 +137,10 @@ __host__ __device__ constexpr size_t nfwd_smem(int cs) {
   return sizeof(C2<float>) * ((size_t)(H / cs) * S::LDC + (size_t)S::GR * S::XS + tw2_size<H>() + tw2_size<NY>() + H + 1);
 }
 template <int H, int NY>
-__host__ __device__ constexpr size_t ninv_smem(int cs) {
+__host__ __device__ constexpr size_t ninv_smem(int cs, int wide = 0) {
   using S = NShape<H, NY>;
-  return sizeof(C2<float>) * ((size_t)(NY / cs) * S::LDR + (size_t)S::XBI + tw2_size<H>() + tw2_size<NY>() + H + 1);
+  return sizeof(C2<float>) * ((size_t)(NY / cs) * (wide == 2 ? H + 2 : S::LDR) + (size_t)S::XBI + tw2_size<H>() +
+                              tw2_size<NY>() + H + 1);
 }
 
 // store v at column k, row y of the column buffer of the CTA that owns column k
@@ -262,14 +263,20 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
 // more consecutive kx of one row of the owner's buffer (128 contiguous bytes or more)
 // instead of two kx of 16 rows.  Remote stores into another CTA's shared memory cost
 // by the write pattern: the wide copy-out makes the scatter far cheaper.
-template <int H, int NY, int CS, bool WIDE>
+// WIDE 2: as 1, with rows H + 2 apart (16-byte aligned), so that a lane of the copy-out
+// carries two adjacent kx in one 16-byte store; the row phase then pairs the line
+// groups of a half-warp on rows 4 apart (with lines of 8 threads; rows 8 apart would
+// fall on the same banks at this pitch).
+template <int H, int NY, int CS, int WIDE>
 __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restrict__ spec, float* __restrict__ sig,
                                                         PassCfg c, int pf) {
   using S = NShape<H, NY>;
   constexpr int CPER = H / CS, ROWS = NY / CS;
+  constexpr int LDR = WIDE == 2 ? H + 2 : S::LDR;
+  static_assert(WIDE != 2 || S::NTH == 8, "the 16-byte copy-out pairs rows for lines of 8 threads");
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<float>* rowb = reinterpret_cast<C2<float>*>(smem_raw);  // [ROWS][LDR]
-  C2<float>* xb = rowb + ROWS * S::LDR;
+  C2<float>* xb = rowb + ROWS * LDR;
   C2<float>* twH = xb + S::XBI;
   C2<float>* twY = twH + tw2_size<H>();
   C2<float>* untw = twY + tw2_size<NY>();
@@ -314,19 +321,33 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
       const bool act = c0 + g < CPER;
       const int kx = h * CPER + (act ? c0 + g : 0);
       if (c0 > 0) load_cols(c0);
-      if constexpr (WIDE) {
+      if constexpr (WIDE != 0) {
         auto st = [&](int k, C2<float> v) { xg[k] = v; };
         reg_fft_loaded<true, NY>(line, XPad<S::R2Y>{xg}, st, twY, t, act);
         __syncthreads();
         if (CS > 1 && c0 == 0) cluster_wait();
         constexpr int GC = S::GC;
         const int ncol = CPER - c0 < GC ? CPER - c0 : GC;
-        for (int e = tid; e < NY * GC; e += kNT) {  // element (row k, column j)
-          const int j = e % GC, k = e / GC;
-          if (j < ncol) {
-            const int owner = k / ROWS;
-            C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
-            base[(k % ROWS) * S::LDR + h * CPER + c0 + j] = xb[j * S::XSYP + k];
+        if constexpr (WIDE == 1) {
+          for (int e = tid; e < NY * GC; e += kNT) {  // element (row k, column j)
+            const int j = e % GC, k = e / GC;
+            if (j < ncol) {
+              const int owner = k / ROWS;
+              C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
+              base[(k % ROWS) * LDR + h * CPER + c0 + j] = xb[j * S::XSYP + k];
+            }
+          }
+        } else {
+          // columns j, j + 1 of row k in one 16-byte store (h * CPER + c0, ncol and GC are
+          // even, and rows start on 16-byte boundaries)
+          for (int e = tid; e < NY * (GC / 2); e += kNT) {
+            const int j = 2 * (e % (GC / 2)), k = e / (GC / 2);
+            if (j < ncol) {
+              const int owner = k / ROWS;
+              C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
+              const C2<float> v0 = xb[j * S::XSYP + k], v1 = xb[(j + 1) * S::XSYP + k];
+              *reinterpret_cast<float4*>(base + (k % ROWS) * LDR + h * CPER + c0 + j) = make_float4(v0.x, v0.y, v1.x, v1.y);
+            }
           }
         }
         __syncthreads();
@@ -334,7 +355,7 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
         auto st = [&](int k, C2<float> v) {
           const int owner = k / ROWS;
           C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
-          base[(k % ROWS) * S::LDR + kx] = v;
+          base[(k % ROWS) * LDR + kx] = v;
         };
         if (CS > 1 && c0 == 0) cluster_wait();
         reg_fft_loaded<true, NY>(line, XPad<S::R2Y>{xg}, st, twY, t, act);
@@ -346,10 +367,11 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   {  // rows along x
     const int g = tid / S::NTH, t = tid % S::NTH;
     for (int r0 = 0; r0 < ROWS; r0 += S::GR) {
-      const int yr = r0 + row_of_group<S::NTH>(g);
+      // WIDE 2: the two groups of a half-warp on rows 4 apart (a bijection on each block of 8)
+      const int yr = r0 + (WIDE == 2 ? (g >> 3) * 8 + ((g >> 1) & 3) + (g & 1) * 4 : row_of_group<S::NTH>(g));
       const bool act = yr < ROWS;
       const int yl = act ? yr : 0;
-      C2<float>* R = rowb + yl * S::LDR;
+      C2<float>* R = rowb + yl * LDR;
       auto ld = [&](int k) {
         if (k == 0) {
           const C2<float> p = R[0];
@@ -639,16 +661,22 @@ int resident_clusters(K k, int cs, size_t smem) {
 
 template <int H, int NY, int CS>
 cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg& c, cudaStream_t st, bool prefetch = false,
-                         bool wide = false) {
+                         int wide = 0) {
   static_assert(H % CS == 0 && NY % CS == 0, "cluster must split rows and columns evenly");
   const dim3 grid(CS, c.ncomp * c.nz);
   if (inverse) {
-    static const int wave = resident_clusters(k_plane_inv_n<H, NY, CS, false>, CS, ninv_smem<H, NY>(CS));
-    if (wide)
-      return launch_k(k_plane_inv_n<H, NY, CS, true>, grid, ninv_smem<H, NY>(CS), CS, st,
-                      static_cast<const C2<float>*>(in), static_cast<float*>(out), c, prefetch ? wave : 0);
-    return launch_k(k_plane_inv_n<H, NY, CS, false>, grid, ninv_smem<H, NY>(CS), CS, st,
-                    static_cast<const C2<float>*>(in), static_cast<float*>(out), c, prefetch ? wave : 0);
+    static const int wave = resident_clusters(k_plane_inv_n<H, NY, CS, 0>, CS, ninv_smem<H, NY>(CS));
+    const int pf = prefetch ? wave : 0;
+    if constexpr (NShape<H, NY>::NTH == 8) {
+      if (wide == 2)
+        return launch_k(k_plane_inv_n<H, NY, CS, 2>, grid, ninv_smem<H, NY>(CS, 2), CS, st,
+                        static_cast<const C2<float>*>(in), static_cast<float*>(out), c, pf);
+    }
+    if (wide == 1)
+      return launch_k(k_plane_inv_n<H, NY, CS, 1>, grid, ninv_smem<H, NY>(CS), CS, st,
+                      static_cast<const C2<float>*>(in), static_cast<float*>(out), c, pf);
+    return launch_k(k_plane_inv_n<H, NY, CS, 0>, grid, ninv_smem<H, NY>(CS), CS, st,
+                    static_cast<const C2<float>*>(in), static_cast<float*>(out), c, pf);
   }
   return launch_k(k_plane_fwd_n<H, NY, CS>, grid, nfwd_smem<H, NY>(CS), CS, st, static_cast<const int32_t*>(in),
                   static_cast<C2<float>*>(out), c);
@@ -688,10 +716,12 @@ cudaError_t plane_inv_staged(const void* in, void* out, const PassCfg& c, cudaSt
 // staged: 1 with 256 threads and two CTAs per SM, 2 with 128 threads and three CTAs
 // per SM, 3 with 256 threads and three CTAs per SM (registers capped at 85); 4 as 0,
 // with the next wave's columns prefetched into L2; 5 and 6 as 0 and 4 with the wide
-// copy-out of the column outputs.
+// copy-out of the column outputs; 7 as 6 with 16-byte stores in the copy-out (lines of
+// 8 threads, nx >= 128, and only while the wider rows keep two CTAs per SM).
 template <int H, int NY>
 int plane_inv_variants() {
-  return 1 | 16 | 32 | 64 | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0);
+  constexpr bool w16 = NShape<H, NY>::NTH == 8 && ninv_smem<H, NY>(ncs<H, NY>(), 2) <= kTwoPerSM;
+  return 1 | 16 | 32 | 64 | (w16 ? 128 : 0) | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0);
 }
 
 template <int H, int NY>
@@ -700,7 +730,8 @@ cudaError_t plane_pair(bool inverse, int variant, const void* in, void* out, con
   if (inverse && variant == 2) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 128, 3>(in, out, c, st);
   if (inverse && variant == 3) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 256, 3>(in, out, c, st);
   if (!inverse) return plane_pair_n<H, NY, ncs<H, NY>()>(false, in, out, c, st);
-  return plane_pair_n<H, NY, ncs<H, NY>()>(true, in, out, c, st, variant == 4 || variant == 6, variant == 5 || variant == 6);
+  return plane_pair_n<H, NY, ncs<H, NY>()>(true, in, out, c, st, variant == 4 || variant == 6 || variant == 7,
+                                          variant == 7 ? 2 : (variant == 5 || variant == 6) ? 1 : 0);
 }
 
 template <int NZ>
