@@ -642,7 +642,7 @@ struct EAcc<double> {
 };
 
 template <class T>
-__global__ void __launch_bounds__(kEnergyThreads) k_energies(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
+__global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_energies(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
                                                              const DefGeo* __restrict__ G, const int* __restrict__ ptr,
                                                              const int* __restrict__ off, const uint8_t* __restrict__ cnt,
                                                              const double* __restrict__ alpha, const double* __restrict__ W,
