@@ -401,13 +401,21 @@ def test_pass_variants_bitwise_equal(n):
 
 
 def test_variants_pinned_by_environment(monkeypatch):
-    """OKMC_VARIANTS=a,b,c pins each pass's variant where it exists (no timing)."""
+    """OKMC_VARIANTS=a,b,c pins each pass's variant where it exists (no timing), and
+    steps captured on a pinned grid follow the tuned grid's trajectory bit for bit."""
     w = scaled_population((64, 64, 64), 8, seed=3, r111=(0.4, 1.0), r100=(0.4, 1.0))
+    ref = make_grid(w)
+    st_ref = ref.step(500.0, 3)
     monkeypatch.setenv('OKMC_VARIANTS', '1,1,4')
     g = make_grid(w)
     cur, avail = g.variants()
     assert cur == [v if (avail[p] >> v) & 1 else 0 for p, v in enumerate((1, 1, 4))]
+    st = g.step(500.0, 3)
+    assert np.array_equal(g.get_positions(), ref.get_positions())
+    assert st['events'] == st_ref['events'] and st['clock'] == st_ref['clock']
+    assert np.array_equal(g.interaction_energies(), ref.interaction_energies())
     g.close()
+    ref.close()
     monkeypatch.setenv('OKMC_VARIANTS', '0,0,30')  # variant 30 exists for no pass
     g = make_grid(w)
     assert g.variants()[0] == [0, 0, 0]
