@@ -598,6 +598,115 @@ def fixed_dt_step(defects, E, Ec, T, seed, step, n, dt, nu0=NU0_DEFAULT):
 
 
 # --------------------------------------------------------------------------
+# dipole approximation of the interaction energy (Sec. 2.1, Eqs. interaction_energy4,
+# dipole_def, dipole_def2; Appendix B): with the external field taken constant over the
+# defect, E_i(Y) ~ -P_i : eps_ext(Y) = -(int eps*_i) : sigma^(-i)(Y), since
+# P_i = C : int eps*_i and sigma^(-i) = C : eps_ext where the other defects' eigenstrain
+# vanishes.
+# --------------------------------------------------------------------------
+def integrated_eigenstrain6(d, h):
+    """int eps*_d dV (6 components, nm^3): the shape volume times e (P = C : this)."""
+    g = defect_geometry(d, h)
+    return g['v_over_h3'] * h ** 3 * to_voigt6(g['e'])
+
+
+def center_voxels(pos):
+    """Voxels whose mean is a field's value at the centre of a defect at pos.  With the
+    subsample coordinates of ``stencil``, a class-1 centre is the centre of its base
+    voxel, and a class-0 centre the corner shared by the 8 voxels base + {-1, 0}^3
+    (trilinear interpolation of voxel-centred values there is their mean)."""
+    b = base_voxel(pos)
+    if pos_class(pos) == 1:
+        return b[None, :]
+    return b[None, :] + np.array([[i, j, k] for i in (-1, 0) for j in (-1, 0) for k in (-1, 0)],
+                                 dtype=np.int64)
+
+
+def sample_center(field6, pos):
+    """field6 (6, nx, ny, nz) at the centre of a defect at half-lattice position pos."""
+    n = np.array(field6.shape[1:])
+    v = np.mod(center_voxels(pos), n[None, :])
+    return field6[:, v[:, 0], v[:, 1], v[:, 2]].mean(axis=1)
+
+
+def dipole_energy_at(d, pos_Y, sigma6, h):
+    """-kappa (int eps*_d) : sigma(Y) for defect d with its centre at pos_Y."""
+    return -KAPPA * ddot6(integrated_eigenstrain6(d, h), sample_center(sigma6, pos_Y))
+
+
+def dipole_energies(defects, n, h, C, k0_mode=MEAN_STRESS_ZERO):
+    """Dipole-approximation energies of every defect at its site and at its eight jumps,
+    with sigma^(-i) = sigma - sigma_i (sigma_i from the solve of defect i alone)."""
+    sig = solve_stress(eigenstrain_field(defects, n, h), C, h, k0_mode)
+    E = np.zeros(len(defects))
+    Ec = np.zeros((len(defects), 8))
+    for i, d in enumerate(defects):
+        s = sig - solve_stress(eigenstrain_field(defects, n, h, only={i}), C, h, k0_mode)
+        E[i] = dipole_energy_at(d, d['pos'], s, h)
+        for j, Y in enumerate(candidate_positions(d['pos'])):
+            Ec[i, j] = dipole_energy_at(d, Y, s, h)
+    return E, Ec
+
+
+def dipole_self_table(d, n, h, C, k0_mode=MEAN_STRESS_ZERO):
+    """D(c, k) = (int eps*_d) : sigma_d(Y_k) (GPa nm^3): the defect's own field at the centre
+    Y_0 of a reference site of class c, or at its jump k - 1, contracted with its
+    integrated eigenstrain.  Kappa times it is the self part that sigma^(-i) removes
+    from a dipole energy.  Translation invariant under whole-voxel shifts, like
+    ``self_term_table``."""
+    D = np.zeros((2, 9))
+    ie = integrated_eigenstrain6(d, h)
+    for c in (0, 1):
+        ref = np.array([c, c, c], dtype=np.int64)
+        dd = as_record(d)
+        dd['pos'] = ref
+        sig = solve_stress(eigenstrain_field([dd], n, h), C, h, k0_mode)
+        D[c, 0] = ddot6(ie, sample_center(sig, ref))
+        for j, Y in enumerate(candidate_positions(ref)):
+            D[c, 1 + j] = ddot6(ie, sample_center(sig, Y))
+    return D
+
+
+def dipole_self_table_fourier(d, n, h, C, k0_mode=MEAN_STRESS_ZERO):
+    """The table of ``dipole_self_table`` by Fourier sums: with w_c the count field of the
+    class-c stencil placed at the origin and q(xi) = e : sigma_hat[e](xi),
+      D(c, k) = V_shape a_c / N  Re sum_xi q(xi) w_c(xi) S_k(xi),
+    S_k(xi) the mean of exp(+i xi.v) over the centre voxels v of Y_k (relative to the
+    reference site's base voxel)."""
+    n = tuple(int(v) for v in n)
+    N = n[0] * n[1] * n[2]
+    g = defect_geometry(d, h)
+    e = g['e']
+    e6 = to_voigt6(e)
+    V = g['v_over_h3'] * h ** 3
+    xs = [frequencies(n[a], n[a] * h) for a in range(3)]
+    fr = [np.fft.fftfreq(n[a]) * n[a] for a in range(3)]
+    q = np.empty(n)
+    for ix in range(n[0]):
+        XI = np.stack(np.meshgrid(np.full(1, xs[0][ix]), xs[1], xs[2], indexing='ij'), axis=-1)[0]
+        zero = np.all(XI == 0.0, axis=-1)
+        eh = np.broadcast_to(e[:, :, None, None], (3, 3) + XI.shape[:2]).astype(complex)
+        sig = green_sigma_hat(C, XI, eh, k0_mode, zero)
+        q[ix] = ddot6(e6[:, None, None], to_voigt6(sig).real)
+    D = np.zeros((2, 9))
+    for c in (0, 1):
+        offs, cnt, a = stencil(d, c, h)
+        f = np.zeros(n)
+        v = np.mod(offs, np.array(n)[None, :])
+        np.add.at(f, (v[:, 0], v[:, 1], v[:, 2]), cnt.astype(float))
+        what = np.fft.fftn(f)
+        ref = np.array([c, c, c], dtype=np.int64)
+        for k, Y in enumerate([ref] + candidate_positions(ref)):
+            S = np.zeros(n, dtype=complex)
+            for vv in center_voxels(Y) - base_voxel(ref)[None, :]:
+                S += np.exp(2j * PI * (fr[0][:, None, None] * vv[0] / n[0] + fr[1][None, :, None] * vv[1] / n[1]
+                                       + fr[2][None, None, :] * vv[2] / n[2]))
+            S /= len(center_voxels(Y))
+            D[c, k] = V * a / N * np.sum(q * what * S).real
+    return D
+
+
+# --------------------------------------------------------------------------
 # dipole-limit helpers for the far-field pin (Sec. 2.1, Eqs. interaction_energy4, dipole_DL)
 # --------------------------------------------------------------------------
 def loop_dipole_tensor(C, b, A):

@@ -429,3 +429,89 @@ def test_p14_table1_conversions():
     B = (g['C11_GPa'] + 2 * g['C12_GPa']) / 3.0
     dv = (P['P11'] + P['P22'] + P['P33']) / O.KAPPA / (3 * B)      # nm^3
     assert abs(dv / omega - g['relaxation_volume_over_Vat']) < 2e-3
+
+
+# ---------------------------------------------------------------- dipole approximation
+# Sec. 2.1, Eqs. interaction_energy4 and dipole_def2: E_dip_i(Y) = -(int eps*_i) : sigma^(-i)(Y)
+def test_dipole_self_table_fourier_equals_real_space():
+    """The self part D(c, k) by Fourier sums equals the single-defect solve sampled at the
+    centres (two independent routes)."""
+    n = (16, 16, 16)
+    for d in _defects_small():
+        D = O.dipole_self_table(d, n, H, C_CUBIC)
+        Df = O.dipole_self_table_fourier(d, n, H, C_CUBIC)
+        assert np.abs(D - Df).max() <= 1e-10 * np.abs(D).max()
+
+
+def test_dipole_table_route_equals_bruteforce():
+    """kappa (int eps*) : sigma(Y) minus the translation-invariant self part equals the
+    energy against sigma - sigma_i (the route the CUDA path takes)."""
+    n = (16, 16, 16)
+    d = _defects_small()
+    E, Ec = O.dipole_energies(d, n, H, C_CUBIC)
+    sig = O.solve_stress(O.eigenstrain_field(d, n, H), C_CUBIC, H)
+    for i in range(len(d)):
+        D = O.dipole_self_table(d[i], n, H, C_CUBIC)
+        c = O.pos_class(d[i]['pos'])
+        ie = O.integrated_eigenstrain6(d[i], H)
+        e0 = -O.KAPPA * (O.ddot6(ie, O.sample_center(sig, d[i]['pos'])) - D[c, 0])
+        assert abs(e0 - E[i]) <= 1e-10 * max(1.0, O.KAPPA * np.abs(D).max())
+        for j, Y in enumerate(O.candidate_positions(d[i]['pos'])):
+            ej = -O.KAPPA * (O.ddot6(ie, O.sample_center(sig, Y)) - D[c, 1 + j])
+            assert abs(ej - Ec[i, j]) <= 1e-10 * max(1.0, O.KAPPA * np.abs(D).max())
+
+
+def test_dipole_equals_exact_when_the_stencil_is_the_centre_sample():
+    """A cluster whose stencil at a class-0 site is the 8 voxels around its centre with
+    equal weights: the exact energy (Eq. interaction_energy3) averages sigma^(-i) over
+    exactly the voxels whose mean is the dipole sample, so the two agree."""
+    n = (16, 16, 16)
+    d = _defects_small()
+    offs, cnt, _ = O.stencil(d[2], 0, H)
+    assert len(cnt) == 8 and np.all(cnt == cnt[0])
+    assert sorted(map(tuple, offs)) == sorted(map(tuple, O.center_voxels(np.zeros(3, np.int64))))
+    E, _ = O.dipole_energies(d, n, H, C_CUBIC)
+    Ex, _ = O.energies_bruteforce(d, n, H, C_CUBIC)
+    assert abs(E[2] - Ex[2]) <= 1e-12 * abs(Ex[2])
+    assert abs(E[0] - Ex[0]) > 1e-3 * abs(Ex[0])        # a loop is not a point defect
+
+
+def test_dipole_approaches_exact_with_separation():
+    """Two small loops along a ray: the relative gap between the dipole and the exact
+    interaction energies falls as the separation grows (Sec. 6: the dipole form holds
+    for sufficiently far defects)."""
+    N = 48
+    n = (N, N, N)
+    gaps = []
+    for step in (3, 5, 8):
+        p1 = np.array([N, N, N])
+        p2 = p1 + step * np.array([2, 2, 0])
+        d = [dict(type=O.LOOP_111, pos=p1, axis=0, radius_nm=0.45, size=0, Em_eV=0.1, mobility=O.ONE_D),
+             dict(type=O.LOOP_111, pos=p2, axis=1, radius_nm=0.45, size=0, Em_eV=0.1, mobility=O.ONE_D)]
+        E, _ = O.dipole_energies(d, n, H, C_CUBIC)
+        Ex, _ = O.energies_bruteforce(d, n, H, C_CUBIC)
+        gaps.append(abs(E[1] - Ex[1]) / abs(Ex[1]))
+    assert gaps[0] > gaps[1] > gaps[2], gaps
+    assert gaps[2] < 0.08, gaps
+
+
+def test_dipole_limit_isotropic_kelvin():
+    """Isotropic medium: energy changes of a small loop's dipole energy along a ray follow
+    the Kelvin dipole-dipole expression P1_ij P2_kl d_j d_l G_ik (cf. P8)."""
+    mu, nu = 82.0, 0.29
+    C = O.stiffness_cubic(*O.isotropic_cubic_constants(mu, nu))
+    N = 96
+    n = (N, N, N)
+    c0 = np.array([N, N, N])
+    loop = dict(type=O.LOOP_111, pos=c0, axis=0, radius_nm=0.35, size=0, Em_eV=0.1, mobility=O.ONE_D)
+    eps = O.eigenstrain_field([loop], n, H)
+    s0 = O.solve_stress(eps, C, H, O.MEAN_STRAIN_ZERO)
+    P = np.einsum('ijkl,kl->ij', C, O.to_tensor(eps.reshape(6, -1).sum(axis=1) * H ** 3))
+    rows = []
+    for step in (8, 10, 12, 14):
+        p2 = c0 + step * np.array([2, 1, -1])
+        rows.append((O.dipole_energy_at(loop, p2, s0, H),
+                     O.dipole_dipole_energy(P, P, (p2 - c0) * H / 2.0, mu, nu) * O.KAPPA))
+    errs = [abs((rows[k + 1][0] - rows[k][0]) / (rows[k + 1][1] - rows[k][1]) - 1.0) for k in range(len(rows) - 1)]
+    assert all(errs[k + 1] < errs[k] for k in range(len(errs) - 1)), errs
+    assert errs[-1] < 1e-2, errs
