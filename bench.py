@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -209,6 +210,64 @@ def _time_steps(g, T, steps, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1), g.stats()['events'] - ev
+
+
+def run_dipole(args):
+    """Exact against dipole-approximation interaction energy of two 1/2<111> loops (the
+    loop-loop geometry of the paper's Sec. 4: radius 3.3 nm, Burgers vectors and normals
+    along [111]; one loop fixed at the centre of a 128^3 box, the other 10 nm away along
+    [1-10] and moved along its glide direction [111]).  For each position: the exact
+    energy (Eq. interaction_energy3) and the dipole one (Eq. interaction_energy4) of the
+    moving loop, and the time of one evaluation after the move (the incremental solve,
+    both energies and their copies to the host)."""
+    import torch
+
+    from paper_2403_09158_gb300 import okmc as ok
+    from paper_2403_09158_gb300.workload import LOOP_111, ONE_D, make_defects
+
+    n = (128, 128, 128)
+    h = 0.2855
+    c0 = np.array([128, 128, 128])
+    off = np.array([50, -50, 0])                      # 10.09 nm along [1-10]
+    steps = list(range(-60, 61, 6))                   # half-lattice steps along [111]
+    defs = make_defects([LOOP_111, LOOP_111], np.array([c0, c0 + off + steps[0]]), [0, 0], [3.3, 3.3], [0, 0],
+                        [0.1, 0.1], [ONE_D, ONE_D])
+    stream = torch.cuda.current_stream()
+    clk = Clocks(torch.cuda.current_device())
+    rows = []
+    g = ok.Grid(n, h, 243.0, 145.0, 116.0, precision=ok.FP32_FIELDS, stream=stream.cuda_stream)
+    g.set_defects(defs)
+    pos = g.get_positions()
+    E = np.zeros(2)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    g.interaction_energies(E)                         # warm-up
+    for k in steps:
+        pos[1] = (c0 + off + k) % (2 * np.asarray(n))
+        g.set_positions(pos)                          # the moved loop's planes become dirty
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.solve_stress(copy=False)                    # incremental: the dirty planes only
+        Ex = g.interaction_energies()
+        Ed, _ = g.dipole_energies()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rows.append((k * math.sqrt(3.0) * h / 2.0, float(Ex[1]), float(Ed[1]), e0.elapsed_time(e1)))
+    g.close()
+    xs = [r[0] for r in rows]
+    gap = max(abs(r[1] - r[2]) for r in rows)
+    far = [abs(r[1] - r[2]) / max(1e-12, abs(r[1])) for r in rows if abs(r[0]) > 12.0]
+    out = {'metric': 'exact vs dipole interaction energy, two 1/2<111> loops', 'unit': 'eV',
+           'data': 'synthetic', 'dtype': 'f32 fields / f64 energies',
+           'config': {'workload': 'loop_loop_128cubed (R = 3.3 nm loops, b || n || [111], 10.09 nm apart along '
+                                  '[1-10], the second moved along [111]; Fe cubic C11/C12/C44 = 243/145/116 GPa)'},
+           'x_nm': xs, 'E_exact_eV': [r[1] for r in rows], 'E_dipole_eV': [r[2] for r in rows],
+           'max_abs_gap_eV': gap, 'rel_gap_beyond_12nm_max': max(far) if far else None,
+           'ms_per_evaluation_median': float(np.median([r[3] for r in rows])),
+           'evaluation': 'after each move: incremental solve, exact and dipole energies, both copied to the host',
+           'clocks': clk.stop()}
+    print(json.dumps(out))
+    return 0
 
 
 def run_config(args, which):
@@ -455,7 +514,7 @@ def main():
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--workload', default='large', choices=['large', 'batch', 'serve', 'small', 'medium'],
+    ap.add_argument('--workload', default='large', choices=['large', 'batch', 'serve', 'small', 'medium', 'dipole'],
                     help='large: the 256^3 single-replica step (default); batch: the 64-replica ensemble; '
                          'serve: the request server under Poisson load; small / medium: the 32^3 FP64 and '
                          'the 128^3 workloads')
@@ -481,6 +540,8 @@ def main():
         return run_serve(args) if rank == 0 else 0
     if args.workload in ('small', 'medium'):
         return run_config(args, args.workload) if rank == 0 else 0
+    if args.workload == 'dipole':
+        return run_dipole(args) if rank == 0 else 0
     r = run_ours(args, ws, rank)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -164,6 +164,22 @@ int okmc_interaction_energies(okmc_grid* g, double* E, int out_on_device);
  * marks the jumps the defect's mobility allows (Sec. 5). */
 int okmc_candidate_energies(okmc_grid* g, double* E, uint8_t* valid, int out_on_device);
 
+/* Dipole approximation of the same energies (Sec. 2.1, Eq. interaction_energy4 with
+ * the dipole tensor P = C : int eps* of Eq. dipole_def2): the external field is taken
+ * constant over the defect, E_i(Y) = -P_i : eps_ext(Y) = -(int eps*_i) : sigma^(-i)(Y),
+ * sigma^(-i) = sigma - sigma_i read at the defect's centre (the base voxel of a class-1
+ * site, the mean of the 8 voxels around the corner of a class-0 site).  E[n] at the
+ * sites, Ec[n][8] (nullable) after the eight jumps (order as above), eV (FP64).
+ * Solves first if the stress is stale.  Same ownership and errors as
+ * okmc_interaction_energies. */
+int okmc_dipole_energies(okmc_grid* g, double* E, double* Ec, int out_on_device);
+
+/* Self part of the dipole energies, D[n][2][9] in GPa nm^3 (FP64): D[i][c][k] =
+ * (int eps*_i) : sigma_i(Y_k), defect i's own field at the centre of a class-c site
+ * (k = 0) or of its jump k - 1; the dipole energy is -kappa ((int eps*_i) : sigma(Y) -
+ * D).  Translation invariant, summed in Fourier space with the self-term table. */
+int okmc_dipole_self_terms(okmc_grid* g, double* D, int out_on_device);
+
 /* Self-term table W[n][2][9] in eV (FP64): W[i][c][0] is the self energy of
  * defect i's eigenstrain at a class-c site against its own periodic field,
  * W[i][c][1+j] the same after jump j.  Translation invariant. */

@@ -63,6 +63,13 @@ cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const doubl
 bool fast_solve_supported(const PassCfg& c);
 cudaError_t launch_plane_fast(bool inverse, int variant, const void* in, void* out, const PassCfg& c, cudaStream_t st);
 int plane_inv_variant_mask(const PassCfg& c);
+template <class T, class QT>
+cudaError_t launch_dipself(const C2<T>* spec, const PassCfg& c, const WBatch& b, const QT* qtab, const double2* phx,
+                           const double2* phy, const double2* phz, double* partial, int nblocks, const double* alpha,
+                           const DefGeo* G, double scale, double* D, cudaStream_t st);
+template <class T>
+cudaError_t launch_dipole_energies(const T* sig, int3 n, const okmc_defect* def, const DefGeo* G, const double* D, int nd,
+                                   double h3, double* E, double* Ec, cudaStream_t st);
 cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st);
 int pencil_variant_mask(const PassCfg& c);
 }  // namespace okmc
@@ -126,6 +133,8 @@ struct okmc_grid {
   long long* d_sumcnt = nullptr;
   int* d_nnz = nullptr;
   double* d_W = nullptr;
+  double* d_D = nullptr;    // [nd][2][9] dipole self parts (int eps*) : sigma_i at the site centres
+  double* d_dip = nullptr;  // [nd] dipole site energies, then [nd][8] candidate energies
   double* d_E = nullptr;
   double* d_Ec = nullptr;
   int* d_order = nullptr;  // defects by decreasing stencil size (energy block order)
@@ -475,18 +484,24 @@ int build_self_terms(okmc_grid* g) {
       return launch_selfterm<T>((const C2<T>*)g->spec, c, b, qtab, phx, phy, phz, g->d_partial, kSelfBlocks, g->d_alpha, pref,
                                 g->d_W, g->st);
     }));
+    OKMC_TRY(run(g, "dipole_self", [&] {
+      return launch_dipself<T, T>((const C2<T>*)g->spec, c, b, qtab, phx, phy, phz, g->d_partial, kSelfBlocks, g->d_alpha,
+                                  g->d_geo, g->h * g->h * g->h / (double)N, g->d_D, g->st);
+    }));
     e = cudaMemsetAsync(g->eps, 0, 6 * N * sizeof(Q), g->st);
     if (e != cudaSuccess) return cuda_fail(g, e, "memset");
   }
-  if (reps.size() < (size_t)nd) {  // copy each shape's row to the defects that share it
-    std::vector<double> W((size_t)nd * 18);
-    e = cudaMemcpyAsync(W.data(), g->d_W, W.size() * sizeof(double), cudaMemcpyDeviceToHost, g->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
-    for (int i = 0; i < nd && e == cudaSuccess; ++i)
-      if (rep[i] != i) std::copy(W.begin() + (size_t)rep[i] * 18, W.begin() + (size_t)rep[i] * 18 + 18, W.begin() + (size_t)i * 18);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_W, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, g->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
-    if (e != cudaSuccess) return cuda_fail(g, e, "self-term copy");
+  if (reps.size() < (size_t)nd) {  // copy each shape's rows (W and D) to the defects that share it
+    for (double* tab : {g->d_W, g->d_D}) {
+      std::vector<double> W((size_t)nd * 18);
+      e = cudaMemcpyAsync(W.data(), tab, W.size() * sizeof(double), cudaMemcpyDeviceToHost, g->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+      for (int i = 0; i < nd && e == cudaSuccess; ++i)
+        if (rep[i] != i) std::copy(W.begin() + (size_t)rep[i] * 18, W.begin() + (size_t)rep[i] * 18 + 18, W.begin() + (size_t)i * 18);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(tab, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, g->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "self-term copy");
+    }
   }
   g->sigma_valid = false;
   return OKMC_OK;
@@ -541,7 +556,8 @@ int voxelise_all(okmc_grid* g) {
 
 void free_defects(okmc_grid* g) {
   void** bufs[] = {(void**)&g->d_def, (void**)&g->d_geo, (void**)&g->d_ptr, (void**)&g->d_off, (void**)&g->d_cnt,
-                   (void**)&g->d_alpha, (void**)&g->d_sumcnt, (void**)&g->d_nnz, (void**)&g->d_W, (void**)&g->d_E,
+                   (void**)&g->d_alpha, (void**)&g->d_sumcnt, (void**)&g->d_nnz, (void**)&g->d_W, (void**)&g->d_D,
+                   (void**)&g->d_dip, (void**)&g->d_E,
                    (void**)&g->d_Ec, (void**)&g->d_order, (void**)&g->d_rates, (void**)&g->d_rsum, (void**)&g->d_moves, (void**)&g->d_pos,
                    (void**)&g->d_dl, (void**)&g->d_doff, (void**)&g->d_dcnt};
   for (void** b : bufs) {
@@ -925,6 +941,8 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
     OKMC_TRY(dalloc(g, (void**)&g->d_sumcnt, 2 * n1 * sizeof(long long)));
     OKMC_TRY(dalloc(g, (void**)&g->d_nnz, 2 * n1 * sizeof(int)));
     OKMC_TRY(dalloc(g, (void**)&g->d_W, 18 * n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_D, 18 * n1 * sizeof(double)));
+    OKMC_TRY(dalloc(g, (void**)&g->d_dip, 9 * n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_E, n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_Ec, 8 * n1 * sizeof(double)));
     OKMC_TRY(dalloc(g, (void**)&g->d_rates, 8 * n1 * sizeof(double)));
@@ -1072,6 +1090,29 @@ int okmc_candidate_energies(okmc_grid* g, double* E, uint8_t* valid, int out_on_
     if (e != cudaSuccess) return cuda_fail(g, e, "valid mask");
   }
   return OKMC_OK;
+}
+
+int okmc_dipole_energies(okmc_grid* g, double* E, double* Ec, int out_on_device) {
+  if (!g || !E) return OKMC_EINVAL;
+  if (!g->nd) return OKMC_OK;
+  OKMC_TRY(solve(g));
+  const double h3 = g->h * g->h * g->h;
+  OKMC_TRY(run(g, "dipole_energies", [&] {
+    if (fp64(g))
+      return launch_dipole_energies<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->d_D, g->nd, h3, g->d_dip,
+                                            g->d_dip + g->nd, g->st);
+    return launch_dipole_energies<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->d_D, g->nd, h3, g->d_dip,
+                                         g->d_dip + g->nd, g->st);
+  }));
+  OKMC_TRY(copy_out(g, E, g->d_dip, g->nd * sizeof(double), out_on_device));
+  if (Ec) OKMC_TRY(copy_out(g, Ec, g->d_dip + g->nd, g->nd * 8 * sizeof(double), out_on_device));
+  return OKMC_OK;
+}
+
+int okmc_dipole_self_terms(okmc_grid* g, double* D, int out_on_device) {
+  if (!g || !D) return OKMC_EINVAL;
+  if (!g->nd) return OKMC_OK;
+  return copy_out(g, D, g->d_D, g->nd * 18 * sizeof(double), out_on_device);
 }
 
 int okmc_self_terms(okmc_grid* g, double* W, int out_on_device) {

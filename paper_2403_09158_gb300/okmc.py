@@ -26,7 +26,8 @@ RESIDENCE, FIXED_DT = 0, 1
 EXPORTED = [
     'okmc_grid_create', 'okmc_grid_destroy', 'okmc_last_error', 'okmc_set_stream', 'okmc_set_defects',
     'okmc_get_defects', 'okmc_set_positions', 'okmc_get_positions', 'okmc_solve_stress', 'okmc_eigenstrain',
-    'okmc_interaction_energies', 'okmc_candidate_energies', 'okmc_self_terms', 'okmc_get_stencil', 'okmc_step',
+    'okmc_interaction_energies', 'okmc_candidate_energies', 'okmc_self_terms', 'okmc_dipole_energies',
+    'okmc_dipole_self_terms', 'okmc_get_stencil', 'okmc_step',
     'okmc_get_stats', 'okmc_device_bytes', 'okmc_set_profiling', 'okmc_kernel_times', 'okmc_reset_kernel_times',
     'okmc_launch_shape', 'okmc_solve_stress_static', 'okmc_set_graphs', 'okmc_batch_create', 'okmc_batch_step',
     'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_get_variants', 'okmc_set_variant',
@@ -108,6 +109,8 @@ def load(path=LIB_PATH):
         'okmc_interaction_energies': (C.c_int, [vp, dp, C.c_int]),
         'okmc_candidate_energies': (C.c_int, [vp, dp, dp, C.c_int]),
         'okmc_self_terms': (C.c_int, [vp, dp, C.c_int]),
+        'okmc_dipole_energies': (C.c_int, [vp, dp, dp, C.c_int]),
+        'okmc_dipole_self_terms': (C.c_int, [vp, dp, C.c_int]),
         'okmc_get_stencil': (C.c_int, [vp, i32, i32, dp, dp, i32, C.POINTER(i32), C.POINTER(C.c_double)]),
         'okmc_step': (C.c_int, [vp, C.POINTER(StepParams), i64, C.POINTER(StepStats)]),
         'okmc_get_stats': (C.c_int, [vp, C.POINTER(StepStats)]),
@@ -254,6 +257,18 @@ class Grid:
     def self_terms(self):
         out = np.zeros((self.nd, 2, 9))
         self._chk(self.lib.okmc_self_terms(self.h, out.ctypes.data, 0))
+        return out
+
+    def dipole_energies(self):
+        """(E[n], Ec[n][8]): dipole-approximation energies at the sites and after the jumps."""
+        E = np.zeros(self.nd)
+        Ec = np.zeros((self.nd, 8))
+        self._chk(self.lib.okmc_dipole_energies(self.h, E.ctypes.data, Ec.ctypes.data, 0))
+        return E, Ec
+
+    def dipole_self_terms(self):
+        out = np.zeros((self.nd, 2, 9))
+        self._chk(self.lib.okmc_dipole_self_terms(self.h, out.ctypes.data, 0))
         return out
 
     def stencil(self, i, c):

@@ -171,6 +171,35 @@ def test_self_terms_match_oracle():
     g.close()
 
 
+# ------------------------------------------------------------------ dipole approximation
+@pytest.mark.parametrize('precision', [ok.FP32_FIELDS, ok.FP64_FIELDS])
+def test_dipole_energies_match_oracle(precision):
+    """Dipole-approximation energies (Eq. interaction_energy4, P = C : int eps*) at the
+    sites and after the jumps, and their self part, against the oracle's sigma - sigma_i
+    route and its Fourier table."""
+    w = config_small()
+    g = make_grid(w, precision)
+    E, Ec = g.dipole_energies()
+    D = g.dipole_self_terms()
+    Ex = g.interaction_energies()
+    g.close()
+    C = O.stiffness_cubic(*w.C)
+    Eo, Eco = O.dipole_energies(w.defects, w.n, w.voxel_nm, C)
+    Do = np.array([O.dipole_self_table_fourier(d, w.n, w.voxel_nm, C) for d in w.defects])
+    if precision == ok.FP64_FIELDS:
+        assert np.abs(D - Do).max() <= 1e-9 * max(1.0, np.abs(Do).max())
+        tol = np.full(len(E), ENERGY_TOL[ok.FP64_FIELDS])
+    else:
+        # FP32 spectra: the self part carries the transform's ~1e-7 relative error, and
+        # the energy subtracts it from the sampled total field
+        assert np.abs(D - Do).max() <= 5e-7 * np.abs(Do).max() + 1e-6
+        tol = ENERGY_TOL[ok.FP32_FIELDS] + 1e-6 * O.KAPPA * np.abs(Do.reshape(len(E), -1)).max(axis=1)
+    assert np.all(np.abs(E - Eo) <= tol), (np.abs(E - Eo), tol)
+    assert np.all(np.abs(Ec - Eco).max(axis=1) <= tol), (np.abs(Ec - Eco).max(axis=1), tol)
+    # the approximation differs from the exact energy of an extended defect
+    assert np.abs(E - Ex).max() > 1e-4
+
+
 # ------------------------------------------------------------------ kinetics
 def test_incremental_field_equals_fresh_voxelisation():
     w = config_small()
