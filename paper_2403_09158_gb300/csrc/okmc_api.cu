@@ -135,6 +135,7 @@ struct okmc_grid {
   double* d_W = nullptr;
   double* d_D = nullptr;    // [nd][2][9] dipole self parts (int eps*) : sigma_i at the site centres
   double* d_dip = nullptr;  // [nd] dipole site energies, then [nd][8] candidate energies
+  bool dip_valid = false;   // d_D holds the current defects' dipole self parts
   double* d_E = nullptr;
   double* d_Ec = nullptr;
   int* d_order = nullptr;  // defects by decreasing stencil size (energy block order)
@@ -397,8 +398,10 @@ int validate_defects(okmc_grid* g, const okmc_defect* d, int nd) {
 // the scalar count fields of three defects' stencils (both classes) are transformed
 // with the forward plane and pencil passes, and k_selfterm_partial sums them against
 // the type tables Q_t, which k_qtable leaves in the (idle) stress buffer.
+// want_W / want_D: which tables the shape batches sum (D, the dipole self parts, is
+// built on first use by ensure_dipole_tables).
 template <class T, class Q>
-int build_self_terms(okmc_grid* g) {
+int build_self_terms(okmc_grid* g, bool want_W = true, bool want_D = false) {
   const size_t N = g->N;
   const int3 n = dims(g);
   const int nd = g->nd;
@@ -480,19 +483,22 @@ int build_self_terms(okmc_grid* g) {
       OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)g->spec, c, g->st); }));
       OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil<T>((C2<T>*)g->spec, c, g->st); }));
     }
-    OKMC_TRY(run(g, "self_terms", [&] {
-      return launch_selfterm<T>((const C2<T>*)g->spec, c, b, qtab, phx, phy, phz, g->d_partial, kSelfBlocks, g->d_alpha, pref,
-                                g->d_W, g->st);
-    }));
-    OKMC_TRY(run(g, "dipole_self", [&] {
-      return launch_dipself<T, T>((const C2<T>*)g->spec, c, b, qtab, phx, phy, phz, g->d_partial, kSelfBlocks, g->d_alpha,
-                                  g->d_geo, g->h * g->h * g->h / (double)N, g->d_D, g->st);
-    }));
+    if (want_W)
+      OKMC_TRY(run(g, "self_terms", [&] {
+        return launch_selfterm<T>((const C2<T>*)g->spec, c, b, qtab, phx, phy, phz, g->d_partial, kSelfBlocks, g->d_alpha,
+                                  pref, g->d_W, g->st);
+      }));
+    if (want_D)
+      OKMC_TRY(run(g, "dipole_self", [&] {
+        return launch_dipself<T, T>((const C2<T>*)g->spec, c, b, qtab, phx, phy, phz, g->d_partial, kSelfBlocks, g->d_alpha,
+                                    g->d_geo, g->h * g->h * g->h / (double)N, g->d_D, g->st);
+      }));
     e = cudaMemsetAsync(g->eps, 0, 6 * N * sizeof(Q), g->st);
     if (e != cudaSuccess) return cuda_fail(g, e, "memset");
   }
   if (reps.size() < (size_t)nd) {  // copy each shape's rows (W and D) to the defects that share it
-    for (double* tab : {g->d_W, g->d_D}) {
+    for (double* tab : {want_W ? g->d_W : nullptr, want_D ? g->d_D : nullptr}) {
+      if (!tab) continue;
       std::vector<double> W((size_t)nd * 18);
       e = cudaMemcpyAsync(W.data(), tab, W.size() * sizeof(double), cudaMemcpyDeviceToHost, g->st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
@@ -724,6 +730,19 @@ int autotune(okmc_grid* g) {
   if (e != cudaSuccess) return cuda_fail(g, e, "tune");
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = {g->variant[0], g->variant[1], g->variant[2]};
+  return OKMC_OK;
+}
+
+// The dipole self parts D, summed on first use (a dipole-free run pays nothing for
+// them).  The shape batches use the field buffers as scratch, so the eigenstrain field
+// is voxelised again from the current positions after them.
+int ensure_dipole_tables(okmc_grid* g) {
+  if (g->dip_valid) return OKMC_OK;
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);  // as set_defects: setup work
+  OKMC_TRY((fp64(g) ? build_self_terms<double, int64_t>(g, false, true) : build_self_terms<float, int32_t>(g, false, true)));
+  OKMC_TRY(voxelise_all(g));
+  OKMC_TRY(check_device_error(g));
+  g->dip_valid = true;
   return OKMC_OK;
 }
 
@@ -993,6 +1012,7 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
       OKMC_TRY(build_dilated_lists(g));
       OKMC_TRY((fp64(g) ? build_self_terms<double, int64_t>(g) : build_self_terms<float, int32_t>(g)));
     }
+    g->dip_valid = false;
     OKMC_TRY(voxelise_all(g));
     OKMC_TRY(check_device_error(g));
     g->sigma_valid = false;
@@ -1095,6 +1115,7 @@ int okmc_candidate_energies(okmc_grid* g, double* E, uint8_t* valid, int out_on_
 int okmc_dipole_energies(okmc_grid* g, double* E, double* Ec, int out_on_device) {
   if (!g || !E) return OKMC_EINVAL;
   if (!g->nd) return OKMC_OK;
+  OKMC_TRY(ensure_dipole_tables(g));
   OKMC_TRY(solve(g));
   const double h3 = g->h * g->h * g->h;
   OKMC_TRY(run(g, "dipole_energies", [&] {
@@ -1112,6 +1133,7 @@ int okmc_dipole_energies(okmc_grid* g, double* E, double* Ec, int out_on_device)
 int okmc_dipole_self_terms(okmc_grid* g, double* D, int out_on_device) {
   if (!g || !D) return OKMC_EINVAL;
   if (!g->nd) return OKMC_OK;
+  OKMC_TRY(ensure_dipole_tables(g));
   return copy_out(g, D, g->d_D, g->nd * 18 * sizeof(double), out_on_device);
 }
 

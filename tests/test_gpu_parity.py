@@ -179,9 +179,12 @@ def test_dipole_energies_match_oracle(precision):
     route and its Fourier table."""
     w = config_small()
     g = make_grid(w, precision)
+    Ex = g.interaction_energies()
     E, Ec = g.dipole_energies()
     D = g.dipole_self_terms()
-    Ex = g.interaction_energies()
+    # the tables are built on first use with the field buffers as scratch; the field is
+    # rebuilt from the positions, so the exact energies do not change
+    assert np.array_equal(g.interaction_energies(), Ex)
     g.close()
     C = O.stiffness_cubic(*w.C)
     Eo, Eco = O.dipole_energies(w.defects, w.n, w.voxel_nm, C)
@@ -198,6 +201,23 @@ def test_dipole_energies_match_oracle(precision):
     assert np.all(np.abs(Ec - Eco).max(axis=1) <= tol), (np.abs(Ec - Eco).max(axis=1), tol)
     # the approximation differs from the exact energy of an extended defect
     assert np.abs(E - Ex).max() > 1e-4
+
+
+def test_dipole_tables_leave_the_trajectory_unchanged():
+    """Computing dipole energies between steps (which builds their tables once) does not
+    change the kinetics: same positions and statistics as a grid that never does."""
+    w = config_small()
+    a, b = make_grid(w), make_grid(w)
+    a.step(w.T_K, 4)
+    a.dipole_energies()
+    sa = a.step(w.T_K, 4)
+    b.step(w.T_K, 4)
+    sb = b.step(w.T_K, 4)
+    assert np.array_equal(a.get_positions(), b.get_positions())
+    assert sa['events'] == sb['events'] and sa['clock'] == sb['clock']
+    assert np.array_equal(a.interaction_energies(), b.interaction_energies())
+    a.close()
+    b.close()
 
 
 # ------------------------------------------------------------------ kinetics
