@@ -17,7 +17,11 @@ What it computes, in the paper's order (Santos-Gueemes, Ortiz, Segurado,
 3. Interaction energies (Sec. 2, Eq. interaction_energy3), written as
    E_i(Y) = -int eps*_i(Y) : sigma^(-i) dV, with sigma^(-i) the stress of all
    defects except i.
-4. Rates (Sec. 5, Eqs. unbiased_boltzmann, biased_forward/backward_boltzmann),
+4. The dipole approximation of the same energies (Sec. 2.1, Eq. interaction_energy4)
+   and dislocation lines by field dislocation mechanics (Sec. 3.2, Eqs. Nye2,
+   eq_EIG_fourier, plastic_0): the Nye tensor of a line, the incompatible plastic
+   distortion in Fourier space and its symmetric part as eigenstrain.
+5. Rates (Sec. 5, Eqs. unbiased_boltzmann, biased_forward/backward_boltzmann),
    the frequency line and jump selection (Eqs. frequency_line, selection_jump),
    the fixed time step and Poisson event counts (Eqs. time_step, poisson;
    Appendix A, Algorithm 1), and a residence-time (one event per step) variant.
@@ -41,6 +45,13 @@ repository's design notes):
 * Lattice parameter a0 equals the voxel edge h; positions are integers in
   units of a0/2 on the bcc lattice (all even or all odd); the parity is the
   rasterisation class.
+* Dislocation lines: the Burgers vector density of each sub-segment (at most h/4 long)
+  is spread to the 8 surrounding voxel centres with trilinear weights; a loop's line
+  runs clockwise seen from the tip of its oriented area A (so that curl U^p = -alpha,
+  Eq. curlUe, holds with U^p = b (x) n on the loop's surface); a straight line is one
+  period of a periodic line, whose net Burgers vector drops out with the xi = 0 term
+  (a uniform compensating density); the compatible part of Eq. plastic_0 is a uniform
+  distortion.
 * Rates: nu_ij = (1/z_i) nu0 exp(-(E_m,i + (E_i(X+lambda_j) - E_i(X))/2)/k_B T)
   over the z_i allowed jumps (Eq. biased_forward_boltzmann generalised from
   z = 2 to z jumps).
@@ -595,6 +606,92 @@ def fixed_dt_step(defects, E, Ec, T, seed, step, n, dt, nu0=NU0_DEFAULT):
         defects[i]['pos'] = np.mod(np.asarray(defects[i]['pos'], dtype=np.int64) + JUMPS[j],
                                    2 * np.asarray(n))
     return moves
+
+
+# --------------------------------------------------------------------------
+# dislocation lines by field dislocation mechanics (Sec. 3.2: Eqs. Nye2, curlUe,
+# eq_EIG_fourier, plastic_0); voxel centres at (v + 1/2) h (Sec. 3.4)
+# --------------------------------------------------------------------------
+LEVI_CIVITA = np.zeros((3, 3, 3))
+for _i, _j, _k in ((0, 1, 2), (1, 2, 0), (2, 0, 1)):
+    LEVI_CIVITA[_i, _j, _k] = 1.0
+    LEVI_CIVITA[_i, _k, _j] = -1.0
+
+
+def nye_tensor(points, b, n, h, closed=True, ds_max=None):
+    """Nye tensor alpha_ij (3, 3, nx, ny, nz) of a polyline dislocation with Burgers
+    vector b (nm): Eq. Nye2, the Burgers vector density of each sub-segment (length at
+    most ds_max, default h/4) spread to the 8 voxel centres around its midpoint with
+    trilinear weights (the paper spreads the core over the 8 surrounding grid points,
+    Sec. 4).  alpha_ij(v) = sum_s b_i t_j ds w_s(v) / h^3.  An open polyline whose end
+    is a lattice translate of its start is a periodic (infinite) line."""
+    n = tuple(int(v) for v in n)
+    ds_max = ds_max or 0.25 * h
+    P = np.asarray(points, dtype=np.float64)
+    ends = list(zip(P[:-1], P[1:])) + ([(P[-1], P[0])] if closed else [])
+    xs, ts, dss = [], [], []
+    for p, q in ends:
+        d = q - p
+        L = float(np.linalg.norm(d))
+        m = max(1, int(math.ceil(L / ds_max)))
+        t = d / L
+        k = (np.arange(m) + 0.5)[:, None]
+        xs.append(p[None, :] + k * (L / m) * t[None, :])
+        ts.append(np.repeat(t[None, :], m, axis=0))
+        dss.append(np.full(m, L / m))
+    X, T, DS = np.concatenate(xs), np.concatenate(ts), np.concatenate(dss)
+    u = X / h - 0.5
+    i0 = np.floor(u).astype(np.int64)
+    f = u - i0
+    alpha = np.zeros((3, 3) + n)
+    bt = np.einsum('i,sj->sij', np.asarray(b, float), T) * (DS / h ** 3)[:, None, None]
+    for cx in (0, 1):
+        for cy in (0, 1):
+            for cz in (0, 1):
+                w = ((f[:, 0] if cx else 1 - f[:, 0]) * (f[:, 1] if cy else 1 - f[:, 1])
+                     * (f[:, 2] if cz else 1 - f[:, 2]))
+                idx = np.mod(i0 + np.array([cx, cy, cz])[None, :], np.array(n)[None, :])
+                for i in range(3):
+                    for j in range(3):
+                        np.add.at(alpha[i, j], (idx[:, 0], idx[:, 1], idx[:, 2]), w * bt[:, i, j])
+    return alpha
+
+
+def plastic_distortion(alpha, h, U0=None):
+    """U^p (3, 3, nx, ny, nz): the incompatible part of Eq. eq_EIG_fourier,
+    U_hat_ij = -i xi_k / |xi|^2 eps_jkl alpha_hat_il for xi != 0, plus a uniform
+    compatible part U0 (3x3) as the xi = 0 term (Eq. plastic_0); the real part of the
+    inverse transform (the even-edge Nyquist reading of the stress solve)."""
+    n = alpha.shape[2:]
+    xs = [frequencies(n[a], n[a] * h) for a in range(3)]
+    XI = np.stack(np.meshgrid(xs[0], xs[1], xs[2], indexing='ij'))          # (3, nx, ny, nz)
+    xi2 = np.sum(XI * XI, axis=0)
+    zero = xi2 == 0.0
+    q = XI / np.where(zero, 1.0, xi2)[None]
+    ah = np.fft.fftn(alpha, axes=(-3, -2, -1))
+    Uh = -1j * np.einsum('kxyz,jkl,ilxyz->ijxyz', q, LEVI_CIVITA, ah)
+    Uh[:, :, zero] = 0.0
+    if U0 is not None:
+        Uh[:, :, zero] = (np.asarray(U0, float) * np.prod(n))[:, :, None]
+    return np.fft.ifftn(Uh, axes=(-3, -2, -1)).real
+
+
+def dislocation_eigenstrain6(alpha, h, U0=None):
+    """eps_EIG = sym(U^p), 6 components (the plastic strain taken as eigenstrain)."""
+    U = plastic_distortion(alpha, h, U0)
+    return to_voigt6(0.5 * (U + np.transpose(U, (1, 0, 2, 3, 4))))
+
+
+def circle_points(center, normal, R, m=256):
+    """m points of the circle of radius R about `normal` (unit), counter-clockwise seen
+    from the normal's tip, so that its oriented area is pi R^2 normal."""
+    nv = np.asarray(normal, float) / np.linalg.norm(normal)
+    a = np.array([1.0, 0.0, 0.0]) if abs(nv[0]) < 0.9 else np.array([0.0, 1.0, 0.0])
+    e1 = np.cross(nv, a)
+    e1 /= np.linalg.norm(e1)
+    e2 = np.cross(nv, e1)
+    th = 2.0 * PI * np.arange(m) / m
+    return np.asarray(center, float)[None, :] + R * (np.cos(th)[:, None] * e1[None, :] + np.sin(th)[:, None] * e2[None, :])
 
 
 # --------------------------------------------------------------------------

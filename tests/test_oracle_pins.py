@@ -515,3 +515,96 @@ def test_dipole_limit_isotropic_kelvin():
     errs = [abs((rows[k + 1][0] - rows[k][0]) / (rows[k + 1][1] - rows[k][1]) - 1.0) for k in range(len(rows) - 1)]
     assert all(errs[k + 1] < errs[k] for k in range(len(errs) - 1)), errs
     assert errs[-1] < 1e-2, errs
+
+
+# ---------------------------------------------------------------- dislocation lines (FDM)
+# Sec. 3.2, Eqs. Nye2, curlUe, eq_EIG_fourier, plastic_0
+def _edge_dislocation_stress(N, mu, nu, b=0.25):
+    """Stress of a straight edge dislocation (line along z through a voxel corner at the
+    box centre, b along x) by the FDM route, and the Volterra isotropic solution at the
+    voxel centres (Hirth & Lothe, Eq. 3-43)."""
+    C = O.stiffness_cubic(*O.isotropic_cubic_constants(mu, nu))
+    n = (N, N, N)
+    x0 = np.array([N / 2 * H, N / 2 * H, 0.0])
+    bv = np.array([b, 0.0, 0.0])
+    alpha = O.nye_tensor(np.array([x0, x0 + np.array([0.0, 0.0, N * H])]), bv, n, H, closed=False)
+    s = O.solve_stress(O.dislocation_eigenstrain6(alpha, H), C, H).reshape(6, -1)
+    xc = (np.indices(n).reshape(3, -1).T + 0.5) * H
+    x, y = xc[:, 0] - x0[0], xc[:, 1] - x0[1]
+    r4 = (x * x + y * y) ** 2
+    D = mu * b / (2.0 * PI_ * (1.0 - nu))
+    v = np.zeros_like(s)
+    v[0] = -D * y * (3 * x * x + y * y) / r4
+    v[1] = D * y * (x * x - y * y) / r4
+    v[5] = D * x * (x * x - y * y) / r4
+    v[2] = nu * (v[0] + v[1])
+    return s, v, np.hypot(x, y)
+
+
+PI_ = math.pi
+
+
+def test_fdm_edge_dislocation_matches_volterra():
+    """Isotropic medium: near the core (far from the periodic images) the FDM stress of a
+    straight edge dislocation is Volterra's; the gap further out falls as the box grows
+    (the images and the uniform compensating density of a net Burgers vector)."""
+    mu, nu = 82.0, 0.29
+    s64, v64, r64 = _edge_dislocation_stress(64, mu, nu)
+    m = (r64 >= 0.8) & (r64 < 2.5)
+    assert np.linalg.norm(s64[:, m] - v64[:, m]) <= 0.06 * np.linalg.norm(v64[:, m])
+    s96, v96, r96 = _edge_dislocation_stress(96, mu, nu)
+    far = [np.linalg.norm(s[:, (r >= 2.5) & (r < 4.0)] - v[:, (r >= 2.5) & (r < 4.0)])
+           / np.linalg.norm(v[:, (r >= 2.5) & (r < 4.0)]) for s, v, r in ((s64, v64, r64), (s96, v96, r96))]
+    assert far[1] < 0.6 * far[0], far
+
+
+def test_fdm_loop_nye_tensor_moments_and_mean():
+    """A closed loop's Nye tensor integrates to zero, its first moment is b (x) (oriented
+    area) (the loop's dipole), and the compatible part of Eq. plastic_0 gives the mean
+    eigenstrain sym(b (x) A)/V, the slab loop's integrated eigenstrain over the box."""
+    N = 32
+    n = (N, N, N)
+    pos = np.array([N, N, N])
+    R = 1.0
+    loop = dict(type=O.LOOP_111, pos=pos, axis=0, radius_nm=R, size=0, Em_eV=0.1, mobility=O.ONE_D)
+    g = O.defect_geometry(loop, H)
+    X = pos * H / 2.0
+    alpha = O.nye_tensor(O.circle_points(X, g['n'], R, 1024)[::-1], g['b'], n, H)
+    assert np.abs(alpha.reshape(9, -1).sum(axis=1)).max() * H ** 3 < 1e-12
+    d = (np.indices(n).reshape(3, -1).T + 0.5) * H - X
+    M = np.einsum('ilv,vm->ilm', alpha.reshape(3, 3, -1), d) * H ** 3          # int alpha_il x_m
+    A = PI_ * R * R * g['n']
+    # clockwise line seen from A's tip (curl U^p = -alpha with U^p = b (x) n on the loop's
+    # surface): int alpha_il x_m = b_i eps_lmp A'_p, A' the inscribed 1024-gon's area vector
+    Ap = A * (1024 / (2.0 * PI_)) * math.sin(2.0 * PI_ / 1024)
+    expect = np.einsum('i,lmp,p->ilm', g['b'], O.LEVI_CIVITA, Ap)
+    assert np.abs(M - expect).max() <= 1e-9 * np.abs(expect).max()
+    U0 = 0.5 * (np.outer(g['b'], A) + np.outer(A, g['b'])) / (np.prod(n) * H ** 3)
+    eps = O.dislocation_eigenstrain6(alpha, H, U0)
+    slab = O.eigenstrain_field([loop], n, H)
+    assert np.allclose(eps.reshape(6, -1).sum(axis=1), slab.reshape(6, -1).sum(axis=1), rtol=1e-10, atol=1e-12)
+
+
+def test_fdm_loop_approaches_slab_loop_with_resolution():
+    """The same prismatic loop as a line (Nye tensor, this route) and as the one-voxel
+    slab of Eq. eig_shearloop: a loop's stress depends on its line only, so away from the
+    core the two fields approach each other as the voxel shrinks in a fixed box."""
+    Lbox, R = 32 * H, 1.2
+    C = C_CUBIC
+    gaps = []
+    for N in (24, 32, 48):
+        h = Lbox / N
+        n = (N, N, N)
+        pos = np.array([N, N, N])
+        loop = dict(type=O.LOOP_111, pos=pos, axis=0, radius_nm=R, size=0, Em_eV=0.1, mobility=O.ONE_D)
+        g = O.defect_geometry(loop, h)
+        X = pos * h / 2.0
+        s_slab = O.solve_stress(O.eigenstrain_field([loop], n, h), C, h).reshape(6, -1)
+        alpha = O.nye_tensor(O.circle_points(X, g['n'], R, 1024)[::-1], g['b'], n, h)
+        s_fdm = O.solve_stress(O.dislocation_eigenstrain6(alpha, h), C, h).reshape(6, -1)
+        d = (np.indices(n).reshape(3, -1).T + 0.5) * h - X
+        r = np.linalg.norm(d - np.round(d / Lbox) * Lbox, axis=1)
+        m = (r >= 2.0) & (r < 3.5)
+        gaps.append(np.linalg.norm(s_slab[:, m] - s_fdm[:, m]) / np.linalg.norm(s_slab[:, m]))
+    assert gaps[0] > gaps[1] > gaps[2], gaps
+    assert gaps[2] < 0.35, gaps
