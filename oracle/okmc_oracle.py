@@ -17,7 +17,8 @@ What it computes, in the paper's order (Santos-Gueemes, Ortiz, Segurado,
 3. Interaction energies (Sec. 2, Eq. interaction_energy3), written as
    E_i(Y) = -int eps*_i(Y) : sigma^(-i) dV, with sigma^(-i) the stress of all
    defects except i.
-4. The dipole approximation of the same energies (Sec. 2.1, Eq. interaction_energy4)
+4. The paper's translation of a defect's field by the shift theorem (Sec. 3.3, Eq.
+   shift), the dipole approximation of the same energies (Sec. 2.1, Eq. interaction_energy4)
    and dislocation lines by field dislocation mechanics (Sec. 3.2, Eqs. Nye2,
    eq_EIG_fourier, plastic_0): the Nye tensor of a line, the incompatible plastic
    distortion in Fourier space and its symmetric part as eigenstrain.
@@ -606,6 +607,48 @@ def fixed_dt_step(defects, E, Ec, T, seed, step, n, dt, nu0=NU0_DEFAULT):
         defects[i]['pos'] = np.mod(np.asarray(defects[i]['pos'], dtype=np.int64) + JUMPS[j],
                                    2 * np.asarray(n))
     return moves
+
+
+# --------------------------------------------------------------------------
+# the paper's translation of a defect's field by the shift theorem (Sec. 3.3, Eq. shift):
+# the elastic strain spectrum of the defect at a reference site is stored once and
+# moved to any (continuous) position X by exp(-i xi.(X - X0)); the energy is the paper
+# form of Eq. interaction_energy3, kappa int sigma_ext : eps^{d,e}(X) dV
+# --------------------------------------------------------------------------
+def elastic_strain_spectrum(d, n, h, C, k0_mode=MEAN_STRESS_ZERO):
+    """(X0 in nm, eps_hat (6, nx, ny, nz)): the defect alone at the class-0 reference site
+    pos = 0 (centre at the origin corner), its elastic strain C^-1 : sigma_d (engineering
+    shears halved to tensor components) and that field's transform."""
+    dd = as_record(d)
+    dd['pos'] = np.zeros(3, dtype=np.int64)
+    sig = solve_stress(eigenstrain_field([dd], n, h), C, h, k0_mode)
+    S = np.linalg.inv(stiffness_matrix(C))
+    eps = np.einsum('ab,b...->a...', S, sig)
+    eps[3:] *= 0.5
+    return np.zeros(3), np.fft.fftn(eps, axes=(-3, -2, -1))
+
+
+def shifted_field(eps_hat, shift, h):
+    """The field of eps_hat moved by `shift` (nm): Re ifft(exp(-i xi.shift) eps_hat)."""
+    n = eps_hat.shape[1:]
+    xs = [frequencies(n[a], n[a] * h) for a in range(3)]
+    ph = np.exp(-1j * (xs[0][:, None, None] * shift[0] + xs[1][None, :, None] * shift[1]
+                       + xs[2][None, None, :] * shift[2]))
+    return np.fft.ifftn(eps_hat * ph[None], axes=(-3, -2, -1)).real
+
+
+def energy_shift_theorem(eps_ref, X, sigma_ext, h):
+    """kappa int sigma_ext : eps^{d,e}(X) dV with the defect's elastic strain moved from
+    the reference site to X (nm) by Eq. shift, summed by Parseval:
+      (h^3 / N) Re sum_xi conj(sigma_ext_hat) : eps_hat exp(-i xi.(X - X0))."""
+    X0, eps_hat = eps_ref
+    n = sigma_ext.shape[1:]
+    xs = [frequencies(n[a], n[a] * h) for a in range(3)]
+    dX = np.asarray(X, float) - X0
+    ph = np.exp(-1j * (xs[0][:, None, None] * dX[0] + xs[1][None, :, None] * dX[1]
+                       + xs[2][None, None, :] * dX[2]))
+    sh = np.fft.fftn(sigma_ext, axes=(-3, -2, -1))
+    return KAPPA * h ** 3 / np.prod(n) * float(np.sum(ddot6(np.conj(sh), eps_hat * ph[None])).real)
 
 
 # --------------------------------------------------------------------------

@@ -608,3 +608,46 @@ def test_fdm_loop_approaches_slab_loop_with_resolution():
         gaps.append(np.linalg.norm(s_slab[:, m] - s_fdm[:, m]) / np.linalg.norm(s_slab[:, m]))
     assert gaps[0] > gaps[1] > gaps[2], gaps
     assert gaps[2] < 0.35, gaps
+
+
+# ---------------------------------------------------------------- shift theorem (Sec. 3.3, Eq. shift)
+def _paper_form_direct(d, i, n, C):
+    """kappa int sigma_ext : eps^{i,e} with defect i rasterised at its position."""
+    s_ext = O.solve_stress(O.eigenstrain_field(d, n, H, exclude={i}), C, H)
+    s_i = O.solve_stress(O.eigenstrain_field(d, n, H, only={i}), C, H)
+    S = np.linalg.inv(O.stiffness_matrix(C))
+    e = np.einsum('ab,b...->a...', S, s_i)
+    e[3:] *= 0.5
+    return s_ext, O.KAPPA * H ** 3 * np.sum(O.ddot6(s_ext, e))
+
+
+@pytest.mark.parametrize('n', [(15, 15, 15), (16, 16, 16)])
+def test_shift_theorem_whole_voxel_shift_equals_rasterised(n):
+    """A reference field moved by a whole-voxel vector (Eq. shift) is the defect rasterised
+    there: same paper-form energy; on odd edges also the eigenstrain-form energy."""
+    d = _defects_small()
+    E, _ = O.energies_bruteforce(d, n, H, C_CUBIC)
+    for i in (0, 2):                                  # class-0 sites
+        s_ext, e_dir = _paper_form_direct(d, i, n, C_CUBIC)
+        ref = O.elastic_strain_spectrum(d[i], n, H, C_CUBIC)
+        e_sh = O.energy_shift_theorem(ref, np.asarray(d[i]['pos']) * H / 2.0, s_ext, H)
+        assert abs(e_sh - e_dir) <= 1e-10 * max(1.0, abs(e_dir))
+        if n[0] % 2:
+            assert abs(e_sh - E[i]) <= 1e-10 * max(1.0, abs(E[i]))
+
+
+def test_shift_theorem_routes_agree_and_uniform_field_is_position_independent():
+    """At continuous positions the Parseval sum equals the explicit inverse transform of
+    the moved field, and in a uniform external stress the energy does not depend on X."""
+    n = (16, 16, 16)
+    d = _defects_small()
+    ref = O.elastic_strain_spectrum(d[0], n, H, C_CUBIC)
+    s_ext = O.solve_stress(O.eigenstrain_field(d, n, H, exclude={0}), C_CUBIC, H)
+    rng = np.random.default_rng(5)
+    for X in rng.uniform(0.0, 16 * H, size=(3, 3)):
+        e1 = O.energy_shift_theorem(ref, X, s_ext, H)
+        e2 = O.KAPPA * H ** 3 * np.sum(O.ddot6(s_ext, O.shifted_field(ref[1], X - ref[0], H)))
+        assert abs(e1 - e2) <= 1e-10 * max(1.0, abs(e1))
+    uniform = np.broadcast_to(np.array([1.0, -0.5, 0.3, 0.2, -0.1, 0.4])[:, None, None, None], (6,) + n).copy()
+    vals = [O.energy_shift_theorem(ref, X, uniform, H) for X in rng.uniform(0.0, 16 * H, size=(4, 3))]
+    assert max(vals) - min(vals) <= 1e-12 * max(1.0, abs(vals[0]))
