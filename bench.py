@@ -270,6 +270,67 @@ def run_dipole(args):
     return 0
 
 
+def run_kinetics(args):
+    """The paper's two-loop kinetics (Sec. 5.1): two 1/2<111> loops 10 nm apart across
+    their glide axis and x_rel = 10 nm (inside the attraction well) or 20 nm (outside it)
+    along it; 500 fixed-time-step steps (Algorithm 1, dt from the nominal barrier) at
+    300 K, 10 runs per case as one batch of replicas with different seeds.  Reports the
+    mean and the envelope of both loops' coordinates along [111] against time."""
+    import torch
+
+    from paper_2403_09158_gb300 import okmc as ok
+    from paper_2403_09158_gb300.workload import config_kinetics
+
+    runs, steps, every = 10, 500, 10
+    stream = torch.cuda.current_stream()
+    clk = Clocks(torch.cuda.current_device())
+    cases = []
+    t_total = 0.0
+    for x_rel in (10.0, 20.0):
+        w = config_kinetics(x_rel)
+        unit = 0.5 * w.voxel_nm
+        grids = []
+        for r in range(runs):
+            g = ok.Grid(w.n, w.voxel_nm, *w.C, seed=2000 + r, stream=stream.cuda_stream)
+            g.set_defects(w.defects)
+            grids.append(g)
+        batch = ok.Batch(grids, stream=stream.cuda_stream)
+        p0 = grids[0].get_positions().astype(np.int64)
+        tr = np.zeros((runs, steps // every + 1, 2))          # loop coordinates along [111], nm
+        clock = np.zeros((runs, steps // every + 1))
+        for r in range(runs):
+            tr[r, 0] = (p0 @ np.ones(3)) * unit / math.sqrt(3.0)
+        t0 = time.perf_counter()
+        for k in range(1, steps // every + 1):
+            st = batch.step(w.T_K, every, mode=ok.FIXED_DT)
+            for r, g in enumerate(grids):
+                p = g.get_positions().astype(np.int64)
+                d = p - p0
+                d -= np.round(d / (2.0 * np.asarray(w.n))).astype(np.int64) * 2 * np.asarray(w.n)   # unwrap
+                tr[r, k] = ((p0 + d) @ np.ones(3)) * unit / math.sqrt(3.0)
+                clock[r, k] = st[r]['clock']
+        torch.cuda.synchronize()
+        t_total += time.perf_counter() - t0
+        batch.close()
+        for g in grids:
+            g.close()
+        rel = tr[:, :, 1] - tr[:, :, 0]
+        cases.append({'x_rel_nm': w.extra['x_rel_nm'], 'z_rel_nm': w.extra['z_rel_nm'],
+                      'time_ns': (clock.mean(axis=0) * 1e9).tolist(),
+                      'x1_mean_nm': tr[:, :, 0].mean(axis=0).tolist(), 'x2_mean_nm': tr[:, :, 1].mean(axis=0).tolist(),
+                      'x1_envelope_nm': [tr[:, :, 0].min(axis=0).tolist(), tr[:, :, 0].max(axis=0).tolist()],
+                      'x2_envelope_nm': [tr[:, :, 1].min(axis=0).tolist(), tr[:, :, 1].max(axis=0).tolist()],
+                      'x_rel_final_mean_nm': float(rel[:, -1].mean()), 'x_rel_final_min_max_nm': [float(rel[:, -1].min()),
+                                                                                             float(rel[:, -1].max())]})
+    out = {'metric': 'two-loop kinetics, loop coordinates along [111] against time', 'unit': 'nm',
+           'data': 'synthetic', 'dtype': 'f32 fields / f64 energies',
+           'config': {'workload': 'kinetics_two_loops_256cubed (1/2<111> loops R = 3.3 nm, E_m = 0.1 eV, 300 K, '
+                                  'Table 1 constants, 500 fixed-dt steps, 10 runs per case)'},
+           'cases': cases, 'seconds': t_total, 'clocks': clk.stop()}
+    print(json.dumps(out))
+    return 0
+
+
 def run_config(args, which):
     """The small (32^3, FP64 fields) and medium (128^3, FP32 fields beside the FP64 GPU
     path) workloads: residence-time steps per second and the latency of one
@@ -514,7 +575,8 @@ def main():
     ap.add_argument('--warmup', type=int, default=5)
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--workload', default='large', choices=['large', 'batch', 'serve', 'small', 'medium', 'dipole'],
+    ap.add_argument('--workload', default='large', choices=['large', 'batch', 'serve', 'small', 'medium', 'dipole',
+                                                            'kinetics'],
                     help='large: the 256^3 single-replica step (default); batch: the 64-replica ensemble; '
                          'serve: the request server under Poisson load; small / medium: the 32^3 FP64 and '
                          'the 128^3 workloads')
@@ -542,6 +604,8 @@ def main():
         return run_config(args, args.workload) if rank == 0 else 0
     if args.workload == 'dipole':
         return run_dipole(args) if rank == 0 else 0
+    if args.workload == 'kinetics':
+        return run_kinetics(args) if rank == 0 else 0
     r = run_ours(args, ws, rank)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -205,6 +205,24 @@ def _placed_population(n, nd, seed, r111, r100):
             nd = max(1, int(nd * 0.9))
 
 
+def config_kinetics(x_rel_nm, n=256, h=VOXEL_NM, z_rel_nm=10.0, R_nm=3.3, T_K=300.0):
+    """The paper's two-loop kinetics setting (Sec. 5.1): two 1/2<111> loops of radius
+    3.3 nm (the loops of Sec. 4), Burgers vectors, normals and glide along [111] (the
+    paper's x axis), separated by z_rel across the glide axis along [1-10] (the paper's
+    z) and by x_rel along it; E_m = 0.1 eV, 300 K, the elastic constants of Table 1.
+    Loop 1 sits at the box centre; both positions are bcc sites in units of a0/2."""
+    unit = 0.5 * h                                   # a0/2 in nm
+    kz = 2 * int(round(z_rel_nm / (unit * math.sqrt(2.0)) / 2.0))   # even: keeps the parity
+    kx = int(round(x_rel_nm / (unit * math.sqrt(3.0))))
+    c0 = np.array([n, n, n])
+    p2 = c0 + np.array([kz, -kz, 0]) + kx
+    defs = make_defects([LOOP_111, LOOP_111], np.array([c0, p2]), [0, 0], [R_nm, R_nm], [0, 0], [0.1, 0.1],
+                        [ONE_D, ONE_D])
+    return Workload(name='kinetics_two_loops_x%.0fA' % (10 * x_rel_nm), n=(n, n, n), voxel_nm=h, defects=defs,
+                    T_K=T_K, C=FE_TABLE1,
+                    extra={'x_rel_nm': kx * unit * math.sqrt(3.0), 'z_rel_nm': kz * unit * math.sqrt(2.0)})
+
+
 def config_batch(seed=1004, n_replicas=64, edges=(64, 96, 128, 160, 192), nd_range=(50, 800),
                  T_range=(300.0, 600.0)):
     """Ensemble of independent replicas: edge ~ U(edges), defect count ~ U{50..800}

@@ -137,3 +137,24 @@ def test_isotropic_stiffness_matches_the_lame_relations(lib):
     for mu, nu in ((0.0, 0.3), (-1.0, 0.3), (80.0, 0.5), (80.0, -1.0), (float('nan'), 0.3)):
         with pytest.raises(ok.OkmcError):
             ok.isotropic_stiffness(mu, nu)
+
+
+def test_kinetics_workload_geometry():
+    """The two-loop kinetics setting (Sec. 5.1): both loops on bcc sites (all three
+    half-lattice coordinates of one parity), 1D glide along [111], separated by about
+    10 nm along [1-10] and by x_rel along [111]."""
+    from paper_2403_09158_gb300.workload import LOOP_111, ONE_D, config_kinetics
+    for x_rel in (10.0, 20.0):
+        w = config_kinetics(x_rel)
+        d = w.defects
+        assert list(d['type']) == [LOOP_111, LOOP_111] and list(d['mobility']) == [ONE_D, ONE_D]
+        assert list(d['axis']) == [0, 0] and np.allclose(d['radius_nm'], 3.3) and np.allclose(d['Em_eV'], 0.1)
+        for p in d['pos']:
+            assert len({int(v) % 2 for v in p}) == 1
+            assert np.all((p >= 0) & (p < 2 * np.asarray(w.n)))
+        sep = (d['pos'][1] - d['pos'][0]) * 0.5 * w.voxel_nm
+        along = sep @ np.ones(3) / np.sqrt(3.0)
+        across = sep @ np.array([1.0, -1.0, 0.0]) / np.sqrt(2.0)
+        assert abs(along - x_rel) < 0.25 and abs(across - 10.0) < 0.25
+        assert abs(sep @ np.array([1.0, 1.0, -2.0])) < 1e-12       # no offset along [11-2]
+        assert np.isclose(w.extra['x_rel_nm'], along) and np.isclose(w.extra['z_rel_nm'], across)
