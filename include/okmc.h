@@ -134,6 +134,31 @@ int okmc_set_stream(okmc_grid* g, void* stream);
  * half the grid), ENOMEM, ECUDA. */
 int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t n);
 
+/* Immobile dislocation lines as eigenstrain, by static field dislocation mechanics
+ * (Sec. 2.2: Eqs. curlUe, Nye2, eq_EIG_fourier, plastic_0).  On the device: the Nye
+ * tensor alpha_ij = b_i t_j ds / h^3 of every sub-segment (each segment cut into
+ * ceil(L / ds_max) equal parts) spread to the 8 voxel centres (i + 1/2) h around the
+ * sub-segment's midpoint with trilinear weights; the incompatible plastic distortion
+ * U_ij = -i xi_k / |xi|^2 eps_jkl alpha_il at xi != 0; at xi = 0 the compatible part
+ * sum over closed lines of (b (x) A + A (x) b) / (2 V), with A = -1/2 sum x_a x x_{a+1}
+ * (a closed line runs clockwise seen from the tip of its oriented area); the symmetric
+ * part, rounded to the grid's eigenstrain quantum, is kept as a background to which the
+ * defects' eigenstrain is added from then on (okmc_set_defects keeps it; the stress,
+ * the energies and the kinetics see the lines' field; the lines do not move).  On a
+ * Nyquist plane the operator is averaged over the sign of the Nyquist component.
+ * points: double[sum counts][3], vertices in nm, the lines one after another (host).
+ * counts[n_lines]: vertices per line (>= 2; >= 3 when closed).  closed[n_lines]: 1 for
+ * a loop (its last vertex joins its first), 0 for an open line (an open line whose
+ * last vertex is a lattice translate of its first is one period of an infinite line;
+ * a net Burgers vector drops out with the xi = 0 term).  burgers: double[n_lines][3]
+ * in nm.  ds_max_nm: largest sub-segment length (<= 0 selects h/4).  n_lines = 0
+ * removes the background.  Temporary device memory: 9 N int64 and a nine-component
+ * half spectrum.  Errors: EINVAL (counts, closed flags, non-finite or coincident
+ * vertices, too many sub-segments), ENOMEM, ERANGE (the plastic strain leaves the
+ * fixed-point range), ECUDA; on error the background is removed. */
+int okmc_set_dislocations(okmc_grid* g, const double* points, const int32_t* counts, const int32_t* closed,
+                          const double* burgers, int32_t n_lines, double ds_max_nm);
+
 /* Copy the current defect records (positions included) to host memory. */
 int okmc_get_defects(okmc_grid* g, okmc_defect* out, int32_t n);
 

@@ -72,6 +72,13 @@ cudaError_t launch_dipole_energies(const T* sig, int3 n, const okmc_defect* def,
                                    double h3, double* E, double* Ec, cudaStream_t st);
 cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st);
 int pencil_variant_mask(const PassCfg& c);
+template <class T> int fdm_pencil_tile(int ny, int nz, size_t limit);
+template <class T, class Q>
+cudaError_t launch_dislocation_eigenstrain(const double* pts, const int2* seg, const int* seg_line, int nseg,
+                                           const int* first, const int* closed, const double* burgers, double* area,
+                                           int nl, double ds_max, const PassCfg& c0, double h, int tw,
+                                           unsigned long long* alpha_q, C2<T>* spec, Q* bg, double q, double qlim,
+                                           int* err, cudaStream_t st);
 }  // namespace okmc
 
 namespace {
@@ -149,6 +156,7 @@ struct okmc_grid {
   int* d_dl = nullptr;                  // [4 nd]: start and end of each dilated candidate list
   int* d_doff = nullptr;                // dilated lists: packed offsets
   unsigned long long* d_dcnt = nullptr; // dilated lists: eight candidate counts
+  void* d_bg = nullptr;     // [6][nz][ny][nx] fixed-point plastic strain of the dislocation lines (or none)
   std::vector<okmc_defect> h_def;
   bool sigma_valid = false;
   bool any_mobile = false;
@@ -546,7 +554,9 @@ int build_dilated_lists(okmc_grid* g) {
 }
 
 int voxelise_all(okmc_grid* g) {
-  cudaError_t e = cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st);
+  // the defects' stencils are added to the dislocation lines' plastic strain, if any
+  cudaError_t e = g->d_bg ? cudaMemcpyAsync(g->eps, g->d_bg, 6 * g->N * qsize(g), cudaMemcpyDeviceToDevice, g->st)
+                          : cudaMemsetAsync(g->eps, 0, 6 * g->N * qsize(g), g->st);
   // every plane transform is stale (the self-term build also used spec as scratch)
   if (e == cudaSuccess) e = cudaMemsetAsync(g->d_dirty, 1, sizeof(int) * 6 * g->n[2], g->st);
   if (e != cudaSuccess) return cuda_fail(g, e, "memset");
@@ -1135,6 +1145,121 @@ int okmc_dipole_self_terms(okmc_grid* g, double* D, int out_on_device) {
   if (!g->nd) return OKMC_OK;
   OKMC_TRY(ensure_dipole_tables(g));
   return copy_out(g, D, g->d_D, g->nd * 18 * sizeof(double), out_on_device);
+}
+
+int okmc_set_dislocations(okmc_grid* g, const double* points, const int32_t* counts, const int32_t* closed,
+                          const double* burgers, int32_t n_lines, double ds_max_nm) {
+  if (!g) return OKMC_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);
+  if (n_lines < 0 || (n_lines > 0 && (!points || !counts || !closed || !burgers)))
+    return fail(g, OKMC_EINVAL, "bad dislocation arrays");
+  if (!(ds_max_nm <= 0.0) && !(ds_max_nm > 0.0 && std::isfinite(ds_max_nm))) return fail(g, OKMC_EINVAL, "bad ds_max_nm");
+  const double ds = ds_max_nm > 0.0 ? ds_max_nm : 0.25 * g->h;
+  try {
+    // host side: argument checks and the segment index (vertex pairs), nothing else
+    std::vector<int> first(n_lines + 1, 0), flag(n_lines), seg_line;
+    std::vector<int2> seg;
+    double sub = 0.0;
+    for (int l = 0; l < n_lines; ++l) {
+      if (counts[l] < 2 || (closed[l] != 0 && closed[l] != 1) || (closed[l] && counts[l] < 3))
+        return fail(g, OKMC_EINVAL, "a line needs 2 vertices (3 when closed) and closed in {0, 1}");
+      if ((long long)first[l] + counts[l] > (1ll << 28)) return fail(g, OKMC_EINVAL, "too many vertices");
+      first[l + 1] = first[l] + counts[l];
+      flag[l] = closed[l];
+      for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(burgers[3 * l + a])) return fail(g, OKMC_EINVAL, "non-finite Burgers vector");
+    }
+    const int np = first[n_lines];
+    for (long long k = 0; k < 3ll * np; ++k)
+      if (!std::isfinite(points[k]) || std::fabs(points[k]) > 1e9) return fail(g, OKMC_EINVAL, "non-finite vertex");
+    for (int l = 0; l < n_lines; ++l) {
+      const int a0 = first[l], a1 = first[l + 1];
+      const int ns = closed[l] ? counts[l] : counts[l] - 1;
+      for (int k = 0; k < ns; ++k) {
+        const int a = a0 + k, b = (a + 1 < a1) ? a + 1 : a0;
+        const double dx = points[3 * b] - points[3 * a], dy = points[3 * b + 1] - points[3 * a + 1],
+                     dz = points[3 * b + 2] - points[3 * a + 2];
+        const double L = std::sqrt(dx * dx + dy * dy + dz * dz);
+        if (!(L > 0.0)) return fail(g, OKMC_EINVAL, "zero-length segment");
+        sub += std::ceil(L / ds) + 1.0;
+        seg.push_back(make_int2(a, b));
+        seg_line.push_back(l);
+      }
+    }
+    if (sub > 1e9 || seg.size() > 0x7fffffffu) return fail(g, OKMC_EINVAL, "too many sub-segments");
+    cudaStreamSynchronize(g->st);
+    drop_graphs(g);
+    g->gen += 1;
+    dfree(g, g->d_bg);
+    g->d_bg = nullptr;
+    if (n_lines == 0) {
+      OKMC_TRY(voxelise_all(g));
+      return check_device_error(g);
+    }
+    const size_t N = g->N;
+    const size_t nspec = 9 * (size_t)g->n[2] * g->P * 2 * tsize(g);
+    const int tw = fp64(g) ? fdm_pencil_tile<double>(g->n[1], g->n[2], kSmemLimit)
+                           : fdm_pencil_tile<float>(g->n[1], g->n[2], kSmemLimit);
+    if (!tw) return fail(g, OKMC_EINVAL, "no pencil tile fits shared memory");
+    double *d_pts = nullptr, *d_b = nullptr, *d_area = nullptr;
+    int2* d_seg = nullptr;
+    int *d_segl = nullptr, *d_first = nullptr, *d_closed = nullptr;
+    unsigned long long* d_aq = nullptr;
+    void* d_spec = nullptr;
+    auto release = [&] {
+      void* t[] = {d_pts, d_b, d_area, d_seg, d_segl, d_first, d_closed, d_aq, d_spec};
+      for (void* p : t) dfree(g, p);
+    };
+    int rc = OKMC_OK;
+    auto bail = [&](int code) {
+      release();
+      dfree(g, g->d_bg);
+      g->d_bg = nullptr;
+      voxelise_all(g);
+      return code;
+    };
+    if ((rc = dalloc(g, (void**)&d_pts, 3 * (size_t)np * sizeof(double))) ||
+        (rc = dalloc(g, (void**)&d_b, 3 * (size_t)n_lines * sizeof(double))) ||
+        (rc = dalloc(g, (void**)&d_area, 3 * (size_t)n_lines * sizeof(double))) ||
+        (rc = dalloc(g, (void**)&d_seg, seg.size() * sizeof(int2))) ||
+        (rc = dalloc(g, (void**)&d_segl, seg.size() * sizeof(int))) ||
+        (rc = dalloc(g, (void**)&d_first, first.size() * sizeof(int))) ||
+        (rc = dalloc(g, (void**)&d_closed, flag.size() * sizeof(int))) ||
+        (rc = dalloc(g, (void**)&d_aq, 9 * N * sizeof(unsigned long long))) || (rc = dalloc(g, &d_spec, nspec)) ||
+        (rc = dalloc(g, &g->d_bg, 6 * N * qsize(g))))
+      return bail(rc);
+    cudaError_t e = cudaMemcpyAsync(d_pts, points, 3 * (size_t)np * sizeof(double), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_b, burgers, 3 * (size_t)n_lines * sizeof(double), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess && !seg.empty())
+      e = cudaMemcpyAsync(d_seg, seg.data(), seg.size() * sizeof(int2), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess && !seg.empty())
+      e = cudaMemcpyAsync(d_segl, seg_line.data(), seg_line.size() * sizeof(int), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_first, first.data(), first.size() * sizeof(int), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_closed, flag.data(), flag.size() * sizeof(int), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st);
+    if (e != cudaSuccess) {
+      cuda_fail(g, e, "dislocation upload");
+      return bail(OKMC_ECUDA);
+    }
+    rc = run(g, "dislocation_eigenstrain", [&] {
+      if (fp64(g))
+        return launch_dislocation_eigenstrain<double, int64_t>(d_pts, d_seg, d_segl, (int)seg.size(), d_first, d_closed, d_b,
+                                                               d_area, n_lines, ds, g->cfg, g->h, tw, d_aq,
+                                                               (C2<double>*)d_spec, (int64_t*)g->d_bg, quantum(g), qlimit(g),
+                                                               g->d_err, g->st);
+      return launch_dislocation_eigenstrain<float, int32_t>(d_pts, d_seg, d_segl, (int)seg.size(), d_first, d_closed, d_b,
+                                                            d_area, n_lines, ds, g->cfg, g->h, tw, d_aq,
+                                                            (C2<float>*)d_spec, (int32_t*)g->d_bg, quantum(g), qlimit(g),
+                                                            g->d_err, g->st);
+    });
+    if (rc) return bail(rc);
+    if ((rc = check_device_error(g))) return bail(rc);
+    release();
+    OKMC_TRY(voxelise_all(g));
+    return check_device_error(g);
+  } catch (const std::bad_alloc&) {
+    return fail(g, OKMC_ENOMEM, "host allocation failed");
+  }
 }
 
 int okmc_self_terms(okmc_grid* g, double* W, int out_on_device) {

@@ -52,6 +52,17 @@ struct RowSrcQ<double, int64_t> {
   }
 };
 
+// FP32 transforms of an int64 fixed-point input (the Nye tensor of dislocation lines)
+template <>
+struct RowSrcQ<float, int64_t> {
+  const int64_t* p;
+  float q;
+  __device__ __forceinline__ C2<float> ld(int i) const {
+    const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(p) + i);
+    return {__ll2float_rn(v.x) * q, __ll2float_rn(v.y) * q};
+  }
+};
+
 // ---------------------------------------------------------------- smem layout
 template <class T>
 struct PlaneSmem {
@@ -330,6 +341,7 @@ cudaError_t launch_pencil(C2<T>* spec, const PassCfg& c, cudaStream_t st) {
 
 template cudaError_t launch_plane_fwd<float, int32_t>(const int32_t*, C2<float>*, const PassCfg&, cudaStream_t);
 template cudaError_t launch_plane_fwd<double, int64_t>(const int64_t*, C2<double>*, const PassCfg&, cudaStream_t);
+template cudaError_t launch_plane_fwd<float, int64_t>(const int64_t*, C2<float>*, const PassCfg&, cudaStream_t);
 template cudaError_t launch_plane_inv<float>(const C2<float>*, float*, const PassCfg&, cudaStream_t);
 template cudaError_t launch_plane_inv<double>(const C2<double>*, double*, const PassCfg&, cudaStream_t);
 template cudaError_t launch_pencil<float>(C2<float>*, const PassCfg&, cudaStream_t);

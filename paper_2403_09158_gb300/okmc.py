@@ -33,7 +33,7 @@ EXPORTED = [
     'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_get_variants', 'okmc_set_variant',
     'okmc_set_kinetic_state', 'okmc_estimate_field_bytes', 'okmc_server_create', 'okmc_server_add_replica',
     'okmc_server_submit', 'okmc_server_wait', 'okmc_server_get_stats', 'okmc_server_last_error', 'okmc_server_destroy',
-    'okmc_isotropic_stiffness',
+    'okmc_isotropic_stiffness', 'okmc_set_dislocations',
 ]
 
 
@@ -109,6 +109,7 @@ def load(path=LIB_PATH):
         'okmc_interaction_energies': (C.c_int, [vp, dp, C.c_int]),
         'okmc_candidate_energies': (C.c_int, [vp, dp, dp, C.c_int]),
         'okmc_self_terms': (C.c_int, [vp, dp, C.c_int]),
+        'okmc_set_dislocations': (C.c_int, [vp, dp, dp, dp, dp, i32, C.c_double]),
         'okmc_dipole_energies': (C.c_int, [vp, dp, dp, C.c_int]),
         'okmc_dipole_self_terms': (C.c_int, [vp, dp, C.c_int]),
         'okmc_get_stencil': (C.c_int, [vp, i32, i32, dp, dp, i32, C.POINTER(i32), C.POINTER(C.c_double)]),
@@ -253,6 +254,19 @@ class Grid:
         v, _ = _ptr(valid)
         self._chk(self.lib.okmc_candidate_energies(self.h, p, v, dev))
         return out, valid
+
+    def set_dislocations(self, lines, ds_max_nm=0.0):
+        """Immobile dislocation lines (okmc_set_dislocations): `lines` is a list of
+        (points (m, 3) nm, burgers (3,) nm, closed) tuples; [] removes them."""
+        pts = np.ascontiguousarray(np.concatenate([np.asarray(p, np.float64).reshape(-1, 3) for p, _, _ in lines])
+                                   if lines else np.zeros((0, 3)), dtype=np.float64)
+        cnt = np.ascontiguousarray([len(np.asarray(p).reshape(-1, 3)) for p, _, _ in lines], dtype=np.int32)
+        cl = np.ascontiguousarray([1 if c else 0 for _, _, c in lines], dtype=np.int32)
+        b = np.ascontiguousarray(np.asarray([bv for _, bv, _ in lines], np.float64).reshape(-1, 3))
+        n = len(lines)
+        self._chk(self.lib.okmc_set_dislocations(self.h, pts.ctypes.data if n else None, cnt.ctypes.data if n else None,
+                                                 cl.ctypes.data if n else None, b.ctypes.data if n else None, n,
+                                                 float(ds_max_nm)))
 
     def self_terms(self):
         out = np.zeros((self.nd, 2, 9))

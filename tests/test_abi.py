@@ -83,6 +83,7 @@ def test_null_handle_errors_without_gpu(lib):
     assert lib.okmc_grid_destroy(None) == ok.OKMC_OK
     assert lib.okmc_last_error(None) == b'null handle'
     assert lib.okmc_solve_stress(None, None, 0) == ok.OKMC_EINVAL
+    assert lib.okmc_set_dislocations(None, None, None, None, None, 0, 0.0) == ok.OKMC_EINVAL
     d = ok.GridDesc()
     d.n[:] = (20, 32, 32)       # 20 is not a multiple of 16
     d.voxel_nm, d.C11, d.C12, d.C44 = 0.2855, 243.0, 145.0, 116.0

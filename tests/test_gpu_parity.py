@@ -515,3 +515,89 @@ def test_batch_replicas_equal_alone():
     batch.close()
     for g in grids:
         g.close()
+
+
+# ------------------------------------------------------------------ dislocation lines (field dislocation mechanics)
+def _dislocation_case(n, h):
+    """A clockwise 1/2[111] loop (off-grid centre, 48 vertices) and one period of a
+    straight mixed dislocation along y, with their Burgers vectors."""
+    n111 = np.ones(3) / np.sqrt(3.0)
+    L = np.asarray(n) * h
+    loop = O.circle_points(np.array([0.41, 0.37, 0.52]) * L, n111, 1.1, 48)[::-1]
+    line = np.array([[0.2 * L[0], 0.3, 0.6 * L[2]], [0.2 * L[0], 0.3 + L[1], 0.6 * L[2]]])
+    return [(loop, 0.5 * h * np.ones(3), True), (line, 0.5 * h * np.array([1.0, -1.0, 1.0]), False)]
+
+
+def _oracle_dislocation_eigenstrain(lines, n, h, ds_max):
+    """Nye tensor of every line (Eq. Nye2), Eq. eq_EIG_fourier with Eq. plastic_0 at xi = 0
+    for the closed ones: A = -1/2 sum x_a x x_{a+1} for a line running clockwise about A."""
+    alpha = sum(O.nye_tensor(p, b, n, h, closed=c, ds_max=ds_max) for p, b, c in lines)
+    V = np.prod(n) * h ** 3
+    U0 = np.zeros((3, 3))
+    for p, b, c in lines:
+        if c:
+            A = -0.5 * np.sum(np.cross(p, np.roll(p, -1, axis=0)), axis=0)
+            U0 += (np.outer(b, A) + np.outer(A, b)) / (2.0 * V)
+    return O.dislocation_eigenstrain6(alpha, h, U0)
+
+
+@pytest.mark.parametrize('precision,n', [(ok.FP64_FIELDS, (32, 48, 32)), (ok.FP32_FIELDS, (32, 48, 32)),
+                                         (ok.FP32_FIELDS, (64, 64, 64))])
+def test_dislocation_eigenstrain_stress_and_energies_match_oracle(precision, n):
+    """Plastic strain of dislocation lines (Eqs. Nye2, eq_EIG_fourier, plastic_0), its
+    stress, and the energies of defects in the lines' field, against the oracle."""
+    h, ds_max = 0.2855, 0.27 * 0.2855   # ds_max keeps L / ds_max away from integers
+    lines = _dislocation_case(n, h)
+    eps_d = _oracle_dislocation_eigenstrain(lines, n, h, ds_max)
+    C = O.stiffness_cubic(*FE_CUBIC)
+    g = ok.Grid(n, h, *FE_CUBIC, precision=precision, seed=3)
+    g.set_dislocations(lines, ds_max_nm=ds_max)
+    eps = g.eigenstrain()
+    ref = zyx(eps_d)
+    if precision == ok.FP64_FIELDS:
+        assert np.abs(eps - ref).max() <= 1e-9 * np.abs(ref).max()
+    else:
+        assert rel_l2(eps, ref) <= 1e-5 and np.abs(eps - ref).max() <= 1e-5 * np.abs(ref).max()
+    sig_o = O.solve_stress(eps_d, C, h)
+    assert rel_l2(g.solve_stress(), zyx(sig_o)) <= STRESS_TOL[precision]
+    # two defects in the lines' field: E_i from sigma of (lines + the other defect)
+    defs = make_defects([O.LOOP_111, O.SIA_CLUSTER], np.array([[24, 60, 16], [41, 21, 47]]), [1, 0], [0.6, 0.0],
+                        [0, 3], [0.1, 0.3], [1, 2])
+    g.set_defects(defs)
+    E, Ec = g.interaction_energies(), g.candidate_energies()[0]
+    for i in range(2):
+        sig = O.solve_stress(O.eigenstrain_field(defs, n, h, exclude={i}) + eps_d, C, h)
+        assert abs(E[i] - O.energy_of_stencil(defs[i], defs[i]['pos'], sig, h)) <= ENERGY_TOL[precision]
+        eco = [O.energy_of_stencil(defs[i], Y, sig, h) for Y in O.candidate_positions(defs[i]['pos'])]
+        assert np.abs(Ec[i] - eco).max() <= ENERGY_TOL[precision]
+    g.close()
+
+
+def test_dislocation_background_survives_steps_and_can_be_removed():
+    """The lines' plastic strain stays under the incremental updates of a trajectory:
+    after steps, the field equals a fresh grid's with the defects at their new sites,
+    whichever of set_dislocations and set_defects came first; removing the lines leaves
+    the defects' field alone."""
+    n, h = (64, 64, 64), 0.2855
+    lines = _dislocation_case(n, h)
+    defs = make_defects([O.LOOP_111, O.SIA_CLUSTER, O.SIA_CLUSTER],
+                        np.array([[40, 64, 90], [81, 41, 21], [20, 100, 60]]), [0, 1, 2], [0.8, 0.0, 0.0],
+                        [0, 2, 1], [0.1, 0.3, 0.3], [1, 2, 2])
+    a = ok.Grid(n, h, *FE_CUBIC, seed=5)
+    a.set_dislocations(lines)
+    a.set_defects(defs)
+    a.step(300.0, 30)
+    moved = defs.copy()
+    moved['pos'] = a.get_positions()
+    assert not np.array_equal(moved['pos'], defs['pos'])
+    b = ok.Grid(n, h, *FE_CUBIC, seed=5)
+    b.set_defects(moved)
+    b.set_dislocations(lines)
+    assert np.array_equal(a.eigenstrain(), b.eigenstrain())
+    assert np.array_equal(a.interaction_energies(), b.interaction_energies())
+    a.set_dislocations([])
+    c = ok.Grid(n, h, *FE_CUBIC, seed=5)
+    c.set_defects(moved)
+    assert np.array_equal(a.eigenstrain(), c.eigenstrain())
+    for x in (a, b, c):
+        x.close()
