@@ -270,6 +270,51 @@ def run_dipole(args):
     return 0
 
 
+def _loop_ensemble(ok, w, runs, steps, every, stream, lines=None):
+    """`runs` seeded replicas of workload w (optionally in the field of immobile
+    dislocation lines) advanced as one batch by `steps` fixed-time-step steps (Algorithm
+    1); every `every` steps the loops' coordinates along [111] (unwrapped, nm) and the
+    clock.  Returns (trajectories (runs, K, n_defects), clock (runs, K), seconds)."""
+    import torch
+
+    unit = 0.5 * w.voxel_nm
+    grids = []
+    for r in range(runs):
+        g = ok.Grid(w.n, w.voxel_nm, *w.C, seed=2000 + r, stream=stream.cuda_stream)
+        if lines:
+            g.set_dislocations(lines)
+        g.set_defects(w.defects)
+        grids.append(g)
+    batch = ok.Batch(grids, stream=stream.cuda_stream)
+    p0 = grids[0].get_positions().astype(np.int64)
+    tr = np.zeros((runs, steps // every + 1, len(w.defects)))
+    clock = np.zeros((runs, steps // every + 1))
+    tr[:, 0] = (p0 @ np.ones(3)) * unit / math.sqrt(3.0)
+    box = 2 * np.asarray(w.n)
+    t0 = time.perf_counter()
+    for k in range(1, steps // every + 1):
+        st = batch.step(w.T_K, every, mode=ok.FIXED_DT)
+        for r, g in enumerate(grids):
+            d = g.get_positions().astype(np.int64) - p0
+            d -= np.round(d / box).astype(np.int64) * box          # unwrap the periodic moves
+            tr[r, k] = ((p0 + d) @ np.ones(3)) * unit / math.sqrt(3.0)
+            clock[r, k] = st[r]['clock']
+    torch.cuda.synchronize()
+    seconds = time.perf_counter() - t0
+    batch.close()
+    for g in grids:
+        g.close()
+    return tr, clock, seconds
+
+
+def _trajectory_summary(tr, clock):
+    out = {'time_ns': (clock.mean(axis=0) * 1e9).tolist()}
+    for i in range(tr.shape[2]):
+        out['x%d_mean_nm' % (i + 1)] = tr[:, :, i].mean(axis=0).tolist()
+        out['x%d_envelope_nm' % (i + 1)] = [tr[:, :, i].min(axis=0).tolist(), tr[:, :, i].max(axis=0).tolist()]
+    return out
+
+
 def run_kinetics(args):
     """The paper's two-loop kinetics (Sec. 5.1): two 1/2<111> loops 10 nm apart across
     their glide axis and x_rel = 10 nm (inside the attraction well) or 20 nm (outside it)
@@ -288,45 +333,76 @@ def run_kinetics(args):
     t_total = 0.0
     for x_rel in (10.0, 20.0):
         w = config_kinetics(x_rel)
-        unit = 0.5 * w.voxel_nm
-        grids = []
-        for r in range(runs):
-            g = ok.Grid(w.n, w.voxel_nm, *w.C, seed=2000 + r, stream=stream.cuda_stream)
-            g.set_defects(w.defects)
-            grids.append(g)
-        batch = ok.Batch(grids, stream=stream.cuda_stream)
-        p0 = grids[0].get_positions().astype(np.int64)
-        tr = np.zeros((runs, steps // every + 1, 2))          # loop coordinates along [111], nm
-        clock = np.zeros((runs, steps // every + 1))
-        for r in range(runs):
-            tr[r, 0] = (p0 @ np.ones(3)) * unit / math.sqrt(3.0)
-        t0 = time.perf_counter()
-        for k in range(1, steps // every + 1):
-            st = batch.step(w.T_K, every, mode=ok.FIXED_DT)
-            for r, g in enumerate(grids):
-                p = g.get_positions().astype(np.int64)
-                d = p - p0
-                d -= np.round(d / (2.0 * np.asarray(w.n))).astype(np.int64) * 2 * np.asarray(w.n)   # unwrap
-                tr[r, k] = ((p0 + d) @ np.ones(3)) * unit / math.sqrt(3.0)
-                clock[r, k] = st[r]['clock']
-        torch.cuda.synchronize()
-        t_total += time.perf_counter() - t0
-        batch.close()
-        for g in grids:
-            g.close()
+        tr, clock, sec = _loop_ensemble(ok, w, runs, steps, every, stream)
+        t_total += sec
         rel = tr[:, :, 1] - tr[:, :, 0]
-        cases.append({'x_rel_nm': w.extra['x_rel_nm'], 'z_rel_nm': w.extra['z_rel_nm'],
-                      'time_ns': (clock.mean(axis=0) * 1e9).tolist(),
-                      'x1_mean_nm': tr[:, :, 0].mean(axis=0).tolist(), 'x2_mean_nm': tr[:, :, 1].mean(axis=0).tolist(),
-                      'x1_envelope_nm': [tr[:, :, 0].min(axis=0).tolist(), tr[:, :, 0].max(axis=0).tolist()],
-                      'x2_envelope_nm': [tr[:, :, 1].min(axis=0).tolist(), tr[:, :, 1].max(axis=0).tolist()],
-                      'x_rel_final_mean_nm': float(rel[:, -1].mean()), 'x_rel_final_min_max_nm': [float(rel[:, -1].min()),
-                                                                                             float(rel[:, -1].max())]})
+        case = {'x_rel_nm': w.extra['x_rel_nm'], 'z_rel_nm': w.extra['z_rel_nm']}
+        case.update(_trajectory_summary(tr, clock))
+        case.update({'x_rel_final_mean_nm': float(rel[:, -1].mean()),
+                     'x_rel_final_min_max_nm': [float(rel[:, -1].min()), float(rel[:, -1].max())]})
+        cases.append(case)
     out = {'metric': 'two-loop kinetics, loop coordinates along [111] against time', 'unit': 'nm',
            'data': 'synthetic', 'dtype': 'f32 fields / f64 energies',
            'config': {'workload': 'kinetics_two_loops_256cubed (1/2<111> loops R = 3.3 nm, E_m = 0.1 eV, 300 K, '
                                   'Table 1 constants, 500 fixed-dt steps, 10 runs per case)'},
            'cases': cases, 'seconds': t_total, 'clocks': clk.stop()}
+    print(json.dumps(out))
+    return 0
+
+
+def run_dislocation(args):
+    """Loops near the paper's straight edge dislocation (line along [-1-12] through the
+    box centre, b = (a0/2)[111]; Secs. 4.3 and 5.2), 256^3, Table 1 constants.
+    (1) The interaction energy of one loop (R = 3.3 nm, 4.85 nm from the line along
+    [1-10]) with the dislocation against its position along [111], exact and in the
+    dipole approximation.  (2) Two loops on both sides of the line (z = -/+4.85 nm),
+    x_rel = 9.9 nm, centre of mass 20 or 30 nm from the line: 500 fixed-time-step steps
+    at 300 K, 10 runs per case, the loops' coordinates along [111] against time."""
+    import torch
+
+    from paper_2403_09158_gb300 import okmc as ok
+    from paper_2403_09158_gb300.workload import config_dislocation_loops
+
+    stream = torch.cuda.current_stream()
+    clk = Clocks(torch.cuda.current_device())
+    w = config_dislocation_loops(20.0)
+    lines = w.extra['lines']
+    # (1) energy profile of loop 2 alone
+    g = ok.Grid(w.n, w.voxel_nm, *w.C, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    g.set_dislocations(lines)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    one = w.defects[1:2].copy()
+    z_site = one['pos'][0] - (one['pos'][0] @ np.ones(3) - 3 * w.n[0]) // 3   # the site at x = 0 on loop 2's z line
+    one['pos'][0] = z_site
+    g.set_defects(one)
+    unit = 0.5 * w.voxel_nm
+    profile = []
+    for k in range(-100, 101, 4):
+        pos = (z_site + k).reshape(1, 3).astype(np.int32)
+        g.set_positions(pos)
+        E = float(g.interaction_energies()[0])
+        Ed = float(g.dipole_energies()[0][0])
+        x = float(((pos[0] - np.array(w.n)) @ np.ones(3)) * unit / math.sqrt(3.0))
+        profile.append([x, E, Ed])
+    g.close()
+    # (2) two-loop kinetics beside the line
+    cases = []
+    t_total = 0.0
+    for x_c in (20.0, 30.0):
+        wc = config_dislocation_loops(x_c)
+        tr, clock, sec = _loop_ensemble(ok, wc, 10, 500, 10, stream, lines=lines)
+        t_total += sec
+        case = {'x_c_nm': x_c, 'x_nm': wc.extra['x_nm'], 'z_nm': wc.extra['z_nm']}
+        case.update(_trajectory_summary(tr, clock))
+        cases.append(case)
+    out = {'metric': 'loops near an edge dislocation: energy profile and kinetics along [111]', 'unit': 'eV, nm',
+           'data': 'synthetic', 'dtype': 'f32 fields / f64 energies',
+           'config': {'workload': 'dislocation_two_loops_256cubed (edge dislocation [-1-12], b = a0/2 [111]; '
+                                  '1/2<111> loops R = 3.3 nm, E_m = 0.1 eV, 300 K, Table 1 constants)'},
+           'setup_seconds': t_setup, 'profile_x_E_Edipole': profile, 'cases': cases, 'seconds': t_total,
+           'clocks': clk.stop()}
     print(json.dumps(out))
     return 0
 
@@ -576,7 +652,7 @@ def main():
     ap.add_argument('--impl', default='ours', choices=['ours', 'reference'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='large', choices=['large', 'batch', 'serve', 'small', 'medium', 'dipole',
-                                                            'kinetics'],
+                                                            'kinetics', 'dislocation'],
                     help='large: the 256^3 single-replica step (default); batch: the 64-replica ensemble; '
                          'serve: the request server under Poisson load; small / medium: the 32^3 FP64 and '
                          'the 128^3 workloads')
@@ -606,6 +682,8 @@ def main():
         return run_dipole(args) if rank == 0 else 0
     if args.workload == 'kinetics':
         return run_kinetics(args) if rank == 0 else 0
+    if args.workload == 'dislocation':
+        return run_dislocation(args) if rank == 0 else 0
     r = run_ours(args, ws, rank)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -223,6 +223,47 @@ def config_kinetics(x_rel_nm, n=256, h=VOXEL_NM, z_rel_nm=10.0, R_nm=3.3, T_K=30
                     extra={'x_rel_nm': kx * unit * math.sqrt(3.0), 'z_rel_nm': kz * unit * math.sqrt(2.0)})
 
 
+def frame_111():
+    """The paper's frame for loops and dislocations (Sec. 4): x = [111]/sqrt3 (Burgers
+    vector and glide of the loops), y = [-1-12]/sqrt6, z = [1-10]/sqrt2, as cube-axis
+    unit vectors."""
+    return (np.array([1.0, 1.0, 1.0]) / math.sqrt(3.0), np.array([-1.0, -1.0, 2.0]) / math.sqrt(6.0),
+            np.array([1.0, -1.0, 0.0]) / math.sqrt(2.0))
+
+
+def edge_dislocation_y(n, h):
+    """One period of the paper's straight edge dislocation (Sec. 4.1): line along y =
+    [-1-12] through the box centre, b = (a0/2)[111] along x.  In a cubic box of edge n h
+    with cube-axis grid lines, the period is n (-1,-1,2) h (its end is a lattice
+    translate of its start); the nearest periodic image lies n h / sqrt3 away."""
+    c = 0.5 * np.asarray(n, float) * h
+    d = np.array([-1.0, -1.0, 2.0]) * (0.5 * n[0] * h)
+    return [(np.array([c - d, c + d]), 0.5 * h * np.ones(3), False)]
+
+
+def config_dislocation_loops(x_c_nm, n=256, h=VOXEL_NM, z_nm=5.0, x_rel_nm=10.0, R_nm=3.3, T_K=300.0):
+    """The paper's two loops near an edge dislocation (Sec. 5.2): 1/2<111> loops (R =
+    3.3 nm, E_m = 0.1 eV, 1D glide along x = [111]) on both sides of the line, z = -z_nm
+    (loop 1) and +z_nm (loop 2) along [1-10], their centre of mass x_c_nm from the line
+    along x and x_rel_nm apart (loop 1 behind).  Positions are the nearest bcc sites that
+    keep the z offsets symmetric (even multiples of (1,-1,0) in a0/2 units)."""
+    assert n % 2 == 0
+    unit = 0.5 * h
+    kz = 2 * int(round(z_nm / (unit * math.sqrt(2.0)) / 2.0))
+    k1 = int(round((x_c_nm - 0.5 * x_rel_nm) / (unit * math.sqrt(3.0))))
+    k2 = int(round((x_c_nm + 0.5 * x_rel_nm) / (unit * math.sqrt(3.0))))
+    c0 = np.array([n, n, n])
+    p1 = c0 + np.array([-kz, kz, 0]) + k1
+    p2 = c0 + np.array([kz, -kz, 0]) + k2
+    defs = make_defects([LOOP_111, LOOP_111], np.array([p1, p2]), [0, 0], [R_nm, R_nm], [0, 0], [0.1, 0.1],
+                        [ONE_D, ONE_D])
+    xs = [k * unit * math.sqrt(3.0) for k in (k1, k2)]
+    return Workload(name='dislocation_two_loops_xc%.0fA' % (10 * x_c_nm), n=(n, n, n), voxel_nm=h, defects=defs,
+                    T_K=T_K, C=FE_TABLE1,
+                    extra={'lines': edge_dislocation_y((n, n, n), h), 'x_nm': xs, 'z_nm': [-kz * unit * math.sqrt(2.0),
+                                                                                           kz * unit * math.sqrt(2.0)]})
+
+
 def config_batch(seed=1004, n_replicas=64, edges=(64, 96, 128, 160, 192), nd_range=(50, 800),
                  T_range=(300.0, 600.0)):
     """Ensemble of independent replicas: edge ~ U(edges), defect count ~ U{50..800}

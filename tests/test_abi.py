@@ -159,3 +159,32 @@ def test_kinetics_workload_geometry():
         assert abs(along - x_rel) < 0.25 and abs(across - 10.0) < 0.25
         assert abs(sep @ np.array([1.0, 1.0, -2.0])) < 1e-12       # no offset along [11-2]
         assert np.isclose(w.extra['x_rel_nm'], along) and np.isclose(w.extra['z_rel_nm'], across)
+
+
+def test_dislocation_workload_geometry():
+    """The loops-near-a-dislocation setting (Sec. 5.2): the edge line runs along y =
+    [-1-12] through the box centre for one period (its end a lattice translate of its
+    start) with b = (a0/2)[111] normal to it; the loops sit on bcc sites on both sides
+    of the line (z = -/+ the same offset along [1-10], y = 0), x_rel apart along [111]
+    with their centre of mass x_c from the line."""
+    from paper_2403_09158_gb300.workload import config_dislocation_loops, frame_111
+    X, Y, Z = frame_111()
+    for x_c in (20.0, 30.0):
+        w = config_dislocation_loops(x_c)
+        (pts, b, closed), = w.extra['lines']
+        n, h = np.asarray(w.n), w.voxel_nm
+        assert not closed and pts.shape == (2, 3)
+        per = (pts[1] - pts[0]) / h
+        assert np.allclose(per, np.round(per)) and np.all(np.mod(np.round(per), n) == 0)
+        assert np.allclose(np.cross(per, Y), 0.0) and abs(b @ per) < 1e-12
+        assert np.allclose(b, 0.5 * h * np.ones(3))
+        centre = 0.5 * n * h
+        assert np.allclose(np.cross(centre - pts[0], per), 0.0)            # the line passes through the centre
+        rel = [(p * 0.5 * h - centre) for p in w.defects['pos']]
+        for p in w.defects['pos']:
+            assert len({int(v) % 2 for v in p}) == 1
+        zs = [r @ Z for r in rel]
+        assert abs(zs[0] + zs[1]) < 1e-9 and abs(abs(zs[0]) - 5.0) < 0.2
+        assert all(abs(r @ Y) < 1e-9 for r in rel)
+        xs = [r @ X for r in rel]
+        assert abs(0.5 * (xs[0] + xs[1]) - x_c) < 0.3 and abs(xs[1] - xs[0] - 10.0) < 0.3
