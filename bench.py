@@ -352,10 +352,11 @@ def run_kinetics(args):
 
 def run_dislocation(args):
     """Loops near the paper's straight edge dislocation (line along [-1-12] through the
-    box centre, b = (a0/2)[111]; Secs. 4.3 and 5.2), 256^3, Table 1 constants.
+    box centre, b = (a0/2)[111]; Secs. 4.1, 4.3 and 5.2), 256^3, Table 1 constants.
     (1) The interaction energy of one loop (R = 3.3 nm, 4.85 nm from the line along
     [1-10]) with the dislocation against its position along [111], exact and in the
-    dipole approximation.  (2) Two loops on both sides of the line (z = -/+4.85 nm),
+    dipole approximation, and of a <110> dumbbell SIA (Table 1's dipole tensor) on the
+    same line.  (2) Two loops on both sides of the line (z = -/+4.85 nm),
     x_rel = 9.9 nm, centre of mass 20 or 30 nm from the line: 500 fixed-time-step steps
     at 300 K, 10 runs per case, the loops' coordinates along [111] against time."""
     import torch
@@ -387,6 +388,16 @@ def run_dislocation(args):
         x = float(((pos[0] - np.array(w.n)) @ np.ones(3)) * unit / math.sqrt(3.0))
         profile.append([x, E, Ed])
     g.close()
+    # (1b) Sec. 4.1: a <110> dumbbell SIA (dipole tensor of Table 1) probing the line's
+    # field alone on the same z line
+    g = ok.Grid(w.n, w.voxel_nm, *w.C, stream=stream.cuda_stream)
+    g.set_dislocations(lines)
+    P_sia = np.array([25.832, 21.143, 21.150, 5.122, 0.0, 0.0])       # Table 1, (xx, yy, zz, yz, xz, xy)
+    ks = np.arange(-100, 101, 4)
+    probes = (z_site[None, :] + ks[:, None]).astype(np.int32)
+    E_sia = g.point_dipole_energies(probes, P_sia)
+    profile_sia = [[float(k * unit * math.sqrt(3.0)), float(e)] for k, e in zip(ks, E_sia)]
+    g.close()
     # (2) two-loop kinetics beside the line
     cases = []
     t_total = 0.0
@@ -401,7 +412,8 @@ def run_dislocation(args):
            'data': 'synthetic', 'dtype': 'f32 fields / f64 energies',
            'config': {'workload': 'dislocation_two_loops_256cubed (edge dislocation [-1-12], b = a0/2 [111]; '
                                   '1/2<111> loops R = 3.3 nm, E_m = 0.1 eV, 300 K, Table 1 constants)'},
-           'setup_seconds': t_setup, 'profile_x_E_Edipole': profile, 'cases': cases, 'seconds': t_total,
+           'setup_seconds': t_setup, 'profile_x_E_Edipole': profile, 'profile_sia_x_E': profile_sia,
+           'cases': cases, 'seconds': t_total,
            'clocks': clk.stop()}
     print(json.dumps(out))
     return 0

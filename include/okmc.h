@@ -199,6 +199,18 @@ int okmc_candidate_energies(okmc_grid* g, double* E, uint8_t* valid, int out_on_
  * okmc_interaction_energies. */
 int okmc_dipole_energies(okmc_grid* g, double* E, double* Ec, int out_on_device);
 
+/* Point defects of given dipole tensor in the grid's current field (Sec. 2.1, Eq.
+ * interaction_energy4; Table 1 gives the <110> dumbbell self-interstitial's):
+ * E[k] = -P_k : eps(Y_k), eps = C^-1 : sigma read at the centre of site Y_k (the rule
+ * of okmc_dipole_energies).  The probes are not part of the grid: they feel every
+ * defect and dislocation line and change nothing.  pos: int32[m][3] bcc sites (units
+ * of a0/2, 0 <= pos[a] < 2 n[a], all even or all odd); P: double[m][6] in eV, order
+ * (xx, yy, zz, yz, xz, xy); E: double[m] in eV.  on_device != 0: all three pointers are
+ * device memory (a bad site then gives NaN in E and OKMC_EINVAL).  Solves first if the
+ * stress is stale.  Errors: EINVAL (null pointers, m < 0, sites, non-finite P), ENOMEM,
+ * ECUDA. */
+int okmc_point_dipole_energies(okmc_grid* g, const int32_t* pos, const double* P, int32_t m, double* E, int on_device);
+
 /* Self part of the dipole energies, D[n][2][9] in GPa nm^3 (FP64): D[i][c][k] =
  * (int eps*_i) : sigma_i(Y_k), defect i's own field at the centre of a class-c site
  * (k = 0) or of its jump k - 1; the dipole energy is -kappa ((int eps*_i) : sigma(Y) -

@@ -19,6 +19,7 @@ What it computes, in the paper's order (Santos-Gueemes, Ortiz, Segurado,
    defects except i.
 4. The paper's translation of a defect's field by the shift theorem (Sec. 3.3, Eq.
    shift), the dipole approximation of the same energies (Sec. 2.1, Eq. interaction_energy4)
+   (also for a point defect whose dipole tensor is given, Table 1)
    and dislocation lines by field dislocation mechanics (Sec. 3.2, Eqs. Nye2,
    eq_EIG_fourier, plastic_0): the Nye tensor of a line, the incompatible plastic
    distortion in Fourier space and its symmetric part as eigenstrain.
@@ -772,6 +773,20 @@ def sample_center(field6, pos):
 def dipole_energy_at(d, pos_Y, sigma6, h):
     """-kappa (int eps*_d) : sigma(Y) for defect d with its centre at pos_Y."""
     return -KAPPA * ddot6(integrated_eigenstrain6(d, h), sample_center(sigma6, pos_Y))
+
+
+# Table 1: dipole tensor of the <110> dumbbell self-interstitial in Fe (eV), printed as
+# P11, P22, P33, P12, P13, P23; here in VOIGT order (xx, yy, zz, yz, xz, xy).
+SIA_110_DIPOLE_EV = np.array([25.832, 21.143, 21.150, 5.122, 0.000, 0.000])
+
+
+def point_dipole_energy(P6, pos_Y, sigma6, C):
+    """E = -P : eps(Y) (Eq. interaction_energy4) for a point defect of dipole tensor P
+    (eV; VOIGT order) with its centre at site pos_Y: eps = C^-1 : sigma read at the
+    centre of the site (``sample_center``).  With engineering shear strains, P : eps is
+    the plain sum of the six products."""
+    e = np.linalg.solve(stiffness_matrix(C), sample_center(sigma6, pos_Y))
+    return -float(np.dot(np.asarray(P6, float), e))
 
 
 def dipole_energies(defects, n, h, C, k0_mode=MEAN_STRESS_ZERO):

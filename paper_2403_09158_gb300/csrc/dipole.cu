@@ -171,7 +171,48 @@ __global__ void k_dipole_energies(const T* __restrict__ sig, int3 n, const okmc_
   else if (Ec) Ec[(size_t)i * 8 + k - 1] = e;
 }
 
+// Point defects of given dipole tensor P (eV, (xx, yy, zz, yz, xz, xy)) at bcc sites:
+// E = -P : eps(Y), eps = C^-1 : sigma at the centre of the site.  For cubic C the
+// compliance gives the engineering strains e_a = S11 s_a + S12 (s_b + s_c) (a, b, c the
+// three normal components) and gamma = s / C44 (shear), and P : eps = sum_a P_a e_a.
+// A site off the lattice or outside the box gives NaN and error code 8.
+template <class T>
+__global__ void k_point_dipole(const T* __restrict__ sig, int3 n, const int* __restrict__ pos,
+                               const double* __restrict__ P, int m, double C11, double C12, double C44,
+                               double* __restrict__ E, int* err) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m) return;
+  const int p[3] = {pos[3 * k], pos[3 * k + 1], pos[3 * k + 2]};
+  const bool inside = p[0] >= 0 && p[1] >= 0 && p[2] >= 0 && p[0] < 2 * n.x && p[1] < 2 * n.y && p[2] < 2 * n.z;
+  if (!inside || ((p[0] ^ p[1]) & 1) || ((p[0] ^ p[2]) & 1)) {
+    E[k] = nan("");
+    atomicExch(err, 8);
+    return;
+  }
+  double s[6];
+  centre_stress<T>(sig, n, (size_t)n.x * n.y * n.z, p, s);
+  const double den = (C11 - C12) * (C11 + 2.0 * C12);
+  const double S11 = (C11 + C12) / den, S12 = -C12 / den;
+  const double e[6] = {S11 * s[0] + S12 * (s[1] + s[2]), S11 * s[1] + S12 * (s[0] + s[2]),
+                       S11 * s[2] + S12 * (s[0] + s[1]), s[3] / C44, s[4] / C44, s[5] / C44};
+  double pe = 0.0;
+  for (int a = 0; a < 6; ++a) pe += P[6 * (size_t)k + a] * e[a];
+  E[k] = -pe;
+}
+
 }  // namespace
+
+template <class T>
+cudaError_t launch_point_dipole(const T* sig, int3 n, const int* pos, const double* P, int m, double C11, double C12,
+                                double C44, double* E, int* err, cudaStream_t st) {
+  if (m == 0) return cudaSuccess;
+  k_point_dipole<T><<<(m + 255) / 256, 256, 0, st>>>(sig, n, pos, P, m, C11, C12, C44, E, err);
+  return cudaGetLastError();
+}
+template cudaError_t launch_point_dipole<float>(const float*, int3, const int*, const double*, int, double, double, double,
+                                                double*, int*, cudaStream_t);
+template cudaError_t launch_point_dipole<double>(const double*, int3, const int*, const double*, int, double, double,
+                                                 double, double*, int*, cudaStream_t);
 
 template <class T, class QT>
 cudaError_t launch_dipself(const C2<T>* spec, const PassCfg& c, const WBatch& b, const QT* qtab, const double2* phx,

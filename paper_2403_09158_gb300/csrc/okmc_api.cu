@@ -73,6 +73,9 @@ cudaError_t launch_dipole_energies(const T* sig, int3 n, const okmc_defect* def,
 cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st);
 int pencil_variant_mask(const PassCfg& c);
 template <class T> int fdm_pencil_tile(int ny, int nz, size_t limit);
+template <class T>
+cudaError_t launch_point_dipole(const T* sig, int3 n, const int* pos, const double* P, int m, double C11, double C12,
+                                double C44, double* E, int* err, cudaStream_t st);
 template <class T, class Q>
 cudaError_t launch_dislocation_eigenstrain(const double* pts, const int2* seg, const int* seg_line, int nseg,
                                            const int* first, const int* closed, const double* burgers, double* area,
@@ -1260,6 +1263,69 @@ int okmc_set_dislocations(okmc_grid* g, const double* points, const int32_t* cou
   } catch (const std::bad_alloc&) {
     return fail(g, OKMC_ENOMEM, "host allocation failed");
   }
+}
+
+int okmc_point_dipole_energies(okmc_grid* g, const int32_t* pos, const double* P, int32_t m, double* E, int on_device) {
+  if (!g || m < 0 || (m > 0 && (!pos || !P || !E))) return OKMC_EINVAL;
+  if (m == 0) return OKMC_OK;
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);  // may allocate
+  if (!on_device) {
+    for (int k = 0; k < m; ++k) {
+      const int32_t* p = pos + 3 * k;
+      for (int a = 0; a < 3; ++a)
+        if (p[a] < 0 || p[a] >= 2 * g->n[a]) return fail(g, OKMC_EINVAL, "probe site outside the box");
+      if (((p[0] ^ p[1]) & 1) || ((p[0] ^ p[2]) & 1)) return fail(g, OKMC_EINVAL, "probe site off the bcc lattice");
+      for (int a = 0; a < 6; ++a)
+        if (!std::isfinite(P[6 * k + a])) return fail(g, OKMC_EINVAL, "non-finite dipole tensor");
+    }
+  }
+  OKMC_TRY(solve(g));
+  const int32_t* dpos = pos;
+  const double* dP = P;
+  double* dE = E;
+  void *tpos = nullptr, *tP = nullptr, *tE = nullptr;
+  auto release = [&] {
+    if (tpos || tP || tE) cudaStreamSynchronize(g->st);
+    dfree(g, tpos);
+    dfree(g, tP);
+    dfree(g, tE);
+  };
+  if (!on_device) {
+    int rc = OKMC_OK;
+    if ((rc = dalloc(g, &tpos, 3 * (size_t)m * sizeof(int32_t))) || (rc = dalloc(g, &tP, 6 * (size_t)m * sizeof(double))) ||
+        (rc = dalloc(g, &tE, (size_t)m * sizeof(double)))) {
+      release();
+      return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(tpos, pos, 3 * (size_t)m * sizeof(int32_t), cudaMemcpyHostToDevice, g->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(tP, P, 6 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, g->st);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(g, e, "probe upload");
+    }
+    dpos = (const int32_t*)tpos;
+    dP = (const double*)tP;
+    dE = (double*)tE;
+  }
+  int rc = run(g, "point_dipole", [&] {
+    if (fp64(g))
+      return launch_point_dipole<double>((const double*)g->sig, dims(g), dpos, dP, m, g->cfg.C11, g->cfg.C12, g->cfg.C44, dE,
+                                         g->d_err, g->st);
+    return launch_point_dipole<float>((const float*)g->sig, dims(g), dpos, dP, m, g->cfg.C11, g->cfg.C12, g->cfg.C44, dE,
+                                      g->d_err, g->st);
+  });
+  if (rc == OKMC_OK && !on_device) rc = copy_out(g, E, dE, (size_t)m * sizeof(double), 0);
+  release();
+  if (rc) return rc;
+  int code = 0;
+  cudaError_t e = cudaMemcpyAsync(&code, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "device error check");
+  if (code == 8) {  // a device-side probe was rejected: report it and clear the flag
+    if (cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st) != cudaSuccess) return fail(g, OKMC_ECUDA, "error reset");
+    return fail(g, OKMC_EINVAL, "probe site off the bcc lattice or outside the box");
+  }
+  return check_device_error(g);
 }
 
 int okmc_self_terms(okmc_grid* g, double* W, int out_on_device) {

@@ -33,7 +33,7 @@ EXPORTED = [
     'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_get_variants', 'okmc_set_variant',
     'okmc_set_kinetic_state', 'okmc_estimate_field_bytes', 'okmc_server_create', 'okmc_server_add_replica',
     'okmc_server_submit', 'okmc_server_wait', 'okmc_server_get_stats', 'okmc_server_last_error', 'okmc_server_destroy',
-    'okmc_isotropic_stiffness', 'okmc_set_dislocations',
+    'okmc_isotropic_stiffness', 'okmc_set_dislocations', 'okmc_point_dipole_energies',
 ]
 
 
@@ -110,6 +110,7 @@ def load(path=LIB_PATH):
         'okmc_candidate_energies': (C.c_int, [vp, dp, dp, C.c_int]),
         'okmc_self_terms': (C.c_int, [vp, dp, C.c_int]),
         'okmc_set_dislocations': (C.c_int, [vp, dp, dp, dp, dp, i32, C.c_double]),
+        'okmc_point_dipole_energies': (C.c_int, [vp, dp, dp, i32, dp, C.c_int]),
         'okmc_dipole_energies': (C.c_int, [vp, dp, dp, C.c_int]),
         'okmc_dipole_self_terms': (C.c_int, [vp, dp, C.c_int]),
         'okmc_get_stencil': (C.c_int, [vp, i32, i32, dp, dp, i32, C.POINTER(i32), C.POINTER(C.c_double)]),
@@ -267,6 +268,16 @@ class Grid:
         self._chk(self.lib.okmc_set_dislocations(self.h, pts.ctypes.data if n else None, cnt.ctypes.data if n else None,
                                                  cl.ctypes.data if n else None, b.ctypes.data if n else None, n,
                                                  float(ds_max_nm)))
+
+    def point_dipole_energies(self, pos, P):
+        """okmc_point_dipole_energies on host arrays: pos (m, 3) int32 sites, P (m, 6) eV."""
+        pos = np.ascontiguousarray(pos, dtype=np.int32).reshape(-1, 3)
+        P = np.ascontiguousarray(np.broadcast_to(np.asarray(P, np.float64), (len(pos), 6)))
+        out = np.zeros(len(pos))
+        m = len(pos)
+        self._chk(self.lib.okmc_point_dipole_energies(self.h, pos.ctypes.data if m else None, P.ctypes.data if m else None,
+                                                      m, out.ctypes.data if m else None, 0))
+        return out
 
     def self_terms(self):
         out = np.zeros((self.nd, 2, 9))

@@ -517,6 +517,35 @@ def test_dipole_limit_isotropic_kelvin():
     assert errs[-1] < 1e-2, errs
 
 
+def test_point_dipole_energy_closed_forms_and_defect_dipole():
+    """E = -P : C^-1 : sigma for a given dipole tensor (Table 1's <110> dumbbell):
+    under a uniform hydrostatic stress p it is -tr(P) p / (3K), K = (C11 + 2 C12)/3;
+    under a uniform shear sigma_yz = tau it is -P_yz tau / C44; and with the defect's own
+    dipole tensor P = kappa C : int eps* it equals the defect's dipole energy
+    -kappa (int eps*) : sigma at every site."""
+    C11, C12, C44 = 289.34, 152.34, 107.43     # Table 1
+    C = O.stiffness_cubic(C11, C12, C44)
+    P = O.SIA_110_DIPOLE_EV
+    n = (8, 8, 8)
+    p, tau = 0.7, -0.3
+    hyd = np.zeros((6,) + n)
+    hyd[:3] = p
+    K = (C11 + 2.0 * C12) / 3.0
+    for pos in ([2, 4, 6], [3, 5, 7]):
+        assert abs(O.point_dipole_energy(P, np.array(pos), hyd, C) + P[:3].sum() * p / (3.0 * K)) < 1e-12
+    sh = np.zeros((6,) + n)
+    sh[3] = tau
+    assert abs(O.point_dipole_energy(P, np.array([2, 4, 6]), sh, C) + P[3] * tau / C44) < 1e-12
+    rng = np.random.default_rng(5)
+    sig = rng.normal(size=(6,) + n)
+    loop = dict(type=O.LOOP_111, pos=np.array([6, 8, 4]), axis=2, radius_nm=0.4, size=0, Em_eV=0.1, mobility=O.ONE_D)
+    Pd = O.KAPPA * (O.stiffness_matrix(C) @ (O.integrated_eigenstrain6(loop, H) * np.array([1, 1, 1, 2, 2, 2])))
+    for pos in ([6, 8, 4], [7, 9, 5], [1, 3, 15]):
+        a = O.point_dipole_energy(Pd, np.array(pos), sig, C)
+        b = O.dipole_energy_at(loop, np.array(pos), sig, H)
+        assert abs(a - b) <= 1e-12 * abs(b)
+
+
 # ---------------------------------------------------------------- dislocation lines (FDM)
 # Sec. 3.2, Eqs. Nye2, curlUe, eq_EIG_fourier, plastic_0
 def _edge_dislocation_stress(N, mu, nu, b=0.25):
