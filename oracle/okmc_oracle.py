@@ -870,6 +870,31 @@ def loop_dipole_tensor(C, b, A):
     return np.einsum('ijkl,kl->ij', C, S)
 
 
+def blin_interaction_energy(line1, b1, line2, b2, mu, nu):
+    """Interaction energy (GPa nm^3) of two closed dislocation lines in an infinite
+    isotropic body, by Blin's double line integral (Hirth & Lothe, Theory of
+    Dislocations, Ch. 4):
+      W = -mu/(2 pi) oint oint (b1 x b2).(dl1 x dl2)/R + mu/(4 pi) oint oint (b1.dl1)(b2.dl2)/R
+          + mu/(4 pi (1 - nu)) oint oint (b1 x dl1).T.(b2 x dl2),   T_ij = d_i d_j R,
+    R = |x2 - x1|, evaluated by the midpoint rule over the polylines' segments (the lines
+    must not touch).  T_ij = (delta_ij - u_i u_j)/R with u the unit vector along x2 - x1.
+    Bilinear in (b, dl) of each line, so the result does not depend on the line-sense
+    convention as long as both lines follow the same one."""
+    P1, P2 = np.asarray(line1, float), np.asarray(line2, float)
+    d1 = np.roll(P1, -1, axis=0) - P1
+    d2 = np.roll(P2, -1, axis=0) - P2
+    Rv = (P2 + 0.5 * d2)[None, :, :] - (P1 + 0.5 * d1)[:, None, :]
+    R = np.linalg.norm(Rv, axis=2)
+    u = Rv / R[..., None]
+    b1, b2 = np.asarray(b1, float), np.asarray(b2, float)
+    t1 = np.einsum('k,abk->ab', np.cross(b1, b2), np.cross(d1[:, None, :], d2[None, :, :])) / R
+    t2 = np.outer(d1 @ b1, d2 @ b2) / R
+    c1, c2 = np.cross(b1, d1), np.cross(b2, d2)
+    t3 = (c1 @ c2.T - np.einsum('ai,abi->ab', c1, u) * np.einsum('bi,abi->ab', c2, u)) / R
+    return (-mu / (2.0 * PI) * t1.sum() + mu / (4.0 * PI) * t2.sum()
+            + mu / (4.0 * PI * (1.0 - nu)) * t3.sum())
+
+
 def kelvin_green(x, mu, nu):
     """Isotropic infinite-body Green's function G_ik(x) (Kelvin solution)."""
     r = np.linalg.norm(x)
