@@ -188,3 +188,43 @@ def test_dislocation_workload_geometry():
         assert all(abs(r @ Y) < 1e-9 for r in rel)
         xs = [r @ X for r in rel]
         assert abs(0.5 * (xs[0] + xs[1]) - x_c) < 0.3 and abs(xs[1] - xs[0] - 10.0) < 0.3
+
+
+def test_python_marshalling_of_dislocations_and_point_dipoles():
+    """Grid.set_dislocations and Grid.point_dipole_energies hand the C calls flat,
+    contiguous arrays in the documented layouts (checked with a stand-in library that
+    reads the pointers during the call; no GPU)."""
+    import ctypes as C
+    seen = {}
+
+    def rd(addr, ctype, count):
+        return np.ctypeslib.as_array(C.cast(addr, C.POINTER(ctype)), shape=(count,)).copy()
+
+    class FakeLib:
+        def okmc_set_dislocations(self, h, pts, counts, closed, b, n, ds):
+            cnt = rd(counts, C.c_int32, n)
+            seen['counts'], seen['closed'] = cnt, rd(closed, C.c_int32, n)
+            seen['pts'] = rd(pts, C.c_double, 3 * int(cnt.sum())).reshape(-1, 3)
+            seen['b'], seen['ds'] = rd(b, C.c_double, 3 * n).reshape(-1, 3), ds
+            return ok.OKMC_OK
+
+        def okmc_point_dipole_energies(self, h, pos, P, m, E, on_device):
+            seen['pos'], seen['P'] = rd(pos, C.c_int32, 3 * m).reshape(-1, 3), rd(P, C.c_double, 6 * m).reshape(-1, 6)
+            out = np.ctypeslib.as_array(C.cast(E, C.POINTER(C.c_double)), shape=(m,))
+            out[:] = np.arange(m) + 0.5
+            seen['dev'] = on_device
+            return ok.OKMC_OK
+
+    g = object.__new__(ok.Grid)
+    g.lib, g.h = FakeLib(), C.c_void_p(1)
+    loop = np.arange(12, dtype=np.float32).reshape(4, 3)           # converted to float64
+    line = [[0.0, 0.0, 0.0], [0.0, 5.0, 0.0]]
+    g.set_dislocations([(loop, (1, 2, 3), True), (line, np.array([0.5, 0.0, 0.5]), False)], ds_max_nm=0.05)
+    assert list(seen['counts']) == [4, 2] and list(seen['closed']) == [1, 0]
+    assert np.array_equal(seen['pts'], np.vstack([loop.astype(np.float64), line]))
+    assert np.array_equal(seen['b'], [[1, 2, 3], [0.5, 0.0, 0.5]]) and seen['ds'] == 0.05
+    pos = np.array([[2, 4, 6], [1, 3, 5]], dtype=np.int64)
+    E = g.point_dipole_energies(pos, [1, 2, 3, 4, 5, 6])
+    assert np.array_equal(seen['pos'], pos) and np.array_equal(seen['P'], [[1, 2, 3, 4, 5, 6]] * 2)
+    assert np.array_equal(E, [0.5, 1.5]) and seen['dev'] == 0
+    g.h = None
