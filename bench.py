@@ -219,7 +219,8 @@ def run_dipole(args):
     [1-10] and moved along its glide direction [111]).  For each position: the exact
     energy (Eq. interaction_energy3) and the dipole one (Eq. interaction_energy4) of the
     moving loop, and the time of one evaluation after the move (the incremental solve,
-    both energies and their copies to the host)."""
+    both energies and their copies to the host).  Then the paper's shift-theorem
+    evaluation of the same loop at 121 continuous positions along the glide line."""
     import torch
 
     from paper_2403_09158_gb300 import okmc as ok
@@ -253,8 +254,21 @@ def run_dipole(args):
         e1.record(stream)
         torch.cuda.synchronize()
         rows.append((k * math.sqrt(3.0) * h / 2.0, float(Ex[1]), float(Ed[1]), e0.elapsed_time(e1)))
-    g.close()
     xs = [r[0] for r in rows]
+    # the paper's own evaluation (Sec. 3.3, Eq. shift): the moving loop's field translated
+    # to continuous positions along its glide line; on the lattice sites above it gives
+    # the stencil energies back (up to the Nyquist terms of the even edges)
+    u = np.ones(3) / math.sqrt(3.0)
+    centre = (c0 + off) * h / 2.0
+    xc = np.linspace(xs[0], xs[-1], 121)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    Es = g.shift_energies(1, centre[None, :] + xc[:, None] * u[None, :])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_shift = e0.elapsed_time(e1)
+    Es_sites = g.shift_energies(1, centre[None, :] + np.asarray(xs)[:, None] * u[None, :])
+    g.close()
     gap = max(abs(r[1] - r[2]) for r in rows)
     far = [abs(r[1] - r[2]) / max(1e-12, abs(r[1])) for r in rows if abs(r[0]) > 12.0]
     out = {'metric': 'exact vs dipole interaction energy, two 1/2<111> loops', 'unit': 'eV',
@@ -264,6 +278,9 @@ def run_dipole(args):
            'x_nm': xs, 'E_exact_eV': [r[1] for r in rows], 'E_dipole_eV': [r[2] for r in rows],
            'max_abs_gap_eV': gap, 'rel_gap_beyond_12nm_max': max(far) if far else None,
            'ms_per_evaluation_median': float(np.median([r[3] for r in rows])),
+           'shift_x_nm': xc.tolist(), 'E_shift_eV': Es.tolist(),
+           'shift_minus_exact_at_sites_max_abs_eV': float(np.abs(Es_sites - np.array([r[1] for r in rows])).max()),
+           'ms_shift_call_121_positions': ms_shift,
            'evaluation': 'after each move: incremental solve, exact and dipole energies, both copied to the host',
            'clocks': clk.stop()}
     print(json.dumps(out))

@@ -211,6 +211,22 @@ int okmc_dipole_energies(okmc_grid* g, double* E, double* Ec, int out_on_device)
  * ECUDA. */
 int okmc_point_dipole_energies(okmc_grid* g, const int32_t* pos, const double* P, int32_t m, double* E, int on_device);
 
+/* The paper's evaluation at continuous positions (Sec. 3.3, Eq. shift; Eq.
+ * interaction_energy3 in its elastic-strain form): the interaction energy of defect i if
+ * it sat at X_k instead of its site, E[k] = kappa int sigma^(-i) : eps^e_i(. - X_k) dV.
+ * eps^e_i is the elastic strain C^-1 : sigma of defect i alone with its class-0 stencil
+ * placed at the origin (centre X0 = 0), moved to X_k by exp(-i xi.X_k) and summed by
+ * Parseval over the discrete frequencies; sigma^(-i) is the stress of everything on the
+ * grid (defects and dislocation lines) except defect i at its current site.  At a
+ * whole-voxel move of a class-0 defect this is its stencil energy there (up to the
+ * Nyquist terms of even edges); between lattice sites it is the band-limited reading of
+ * an off-lattice defect.  X: double[m][3] in nm (any finite values; periodic);
+ * E: double[m] in eV.  on_device != 0: X and E are device memory.  Cost: two forward
+ * transforms and one pass over the half spectrum per 8 positions, with temporary
+ * device memory for 8 spectrum components and 2 fixed-point fields.  Errors: EINVAL
+ * (i out of range, m < 0, null or non-finite X), ENOMEM, ECUDA. */
+int okmc_shift_energies(okmc_grid* g, int32_t i, const double* X, int32_t m, double* E, int on_device);
+
 /* Self part of the dipole energies, D[n][2][9] in GPa nm^3 (FP64): D[i][c][k] =
  * (int eps*_i) : sigma_i(Y_k), defect i's own field at the centre of a class-c site
  * (k = 0) or of its jump k - 1; the dipole energy is -kappa ((int eps*_i) : sigma(Y) -

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, 'csrc')
 OUT = os.path.join(HERE, '_lib')
 LIB = os.path.join(OUT, 'libokmc.so')
-SOURCES = ['solve.cu', 'solve_fast.cu', 'defects.cu', 'dipole.cu', 'dislocation.cu', 'okmc_api.cu', 'serve.cu']
+SOURCES = ['solve.cu', 'solve_fast.cu', 'defects.cu', 'dipole.cu', 'dislocation.cu', 'shift.cu', 'okmc_api.cu', 'serve.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '-I' + os.path.join(ROOT, 'include')]
 

@@ -73,6 +73,11 @@ cudaError_t launch_dipole_energies(const T* sig, int3 n, const okmc_defect* def,
 cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st);
 int pencil_variant_mask(const PassCfg& c);
 template <class T> int fdm_pencil_tile(int ny, int nz, size_t limit);
+int shift_positions_per_pass();
+template <class T>
+cudaError_t launch_shift_energies(const C2<T>* spec_e, const C2<T>* spec_w, const PassCfg& c, const okmc_defect* def,
+                                  const DefGeo* G, const double* alpha, int i, const double* X, int m, double h,
+                                  double* partial, int nblocks, double* E, cudaStream_t st);
 template <class T>
 cudaError_t launch_point_dipole(const T* sig, int3 n, const int* pos, const double* P, int m, double C11, double C12,
                                 double C44, double* E, int* err, cudaStream_t st);
@@ -1325,6 +1330,96 @@ int okmc_point_dipole_energies(okmc_grid* g, const int32_t* pos, const double* P
     if (cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st) != cudaSuccess) return fail(g, OKMC_ECUDA, "error reset");
     return fail(g, OKMC_EINVAL, "probe site off the bcc lattice or outside the box");
   }
+  return check_device_error(g);
+}
+
+}  // extern "C"
+
+namespace {
+template <class T, class Q>
+int shift_energies(okmc_grid* g, int i, const double* dX, int m, double* dE) {
+  const size_t N = g->N;
+  const size_t sp = (size_t)g->n[2] * g->P * 2 * sizeof(T);  // one component of half spectrum
+  void *spec_e = nullptr, *spec_w = nullptr, *fw = nullptr;
+  auto release = [&] {
+    cudaStreamSynchronize(g->st);
+    dfree(g, spec_e);
+    dfree(g, spec_w);
+    dfree(g, fw);
+  };
+  int rc = OKMC_OK;
+  if ((rc = dalloc(g, &spec_e, 6 * sp)) || (rc = dalloc(g, &spec_w, 2 * sp)) || (rc = dalloc(g, &fw, 2 * N * sizeof(Q)))) {
+    release();
+    return rc;
+  }
+  PassCfg c = g->cfg;
+  c.forward_only = 1;
+  c.dirty = nullptr;
+  // the grid's eigenstrain, transformed
+  c.q = quantum(g);
+  c.ncomp = 6;
+  rc = run(g, "shift_eps_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)spec_e, c, g->st); });
+  if (!rc) rc = run(g, "shift_eps_pencil", [&] { return launch_pencil<T>((C2<T>*)spec_e, c, g->st); });
+  // the count fields of defect i's two stencils with their base voxel at the origin
+  if (!rc && cudaMemsetAsync(fw, 0, 2 * N * sizeof(Q), g->st) != cudaSuccess) rc = fail(g, OKMC_ECUDA, "memset");
+  WBatch b{};
+  b.nb = 1;
+  b.idx[0] = i;
+  if (!rc) rc = run(g, "shift_fields", [&] { return launch_wfields<Q>((Q*)fw, dims(g), g->d_ptr, g->d_off, g->d_cnt, b, g->st); });
+  c.q = 1.0;
+  c.ncomp = 2;
+  if (!rc) rc = run(g, "shift_w_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)fw, (C2<T>*)spec_w, c, g->st); });
+  if (!rc) rc = run(g, "shift_w_pencil", [&] { return launch_pencil<T>((C2<T>*)spec_w, c, g->st); });
+  c.ncomp = 6;
+  const int per = shift_positions_per_pass();
+  for (int k0 = 0; k0 < m && !rc; k0 += per) {
+    const int mk = std::min(per, m - k0);
+    rc = run(g, "shift_energies", [&] {
+      return launch_shift_energies<T>((const C2<T>*)spec_e, (const C2<T>*)spec_w, c, g->d_def, g->d_geo, g->d_alpha, i,
+                                      dX + 3 * (size_t)k0, mk, g->h, g->d_partial, kSelfBlocks, dE + k0, g->st);
+    });
+  }
+  release();
+  return rc;
+}
+}  // namespace
+
+extern "C" {
+
+int okmc_shift_energies(okmc_grid* g, int32_t i, const double* X, int32_t m, double* E, int on_device) {
+  if (!g || m < 0 || (m > 0 && (!X || !E))) return OKMC_EINVAL;
+  std::lock_guard<std::recursive_mutex> lk(g_capture_mu);  // allocates
+  if (i < 0 || i >= g->nd) return fail(g, OKMC_EINVAL, "defect index out of range");
+  if (m == 0) return OKMC_OK;
+  if (!on_device)
+    for (long long k = 0; k < 3ll * m; ++k)
+      if (!std::isfinite(X[k]) || std::fabs(X[k]) > 1e9) return fail(g, OKMC_EINVAL, "non-finite position");
+  const double* dX = X;
+  double* dE = E;
+  void *tX = nullptr, *tE = nullptr;
+  auto release = [&] {
+    if (tX || tE) cudaStreamSynchronize(g->st);
+    dfree(g, tX);
+    dfree(g, tE);
+  };
+  if (!on_device) {
+    int rc = OKMC_OK;
+    if ((rc = dalloc(g, &tX, 3 * (size_t)m * sizeof(double))) || (rc = dalloc(g, &tE, (size_t)m * sizeof(double)))) {
+      release();
+      return rc;
+    }
+    cudaError_t e = cudaMemcpyAsync(tX, X, 3 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, g->st);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(g, e, "position upload");
+    }
+    dX = (const double*)tX;
+    dE = (double*)tE;
+  }
+  int rc = fp64(g) ? shift_energies<double, int64_t>(g, i, dX, m, dE) : shift_energies<float, int32_t>(g, i, dX, m, dE);
+  if (!rc && !on_device) rc = copy_out(g, E, dE, (size_t)m * sizeof(double), 0);
+  release();
+  if (rc) return rc;
   return check_device_error(g);
 }
 

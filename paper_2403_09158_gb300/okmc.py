@@ -33,7 +33,7 @@ EXPORTED = [
     'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_get_variants', 'okmc_set_variant',
     'okmc_set_kinetic_state', 'okmc_estimate_field_bytes', 'okmc_server_create', 'okmc_server_add_replica',
     'okmc_server_submit', 'okmc_server_wait', 'okmc_server_get_stats', 'okmc_server_last_error', 'okmc_server_destroy',
-    'okmc_isotropic_stiffness', 'okmc_set_dislocations', 'okmc_point_dipole_energies',
+    'okmc_isotropic_stiffness', 'okmc_set_dislocations', 'okmc_point_dipole_energies', 'okmc_shift_energies',
 ]
 
 
@@ -111,6 +111,7 @@ def load(path=LIB_PATH):
         'okmc_self_terms': (C.c_int, [vp, dp, C.c_int]),
         'okmc_set_dislocations': (C.c_int, [vp, dp, dp, dp, dp, i32, C.c_double]),
         'okmc_point_dipole_energies': (C.c_int, [vp, dp, dp, i32, dp, C.c_int]),
+        'okmc_shift_energies': (C.c_int, [vp, i32, dp, i32, dp, C.c_int]),
         'okmc_dipole_energies': (C.c_int, [vp, dp, dp, C.c_int]),
         'okmc_dipole_self_terms': (C.c_int, [vp, dp, C.c_int]),
         'okmc_get_stencil': (C.c_int, [vp, i32, i32, dp, dp, i32, C.POINTER(i32), C.POINTER(C.c_double)]),
@@ -277,6 +278,15 @@ class Grid:
         m = len(pos)
         self._chk(self.lib.okmc_point_dipole_energies(self.h, pos.ctypes.data if m else None, P.ctypes.data if m else None,
                                                       m, out.ctypes.data if m else None, 0))
+        return out
+
+    def shift_energies(self, i, X):
+        """okmc_shift_energies on host arrays: defect i moved to positions X (m, 3) nm."""
+        X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+        out = np.zeros(len(X))
+        m = len(X)
+        self._chk(self.lib.okmc_shift_energies(self.h, int(i), X.ctypes.data if m else None, m,
+                                               out.ctypes.data if m else None, 0))
         return out
 
     def self_terms(self):

@@ -191,7 +191,7 @@ def test_dislocation_workload_geometry():
 
 
 def test_python_marshalling_of_dislocations_and_point_dipoles():
-    """Grid.set_dislocations and Grid.point_dipole_energies hand the C calls flat,
+    """Grid.set_dislocations, point_dipole_energies and shift_energies hand the C calls flat,
     contiguous arrays in the documented layouts (checked with a stand-in library that
     reads the pointers during the call; no GPU)."""
     import ctypes as C
@@ -215,6 +215,11 @@ def test_python_marshalling_of_dislocations_and_point_dipoles():
             seen['dev'] = on_device
             return ok.OKMC_OK
 
+        def okmc_shift_energies(self, h, i, X, m, E, on_device):
+            seen['i'], seen['X'] = i, rd(X, C.c_double, 3 * m).reshape(-1, 3)
+            np.ctypeslib.as_array(C.cast(E, C.POINTER(C.c_double)), shape=(m,))[:] = -np.arange(m)
+            return ok.OKMC_OK
+
     g = object.__new__(ok.Grid)
     g.lib, g.h = FakeLib(), C.c_void_p(1)
     loop = np.arange(12, dtype=np.float32).reshape(4, 3)           # converted to float64
@@ -227,4 +232,7 @@ def test_python_marshalling_of_dislocations_and_point_dipoles():
     E = g.point_dipole_energies(pos, [1, 2, 3, 4, 5, 6])
     assert np.array_equal(seen['pos'], pos) and np.array_equal(seen['P'], [[1, 2, 3, 4, 5, 6]] * 2)
     assert np.array_equal(E, [0.5, 1.5]) and seen['dev'] == 0
+    X = np.arange(9, dtype=np.float32).reshape(3, 3) * 0.1
+    assert np.array_equal(g.shift_energies(2, X), [0.0, -1.0, -2.0])
+    assert seen['i'] == 2 and np.array_equal(seen['X'], X.astype(np.float64))
     g.h = None
