@@ -601,30 +601,3 @@ def test_dislocation_background_survives_steps_and_can_be_removed():
     assert np.array_equal(a.eigenstrain(), c.eigenstrain())
     for x in (a, b, c):
         x.close()
-
-
-@pytest.mark.parametrize('precision', [ok.FP64_FIELDS, ok.FP32_FIELDS])
-def test_point_dipole_energies_match_oracle(precision):
-    """Point defects of given dipole tensor (Table 1's <110> dumbbell and an arbitrary
-    one) probing the field of dislocation lines and two defects (Eq.
-    interaction_energy4, eps = C^-1 : sigma at the site centre), against the oracle;
-    a site off the lattice is rejected."""
-    n, h = (32, 48, 32), 0.2855
-    lines = _dislocation_case(n, h)
-    defs = make_defects([O.LOOP_111, O.SIA_CLUSTER], np.array([[24, 60, 16], [41, 21, 47]]), [1, 0], [0.6, 0.0],
-                        [0, 3], [0.1, 0.3], [1, 2])
-    C = O.stiffness_cubic(*FE_CUBIC)
-    g = ok.Grid(n, h, *FE_CUBIC, precision=precision, seed=3)
-    g.set_dislocations(lines)
-    g.set_defects(defs)
-    sig = O.solve_stress(O.eigenstrain_field(defs, n, h) + _oracle_dislocation_eigenstrain(lines, n, h, 0.25 * h), C, h)
-    pos = np.array([[10, 20, 30], [11, 21, 31], [0, 0, 0], [63, 95, 63], [30, 60, 20], [33, 7, 45]])
-    P = np.stack([O.SIA_110_DIPOLE_EV] * 3 + [np.array([3.0, -1.0, 2.0, 0.5, -0.7, 1.1])] * 3)
-    E = g.point_dipole_energies(pos, P)
-    Eo = np.array([O.point_dipole_energy(P[k], pos[k], sig, C) for k in range(len(pos))])
-    assert np.abs(E - Eo).max() <= ENERGY_TOL[precision], np.abs(E - Eo)
-    assert np.abs(Eo).max() > 1e-3
-    with pytest.raises(ok.OkmcError):
-        g.point_dipole_energies(np.array([[10, 21, 30]]), P[:1])
-    assert np.allclose(g.point_dipole_energies(pos[:2], P[:2]), E[:2], rtol=0, atol=0)
-    g.close()

@@ -1,6 +1,7 @@
-"""The shift-theorem evaluation at continuous positions (Sec. 3.3, Eq. shift) through the
-C ABI against the oracle's (Parseval sum of the elastic-strain form with the defect's
-class-0 reference field moved by exp(-i xi.X)).
+"""Energies of probes of the field through the C ABI against the oracle: a defect moved
+to continuous positions by the shift theorem (Sec. 3.3, Eq. shift; the Parseval sum of
+the elastic-strain form with the defect's class-0 reference field moved by
+exp(-i xi.X)), and point defects of given dipole tensor (Eq. interaction_energy4, Table 1).
 
 Bars: 1e-8 eV with FP64 fields, 1e-4 eV with FP32 fields.
 """
@@ -72,3 +73,32 @@ def test_shift_energy_at_a_site_is_the_stencil_energy_on_the_grid():
     assert np.array_equal(a.get_positions(), b.get_positions())
     for g in (a, b):
         g.close()
+
+
+@pytest.mark.parametrize('precision', [ok.FP64_FIELDS, ok.FP32_FIELDS])
+def test_point_dipole_energies_match_oracle(precision):
+    """Point defects of given dipole tensor (Table 1's <110> dumbbell and an arbitrary
+    one) probing the field of a dislocation line and two defects (eps = C^-1 : sigma at
+    the site centre), against the oracle; a site off the lattice is rejected."""
+    n, h = (32, 48, 32), 0.2855
+    L = np.asarray(n) * h
+    line = np.array([[0.55 * L[0], 0.1, 0.85 * L[2]], [0.55 * L[0], 0.1 + L[1], 0.85 * L[2]]])
+    lines = [(line, 0.5 * h * np.ones(3), False)]
+    defs = make_defects([O.LOOP_111, O.SIA_CLUSTER], np.array([[24, 60, 16], [41, 21, 47]]), [1, 0], [0.6, 0.0],
+                        [0, 3], [0.1, 0.3], [1, 2])
+    C = O.stiffness_cubic(*FE_CUBIC)
+    g = ok.Grid(n, h, *FE_CUBIC, precision=precision, seed=3)
+    g.set_dislocations(lines)
+    g.set_defects(defs)
+    eps_d = O.dislocation_eigenstrain6(O.nye_tensor(line, lines[0][1], n, h, closed=False), h)
+    sig = O.solve_stress(O.eigenstrain_field(defs, n, h) + eps_d, C, h)
+    pos = np.array([[10, 20, 30], [11, 21, 31], [0, 0, 0], [63, 95, 63], [30, 60, 20], [33, 7, 45]])
+    P = np.stack([O.SIA_110_DIPOLE_EV] * 3 + [np.array([3.0, -1.0, 2.0, 0.5, -0.7, 1.1])] * 3)
+    E = g.point_dipole_energies(pos, P)
+    Eo = np.array([O.point_dipole_energy(P[k], pos[k], sig, C) for k in range(len(pos))])
+    assert np.abs(E - Eo).max() <= TOL[precision], np.abs(E - Eo)
+    assert np.abs(Eo).max() > 1e-3
+    with pytest.raises(ok.OkmcError):
+        g.point_dipole_energies(np.array([[10, 21, 30]]), P[:1])
+    assert np.array_equal(g.point_dipole_energies(pos[:2], P[:2]), E[:2])
+    g.close()
