@@ -429,6 +429,8 @@ def test_p14_table1_conversions():
     B = (g['C11_GPa'] + 2 * g['C12_GPa']) / 3.0
     dv = (P['P11'] + P['P22'] + P['P33']) / O.KAPPA / (3 * B)      # nm^3
     assert abs(dv / omega - g['relaxation_volume_over_Vat']) < 2e-3
+    # the oracle's copy of the tensor, in (xx, yy, zz, yz, xz, xy) order
+    assert np.array_equal(O.SIA_110_DIPOLE_EV, [P['P11'], P['P22'], P['P33'], P['P23'], P['P13'], P['P12']])
 
 
 # ---------------------------------------------------------------- dipole approximation
