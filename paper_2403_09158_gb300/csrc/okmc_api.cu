@@ -1219,10 +1219,11 @@ int okmc_set_dislocations(okmc_grid* g, const double* points, const int32_t* cou
       for (void* p : t) dfree(g, p);
     };
     int rc = OKMC_OK;
-    auto bail = [&](int code) {
+    auto bail = [&](int code) {  // the error is reported once: the device flag is cleared
       release();
       dfree(g, g->d_bg);
       g->d_bg = nullptr;
+      cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st);
       voxelise_all(g);
       return code;
     };
