@@ -349,7 +349,7 @@ def run_kinetics(args):
     cases = []
     t_total = 0.0
     for x_rel in (10.0, 20.0):
-        w = config_kinetics(x_rel)
+        w = config_kinetics(x_rel, n=args.box)
         tr, clock, sec = _loop_ensemble(ok, w, runs, steps, every, stream)
         t_total += sec
         rel = tr[:, :, 1] - tr[:, :, 0]
@@ -360,8 +360,8 @@ def run_kinetics(args):
         cases.append(case)
     out = {'metric': 'two-loop kinetics, loop coordinates along [111] against time', 'unit': 'nm',
            'data': 'synthetic', 'dtype': 'f32 fields / f64 energies',
-           'config': {'workload': 'kinetics_two_loops_256cubed (1/2<111> loops R = 3.3 nm, E_m = 0.1 eV, 300 K, '
-                                  'Table 1 constants, 500 fixed-dt steps, 10 runs per case)'},
+           'config': {'workload': 'kinetics_two_loops_%dcubed (1/2<111> loops R = 3.3 nm, E_m = 0.1 eV, 300 K, '
+                                  'Table 1 constants, 500 fixed-dt steps, 10 runs per case)' % args.box},
            'cases': cases, 'seconds': t_total, 'clocks': clk.stop()}
     print(json.dumps(out))
     return 0
@@ -383,7 +383,7 @@ def run_dislocation(args):
 
     stream = torch.cuda.current_stream()
     clk = Clocks(torch.cuda.current_device())
-    w = config_dislocation_loops(20.0)
+    w = config_dislocation_loops(20.0, n=args.box)
     lines = w.extra['lines']
     # (1) energy profile of loop 2 alone
     g = ok.Grid(w.n, w.voxel_nm, *w.C, stream=stream.cuda_stream)
@@ -419,7 +419,7 @@ def run_dislocation(args):
     cases = []
     t_total = 0.0
     for x_c in (20.0, 30.0):
-        wc = config_dislocation_loops(x_c)
+        wc = config_dislocation_loops(x_c, n=args.box)
         tr, clock, sec = _loop_ensemble(ok, wc, 10, 500, 10, stream, lines=lines)
         t_total += sec
         case = {'x_c_nm': x_c, 'x_nm': wc.extra['x_nm'], 'z_nm': wc.extra['z_nm']}
@@ -427,8 +427,8 @@ def run_dislocation(args):
         cases.append(case)
     out = {'metric': 'loops near an edge dislocation: energy profile and kinetics along [111]', 'unit': 'eV, nm',
            'data': 'synthetic', 'dtype': 'f32 fields / f64 energies',
-           'config': {'workload': 'dislocation_two_loops_256cubed (edge dislocation [-1-12], b = a0/2 [111]; '
-                                  '1/2<111> loops R = 3.3 nm, E_m = 0.1 eV, 300 K, Table 1 constants)'},
+           'config': {'workload': 'dislocation_two_loops_%dcubed (edge dislocation [-1-12], b = a0/2 [111]; '
+                                  '1/2<111> loops R = 3.3 nm, E_m = 0.1 eV, 300 K, Table 1 constants)' % args.box},
            'setup_seconds': t_setup, 'profile_x_E_Edipole': profile, 'profile_sia_x_E': profile_sia,
            'cases': cases, 'seconds': t_total,
            'clocks': clk.stop()}
@@ -685,6 +685,8 @@ def main():
                     help='large: the 256^3 single-replica step (default); batch: the 64-replica ensemble; '
                          'serve: the request server under Poisson load; small / medium: the 32^3 FP64 and '
                          'the 128^3 workloads')
+    ap.add_argument('--box', type=int, default=256, help='kinetics, dislocation: box edge in voxels (512 is close to the '
+                                                          "paper's 500 a0)")
     ap.add_argument('--rates', default='10,30,100,300,1000,2000', help='serve: offered request rates (1/s)')
     ap.add_argument('--seconds', type=float, default=4.0, help='serve: length of each rate\'s request stream')
     ap.add_argument('--max-requests', type=int, default=600, help='serve: cap on requests per rate')
