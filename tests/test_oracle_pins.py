@@ -703,6 +703,26 @@ def test_fdm_loop_nye_tensor_moments_and_mean():
     assert np.allclose(eps.reshape(6, -1).sum(axis=1), slab.reshape(6, -1).sum(axis=1), rtol=1e-10, atol=1e-12)
 
 
+def test_fdm_nye_tensor_moments_of_arbitrary_closed_lines():
+    """For any closed polyline (here non-planar random ones, away from the box edges) the
+    spread Nye tensor integrates to zero and its first moment is b_i oint x_m dx_l =
+    b_i eps_mlp A_p with A = 1/2 oint x x dx: trilinear spreading keeps first moments and
+    the midpoint rule is exact on straight segments."""
+    rng = np.random.default_rng(11)
+    n = (24, 24, 24)
+    centre = np.full(3, 12 * H)
+    for trial in range(3):
+        pts = centre + rng.normal(scale=0.6, size=(int(rng.integers(5, 12)), 3))
+        b = rng.normal(size=3) * 0.2
+        alpha = O.nye_tensor(pts, b, n, H, closed=True)
+        assert np.abs(alpha.reshape(9, -1).sum(axis=1)).max() * H ** 3 < 1e-12
+        x = (np.indices(n).reshape(3, -1).T + 0.5) * H
+        M = np.einsum('ilv,vm->ilm', alpha.reshape(3, 3, -1), x) * H ** 3
+        A = 0.5 * np.sum(np.cross(pts, np.roll(pts, -1, axis=0)), axis=0)
+        expect = np.einsum('i,mlp,p->ilm', b, O.LEVI_CIVITA, A)
+        assert np.abs(M - expect).max() <= 1e-10 * max(1.0, np.abs(expect).max()), trial
+
+
 def test_fdm_loop_approaches_slab_loop_with_resolution():
     """The same prismatic loop as a line (Nye tensor, this route) and as the one-voxel
     slab of Eq. eig_shearloop: a loop's stress depends on its line only, so away from the
