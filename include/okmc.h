@@ -403,14 +403,18 @@ int okmc_server_destroy(okmc_server* s);
  * plan, or embedded callers whose allocator forbids cudaMalloc after start-up).
  * It does what okmc_solve_stress does for a grid, from an eigenstrain field the
  * caller provides: eps and sigma are device pointers to 6*nx*ny*nz floats each,
- * layout [c][z][y][x], both owned by the caller; n = {nx, ny, nz} as for
+ * layout [c][z][y][x], both owned by the caller and 8-byte aligned (rows are read
+ * and written as float pairs; a misaligned pointer returns OKMC_EINVAL before any
+ * launch); n = {nx, ny, nz} as for
  * okmc_grid_create; C11, C12, C44 in GPa; k0_mode as in okmc_grid_desc; stream is
  * a cudaStream_t (NULL = legacy stream).  It allocates nothing: the half spectrum
  * and twiddle tables live in one static device array of 6.5 MB (room for
  * 6*(nx/2+1)*ny*nz <= 6*33*64*64 complex values, e.g. 64^3 voxels) that every GPU
  * loading this library keeps until the process exits.  Larger grids return
  * OKMC_EINVAL.  The first call on a device looks up the array's device address
- * (with that device current), so make that first call outside any stream capture.
+ * (with that device current), so make that first call outside any stream capture;
+ * that lookup is done once per device under a lock, so first calls from several
+ * host threads at once are safe.
  * All calls share the array and leave their data in it: two calls whose work
  * overlaps on the GPU (different streams, different host threads) race and give
  * wrong results; serialise them.  Returns OKMC_OK, OKMC_EINVAL or OKMC_ECUDA

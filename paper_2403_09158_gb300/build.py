@@ -4,6 +4,7 @@ Plain nvcc, one object per translation unit compiled in parallel, then one link.
 """
 from __future__ import annotations
 
+import hashlib
 import os
 import shutil
 import subprocess
@@ -26,17 +27,34 @@ def nvcc_path():
     raise RuntimeError('nvcc not found')
 
 
-def _stale():
-    if not os.path.exists(LIB):
+STAMP = LIB + '.sha256'
+
+
+def source_hash():
+    """SHA-256 over the sources, the public header, this script and the compiler flags."""
+    h = hashlib.sha256()
+    deps = sorted(os.path.join(SRC, f) for f in os.listdir(SRC)) + [os.path.join(ROOT, 'include', 'okmc.h'), __file__]
+    for p in deps:
+        h.update(os.path.basename(p).encode())
+        with open(p, 'rb') as f:
+            h.update(f.read())
+    h.update(' '.join(ARCH + FLAGS).encode())
+    return h.hexdigest()
+
+
+def _stale(digest):
+    # keyed on content, not on modification times: a library copied next to its sources
+    # with newer times is still rebuilt unless it was built from exactly these sources
+    if not os.path.exists(LIB) or not os.path.exists(STAMP):
         return True
-    t = os.path.getmtime(LIB)
-    deps = [os.path.join(SRC, f) for f in os.listdir(SRC)] + [os.path.join(ROOT, 'include', 'okmc.h'), __file__]
-    return any(os.path.getmtime(p) > t for p in deps)
+    with open(STAMP) as f:
+        return f.read().strip() != digest
 
 
 def build(force=False, verbose=False):
-    """Build the library if a source is newer than it; return its path."""
-    if not force and not _stale():
+    """Build the library unless it was built from the current sources; return its path."""
+    digest = source_hash()
+    if not force and not _stale(digest):
         return LIB
     os.makedirs(OUT, exist_ok=True)
     nvcc = nvcc_path()
@@ -62,6 +80,8 @@ def build(force=False, verbose=False):
     if r.returncode != 0:
         raise RuntimeError('link failed:\n' + r.stdout.decode(errors='replace'))
     os.replace(tmp, LIB)
+    with open(STAMP, 'w') as f:
+        f.write(digest + '\n')
     return LIB
 
 

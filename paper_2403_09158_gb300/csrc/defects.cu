@@ -69,6 +69,9 @@ __global__ void k_defect_setup(const okmc_defect* __restrict__ d, DefGeo* __rest
   }
   g.allowed = mask;
   g.z = __popc(mask);
+  g.escale = g.kind == 0 ? ((r.type == OKMC_LOOP_111) ? 0.86602540378443864676 : 1.0) / (double)g.a2 : g.e6[0];
+  if (!(g.escale > 0.0)) g.escale = 1.0;
+  for (int a = 0; a < 6; ++a) g.ew[a] = (float)((a < 3 ? 1.0 : 2.0) * g.e6[a] / g.escale);
   G[i] = g;
 }
 
@@ -208,6 +211,24 @@ __device__ __forceinline__ void fixed_add<int64_t>(int64_t* p, long long v) {
 
 __device__ __forceinline__ int wrap(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
 
+// Fixed-point value of one stencil entry: floor(val + u) with u in [0, 1) drawn from a
+// hash of the entry's index k and the component.  Its mean over u is val exactly, and the
+// errors of different entries are independent.  Rounding to nearest would give every
+// voxel of a loop that has the same coverage count (most of them) the same error, a
+// coherent change of the loop's whole eigenstrain by up to half a quantum per voxel:
+// 1.5e-8 relative for a <100> loop, 1.5e-5 eV of its 860 eV self term at 256^3.  A
+// function of (k, comp) only, so a later removal subtracts the very same integer.
+__device__ __forceinline__ long long fixed_of(double val, int k, int comp) {
+  uint32_t h = (uint32_t)k * 6u + (uint32_t)comp;
+  h ^= h >> 16;
+  h *= 0x7feb352dU;
+  h ^= h >> 15;
+  h *= 0x846ca68bU;
+  h ^= h >> 16;
+  const double u = (double)(h >> 8) * (1.0 / 16777216.0);
+  return __double2ll_rd(val + u);
+}
+
 // Adds sign * (count * alpha * eps*) of the class-c stencil of defect i placed at
 // half-lattice position pos to the fixed-point field (quantum q, limit lim).
 template <class Q>
@@ -228,7 +249,7 @@ __device__ void scatter_stencil(Q* __restrict__ eps, int3 n, size_t N, const Def
     for (int comp = 0; comp < 6; ++comp) {
       const double val = w * g.e6[comp] * rq;
       if (fabs(val) > lim) atomicExch(err, 4);
-      const long long iv = __double2ll_rn(val);
+      const long long iv = fixed_of(val, k, comp);
       if (iv) {
         fixed_add<Q>(eps + comp * N + v, sign * iv);
         if (dirty) dirty[comp * n.z + zz] = 1;  // same value from every writer
@@ -459,10 +480,35 @@ __device__ __forceinline__ bool unit_freq(const PassCfg& c, int kx, int ky, int 
   return true;
 }
 
+// A value of Q_t rounded to the table precision.  FP32: rounded up or down at random
+// (a hash of the table index), up with probability (v - lo)/(hi - lo), so that the
+// stored value is v on average.  A loop's spectrum lies in a narrow cone about its
+// normal, where Q_t hardly varies: rounded to nearest, all of those frequencies would
+// carry the same rounding error, a coherent relative error of up to 3e-8 in the loop's
+// self term (2e-5 eV for a 4 nm <100> loop); rounded at random, the errors are
+// independent and average out over the cone.
+template <class QT>
+__device__ __forceinline__ QT table_value(double v, size_t idx);
+template <>
+__device__ __forceinline__ double table_value<double>(double v, size_t) { return v; }
+template <>
+__device__ __forceinline__ float table_value<float>(double v, size_t idx) {
+  const float lo = __double2float_rd(v), hi = __double2float_ru(v);
+  if (lo == hi) return lo;
+  uint32_t h = (uint32_t)idx ^ (uint32_t)(idx >> 32) * 0x9e3779b9U;
+  h ^= h >> 16;
+  h *= 0x7feb352dU;
+  h ^= h >> 15;
+  h *= 0x846ca68bU;
+  h ^= h >> 16;
+  const double u = (double)(h >> 8) * (1.0 / 16777216.0);
+  return u * ((double)hi - (double)lo) < v - (double)lo ? hi : lo;
+}
+
 // Q_t(xi) = E_t : M(xi) : E_t for each defect type present, [t][kz][p].  It is
 // evaluated in FP64 whatever the field precision (a difference of two terms of
 // similar size; an FP32 evaluation biases the self terms by ~2e-7 relative) and
-// stored in QT.  A defect's q is s^2 Q_t with e = s E_t.
+// stored in QT (table_value).  A defect's q is s^2 Q_t with e = s E_t.
 template <class QT>
 __global__ void __launch_bounds__(256) k_qtable(QT* __restrict__ out, PassCfg c, QTypes qt) {
   const size_t P = (size_t)(c.H + 1) * c.ny;
@@ -489,7 +535,7 @@ __global__ void __launch_bounds__(256) k_qtable(QT* __restrict__ out, PassCfg c,
         if (nx_ || ny_ || nz_)
           v = 0.5 * (v + q_of<double>(tau, te, nx_ ? -m0 : m0, ny_ ? -m1 : m1, nz_ ? -m2 : m2, c.C11, c.C12, c.C44));
       }
-      out[(size_t)t * total + idx] = (QT)v;
+      out[(size_t)t * total + idx] = table_value<QT>(v, (size_t)t * total + idx);
     }
   }
 }
@@ -611,6 +657,7 @@ __device__ __forceinline__ double csum_value(const CSum& a) { return (double)a.s
 
 constexpr int kEnergyThreads = 256;
 
+
 template <class T>
 struct EAcc;
 template <>
@@ -655,8 +702,12 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
   const okmc_defect r = d[i];
   const DefGeo g = G[i];
   const int c = r.pos[0] & 1, cp = 1 - c;
+  // the weights e_i (off-diagonals twice) in units of the defect's scale, whose FP64
+  // value multiplies the sums at the end: every weight is 0, +-1 or +-2, exact in FP32,
+  // whereas e itself rounded to FP32 (1/(2 sqrt 3) for a 1/2<111> loop: -1.8e-8
+  // relative) would bias every sum, self part included, by that ratio
   T ew[6];
-  for (int a = 0; a < 6; ++a) ew[a] = T(a < 3 ? g.e6[a] : 2.0 * g.e6[a]);
+  for (int a = 0; a < 6; ++a) ew[a] = T(g.ew[a]);
   // components with zero weight (a <100> loop needs sigma_xx only, a dilatation the
   // trace) are not gathered; adding their zero products would not change any sum
   bool use[6];
@@ -759,8 +810,9 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
   if (lane < 9)
     for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += part[w2][lane];
   double ej = 0.0;
-  if (lane == 0) ej = pref * alpha[2 * i + c] * tot - W[(size_t)i * 18 + c * 9];
-  else if (lane < 9) ej = pref * alpha[2 * i + cp] * tot - W[(size_t)i * 18 + c * 9 + lane];
+  const double es = G[i].escale;  // read again here rather than held in registers
+  if (lane == 0) ej = pref * es * alpha[2 * i + c] * tot - W[(size_t)i * 18 + c * 9];
+  else if (lane < 9) ej = pref * es * alpha[2 * i + cp] * tot - W[(size_t)i * 18 + c * 9 + lane];
   const double e0 = __shfl_sync(0xffffffffu, ej, 0);
   if (lane == 0) E[i] = e0;
   if (!want_cand) return;

@@ -70,58 +70,84 @@ template <bool INV> __device__ __forceinline__ void pdft5(C2<float>* v) {
   v[2] = add_rot<INV>(m2, n2);
   v[3] = sub_rot<INV>(m2, n2);
 }
+// tan(pi j / 240) and sin(2 pi j / 240) for the j that the compile-time twiddles use
+// (multiples of 240/R for R = 6, 8, 10, 12, 16, 20, 24, up to a quarter turn)
+__device__ __forceinline__ float tan240(int j) {
+  switch (j) {
+    case 10: return 0.1316524975873958534715f;
+    case 12: return 0.1583844403245362938388f;
+    case 15: return 0.1989123673796580069115f;
+    case 20: return 0.2679491924311227064725f;
+    case 24: return 0.3249196962329063261558f;
+    case 30: return 0.4142135623730950488016f;
+    case 36: return 0.5095254494944288105137f;
+    case 40: return 0.5773502691896257645091f;
+    case 45: return 0.6681786379192989199977f;
+    case 48: return 0.7265425280053608858954f;
+    case 50: return 0.7673269879789603429230f;
+    case 60: return 1.0000000000000000000000f;
+    default: return 0.0f;
+  }
+}
+__device__ __forceinline__ float sin240(int j) {
+  switch (j) {
+    case 10: return 0.2588190451025207623488f;
+    case 12: return 0.3090169943749474241022f;
+    case 15: return 0.3826834323650897717284f;
+    case 20: return 0.5000000000000000000000f;
+    case 24: return 0.5877852522924731291687f;
+    case 30: return 0.7071067811865475244008f;
+    case 36: return 0.8090169943749474241022f;
+    case 40: return 0.8660254037844386467637f;
+    case 45: return 0.9238795325112867561281f;
+    case 48: return 0.9510565162951535721164f;
+    case 50: return 0.9659258262890682867497f;
+    case 60: return 1.0000000000000000000000f;
+    default: return 0.0f;
+  }
+}
+
+// v * exp(-+2 pi i e / R) (minus sign forward) for a compile-time e and R dividing 240:
+// quarter turns exactly, any other angle as a rotation by three shears (lift).
+template <int R, bool INV>
+__device__ __forceinline__ C2<float> twc(C2<float> v, int e) {
+  e %= R;
+  if (e == 0) return v;
+  if (4 * e == R) return rot<float, INV>(v);
+  if (2 * e == R) return C2<float>{-v.x, -v.y};
+  if (4 * e == 3 * R) return rot<float, !INV>(v);
+  int j = -e * (240 / R);  // forward angle in units of 2 pi / 240, in (-240, 0)
+  if (j <= -120) j += 240;  // (-120, 120]
+  bool neg = false;
+  if (j < -60) {
+    j += 120;
+    neg = true;
+  } else if (j > 60) {
+    j -= 120;
+    neg = true;
+  }
+  if (INV) j = -j;
+  const float t = j >= 0 ? tan240(j) : -tan240(-j);
+  const float s = j >= 0 ? sin240(j) : -sin240(-j);
+  const C2<float> r = lift(v, t, s);
+  return neg ? C2<float>{-r.x, -r.y} : r;
+}
+
 template <bool INV> __device__ __forceinline__ void pdft8(C2<float>* v) {
-  const float h = 0.70710678118654752440f;  // sqrt(1/2)
   C2<float> e[4] = {v[0], v[2], v[4], v[6]};
   C2<float> o[4] = {v[1], v[3], v[5], v[7]};
   pdft4<INV>(e);
   pdft4<INV>(o);
-  // w8 o1 = h * t1 and w8^3 o3 = h * t3 with w8 = exp(-+ i pi / 4)
-  const C2<float> t1 = INV ? C2<float>{o[1].x - o[1].y, o[1].x + o[1].y} : C2<float>{o[1].x + o[1].y, o[1].y - o[1].x};
-  const C2<float> t3 = INV ? C2<float>{-o[3].x - o[3].y, o[3].x - o[3].y} : C2<float>{o[3].y - o[3].x, -o[3].x - o[3].y};
+  // w8 o1 and w8^3 o3 with w8 = exp(-+ i pi / 4)
+  const C2<float> t1 = twc<8, INV>(o[1], 1), t3 = twc<8, INV>(o[3], 3);
   v[0] = padd(e[0], o[0]);
   v[4] = psub(e[0], o[0]);
-  v[1] = pfma(h, t1, e[1]);
-  v[5] = pfma(-h, t1, e[1]);
+  v[1] = padd(e[1], t1);
+  v[5] = psub(e[1], t1);
   v[2] = add_rot<INV>(e[2], o[2]);
   v[6] = sub_rot<INV>(e[2], o[2]);
-  v[3] = pfma(h, t3, e[3]);
-  v[7] = pfma(-h, t3, e[3]);
-}
-
-// cos and sin of 2 pi e / 16 for e = 0..15
-__device__ __forceinline__ float cos16(int e) {
-  switch (e & 15) {
-    case 0: return 1.0f;
-    case 1: return 0.92387953251128676f;
-    case 2: return 0.70710678118654752f;
-    case 3: return 0.38268343236508977f;
-    case 4: return 0.0f;
-    case 5: return -0.38268343236508977f;
-    case 6: return -0.70710678118654752f;
-    case 7: return -0.92387953251128676f;
-    case 8: return -1.0f;
-    case 9: return -0.92387953251128676f;
-    case 10: return -0.70710678118654752f;
-    case 11: return -0.38268343236508977f;
-    case 12: return 0.0f;
-    case 13: return 0.38268343236508977f;
-    case 14: return 0.70710678118654752f;
-    default: return 0.92387953251128676f;
-  }
-}
-__device__ __forceinline__ float sin16(int e) { return cos16(e - 4); }
-
-// v * exp(-+2 pi i e / 16) with the trivial exponents kept exact
-template <bool INV>
-__device__ __forceinline__ C2<float> tw16(C2<float> v, int e) {
-  e &= 15;
-  if (e == 0) return v;
-  if (e == 4) return rot<float, INV>(v);
-  if (e == 8) return C2<float>{-v.x, -v.y};
-  if (e == 12) return rot<float, !INV>(v);
-  const float c = cos16(e), s = INV ? sin16(e) : -sin16(e);
-  return cmul_rn(v, C2<float>{c, s});
+  v[3] = padd(e[3], t3);
+  v[7] = psub(e[3], t3);
 }
 
 template <bool INV>
@@ -132,7 +158,7 @@ __device__ __forceinline__ void dft16(C2<float>* v) {
     C2<float> a[4] = {v[n1], v[n1 + 4], v[n1 + 8], v[n1 + 12]};
     pdft4<INV>(a);
 #pragma unroll
-    for (int k2 = 0; k2 < 4; ++k2) y[n1 * 4 + k2] = tw16<INV>(a[k2], n1 * k2);
+    for (int k2 = 0; k2 < 4; ++k2) y[n1 * 4 + k2] = twc<16, INV>(a[k2], n1 * k2);
   }
 #pragma unroll
   for (int k2 = 0; k2 < 4; ++k2) {
@@ -143,196 +169,8 @@ __device__ __forceinline__ void dft16(C2<float>* v) {
   }
 }
 
-template <int N> __device__ __forceinline__ float cosN(int e);
-template <int N> __device__ __forceinline__ float sinN(int e);
-// cos and sin of 2 pi e / N for the composite register DFTs (e = 0..N-1)
-template <> __device__ __forceinline__ float cosN<6>(int e) {
-  switch (e) {
-    case 0: return 1.0f;
-    case 1: return 0.5f;
-    case 2: return -0.5f;
-    case 3: return -1.0f;
-    case 4: return -0.5f;
-    default: return 0.5f;
-  }
-}
-template <> __device__ __forceinline__ float sinN<6>(int e) {
-  switch (e) {
-    case 0: return 0.0f;
-    case 1: return 0.8660254037844386f;
-    case 2: return 0.86602540378443871f;
-    case 3: return 0.0f;
-    case 4: return -0.86602540378443837f;
-    default: return -0.8660254037844386f;
-  }
-}
-template <> __device__ __forceinline__ float cosN<10>(int e) {
-  switch (e) {
-    case 0: return 1.0f;
-    case 1: return 0.80901699437494745f;
-    case 2: return 0.30901699437494745f;
-    case 3: return -0.30901699437494734f;
-    case 4: return -0.80901699437494734f;
-    case 5: return -1.0f;
-    case 6: return -0.80901699437494756f;
-    case 7: return -0.30901699437494756f;
-    case 8: return 0.30901699437494723f;
-    default: return 0.80901699437494734f;
-  }
-}
-template <> __device__ __forceinline__ float sinN<10>(int e) {
-  switch (e) {
-    case 0: return 0.0f;
-    case 1: return 0.58778525229247314f;
-    case 2: return 0.95105651629515353f;
-    case 3: return 0.95105651629515364f;
-    case 4: return 0.58778525229247325f;
-    case 5: return 0.0f;
-    case 6: return -0.58778525229247303f;
-    case 7: return -0.95105651629515353f;
-    case 8: return -0.95105651629515364f;
-    default: return -0.58778525229247336f;
-  }
-}
-template <> __device__ __forceinline__ float cosN<12>(int e) {
-  switch (e) {
-    case 0: return 1.0f;
-    case 1: return 0.86602540378443871f;
-    case 2: return 0.5f;
-    case 3: return 0.0f;
-    case 4: return -0.5f;
-    case 5: return -0.86602540378443871f;
-    case 6: return -1.0f;
-    case 7: return -0.86602540378443882f;
-    case 8: return -0.5f;
-    case 9: return 0.0f;
-    case 10: return 0.5f;
-    default: return 0.86602540378443837f;
-  }
-}
-template <> __device__ __forceinline__ float sinN<12>(int e) {
-  switch (e) {
-    case 0: return 0.0f;
-    case 1: return 0.5f;
-    case 2: return 0.8660254037844386f;
-    case 3: return 1.0f;
-    case 4: return 0.86602540378443871f;
-    case 5: return 0.5f;
-    case 6: return 0.0f;
-    case 7: return -0.5f;
-    case 8: return -0.86602540378443837f;
-    case 9: return -1.0f;
-    case 10: return -0.8660254037844386f;
-    default: return -0.5f;
-  }
-}
-template <> __device__ __forceinline__ float cosN<20>(int e) {
-  switch (e) {
-    case 0: return 1.0f;
-    case 1: return 0.95105651629515353f;
-    case 2: return 0.80901699437494745f;
-    case 3: return 0.58778525229247314f;
-    case 4: return 0.30901699437494745f;
-    case 5: return 0.0f;
-    case 6: return -0.30901699437494734f;
-    case 7: return -0.58778525229247303f;
-    case 8: return -0.80901699437494734f;
-    case 9: return -0.95105651629515353f;
-    case 10: return -1.0f;
-    case 11: return -0.95105651629515375f;
-    case 12: return -0.80901699437494756f;
-    case 13: return -0.58778525229247325f;
-    case 14: return -0.30901699437494756f;
-    case 15: return 0.0f;
-    case 16: return 0.30901699437494723f;
-    case 17: return 0.58778525229247292f;
-    case 18: return 0.80901699437494734f;
-    default: return 0.95105651629515353f;
-  }
-}
-template <> __device__ __forceinline__ float sinN<20>(int e) {
-  switch (e) {
-    case 0: return 0.0f;
-    case 1: return 0.3090169943749474f;
-    case 2: return 0.58778525229247314f;
-    case 3: return 0.80901699437494745f;
-    case 4: return 0.95105651629515353f;
-    case 5: return 1.0f;
-    case 6: return 0.95105651629515364f;
-    case 7: return 0.80901699437494745f;
-    case 8: return 0.58778525229247325f;
-    case 9: return 0.30901699437494751f;
-    case 10: return 0.0f;
-    case 11: return -0.3090169943749469f;
-    case 12: return -0.58778525229247303f;
-    case 13: return -0.80901699437494734f;
-    case 14: return -0.95105651629515353f;
-    case 15: return -1.0f;
-    case 16: return -0.95105651629515364f;
-    case 17: return -0.80901699437494756f;
-    case 18: return -0.58778525229247336f;
-    default: return -0.30901699437494762f;
-  }
-}
-template <> __device__ __forceinline__ float cosN<24>(int e) {
-  switch (e) {
-    case 0: return 1.0f;
-    case 1: return 0.96592582628906831f;
-    case 2: return 0.86602540378443871f;
-    case 3: return 0.70710678118654757f;
-    case 4: return 0.5f;
-    case 5: return 0.25881904510252074f;
-    case 6: return 0.0f;
-    case 7: return -0.25881904510252063f;
-    case 8: return -0.5f;
-    case 9: return -0.70710678118654746f;
-    case 10: return -0.86602540378443871f;
-    case 11: return -0.9659258262890682f;
-    case 12: return -1.0f;
-    case 13: return -0.96592582628906831f;
-    case 14: return -0.86602540378443882f;
-    case 15: return -0.70710678118654791f;
-    case 16: return -0.5f;
-    case 17: return -0.25881904510252063f;
-    case 18: return 0.0f;
-    case 19: return 0.2588190451025203f;
-    case 20: return 0.5f;
-    case 21: return 0.70710678118654735f;
-    case 22: return 0.86602540378443837f;
-    default: return 0.96592582628906809f;
-  }
-}
-template <> __device__ __forceinline__ float sinN<24>(int e) {
-  switch (e) {
-    case 0: return 0.0f;
-    case 1: return 0.25881904510252074f;
-    case 2: return 0.5f;
-    case 3: return 0.70710678118654746f;
-    case 4: return 0.8660254037844386f;
-    case 5: return 0.96592582628906831f;
-    case 6: return 1.0f;
-    case 7: return 0.96592582628906831f;
-    case 8: return 0.86602540378443871f;
-    case 9: return 0.70710678118654757f;
-    case 10: return 0.5f;
-    case 11: return 0.25881904510252102f;
-    case 12: return 0.0f;
-    case 13: return -0.25881904510252079f;
-    case 14: return -0.5f;
-    case 15: return -0.70710678118654713f;
-    case 16: return -0.86602540378443837f;
-    case 17: return -0.96592582628906831f;
-    case 18: return -1.0f;
-    case 19: return -0.96592582628906842f;
-    case 20: return -0.8660254037844386f;
-    case 21: return -0.70710678118654768f;
-    case 22: return -0.5f;
-    default: return -0.25881904510252157f;
-  }
-}
-
 // Composite register DFT of size R = P * Q (Cooley-Tukey in registers):
-// n = n1 + P n2, k = k2 + Q k1; twiddles exp(-+2 pi i n1 k2 / R) from the tables above.
+// n = n1 + P n2, k = k2 + Q k1; twiddles exp(-+2 pi i n1 k2 / R) as rotations (twc).
 template <int R> struct Split;
 template <> struct Split<6> { static constexpr int P = 2, Q = 3; };
 template <> struct Split<10> { static constexpr int P = 2, Q = 5; };
@@ -354,15 +192,7 @@ __device__ __forceinline__ void dft_composite(C2<float>* v) {
     for (int n2 = 0; n2 < Q; ++n2) a[n2] = v[n1 + P * n2];
     dft_reg<Q, INV>(a);
 #pragma unroll
-    for (int k2 = 0; k2 < Q; ++k2) {
-      const int e = (n1 * k2) % R;
-      if (e == 0) {
-        y[n1 * Q + k2] = a[k2];
-      } else {
-        const float c = cosN<R>(e), s = INV ? sinN<R>(e) : -sinN<R>(e);
-        y[n1 * Q + k2] = cmul_rn(a[k2], C2<float>{c, s});
-      }
-    }
+    for (int k2 = 0; k2 < Q; ++k2) y[n1 * Q + k2] = twc<R, INV>(a[k2], (n1 * k2) % R);
   }
 #pragma unroll
   for (int k2 = 0; k2 < Q; ++k2) {
@@ -405,17 +235,20 @@ struct XSkew {
   }
 };
 
-// Twiddles w_L^(n1*k2) as a padded [R1][R2 + 1] table: a warp's threads (consecutive
-// n1, one k2) then read distinct banks.  tw2 is filled by fill_tw2 from w_L^k.
+// Twiddles w_L^(n1*k2) as rotations (Lw) in a padded [R1][R2 + 1] table: a warp's
+// threads (consecutive n1, one k2) then read distinct banks.  tw2 is filled by fill_tw2
+// from the table of w_L^m, m < L (n1 k2 < R1 R2 = L).
 template <int L>
 __host__ __device__ constexpr int tw2_size() { return RegPlan<L>::R1 * (RegPlan<L>::R2 + 1); }
 template <int L>
-__device__ __forceinline__ void fill_tw2(C2<float>* tw2, const C2<float>* __restrict__ tw) {
+__device__ __forceinline__ Lw tw2_entry(const Lw* __restrict__ lw, int i) {
   constexpr int R2 = RegPlan<L>::R2;
-  for (int i = threadIdx.x; i < tw2_size<L>(); i += blockDim.x) {
-    const int n1 = i / (R2 + 1), k2 = i % (R2 + 1);
-    tw2[i] = k2 < R2 ? tw[n1 * k2] : C2<float>{1.f, 0.f};
-  }
+  const int n1 = i / (R2 + 1), k2 = i % (R2 + 1);
+  return k2 < R2 ? lw[n1 * k2] : Lw{0.f, 0.f, 1.f, 0.f};
+}
+template <int L>
+__device__ __forceinline__ void fill_tw2(Lw* tw2, const Lw* __restrict__ lw) {
+  for (int i = threadIdx.x; i < tw2_size<L>(); i += blockDim.x) tw2[i] = tw2_entry<L>(lw, i);
 }
 
 // The inputs one thread of a line group holds: reg_load fills them, reg_fft_loaded
@@ -439,7 +272,7 @@ __device__ __forceinline__ void reg_load(RegLine<L>& in, const Ld& ld, int t, bo
 }
 
 template <bool INV, int L, class Xch, class St>
-__device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, const St& st, const C2<float>* __restrict__ tw2,
+__device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, const St& st, const Lw* __restrict__ tw2,
                                                int t, bool active) {
   constexpr int R1 = RegPlan<L>::R1, R2 = RegPlan<L>::R2, NT = reg_nt<L>();
   constexpr int A = R1 / NT, B = (R2 + NT - 1) / NT;
@@ -453,11 +286,7 @@ __device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, con
       dft_reg<R2, INV>(v[a]);
       x(n1, 0) = v[a][0];
 #pragma unroll
-      for (int k2 = 1; k2 < R2; ++k2) {
-        C2<float> w = tw2[n1 * (R2 + 1) + k2];
-        if (INV) w.y = -w.y;
-        x(n1, k2) = cmul_rn(v[a][k2], w);
-      }
+      for (int k2 = 1; k2 < R2; ++k2) x(n1, k2) = lw_mul<INV>(tw2[n1 * (R2 + 1) + k2], v[a][k2]);
     }
   }
   __syncwarp();
@@ -484,7 +313,7 @@ __device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, con
 }
 
 template <bool INV, int L, class Ld, class Xch, class St>
-__device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const C2<float>* __restrict__ tw2, int t,
+__device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const Lw* __restrict__ tw2, int t,
                                         bool active) {
   RegLine<L> in;
   reg_load<L>(in, ld, t, active);

@@ -118,6 +118,26 @@ void twiddles(std::vector<C2<T>>& out, int L, int count, double sign) {
     out.push_back(C2<T>{(T)std::cos(ang), (T)(sign * std::sin(ang))});
   }
 }
+
+// Twiddles exp(-2 pi i m / L), m < count, as rotations by three shears (Lw): the angle,
+// reduced to (-pi, pi] from the integer m (exactly), then by a half turn to |theta'| <= pi/2.
+void lift_twiddles(std::vector<Lw>& out, int L, int count) {
+  for (int m = 0; m < count; ++m) {
+    long long j = -(long long)m % L;  // forward angle 2 pi j / L
+    if (2 * j <= -(long long)L) j += L;  // (-L/2, L/2]
+    float g = 1.f;
+    if (4 * j < -(long long)L) {
+      j += L / 2;  // + pi
+      g = -1.f;
+    } else if (4 * j > (long long)L) {
+      j -= L / 2;
+      g = -1.f;
+    }
+    // (the register-FFT edges are multiples of 16, so the half turn L/2 is exact in j)
+    const double th = 2.0 * kPi * (double)j / (double)L;
+    out.push_back(Lw{(float)std::tan(0.5 * th), (float)std::sin(th), g, 0.f});
+  }
+}
 }  // namespace
 
 struct okmc_grid {
@@ -136,6 +156,7 @@ struct okmc_grid {
   void* spec2 = nullptr;  // fast path: Green operator output (spec keeps the plane transforms)
   int* d_dirty = nullptr;  // [6][nz] planes whose eigenstrain changed since their last transform
   void* tw = nullptr;
+  void* lw = nullptr;  // FP32 fields: the twiddles as rotations (Lw), for the register-FFT passes
   double2* ph = nullptr;
   PassCfg cfg{};
   int nd = 0;
@@ -816,7 +837,7 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   if ((rc = dalloc(g, (void**)&g->d_err, sizeof(int)))) return cleanup(rc);
   if ((rc = dalloc(g, (void**)&g->d_partial, sizeof(double) * 30 * kSelfBlocks))) return cleanup(rc);
   // twiddle tables: w_H^k, w_ny^k, w_nz^k, exp(-2 pi i k/nx) for k <= H
-  size_t off_tw[4];
+  size_t off_tw[4], off_lw[4] = {0, 0, 0, 0};
   cudaError_t e;
   if (f64) {
     std::vector<C2<double>> t;
@@ -842,6 +863,17 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
     e = cudaMemcpyAsync(g->tw, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice, g->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     for (int k = 0; k < 4; ++k) off_tw[k] *= sizeof(C2<float>);
+    if (e == cudaSuccess) {
+      std::vector<Lw> l;
+      off_lw[0] = l.size(); lift_twiddles(l, g->H, g->H);
+      off_lw[1] = l.size(); lift_twiddles(l, g->n[1], g->n[1]);
+      off_lw[2] = l.size(); lift_twiddles(l, g->n[2], g->n[2]);
+      off_lw[3] = l.size(); lift_twiddles(l, g->n[0], g->H + 1);
+      if ((rc = dalloc(g, &g->lw, l.size() * sizeof(Lw)))) return cleanup(rc);
+      e = cudaMemcpyAsync(g->lw, l.data(), l.size() * sizeof(Lw), cudaMemcpyHostToDevice, g->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+      for (int k = 0; k < 4; ++k) off_lw[k] *= sizeof(Lw);
+    }
   }
   if (e != cudaSuccess) return cleanup(OKMC_ECUDA);
   // phase tables exp(+2 pi i f / n) for the self-term shifts (f: signed frequency)
@@ -884,6 +916,12 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   c.twY = (const char*)g->tw + off_tw[1];
   c.twZ = (const char*)g->tw + off_tw[2];
   c.untw = (const char*)g->tw + off_tw[3];
+  if (g->lw) {
+    c.lwH = (const char*)g->lw + off_lw[0];
+    c.lwY = (const char*)g->lw + off_lw[1];
+    c.lwZ = (const char*)g->lw + off_lw[2];
+    c.lwU = (const char*)g->lw + off_lw[3];
+  }
   c.err = g->d_err;
   // OKMC_GENERIC_FFT=1 keeps the generic passes (diagnostics and cross-checks)
   {
@@ -930,6 +968,7 @@ size_t okmc_estimate_field_bytes(const okmc_grid_desc* d) {
   size_t b = 6 * N * w * 2 + 6 * d->n[2] * P * 2 * w * (fast ? 2 : 1);
   b += sizeof(DevState) + sizeof(int) + sizeof(double) * 30 * kSelfBlocks + sizeof(int) * 6 * d->n[2];
   b += (2 * H + 1 + d->n[1] + d->n[2]) * 2 * w + (H + 1 + d->n[1] + d->n[2]) * sizeof(double2);
+  if (!f64) b += (2 * H + 1 + d->n[1] + d->n[2]) * sizeof(Lw);
   return b;
 }
 

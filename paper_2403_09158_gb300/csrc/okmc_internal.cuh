@@ -62,6 +62,36 @@ __device__ __forceinline__ C2<float> pscale(float s, C2<float> a) { return un(__
 __device__ __forceinline__ C2<float> pfma(float s, C2<float> a, C2<float> c) {
   return un(__ffma2_rn(make_float2(s, s), pk(a), pk(c)));
 }
+// ---------------------------------------------------------------- rotations by three shears
+// Multiplying by a twiddle exp(i theta) rounded to FP32 as (cos, sin) scales the value by
+// |w| = 1 + O(2^-24), and for the few twiddles that a transform applies over and over
+// (cos and sin of pi/8, sqrt(1/2)) the rounding leaves |w| below one: a 256-point
+// transform then shrinks its output by about 2.6e-8 on average, and a forward and
+// inverse 3D solve by about 1.5e-7, a systematic error of 1e-4 eV in the interaction
+// energy of a 4 nm loop.  A rotation written as three shears,
+//   x1 = x - t y,  y1 = y + s x1,  x2 = x1 - t y1,  t = tan(theta/2), s = sin(theta),
+// has determinant one whatever the rounding of t and s, so its scale error vanishes to
+// first order; each fma rounds once and without bias.  |theta| <= pi/2 keeps |t| <= 1;
+// other angles are reduced by a half turn (g = -1, exact).  Same count as a complex
+// multiply: three fma and (for table twiddles) one paired multiply by g.
+__device__ __forceinline__ C2<float> lift(C2<float> v, float t, float s) {
+  const float x1 = __fmaf_rn(-t, v.y, v.x);
+  const float y1 = __fmaf_rn(s, x1, v.y);
+  const float x2 = __fmaf_rn(-t, y1, x1);
+  return C2<float>{x2, y1};
+}
+// A table twiddle exp(-2 pi i m / L) (forward angle) as a rotation by theta', |theta'| <=
+// pi/2, times g = +-1: t = tan(theta'/2), s = sin(theta').  16 bytes per entry.
+struct alignas(16) Lw {
+  float t, s, g, pad;
+};
+// v * w (forward) or v * conj(w) (inverse)
+template <bool INV>
+__device__ __forceinline__ C2<float> lw_mul(const Lw& w, C2<float> v) {
+  const C2<float> r = lift(v, INV ? -w.t : w.t, INV ? -w.s : w.s);
+  return un(__fmul2_rn(make_float2(w.g, w.g), pk(r)));
+}
+
 // b + rot(e) and b - rot(e), rot = multiply by -i (forward) or +i (inverse)
 template <bool INV> __device__ __forceinline__ C2<float> add_rot(C2<float> b, C2<float> e) {
   return INV ? C2<float>{b.x - e.y, b.y + e.x} : C2<float>{b.x + e.y, b.y - e.x};
@@ -274,6 +304,11 @@ struct PassCfg {
   const void* twY;     // C2<T>[ny]
   const void* twZ;     // C2<T>[nz]
   const void* untw;    // C2<T>[H+1]    exp(-2 pi i k / nx)
+  // the same twiddles as rotations by three shears (Lw, FP32 register-FFT passes only):
+  const void* lwH;     // Lw[H]          w_H^m
+  const void* lwY;     // Lw[ny]
+  const void* lwZ;     // Lw[nz]
+  const void* lwU;     // Lw[H+1]        exp(-2 pi i k / nx)
   int* err;            // device error word (bounded waits that gave up set it)
   float rn[3];         // 1/nx, 1/ny, 1/nz (rounded from FP64)
   int* dirty;          // fast forward plane pass: per plane (c*nz + z) flag, nonzero when the
@@ -284,6 +319,8 @@ struct PassCfg {
 // ---------------------------------------------------------------- defects
 struct DefGeo {
   double e6[6];       // eigenstrain tensor (xx, yy, zz, yz, xz, xy)
+  double escale;      // e6 = escale * (pattern of 0 and +-1): |b|/(h |a|^2) for loops, the dilatation
+  float ew[6];        // energy weights e6 / escale with the off-diagonals doubled (0, +-1, +-2: exact)
   double v_over_h3;   // shape volume / h^3
   double thr;         // disk: |a|^2 (8R/h)^2; sphere: (8 rho)^6
   int kind;           // 0 disk, 1 sphere
@@ -436,8 +473,38 @@ __device__ __forceinline__ void sigma_of(const C2<T>* e, T q0, T q1, T q2, const
 // packed fma; the adjugate and the determinant stay scalar.  Every operation is an
 // explicit intrinsic, so the rounding does not depend on how the compiler contracts
 // products and sums where this is inlined (launch variants agree bit for bit).
-__device__ __forceinline__ void sigma_of(const C2<float>* e, float q0, float q1, float q2, const GreenC<float>& C,
+//
+// The operator annihilates compatible strains, sym(q (x) a) for any vector a, so it is
+// applied to the transverse part eta = e - sym(q (x) a) with a chosen such that
+// eta q = 0: a = (2 e q - (q.e.q / |q|^2) q) / |q|^2.  For the one-voxel-thick loops
+// nearly all of e is compatible at the frequencies that carry their spectrum, and
+// C:sym(q (x) w) and tau = C:e then cancel to a few percent.  Applied to e itself, the
+// rounding of those two large terms is an error on the output side, at the scale of
+// the loop's unrelaxed energy (about 30 times its elastic energy for a 4 nm loop).
+// Applied to eta, every intermediate is of the size of the result; the rounding of
+// eta itself acts as a perturbation of the input, which the operator then maps
+// exactly, and which pairs with the (small) relaxed field of any defect.
+__device__ __forceinline__ void sigma_of(const C2<float>* e_in, float q0, float q1, float q2, const GreenC<float>& C,
                                          const GreenC<float>& Cs, C2<float>* s) {
+  C2<float> e[6];
+  {
+    const float qq = __fmaf_rn(q2, q2, __fmaf_rn(q1, q1, __fmul_rn(q0, q0)));
+    const float rqq = __frcp_rn(qq);
+    const C2<float> u0 = pfma(q2, e_in[4], pfma(q1, e_in[5], pscale(q0, e_in[0])));
+    const C2<float> u1 = pfma(q2, e_in[3], pfma(q1, e_in[1], pscale(q0, e_in[5])));
+    const C2<float> u2 = pfma(q2, e_in[2], pfma(q1, e_in[3], pscale(q0, e_in[4])));
+    // r = (q.e.q) / |q|^2; a_i = (2 u_i - r q_i) / |q|^2
+    const C2<float> r = pscale(rqq, pfma(q2, u2, pfma(q1, u1, pscale(q0, u0))));
+    const C2<float> a0 = pscale(rqq, pfma(-q0, r, pscale(2.f, u0)));
+    const C2<float> a1 = pscale(rqq, pfma(-q1, r, pscale(2.f, u1)));
+    const C2<float> a2 = pscale(rqq, pfma(-q2, r, pscale(2.f, u2)));
+    e[0] = pfma(-q0, a0, e_in[0]);
+    e[1] = pfma(-q1, a1, e_in[1]);
+    e[2] = pfma(-q2, a2, e_in[2]);
+    e[3] = pfma(-0.5f, pfma(q1, a2, pscale(q2, a1)), e_in[3]);
+    e[4] = pfma(-0.5f, pfma(q0, a2, pscale(q2, a0)), e_in[4]);
+    e[5] = pfma(-0.5f, pfma(q0, a1, pscale(q1, a0)), e_in[5]);
+  }
   const float ds = __fsub_rn(Cs.C11, Cs.C12), gs = __fmul_rn(2.f, Cs.C44);
   const C2<float> tr = padd(padd(e[0], e[1]), e[2]);
   const C2<float> c12tr = pscale(Cs.C12, tr);

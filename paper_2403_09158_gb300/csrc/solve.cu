@@ -18,7 +18,9 @@
 //               the inverse x transform, and writes real stress rows.
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 
 #include "okmc_internal.cuh"
 
@@ -123,7 +125,10 @@ __global__ void __launch_bounds__(kThreads) k_plane_fwd(const Q* __restrict__ ep
   const int cols_per = H / cs;
   const size_t P = (size_t)(H + 1) * ny;
   load_twiddles(s, c);
-  __syncthreads();
+  // the row phase stores into the other CTAs' shared memory, which may only be
+  // touched once every CTA of the cluster runs: a full cluster barrier first
+  if (cs > 1) cluster.sync();
+  else __syncthreads();
 
   C2<T>* bufA = s.scr + (size_t)warp * 2 * s.lmax;
   C2<T>* bufB = bufA + s.lmax;
@@ -386,8 +391,11 @@ __global__ void k_static_twiddles(C2<float>* tw, int nx, int ny, int nz) {
 }
 
 namespace {
-int g_static_ready[64];
-C2<float>* g_static_ptr[64];
+// Per-device address of g_static_scratch.  Looked up once per device under a mutex,
+// so two host threads making their first call at the same time do not race on the
+// lookup; later calls read the published pointer without locking.
+std::atomic<C2<float>*> g_static_ptr[64];
+std::mutex g_static_mu;
 
 bool edge_ok(int n) {
   if (n < 16 || n > 512 || n % 16) return false;
@@ -403,6 +411,8 @@ extern "C" int okmc_solve_stress_static(const float* eps, float* sigma, const in
                                         double C44, int32_t k0_mode, void* stream) {
   using namespace okmc;
   if (!eps || !sigma || !n) return OKMC_EINVAL;
+  // rows are read and written as pairs of floats (8-byte accesses)
+  if (((uintptr_t)eps | (uintptr_t)sigma) & 7) return OKMC_EINVAL;
   for (int a = 0; a < 3; ++a)
     if (!edge_ok(n[a])) return OKMC_EINVAL;
   const int H = n[0] / 2;
@@ -411,15 +421,19 @@ extern "C" int okmc_solve_stress_static(const float* eps, float* sigma, const in
   if (k0_mode != OKMC_MEAN_STRESS_ZERO && k0_mode != OKMC_MEAN_STRAIN_ZERO) return OKMC_EINVAL;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return OKMC_ECUDA;
-  if (!g_static_ready[dev]) {
+  C2<float>* spec = g_static_ptr[dev].load(std::memory_order_acquire);
+  if (!spec) {
     // host code cannot use the array's name as a device address: ask the runtime for
     // it once per device, with that device current
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return OKMC_ECUDA;
-    g_static_ptr[dev] = static_cast<C2<float>*>(p);
-    g_static_ready[dev] = 1;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    spec = g_static_ptr[dev].load(std::memory_order_relaxed);
+    if (!spec) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) return OKMC_ECUDA;
+      spec = static_cast<C2<float>*>(p);
+      g_static_ptr[dev].store(spec, std::memory_order_release);
+    }
   }
-  C2<float>* spec = g_static_ptr[dev];
   C2<float>* tw = spec + kStaticSpec;
   cudaStream_t st = (cudaStream_t)stream;
   PassCfg c = {};

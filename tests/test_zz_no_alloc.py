@@ -40,12 +40,31 @@ def test_static_solve_equals_handle_solve_twice(case):
         ref = g.solve_stress()
         g.close()
         eps_d = torch.from_numpy(eps).cuda()
+        sigs = [torch.full_like(eps_d, float('nan')) for _ in range(2)]
+        free = []
         for call in range(2):
-            sig_d = torch.full_like(eps_d, float('nan'))
-            assert _static_solve(lib, torch, eps_d, sig_d, w, k0) == ok.OKMC_OK
-            sig = sig_d.cpu().numpy()
+            free.append(torch.cuda.mem_get_info()[0])
+            assert _static_solve(lib, torch, eps_d, sigs[call], w, k0) == ok.OKMC_OK
+            sig = sigs[call].cpu().numpy()
             rel = np.linalg.norm(sig.astype(np.float64) - ref) / np.linalg.norm(ref)
             assert rel <= 1e-5, (case, k0, call, rel)
+        # the first call of the process may load the module (and with it the static
+        # array); from then on a call takes no device memory at all
+        free.append(torch.cuda.mem_get_info()[0])
+        assert free[2] == free[1], (case, k0, free)
+
+
+def test_static_solve_rejects_misaligned_pointers():
+    torch = pytest.importorskip('torch')
+    __graft_entry__.build()
+    lib = ok.load()
+    w = config_small()
+    N = 6 * int(np.prod(w.n))
+    buf = torch.zeros(N + 1, device='cuda')
+    good = torch.zeros(N, device='cuda')
+    # a view one float in: 4-byte aligned only; the call must refuse it on the host
+    assert _static_solve(lib, torch, buf[1:], good, w, ok.MEAN_STRESS_ZERO) == ok.OKMC_EINVAL
+    assert _static_solve(lib, torch, good, buf[1:], w, ok.MEAN_STRESS_ZERO) == ok.OKMC_EINVAL
 
 
 def test_static_solve_rejects_oversize_grid():
