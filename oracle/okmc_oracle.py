@@ -493,6 +493,88 @@ def self_term_table_fourier(d, n, h, C, k0_mode=MEAN_STRESS_ZERO):
     return W
 
 
+def unit_tensor(d, h):
+    """(E, s) with the defect's eigenstrain e = s E and s its largest |component|:
+    defects of one type and axis share E (the 1/2<111> and <100> loops per axis, the
+    dilatational clusters), so a per-E kernel serves all of them."""
+    e = defect_geometry(d, h)['e']
+    s = float(np.abs(e).max())
+    return e / s, s
+
+
+def unit_kernel(E, n, h, C, k0_mode=MEAN_STRESS_ZERO):
+    """Real-space kernel of a unit eigenstrain tensor E on the periodic grid,
+    K(r) = (1/N) sum_xi Q(xi) exp(+i xi.r) with Q(xi) = E : sigma_hat[E](xi), the q of
+    self_term_table_fourier for e = E (Eqs. EIG_elastic_fourier, basicgammacomplete,
+    summaryEL on every discrete frequency).  Q is real and even, so only the real part
+    of K enters the (symmetric, real) sums below: it is the real part of the inverse
+    transform, the even-edge reading of the solve.  (nx, ny, nz) FP64."""
+    n = tuple(int(v) for v in n)
+    xs = [frequencies(n[a], n[a] * h) for a in range(3)]
+    E6 = to_voigt6(E)
+    Q = np.empty(n)
+    for ix in range(n[0]):
+        XI = np.stack(np.meshgrid(np.full(1, xs[0][ix]), xs[1], xs[2], indexing='ij'), axis=-1)[0]
+        zero = np.all(XI == 0.0, axis=-1)
+        eh = np.broadcast_to(E[:, :, None, None], (3, 3) + XI.shape[:2]).astype(complex)
+        sig = green_sigma_hat(C, XI, eh, k0_mode, zero)
+        Q[ix] = ddot6(E6[:, None, None], to_voigt6(sig).real)
+    return np.fft.ifftn(Q).real
+
+
+def self_term_table_realspace(d, n, h, K, s):
+    """The table of ``self_term_table`` as a double sum over the two stencils in real
+    space (convolution theorem applied to self_term_table_fourier): with K the kernel of
+    the defect's unit tensor (e = s E) and w_c the class-c counts placed at the origin,
+      W(c, 0)     = -kappa h^3 a_c^2 s^2   sum_{v,v'} w_c(v) w_c(v')  K(v' - v)
+      W(c, 1 + j) = -kappa h^3 a_c a_c' s^2 sum_{v,v'} w_c(v) w_c'(v') K(v' + d_cj - v)
+    with c' = 1 - c and d_cj the whole-voxel shift between the two stencils."""
+    n = np.array([int(v) for v in n])
+    st = [stencil(d, c, h) for c in (0, 1)]
+    pref = -KAPPA * h ** 3 * s * s
+
+    def pair_sum(c, cp, shift):
+        oc, wc, _ = st[c]
+        op, wp, _ = st[cp]
+        tot = 0.0
+        for r0 in range(0, len(oc), 256):          # rows in chunks keep the index arrays small
+            r = np.mod(op[None, :, :] + shift[None, None, :] - oc[r0:r0 + 256, None, :], n)
+            tot += float(np.sum(wc[r0:r0 + 256, None] * wp[None, :] * K[r[..., 0], r[..., 1], r[..., 2]]))
+        return tot
+
+    W = np.zeros((2, 9))
+    for c in (0, 1):
+        cp = 1 - c
+        W[c, 0] = pref * st[c][2] ** 2 * pair_sum(c, c, np.zeros(3, dtype=np.int64))
+        ref = np.array([c, c, c], dtype=np.int64)
+        for j in range(8):
+            dvec = base_voxel(ref + JUMPS[j]) - base_voxel(ref)
+            W[c, 1 + j] = pref * st[c][2] * st[cp][2] * pair_sum(c, cp, dvec)
+    return W
+
+
+def energies_sampled(defects, sample, sigma_total, n, h, C, k0_mode=MEAN_STRESS_ZERO):
+    """E_i(X_i) and E_i(X_i + lambda_j) for the sampled defects by the sigma - W route
+    (Sec. 2, Eq. interaction_energy3): the stencil sum over the total stress minus the
+    self term, with W from self_term_table_realspace and one kernel per unit tensor.
+    Returns {i: (e0, ec[8])}."""
+    kernels = {}
+    out = {}
+    for i in sample:
+        d = defects[i]
+        E, s = unit_tensor(d, h)
+        key = tuple(np.round(E.ravel(), 12))
+        if key not in kernels:
+            kernels[key] = unit_kernel(E, n, h, C, k0_mode)
+        W = self_term_table_realspace(d, n, h, kernels[key], s)
+        c = pos_class(d['pos'])
+        e0 = energy_of_stencil(d, d['pos'], sigma_total, h) - W[c, 0]
+        ec = np.array([energy_of_stencil(d, Y, sigma_total, h) - W[c, 1 + j]
+                       for j, Y in enumerate(candidate_positions(d['pos']))])
+        out[int(i)] = (e0, ec)
+    return out
+
+
 # --------------------------------------------------------------------------
 # rates and event selection (Sec. 5; Appendix A, Algorithm 1)
 # --------------------------------------------------------------------------

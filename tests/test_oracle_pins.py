@@ -146,6 +146,24 @@ def test_p6_bruteforce_equals_self_field_and_table():
             assert abs(ej - Ec[i, jj]) <= 1e-9 * max(1.0, np.abs(W).max())
 
 
+@pytest.mark.parametrize('n,k0', [((16, 16, 16), O.MEAN_STRESS_ZERO), ((12, 16, 20), O.MEAN_STRAIN_ZERO)])
+def test_p6_realspace_self_terms_equal_bruteforce(n, k0):
+    """The sampled-energy route used at full sizes (self terms as real-space double sums
+    over one kernel per unit tensor) against brute force (N_d + 1 solves)."""
+    d = _defects_small()
+    E, Ec = O.energies_bruteforce(d, n, H, C_CUBIC, k0)
+    sig = O.solve_stress(O.eigenstrain_field(d, n, H), C_CUBIC, H, k0)
+    res = O.energies_sampled(d, range(len(d)), sig, n, H, C_CUBIC, k0)
+    for i in range(len(d)):
+        W = O.self_term_table_fourier(d[i], n, H, C_CUBIC, k0)
+        E_, s = O.unit_tensor(d[i], H)
+        assert abs(s * E_ - O.defect_geometry(d[i], H)['e']).max() <= 1e-15
+        Wr = O.self_term_table_realspace(d[i], n, H, O.unit_kernel(E_, n, H, C_CUBIC, k0), s)
+        assert np.abs(Wr - W).max() <= 1e-12 * np.abs(W).max()
+        assert abs(res[i][0] - E[i]) <= 1e-9 * max(1.0, np.abs(W).max())
+        assert np.abs(res[i][1] - Ec[i]).max() <= 1e-9 * max(1.0, np.abs(W).max())
+
+
 def test_p6_paper_form_equals_eigenstrain_form():
     # Eq. interaction_energy3: int sigma_ext : eps^{d,e} = -int sigma_ext : eps*_d.  Exact on
     # odd edges; on even edges the averaged Nyquist operator breaks it by a few 1e-3.
