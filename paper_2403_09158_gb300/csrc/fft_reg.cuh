@@ -34,6 +34,17 @@ template <> struct RegPlan<192> { static constexpr int R1 = 8, R2 = 24; };
 template <> struct RegPlan<256> { static constexpr int R1 = 16, R2 = 16; };
 template <> struct RegPlan<320> { static constexpr int R1 = 16, R2 = 20; };
 template <int L> __host__ __device__ constexpr int reg_nt() { return RegPlan<L>::R1 < RegPlan<L>::R2 ? RegPlan<L>::R1 : RegPlan<L>::R2; }
+// (R1, R2) of a register-FFT length known only at run time (host code); false if L has no plan
+inline bool reg_split(int L, int& R1, int& R2) {
+  switch (L) {
+#define OKMC_SPLIT(n) \
+  case n: R1 = RegPlan<n>::R1; R2 = RegPlan<n>::R2; return true;
+    OKMC_SPLIT(16) OKMC_SPLIT(24) OKMC_SPLIT(32) OKMC_SPLIT(48) OKMC_SPLIT(64) OKMC_SPLIT(80) OKMC_SPLIT(96)
+    OKMC_SPLIT(128) OKMC_SPLIT(160) OKMC_SPLIT(192) OKMC_SPLIT(256) OKMC_SPLIT(320)
+#undef OKMC_SPLIT
+    default: return false;
+  }
+}
 
 // Small DFTs on packed pairs; X_k = sum_n x_n exp(-+2 pi i n k / R), minus sign forward.
 template <bool INV> __device__ __forceinline__ void pdft2(C2<float>* v) {
@@ -235,20 +246,20 @@ struct XSkew {
   }
 };
 
-// Twiddles w_L^(n1*k2) as rotations (Lw) in a padded [R1][R2 + 1] table: a warp's
-// threads (consecutive n1, one k2) then read distinct banks.  tw2 is filled by fill_tw2
-// from the table of w_L^m, m < L (n1 k2 < R1 R2 = L).
+// Twiddles w_L^(n1*k2) in a padded [R1][R2 + 1] table: a warp's threads (consecutive
+// n1, one k2) then read distinct banks.  tw2 is filled by fill_tw2 from the table of
+// w_L^m, m < L (n1 k2 < R1 R2 = L).
 template <int L>
 __host__ __device__ constexpr int tw2_size() { return RegPlan<L>::R1 * (RegPlan<L>::R2 + 1); }
 template <int L>
-__device__ __forceinline__ Lw tw2_entry(const Lw* __restrict__ lw, int i) {
+__device__ __forceinline__ C2<float> tw2_entry(const C2<float>* __restrict__ tw, int i) {
   constexpr int R2 = RegPlan<L>::R2;
   const int n1 = i / (R2 + 1), k2 = i % (R2 + 1);
-  return k2 < R2 ? lw[n1 * k2] : Lw{0.f, 0.f, 1.f, 0.f};
+  return k2 < R2 ? tw[n1 * k2] : C2<float>{1.f, 0.f};
 }
 template <int L>
-__device__ __forceinline__ void fill_tw2(Lw* tw2, const Lw* __restrict__ lw) {
-  for (int i = threadIdx.x; i < tw2_size<L>(); i += blockDim.x) tw2[i] = tw2_entry<L>(lw, i);
+__device__ __forceinline__ void fill_tw2(C2<float>* tw2, const C2<float>* __restrict__ tw) {
+  for (int i = threadIdx.x; i < tw2_size<L>(); i += blockDim.x) tw2[i] = tw2_entry<L>(tw, i);
 }
 
 // The inputs one thread of a line group holds: reg_load fills them, reg_fft_loaded
@@ -272,7 +283,7 @@ __device__ __forceinline__ void reg_load(RegLine<L>& in, const Ld& ld, int t, bo
 }
 
 template <bool INV, int L, class Xch, class St>
-__device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, const St& st, const Lw* __restrict__ tw2,
+__device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, const St& st, const C2<float>* __restrict__ tw2,
                                                int t, bool active) {
   constexpr int R1 = RegPlan<L>::R1, R2 = RegPlan<L>::R2, NT = reg_nt<L>();
   constexpr int A = R1 / NT, B = (R2 + NT - 1) / NT;
@@ -286,7 +297,11 @@ __device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, con
       dft_reg<R2, INV>(v[a]);
       x(n1, 0) = v[a][0];
 #pragma unroll
-      for (int k2 = 1; k2 < R2; ++k2) x(n1, k2) = lw_mul<INV>(tw2[n1 * (R2 + 1) + k2], v[a][k2]);
+      for (int k2 = 1; k2 < R2; ++k2) {
+        C2<float> w = tw2[n1 * (R2 + 1) + k2];
+        if (INV) w.y = -w.y;
+        x(n1, k2) = cmul_rn(v[a][k2], w);
+      }
     }
   }
   __syncwarp();
@@ -313,7 +328,7 @@ __device__ __forceinline__ void reg_fft_loaded(RegLine<L>& in, const Xch& x, con
 }
 
 template <bool INV, int L, class Ld, class Xch, class St>
-__device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const Lw* __restrict__ tw2, int t,
+__device__ __forceinline__ void reg_fft(const Ld& ld, const Xch& x, const St& st, const C2<float>* __restrict__ tw2, int t,
                                         bool active) {
   RegLine<L> in;
   reg_load<L>(in, ld, t, active);

@@ -16,6 +16,7 @@
 #include <utility>
 #include <vector>
 
+#include "fft_reg.cuh"
 #include "okmc_internal.cuh"
 
 using namespace okmc;
@@ -119,24 +120,63 @@ void twiddles(std::vector<C2<T>>& out, int L, int count, double sign) {
   }
 }
 
-// Twiddles exp(-2 pi i m / L), m < count, as rotations by three shears (Lw): the angle,
-// reduced to (-pi, pi] from the integer m (exactly), then by a half turn to |theta'| <= pi/2.
-void lift_twiddles(std::vector<Lw>& out, int L, int count) {
+// Twiddles exp(-2 pi i m / L), m < count, for the FP32 register-FFT passes.  Rounding
+// cos and sin to nearest leaves |w| = 1 + d_m with d_m of either sign; a transform
+// scales its output by the mean of the d_m it applies (weighted by how often it applies
+// each twiddle), and for the tables of the solve that mean is a few 1e-9, a systematic
+// error of the self term of every defect.  Each entry is therefore chosen among the
+// FP32 pairs within two units in the last place of (cos, sin) whose phase error stays
+// below 6e-8 rad, as the one that keeps the weighted running sum of d_m closest to
+// zero (error diffusion): the table's weighted mean magnitude error then vanishes to
+// within one entry's error over the table.  weight[m]: how often m is applied (empty:
+// every entry once).
+void balanced_twiddles(std::vector<C2<float>>& out, int L, int count, const std::vector<int>& weight) {
+  double run = 0.0;
   for (int m = 0; m < count; ++m) {
-    long long j = -(long long)m % L;  // forward angle 2 pi j / L
-    if (2 * j <= -(long long)L) j += L;  // (-L/2, L/2]
-    float g = 1.f;
-    if (4 * j < -(long long)L) {
-      j += L / 2;  // + pi
-      g = -1.f;
-    } else if (4 * j > (long long)L) {
-      j -= L / 2;
-      g = -1.f;
+    const double th = -2.0 * kPi * (double)m / (double)L;
+    const double c = std::cos(th), s = std::sin(th);
+    const int wgt = weight.empty() ? 1 : weight[m];
+    C2<float> best{(float)c, (float)s};
+    double best_d = (double)best.x * best.x + (double)best.y * best.y - 1.0, best_key = std::fabs(run + wgt * best_d);
+    if (wgt > 0) {
+      // the rounded values and their neighbours up to two units in the last place
+      float cs[5], ss[5];
+      cs[0] = (float)c;
+      ss[0] = (float)s;
+      float cu = cs[0], cd = cs[0], su = ss[0], sd = ss[0];
+      for (int k = 1; k <= 2; ++k) {
+        cs[2 * k - 1] = cu = std::nextafter(cu, 2.f);
+        cs[2 * k] = cd = std::nextafter(cd, -2.f);
+        ss[2 * k - 1] = su = std::nextafter(su, 2.f);
+        ss[2 * k] = sd = std::nextafter(sd, -2.f);
+      }
+      for (float cc : cs)
+        for (float sv : ss) {
+          const double ph = c * ((double)sv - s) - s * ((double)cc - c);
+          if (std::fabs(ph) > 6e-8) continue;
+          const double d = (double)cc * cc + (double)sv * sv - 1.0;
+          const double key = std::fabs(run + wgt * d);
+          if (key < best_key) {
+            best_key = key;
+            best_d = d;
+            best = C2<float>{cc, sv};
+          }
+        }
     }
-    // (the register-FFT edges are multiples of 16, so the half turn L/2 is exact in j)
-    const double th = 2.0 * kPi * (double)j / (double)L;
-    out.push_back(Lw{(float)std::tan(0.5 * th), (float)std::sin(th), g, 0.f});
+    run += wgt * best_d;
+    out.push_back(best);
   }
+}
+
+// How often the two-step register FFT of length L applies w_L^m between its steps
+// (m = n1 k2, n1 < R1, 0 < k2 < R2).
+std::vector<int> twiddle_use(int L) {
+  std::vector<int> w(L, 0);
+  int R1 = 0, R2 = 0;
+  if (!reg_split(L, R1, R2)) return {};
+  for (int n1 = 0; n1 < R1; ++n1)
+    for (int k2 = 1; k2 < R2; ++k2) ++w[(n1 * k2) % L];
+  return w;
 }
 }  // namespace
 
@@ -156,7 +196,7 @@ struct okmc_grid {
   void* spec2 = nullptr;  // fast path: Green operator output (spec keeps the plane transforms)
   int* d_dirty = nullptr;  // [6][nz] planes whose eigenstrain changed since their last transform
   void* tw = nullptr;
-  void* lw = nullptr;  // FP32 fields: the twiddles as rotations (Lw), for the register-FFT passes
+  void* ftw = nullptr;  // FP32 fields: twiddles with balanced magnitude errors, for the register-FFT passes
   double2* ph = nullptr;
   PassCfg cfg{};
   int nd = 0;
@@ -864,15 +904,15 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
     for (int k = 0; k < 4; ++k) off_tw[k] *= sizeof(C2<float>);
     if (e == cudaSuccess) {
-      std::vector<Lw> l;
-      off_lw[0] = l.size(); lift_twiddles(l, g->H, g->H);
-      off_lw[1] = l.size(); lift_twiddles(l, g->n[1], g->n[1]);
-      off_lw[2] = l.size(); lift_twiddles(l, g->n[2], g->n[2]);
-      off_lw[3] = l.size(); lift_twiddles(l, g->n[0], g->H + 1);
-      if ((rc = dalloc(g, &g->lw, l.size() * sizeof(Lw)))) return cleanup(rc);
-      e = cudaMemcpyAsync(g->lw, l.data(), l.size() * sizeof(Lw), cudaMemcpyHostToDevice, g->st);
+      std::vector<C2<float>> l;
+      off_lw[0] = l.size(); balanced_twiddles(l, g->H, g->H, twiddle_use(g->H));
+      off_lw[1] = l.size(); balanced_twiddles(l, g->n[1], g->n[1], twiddle_use(g->n[1]));
+      off_lw[2] = l.size(); balanced_twiddles(l, g->n[2], g->n[2], twiddle_use(g->n[2]));
+      off_lw[3] = l.size(); balanced_twiddles(l, g->n[0], g->H + 1, {});
+      if ((rc = dalloc(g, &g->ftw, l.size() * sizeof(l[0])))) return cleanup(rc);
+      e = cudaMemcpyAsync(g->ftw, l.data(), l.size() * sizeof(l[0]), cudaMemcpyHostToDevice, g->st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
-      for (int k = 0; k < 4; ++k) off_lw[k] *= sizeof(Lw);
+      for (int k = 0; k < 4; ++k) off_lw[k] *= sizeof(l[0]);
     }
   }
   if (e != cudaSuccess) return cleanup(OKMC_ECUDA);
@@ -916,11 +956,11 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   c.twY = (const char*)g->tw + off_tw[1];
   c.twZ = (const char*)g->tw + off_tw[2];
   c.untw = (const char*)g->tw + off_tw[3];
-  if (g->lw) {
-    c.lwH = (const char*)g->lw + off_lw[0];
-    c.lwY = (const char*)g->lw + off_lw[1];
-    c.lwZ = (const char*)g->lw + off_lw[2];
-    c.lwU = (const char*)g->lw + off_lw[3];
+  if (g->ftw) {
+    c.ftwH = (const char*)g->ftw + off_lw[0];
+    c.ftwY = (const char*)g->ftw + off_lw[1];
+    c.ftwZ = (const char*)g->ftw + off_lw[2];
+    c.ftwU = (const char*)g->ftw + off_lw[3];
   }
   c.err = g->d_err;
   // OKMC_GENERIC_FFT=1 keeps the generic passes (diagnostics and cross-checks)
@@ -968,7 +1008,7 @@ size_t okmc_estimate_field_bytes(const okmc_grid_desc* d) {
   size_t b = 6 * N * w * 2 + 6 * d->n[2] * P * 2 * w * (fast ? 2 : 1);
   b += sizeof(DevState) + sizeof(int) + sizeof(double) * 30 * kSelfBlocks + sizeof(int) * 6 * d->n[2];
   b += (2 * H + 1 + d->n[1] + d->n[2]) * 2 * w + (H + 1 + d->n[1] + d->n[2]) * sizeof(double2);
-  if (!f64) b += (2 * H + 1 + d->n[1] + d->n[2]) * sizeof(Lw);
+  if (!f64) b += (2 * H + 1 + d->n[1] + d->n[2]) * 2 * w;
   return b;
 }
 

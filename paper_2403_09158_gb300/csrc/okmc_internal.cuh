@@ -73,25 +73,15 @@ __device__ __forceinline__ C2<float> pfma(float s, C2<float> a, C2<float> c) {
 // has determinant one whatever the rounding of t and s, so its scale error vanishes to
 // first order; each fma rounds once and without bias.  |theta| <= pi/2 keeps |t| <= 1;
 // other angles are reduced by a half turn (g = -1, exact).  Same count as a complex
-// multiply: three fma and (for table twiddles) one paired multiply by g.
+// multiply: three fma.  (Used for the compile-time twiddles of the register DFTs; the
+// table twiddles are rounded so that their magnitude errors cancel, see the grid's
+// table set-up.)
 __device__ __forceinline__ C2<float> lift(C2<float> v, float t, float s) {
   const float x1 = __fmaf_rn(-t, v.y, v.x);
   const float y1 = __fmaf_rn(s, x1, v.y);
   const float x2 = __fmaf_rn(-t, y1, x1);
   return C2<float>{x2, y1};
 }
-// A table twiddle exp(-2 pi i m / L) (forward angle) as a rotation by theta', |theta'| <=
-// pi/2, times g = +-1: t = tan(theta'/2), s = sin(theta').  16 bytes per entry.
-struct alignas(16) Lw {
-  float t, s, g, pad;
-};
-// v * w (forward) or v * conj(w) (inverse)
-template <bool INV>
-__device__ __forceinline__ C2<float> lw_mul(const Lw& w, C2<float> v) {
-  const C2<float> r = lift(v, INV ? -w.t : w.t, INV ? -w.s : w.s);
-  return un(__fmul2_rn(make_float2(w.g, w.g), pk(r)));
-}
-
 // b + rot(e) and b - rot(e), rot = multiply by -i (forward) or +i (inverse)
 template <bool INV> __device__ __forceinline__ C2<float> add_rot(C2<float> b, C2<float> e) {
   return INV ? C2<float>{b.x - e.y, b.y + e.x} : C2<float>{b.x + e.y, b.y - e.x};
@@ -304,11 +294,12 @@ struct PassCfg {
   const void* twY;     // C2<T>[ny]
   const void* twZ;     // C2<T>[nz]
   const void* untw;    // C2<T>[H+1]    exp(-2 pi i k / nx)
-  // the same twiddles as rotations by three shears (Lw, FP32 register-FFT passes only):
-  const void* lwH;     // Lw[H]          w_H^m
-  const void* lwY;     // Lw[ny]
-  const void* lwZ;     // Lw[nz]
-  const void* lwU;     // Lw[H+1]        exp(-2 pi i k / nx)
+  // the same twiddles for the FP32 register-FFT passes, each rounded to the FP32 pair
+  // whose magnitude error keeps the running sum of the table's errors near zero:
+  const void* ftwH;    // C2<float>[H]   w_H^m
+  const void* ftwY;    // C2<float>[ny]
+  const void* ftwZ;    // C2<float>[nz]
+  const void* ftwU;    // C2<float>[H+1] exp(-2 pi i k / nx)
   int* err;            // device error word (bounded waits that gave up set it)
   float rn[3];         // 1/nx, 1/ny, 1/nz (rounded from FP64)
   int* dirty;          // fast forward plane pass: per plane (c*nz + z) flag, nonzero when the

@@ -49,18 +49,18 @@ __device__ __forceinline__ void cp_async_wait_all() {
 }  // namespace
 
 template <int H, int NY>
-__device__ __forceinline__ void load_tw(Lw* twH, Lw* twY, Lw* untw, const PassCfg& c) {
-  fill_tw2<H>(twH, reinterpret_cast<const Lw*>(c.lwH));
-  fill_tw2<NY>(twY, reinterpret_cast<const Lw*>(c.lwY));
-  const Lw* gU = reinterpret_cast<const Lw*>(c.lwU);
+__device__ __forceinline__ void load_tw(C2<float>* twH, C2<float>* twY, C2<float>* untw, const PassCfg& c) {
+  fill_tw2<H>(twH, reinterpret_cast<const C2<float>*>(c.ftwH));
+  fill_tw2<NY>(twY, reinterpret_cast<const C2<float>*>(c.ftwY));
+  const C2<float>* gU = reinterpret_cast<const C2<float>*>(c.ftwU);
   for (int i = threadIdx.x; i <= H; i += blockDim.x) untw[i] = gU[i];
 }
 
-// Twiddle tables of a plane pass at the start of its shared memory (16-byte entries, so
-// every buffer after them stays 16-byte aligned)
+// Twiddle tables of a plane pass at the start of its shared memory, padded to a whole
+// number of 16-byte units so that every buffer after them stays 16-byte aligned
 template <int H, int NY>
 __host__ __device__ constexpr size_t plane_tw_bytes() {
-  return sizeof(Lw) * ((size_t)tw2_size<H>() + tw2_size<NY>() + H + 1);
+  return (sizeof(C2<float>) * ((size_t)tw2_size<H>() + tw2_size<NY>() + H + 1) + 15) / 16 * 16;
 }
 
 // The twiddle tables of a plane pass staged through registers (at most a few values per
@@ -70,11 +70,11 @@ template <int H, int NY, int NTHR>
 struct TwStage {
   static constexpr int NH = (tw2_size<H>() + NTHR - 1) / NTHR, NYs = (tw2_size<NY>() + NTHR - 1) / NTHR;
   static constexpr int NU = (H + 1 + NTHR - 1) / NTHR;
-  Lw h[NH], y[NYs], u[NU];
+  C2<float> h[NH], y[NYs], u[NU];
   __device__ __forceinline__ void load(const PassCfg& c, int tid) {
-    const Lw* gH = reinterpret_cast<const Lw*>(c.lwH);
-    const Lw* gY = reinterpret_cast<const Lw*>(c.lwY);
-    const Lw* gU = reinterpret_cast<const Lw*>(c.lwU);
+    const C2<float>* gH = reinterpret_cast<const C2<float>*>(c.ftwH);
+    const C2<float>* gY = reinterpret_cast<const C2<float>*>(c.ftwY);
+    const C2<float>* gU = reinterpret_cast<const C2<float>*>(c.ftwU);
 #pragma unroll
     for (int j = 0; j < NH; ++j)
       if (tid + NTHR * j < tw2_size<H>()) h[j] = tw2_entry<H>(gH, tid + NTHR * j);
@@ -85,7 +85,7 @@ struct TwStage {
     for (int j = 0; j < NU; ++j)
       if (tid + NTHR * j <= H) u[j] = gU[tid + NTHR * j];
   }
-  __device__ __forceinline__ void store(Lw* twH, Lw* twY, Lw* untw, int tid) const {
+  __device__ __forceinline__ void store(C2<float>* twH, C2<float>* twY, C2<float>* untw, int tid) const {
 #pragma unroll
     for (int j = 0; j < NH; ++j)
       if (tid + NTHR * j < tw2_size<H>()) twH[tid + NTHR * j] = h[j];
@@ -157,10 +157,11 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
   using S = NShape<H, NY>;
   constexpr int CPER = H / CS, ROWS = NY / CS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Lw* twH = reinterpret_cast<Lw*>(smem_raw);
-  Lw* twY = twH + tw2_size<H>();
-  Lw* untw = twY + tw2_size<NY>();
-  C2<float>* col = reinterpret_cast<C2<float>*>(untw + H + 1);  // [CPER][LDC]
+  C2<float>* twH = reinterpret_cast<C2<float>*>(smem_raw);
+  C2<float>* twY = twH + tw2_size<H>();
+  C2<float>* untw = twY + tw2_size<NY>();
+  unsigned char* after_tw = smem_raw + plane_tw_bytes<H, NY>();
+  C2<float>* col = reinterpret_cast<C2<float>*>(after_tw);  // [CPER][LDC]
   C2<float>* xb = col + CPER * S::LDC;                            // [GR][XS]
   cg::cluster_group cluster = cg::this_cluster();
   const int h = CS > 1 ? (int)cluster.block_rank() : 0;
@@ -211,10 +212,11 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
             continue;
           }
           const C2<float> B = conjg(xg[H - k]);
-          const C2<float> sum = A + B, d1 = lw_mul<false>(untw[k], A - B);
+          const C2<float> sum = A + B, d1 = cmul_rn(untw[k], A - B);
           put_col<CS, CPER, S::LDC>(cluster, col, h, k, y, C2<float>{0.5f * (sum.x + d1.y), 0.5f * (sum.y - d1.x)});
           if (2 * k != H) {
-            const C2<float> d2 = lw_mul<false>(untw[H - k], conjg(B - A));
+            // w^(H-k) = -conj(w^k), so w^(H-k) conj(B - A) = conj(w^k (A - B)) = conj(d1)
+            const C2<float> d2 = conjg(d1);
             put_col<CS, CPER, S::LDC>(cluster, col, h, H - k, y,
                                       C2<float>{0.5f * (sum.x + d2.y), 0.5f * (-sum.y - d2.x)});
           }
@@ -275,10 +277,11 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   constexpr int LDR = WIDE == 2 ? H + 2 : S::LDR;
   static_assert(WIDE != 2 || S::NTH == 8, "the 16-byte copy-out pairs rows for lines of 8 threads");
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Lw* twH = reinterpret_cast<Lw*>(smem_raw);
-  Lw* twY = twH + tw2_size<H>();
-  Lw* untw = twY + tw2_size<NY>();
-  C2<float>* rowb = reinterpret_cast<C2<float>*>(untw + H + 1);  // [ROWS][LDR]
+  C2<float>* twH = reinterpret_cast<C2<float>*>(smem_raw);
+  C2<float>* twY = twH + tw2_size<H>();
+  C2<float>* untw = twY + tw2_size<NY>();
+  unsigned char* after_tw = smem_raw + plane_tw_bytes<H, NY>();
+  C2<float>* rowb = reinterpret_cast<C2<float>*>(after_tw);  // [ROWS][LDR]
   C2<float>* xb = rowb + ROWS * LDR;
   cg::cluster_group cluster = cg::this_cluster();
   const int h = CS > 1 ? (int)cluster.block_rank() : 0;
@@ -379,7 +382,7 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
         }
         const C2<float> Xk = R[k], Xc = conjg(R[H - k]);
         const C2<float> E = Xk + Xc;
-        const C2<float> O = lw_mul<true>(untw[k], Xk - Xc);
+        const C2<float> O = cmul_rn(conjg(untw[k]), Xk - Xc);
         return C2<float>{E.x - O.y, E.y + O.x};
       };
       C2<float>* orow = reinterpret_cast<C2<float>*>(sig + ((size_t)plane * NY + h * ROWS + yl) * (2 * H));
@@ -406,10 +409,11 @@ __global__ void __launch_bounds__(NTHR, MINB) k_plane_inv_s(const C2<float>* __r
   constexpr int NTY = reg_nt<NY>(), GC = NTHR / NTY, NTH = reg_nt<H>(), GR = NTHR / NTH;
   constexpr int R2Y = RegPlan<NY>::R2, R2H = RegPlan<H>::R2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Lw* twH = reinterpret_cast<Lw*>(smem_raw);
-  Lw* twY = twH + tw2_size<H>();
-  Lw* untw = twY + tw2_size<NY>();
-  C2<float>* stg = reinterpret_cast<C2<float>*>(untw + H + 1);  // [CPER][NY] own columns, then [NY] Nyquist
+  C2<float>* twH = reinterpret_cast<C2<float>*>(smem_raw);
+  C2<float>* twY = twH + tw2_size<H>();
+  C2<float>* untw = twY + tw2_size<NY>();
+  unsigned char* after_tw = smem_raw + plane_tw_bytes<H, NY>();
+  C2<float>* stg = reinterpret_cast<C2<float>*>(after_tw);  // [CPER][NY] own columns, then [NY] Nyquist
   C2<float>* nyq = stg + CPER * NY;
   C2<float>* rowb = nyq + NY;                                     // [ROWS][LDR]
   cg::cluster_group cluster = cg::this_cluster();
@@ -468,7 +472,7 @@ __global__ void __launch_bounds__(NTHR, MINB) k_plane_inv_s(const C2<float>* __r
         }
         const C2<float> Xk = R[k], Xc = conjg(R[H - k]);
         const C2<float> E = Xk + Xc;
-        const C2<float> O = lw_mul<true>(untw[k], Xk - Xc);
+        const C2<float> O = cmul_rn(conjg(untw[k]), Xk - Xc);
         return C2<float>{E.x - O.y, E.y + O.x};
       };
       C2<float>* orow = reinterpret_cast<C2<float>*>(sig + ((size_t)plane * NY + h * ROWS + yl) * (2 * H));
@@ -489,7 +493,7 @@ constexpr int kLDT = kTW + 1;  // padded row of a tile: conflict-free strided li
 // parity without bank conflicts.
 template <int NZ, bool SWZ>
 __host__ __device__ constexpr size_t pencil_fast_smem() {
-  return sizeof(Lw) * (size_t)tw2_size<NZ>() + sizeof(C2<float>) * ((size_t)6 * NZ * (SWZ ? kTW : kLDT));
+  return (sizeof(C2<float>) * (size_t)tw2_size<NZ>() + 15) / 16 * 16 + sizeof(C2<float>) * ((size_t)6 * NZ * (SWZ ? kTW : kLDT));
 }
 template <bool SWZ>
 __device__ __forceinline__ int tile_at(int row, int col) {
@@ -524,8 +528,8 @@ __device__ __forceinline__ int tile_row(int r) { return (r & ~15) + ((r & 1) << 
 template <int NZ, bool SWZ>
 __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<float>* out, PassCfg c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Lw* twZ = reinterpret_cast<Lw*>(smem_raw);
-  C2<float>* tile = reinterpret_cast<C2<float>*>(twZ + tw2_size<NZ>());  // [comp * NZ + kz][8 or 9]
+  C2<float>* twZ = reinterpret_cast<C2<float>*>(smem_raw);
+  C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw + (sizeof(C2<float>) * tw2_size<NZ>() + 15) / 16 * 16);  // [comp * NZ + kz][8 or 9]
   const int tid = threadIdx.x;
   const size_t P = (size_t)(c.H + 1) * c.ny;
   const size_t p0 = (size_t)blockIdx.x * kTW;
@@ -541,7 +545,7 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<f
       cp_async8(tile + row * kLDT + t, in + (size_t)row * P + p0 + t);
     }
   }
-  fill_tw2<NZ>(twZ, reinterpret_cast<const Lw*>(c.lwZ));
+  fill_tw2<NZ>(twZ, reinterpret_cast<const C2<float>*>(c.ftwZ));
   cp_async_wait_all();
   __syncthreads();
   constexpr int NTZ = reg_nt<NZ>(), GL = kT / NTZ, R2Z = RegPlan<NZ>::R2;
