@@ -258,18 +258,20 @@ __device__ void scatter_stencil(Q* __restrict__ eps, int3 n, size_t N, const Def
   }
 }
 
-// ---------------------------------------------------------------- dilated candidate lists
+// ---------------------------------------------------------------- energy lists
 // The eight candidate positions of a defect in class c use the stencil of class
 // cp = 1 - c shifted by s_j, s_j per axis in {-cp, 1 - cp} (bit 2 of j: x, bit 1: y,
-// bit 0: z).  Their voxels are the 2x2x2 dilation of that stencil.  For the energies
-// each voxel u of the dilation is listed once with the eight counts cnt(u - s_j)
-// packed in a uint64, so sigma at u is read once for all eight candidates.  One block
-// per (defect, class c); the count box of the stencil lives in shared memory (side
-// 2E + 1, E the scan half-width), and lists come out in the box's linear order.
-constexpr int kDilateMaxSide = 58;  // 58^3 bytes of shared memory; larger defects use the direct loop
+// bit 0: z).  Their voxels are the 2x2x2 dilation of that stencil, and the site's own
+// class-c stencil lies inside the same box.  For the energies each voxel u of the union
+// is listed once with the site count and the eight counts cnt(u - s_j) (packed in a
+// uint64), so sigma at u is read once for all nine positions.  One block per (defect,
+// class c); the count box of both stencils lives in shared memory (side 2E + 1, E the
+// scan half-width; class c' counts in the low byte, class c in the high byte), and
+// lists come out in the box's linear order.
+constexpr int kDilateMaxSide = 48;  // 2 * 48^3 bytes of shared memory; larger defects use the direct loops
 
 __device__ __forceinline__ int dilate_prepare(const DefGeo& g, const int* __restrict__ ptr, const int* __restrict__ off,
-                                              const uint8_t* __restrict__ cnt, int i, int cp, uint8_t* box) {
+                                              const uint8_t* __restrict__ cnt, int i, int cp, uint16_t* box) {
   const int E = g.extent, side = 2 * E + 1;
   const int nv = side * side * side;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) box[v] = 0;
@@ -280,24 +282,32 @@ __device__ __forceinline__ int dilate_prepare(const DefGeo& g, const int* __rest
     box[((dz + E) * side + (dy + E)) * side + (dx + E)] = cnt[k];
   }
   __syncthreads();
+  const int c = 1 - cp;  // the site's own stencil, in the high byte (each voxel once)
+  for (int k = ptr[2 * i + c] + threadIdx.x; k < ptr[2 * i + c + 1]; k += blockDim.x) {
+    int dx, dy, dz;
+    unpack_off(off[k], dx, dy, dz);
+    uint16_t& b = box[((dz + E) * side + (dy + E)) * side + (dx + E)];
+    b = (uint16_t)(b | ((unsigned)cnt[k] << 8));
+  }
+  __syncthreads();
   return nv;
 }
 
-__device__ __forceinline__ unsigned long long dilate_counts(const uint8_t* box, int E, int cp, int ux, int uy, int uz) {
+__device__ __forceinline__ unsigned long long dilate_counts(const uint16_t* box, int E, int cp, int ux, int uy, int uz) {
   const int side = 2 * E + 1;
   unsigned long long cc = 0;
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
     const int x = ux - (((j >> 2) & 1) - cp), y = uy - (((j >> 1) & 1) - cp), z = uz - ((j & 1) - cp);
     if (x >= -E && x <= E && y >= -E && y <= E && z >= -E && z <= E)
-      cc |= (unsigned long long)box[((z + E) * side + (y + E)) * side + (x + E)] << (8 * j);
+      cc |= (unsigned long long)(box[((z + E) * side + (y + E)) * side + (x + E)] & 255u) << (8 * j);
   }
   return cc;
 }
 
 __global__ void k_dilate_count(const DefGeo* __restrict__ G, const int* __restrict__ ptr, const int* __restrict__ off,
                                const uint8_t* __restrict__ cnt, int* __restrict__ ndil) {
-  extern __shared__ uint8_t box[];
+  extern __shared__ uint16_t box[];
   __shared__ long long sh[32];
   const int i = blockIdx.x >> 1, c = blockIdx.x & 1, cp = 1 - c;
   const DefGeo g = G[i];
@@ -310,7 +320,7 @@ __global__ void k_dilate_count(const DefGeo* __restrict__ G, const int* __restri
   long long n = 0;
   for (int v = threadIdx.x; v < nv; v += blockDim.x) {
     const int ux = v % side - E, uy = (v / side) % side - E, uz = v / (side * side) - E;
-    n += dilate_counts(box, E, cp, ux, uy, uz) != 0ull;
+    n += (dilate_counts(box, E, cp, ux, uy, uz) != 0ull) || (box[v] >> 8) != 0;
   }
   n = block_sum_ll(n, sh);
   if (threadIdx.x == 0) ndil[blockIdx.x] = (int)n;
@@ -318,8 +328,8 @@ __global__ void k_dilate_count(const DefGeo* __restrict__ G, const int* __restri
 
 __global__ void k_dilate_fill(const DefGeo* __restrict__ G, const int* __restrict__ ptr, const int* __restrict__ off,
                               const uint8_t* __restrict__ cnt, DilatedLists dl, int* __restrict__ doff,
-                              unsigned long long* __restrict__ dcnt, int* __restrict__ err) {
-  extern __shared__ uint8_t box[];
+                              unsigned long long* __restrict__ dcnt, uint8_t* __restrict__ dscnt, int* __restrict__ err) {
+  extern __shared__ uint16_t box[];
   __shared__ int wsum[32];
   const int i = blockIdx.x >> 1, c = blockIdx.x & 1, cp = 1 - c;
   const DefGeo g = G[i];
@@ -333,13 +343,16 @@ __global__ void k_dilate_fill(const DefGeo* __restrict__ G, const int* __restric
     const int v = v0 + threadIdx.x;
     int ux = 0, uy = 0, uz = 0;
     unsigned long long cc = 0;
+    unsigned sc = 0;
     if (v < nv) {
       ux = v % side - E;
       uy = (v / side) % side - E;
       uz = v / (side * side) - E;
       cc = dilate_counts(box, E, cp, ux, uy, uz);
+      sc = box[v] >> 8;
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, cc != 0ull);
+    const bool any = cc != 0ull || sc != 0u;
+    const unsigned bal = __ballot_sync(0xffffffffu, any);
     const int rank = __popc(bal & ((1u << lane) - 1u));
     if (lane == 0) wsum[w] = __popc(bal);
     __syncthreads();
@@ -348,11 +361,12 @@ __global__ void k_dilate_fill(const DefGeo* __restrict__ G, const int* __restric
       if (q < w) pre += wsum[q];
       tot += wsum[q];
     }
-    if (cc) {
+    if (any) {
       const int at = base + pre + rank;
       if (at < end) {
         doff[at] = pack_off(ux, uy, uz);
         dcnt[at] = cc;
+        dscnt[at] = (uint8_t)sc;
       } else {
         atomicExch(err, 5);
       }
@@ -719,47 +733,23 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
   // a time, with every load of the group issued before the first use, so that U
   // gathers are in flight per thread (the accumulation order is that of the plain loop).
   constexpr int U = 4;
-  {
-    const int k_end = ptr[2 * i + c + 1];
-    for (int k0 = ptr[2 * i + c] + threadIdx.x; k0 < k_end; k0 += U * blockDim.x) {
-      T sv[U][6], w[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int k = k0 + u * blockDim.x;
-        w[u] = T(0);
-        if (k < k_end) {
-          int dx, dy, dz;
-          unpack_off(off[k], dx, dy, dz);
-          w[u] = T(cnt[k]);
-          const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
-#pragma unroll
-          for (int a = 0; a < 6; ++a) sv[u][a] = use[a] ? __ldg(sig + a * N + v) : T(0);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (k0 + u * (int)blockDim.x >= k_end) break;
-        T dot = T(0);
-#pragma unroll
-        for (int a = 0; a < 6; ++a) dot += ew[a] * sv[u][a];
-        acc[0].add(w[u] * dot);
-      }
-    }
-  }
   if (want_cand && dl.ptr && dl.ptr[2 * i + c] >= 0) {
-    // the dilation of the candidate stencil, each voxel once with its eight counts
+    // the energy list: each voxel of the site and candidate stencils once, nine counts
     const int k_end = dl.end[2 * i + c];
     for (int k0 = dl.ptr[2 * i + c] + threadIdx.x; k0 < k_end; k0 += U * blockDim.x) {
       T sv[U][6];
       unsigned long long cc[U];
+      unsigned sc[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int k = k0 + u * blockDim.x;
         cc[u] = 0ull;
+        sc[u] = 0u;
         if (k < k_end) {
           int ux, uy, uz;
           unpack_off(dl.off[k], ux, uy, uz);
           cc[u] = dl.cnt[k];
+          sc[u] = dl.scnt[k];
           const size_t v = ((size_t)wrap(bz + uz, n.z) * n.y + wrap(by + uy, n.y)) * n.x + wrap(bx + ux, n.x);
 #pragma unroll
           for (int a = 0; a < 6; ++a) sv[u][a] = use[a] ? __ldg(sig + a * N + v) : T(0);
@@ -771,27 +761,57 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
         T dot = T(0);
 #pragma unroll
         for (int a = 0; a < 6; ++a) dot += ew[a] * sv[u][a];
+        if (sc[u]) acc[0].add(T(sc[u]) * dot);
 #pragma unroll
         for (int j = 0; j < 8; ++j) acc[1 + j].add(T((unsigned)(cc[u] >> (8 * j)) & 255u) * dot);
       }
     }
-  } else if (want_cand) {
-    // candidate j sits at base(X + lambda_j) = base(X) + d_j, d_j in {-1,0}^3 (c = 0)
-    // or {0,1}^3 (c = 1); per axis the shift is (s + 1)/2 - (1 - c) with s = +-1
-    for (int k = ptr[2 * i + cp] + threadIdx.x; k < ptr[2 * i + cp + 1]; k += blockDim.x) {
-      int dx, dy, dz;
-      unpack_off(off[k], dx, dy, dz);
-      const T w = T(cnt[k]);
-      const int x0 = wrap(bx + dx - cp, n.x), x1 = wrap(bx + dx + 1 - cp, n.x);
-      const int y0 = wrap(by + dy - cp, n.y), y1 = wrap(by + dy + 1 - cp, n.y);
-      const int z0 = wrap(bz + dz - cp, n.z), z1 = wrap(bz + dz + 1 - cp, n.z);
+  } else {
+    {  // the site stencil
+      const int k_end = ptr[2 * i + c + 1];
+      for (int k0 = ptr[2 * i + c] + threadIdx.x; k0 < k_end; k0 += U * blockDim.x) {
+        T sv[U][6], w[U];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const size_t v = ((size_t)((j & 1) ? z1 : z0) * n.y + ((j & 2) ? y1 : y0)) * n.x + ((j & 4) ? x1 : x0);
-        T dot = T(0);
+        for (int u = 0; u < U; ++u) {
+          const int k = k0 + u * blockDim.x;
+          w[u] = T(0);
+          if (k < k_end) {
+            int dx, dy, dz;
+            unpack_off(off[k], dx, dy, dz);
+            w[u] = T(cnt[k]);
+            const size_t v = ((size_t)wrap(bz + dz, n.z) * n.y + wrap(by + dy, n.y)) * n.x + wrap(bx + dx, n.x);
 #pragma unroll
-        for (int a = 0; a < 6; ++a) dot += ew[a] * (use[a] ? __ldg(sig + a * N + v) : T(0));
-        acc[1 + j].add(w * dot);
+            for (int a = 0; a < 6; ++a) sv[u][a] = use[a] ? __ldg(sig + a * N + v) : T(0);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (k0 + u * (int)blockDim.x >= k_end) break;
+          T dot = T(0);
+#pragma unroll
+          for (int a = 0; a < 6; ++a) dot += ew[a] * sv[u][a];
+          acc[0].add(w[u] * dot);
+        }
+      }
+    }
+    if (want_cand) {
+      // candidate j sits at base(X + lambda_j) = base(X) + d_j, d_j in {-1,0}^3 (c = 0)
+      // or {0,1}^3 (c = 1); per axis the shift is (s + 1)/2 - (1 - c) with s = +-1
+      for (int k = ptr[2 * i + cp] + threadIdx.x; k < ptr[2 * i + cp + 1]; k += blockDim.x) {
+        int dx, dy, dz;
+        unpack_off(off[k], dx, dy, dz);
+        const T w = T(cnt[k]);
+        const int x0 = wrap(bx + dx - cp, n.x), x1 = wrap(bx + dx + 1 - cp, n.x);
+        const int y0 = wrap(by + dy - cp, n.y), y1 = wrap(by + dy + 1 - cp, n.y);
+        const int z0 = wrap(bz + dz - cp, n.z), z1 = wrap(bz + dz + 1 - cp, n.z);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const size_t v = ((size_t)((j & 1) ? z1 : z0) * n.y + ((j & 2) ? y1 : y0)) * n.x + ((j & 4) ? x1 : x0);
+          T dot = T(0);
+#pragma unroll
+          for (int a = 0; a < 6; ++a) dot += ew[a] * (use[a] ? __ldg(sig + a * N + v) : T(0));
+          acc[1 + j].add(w * dot);
+        }
       }
     }
   }
@@ -1041,7 +1061,7 @@ cudaError_t launch_stencil_count(const DefGeo* G, int nd, int* nnz, long long* s
 }
 cudaError_t launch_dilate_count(const DefGeo* G, int nd, const int* ptr, const int* off, const uint8_t* cnt, int* ndil,
                                 cudaStream_t st) {
-  const size_t smem = (size_t)kDilateMaxSide * kDilateMaxSide * kDilateMaxSide;
+  const size_t smem = sizeof(uint16_t) * kDilateMaxSide * kDilateMaxSide * kDilateMaxSide;
   cudaError_t e = cudaFuncSetAttribute(k_dilate_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_dilate_count<<<2 * nd, 256, smem, st>>>(G, ptr, off, cnt, ndil);
@@ -1049,11 +1069,11 @@ cudaError_t launch_dilate_count(const DefGeo* G, int nd, const int* ptr, const i
 }
 cudaError_t launch_dilate_fill(const DefGeo* G, int nd, const int* ptr, const int* off, const uint8_t* cnt,
                                const DilatedLists& dl, int* err, cudaStream_t st) {
-  const size_t smem = (size_t)kDilateMaxSide * kDilateMaxSide * kDilateMaxSide;
+  const size_t smem = sizeof(uint16_t) * kDilateMaxSide * kDilateMaxSide * kDilateMaxSide;
   cudaError_t e = cudaFuncSetAttribute(k_dilate_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   k_dilate_fill<<<2 * nd, 256, smem, st>>>(G, ptr, off, cnt, dl, const_cast<int*>(dl.off),
-                                           const_cast<unsigned long long*>(dl.cnt), err);
+                                           const_cast<unsigned long long*>(dl.cnt), const_cast<uint8_t*>(dl.scnt), err);
   return cudaGetLastError();
 }
 cudaError_t launch_stencil_fill(const DefGeo* G, int nd, const int* ptr, const long long* sumcnt, int* off, uint8_t* cnt,

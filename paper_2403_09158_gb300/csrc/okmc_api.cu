@@ -224,7 +224,8 @@ struct okmc_grid {
   double* d_partial = nullptr;
   int* d_dl = nullptr;                  // [4 nd]: start and end of each dilated candidate list
   int* d_doff = nullptr;                // dilated lists: packed offsets
-  unsigned long long* d_dcnt = nullptr; // dilated lists: eight candidate counts
+  unsigned long long* d_dcnt = nullptr; // energy lists: eight candidate counts
+  uint8_t* d_dscnt = nullptr;           // energy lists: site counts
   void* d_bg = nullptr;     // [6][nz][ny][nx] fixed-point plastic strain of the dislocation lines (or none)
   std::vector<okmc_defect> h_def;
   bool sigma_valid = false;
@@ -401,6 +402,7 @@ int energies(okmc_grid* g, int want_cand, double kT = 0.0) {
     dl.end = g->d_dl + 2 * g->nd;
     dl.off = g->d_doff;
     dl.cnt = g->d_dcnt;
+    dl.scnt = g->d_dscnt;
   }
   return run(g, "energies", [&] {
     if (fp64(g))
@@ -615,9 +617,10 @@ int build_dilated_lists(okmc_grid* g) {
   OKMC_TRY(dalloc(g, (void**)&g->d_dl, 4 * nd * sizeof(int)));
   OKMC_TRY(dalloc(g, (void**)&g->d_doff, (size_t)tot * sizeof(int)));
   OKMC_TRY(dalloc(g, (void**)&g->d_dcnt, (size_t)tot * sizeof(unsigned long long)));
+  OKMC_TRY(dalloc(g, (void**)&g->d_dscnt, (size_t)tot * sizeof(uint8_t)));
   e = cudaMemcpyAsync(g->d_dl, se.data(), se.size() * sizeof(int), cudaMemcpyHostToDevice, g->st);
   if (e != cudaSuccess) return cuda_fail(g, e, "dilated list offsets");
-  DilatedLists dl{g->d_dl, g->d_dl + 2 * nd, g->d_doff, g->d_dcnt};
+  DilatedLists dl{g->d_dl, g->d_dl + 2 * nd, g->d_doff, g->d_dcnt, g->d_dscnt};
   OKMC_TRY(run(g, "dilate_fill", [&] { return launch_dilate_fill(g->d_geo, nd, g->d_ptr, g->d_off, g->d_cnt, dl, g->d_err, g->st); }));
   return check_device_error(g);
 }
@@ -644,7 +647,7 @@ void free_defects(okmc_grid* g) {
                    (void**)&g->d_alpha, (void**)&g->d_sumcnt, (void**)&g->d_nnz, (void**)&g->d_W, (void**)&g->d_D,
                    (void**)&g->d_dip, (void**)&g->d_E,
                    (void**)&g->d_Ec, (void**)&g->d_order, (void**)&g->d_rates, (void**)&g->d_rsum, (void**)&g->d_moves, (void**)&g->d_pos,
-                   (void**)&g->d_dl, (void**)&g->d_doff, (void**)&g->d_dcnt};
+                   (void**)&g->d_dl, (void**)&g->d_doff, (void**)&g->d_dcnt, (void**)&g->d_dscnt};
   for (void** b : bufs) {
     dfree(g, *b);
     *b = nullptr;

@@ -360,13 +360,15 @@ struct WBatch {
   int nb;
 };
 
-// Dilated candidate stencils (one list per defect and current class; ptr < 0: none,
-// the energies kernel then walks the candidate stencil eight times).
+// Energy lists (one per defect and current class; ptr < 0: none, the energies kernel
+// then walks the site stencil once and the candidate stencil eight times): every voxel
+// of the site stencil or of a candidate stencil, once, with its nine counts.
 struct DilatedLists {
   const int* ptr;                 // [2 nd] first entry of list (i, c)
   const int* end;                 // [2 nd] one past the last entry
-  const int* off;                 // packed offsets of the dilation's voxels
+  const int* off;                 // packed offsets of the voxels (relative to the site's base voxel)
   const unsigned long long* cnt;  // counts of the eight candidates, byte j for jump j
+  const uint8_t* scnt;            // count of the site stencil
 };
 
 // Unit eigenstrain tensors of the defect types present (at most eight: four
@@ -475,12 +477,23 @@ __device__ __forceinline__ void sigma_of(const C2<T>* e, T q0, T q1, T q2, const
 // Applied to eta, every intermediate is of the size of the result; the rounding of
 // eta itself acts as a perturbation of the input, which the operator then maps
 // exactly, and which pairs with the (small) relaxed field of any defect.
+// 1/x by the hardware approximation (about one ulp; deterministic, so launch variants
+// still agree bit for bit).  Used where a relative error of one ulp in the reciprocal only
+// rescales a term that is of the size of the result: 1/|q|^2 of the transverse split (an
+// input-side perturbation the operator maps exactly) and 1/det K (the compatible
+// correction w, of the size of the elastic field once e is transverse).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 __device__ __forceinline__ void sigma_of(const C2<float>* e_in, float q0, float q1, float q2, const GreenC<float>& C,
                                          const GreenC<float>& Cs, C2<float>* s) {
   C2<float> e[6];
   {
     const float qq = __fmaf_rn(q2, q2, __fmaf_rn(q1, q1, __fmul_rn(q0, q0)));
-    const float rqq = __frcp_rn(qq);
+    const float rqq = rcp_approx(qq);
     const C2<float> u0 = pfma(q2, e_in[4], pfma(q1, e_in[5], pscale(q0, e_in[0])));
     const C2<float> u1 = pfma(q2, e_in[3], pfma(q1, e_in[1], pscale(q0, e_in[5])));
     const C2<float> u2 = pfma(q2, e_in[2], pfma(q1, e_in[3], pscale(q0, e_in[4])));
@@ -515,7 +528,7 @@ __device__ __forceinline__ void sigma_of(const C2<float>* e_in, float q0, float 
   auto dif = [](float a, float b, float c, float d) { return __fmaf_rn(a, b, -__fmul_rn(c, d)); };
   const float i00 = dif(k11, k22, k12, k12), i01 = dif(k02, k12, k01, k22), i02 = dif(k01, k12, k02, k11);
   const float i11 = dif(k00, k22, k02, k02), i12 = dif(k01, k02, k00, k12), i22 = dif(k00, k11, k01, k01);
-  const float rdet = __frcp_rn(__fmaf_rn(k02, i02, __fmaf_rn(k01, i01, __fmul_rn(k00, i00))));
+  const float rdet = rcp_approx(__fmaf_rn(k02, i02, __fmaf_rn(k01, i01, __fmul_rn(k00, i00))));
   const C2<float> w0 = pscale(rdet, pfma(i02, v2, pfma(i01, v1, pscale(i00, v0))));
   const C2<float> w1 = pscale(rdet, pfma(i12, v2, pfma(i11, v1, pscale(i01, v0))));
   const C2<float> w2 = pscale(rdet, pfma(i22, v2, pfma(i12, v1, pscale(i02, v0))));
