@@ -710,7 +710,11 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
                                                              double pref, int want_cand, const int* __restrict__ order,
                                                              double* __restrict__ E, double* __restrict__ Ec, RateArgs ra,
                                                              DilatedLists dl) {
-  __shared__ double part[kEnergyThreads / 32][9];
+  // per-warp partial sums: FP32 (sum, compensation) pairs for FP32 fields, converted to
+  // FP64 only in the epilogue warp (each conversion of a warp costs a whole FP64 issue
+  // slot, even with one lane active); FP64 sums for FP64 fields
+  __shared__ T part[kEnergyThreads / 32][9];
+  __shared__ T partc[kEnergyThreads / 32][9];
   const int i = order ? order[blockIdx.x] : blockIdx.x;
   const size_t N = (size_t)n.x * n.y * n.z;
   const okmc_defect r = d[i];
@@ -820,7 +824,15 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
 #pragma unroll
   for (int j = 0; j < 9; ++j) {
     acc[j].warp_reduce();
-    if (lane == 0) part[wid][j] = acc[j].value();
+    if (lane == 0) {
+      if constexpr (sizeof(T) == 4) {
+        part[wid][j] = acc[j].v.s;
+        partc[wid][j] = acc[j].v.c;
+      } else {
+        part[wid][j] = acc[j].v;
+        partc[wid][j] = T(0);
+      }
+    }
   }
   __syncthreads();
   // epilogue on warp 0, one lane per position (lane 0: the site, lane 1 + j: jump j),
@@ -828,7 +840,7 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
   if (threadIdx.x >= 32) return;
   double tot = 0.0;
   if (lane < 9)
-    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += part[w2][lane];
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += (double)part[w2][lane] + (double)partc[w2][lane];
   double ej = 0.0;
   const double es = G[i].escale;  // read again here rather than held in registers
   if (lane == 0) ej = pref * es * alpha[2 * i + c] * tot - W[(size_t)i * 18 + c * 9];

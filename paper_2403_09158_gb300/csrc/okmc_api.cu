@@ -13,6 +13,9 @@
 #include <tuple>
 #include <new>
 #include <string>
+
+#include <sys/stat.h>
+#include <unistd.h>
 #include <utility>
 #include <vector>
 
@@ -723,6 +726,94 @@ int capture_step(okmc_grid* g, int mode, double T, cudaGraphExec_t* out) {
 std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int>, std::array<int, 3>> g_tune_cache;  // shape -> variant of each pass
 
+// The choices also persist across processes in a JSON file, one entry per device and
+// grid shape: {"<device name>|<SMs>|<nx>x<ny>x<nz>|<schema>": [v0, v1, v2], ...}.  The file
+// is $OKMC_TUNE_CACHE if set (set and empty: no file), else $XDG_CACHE_HOME/okmc/tune.json
+// or ~/.cache/okmc/tune.json.  It is read once per process; after each new tuning it is
+// rewritten with its current content merged in (a temporary file renamed over it, so a
+// reader never sees half a file).  An unreadable or malformed file counts as empty.
+constexpr const char* kTuneSchema = "passes-v2";  // bump when the variants of a pass change meaning
+bool g_tune_file_read = false;
+std::map<std::string, std::array<int, 3>> g_tune_file;
+
+std::string tune_cache_path() {
+  if (const char* p = std::getenv("OKMC_TUNE_CACHE")) return p;
+  std::string dir;
+  if (const char* x = std::getenv("XDG_CACHE_HOME")) dir = x;
+  else if (const char* h = std::getenv("HOME")) dir = std::string(h) + "/.cache";
+  else return "";
+  return dir + "/okmc/tune.json";
+}
+
+std::map<std::string, std::array<int, 3>> parse_tune_file(const std::string& text) {
+  std::map<std::string, std::array<int, 3>> out;
+  size_t i = 0;
+  while (true) {
+    const size_t a = text.find('"', i);
+    if (a == std::string::npos) break;
+    const size_t b = text.find('"', a + 1);
+    if (b == std::string::npos) return {};
+    const std::string key = text.substr(a + 1, b - a - 1);
+    const size_t l = text.find('[', b);
+    const size_t r = text.find(']', b);
+    if (l == std::string::npos || r == std::string::npos || r < l) return {};
+    std::array<int, 3> v{};
+    const char* q = text.c_str() + l + 1;
+    for (int k = 0; k < 3; ++k) {
+      char* end = nullptr;
+      const long x = std::strtol(q, &end, 10);
+      if (end == q || x < 0 || x > 30) return {};
+      v[k] = (int)x;
+      q = end;
+      while (*q == ' ' || *q == ',' || *q == '\n' || *q == '\t') ++q;
+    }
+    out[key] = v;
+    i = r + 1;
+  }
+  return out;
+}
+
+std::map<std::string, std::array<int, 3>> read_tune_file(const std::string& path) {
+  std::FILE* f = path.empty() ? nullptr : std::fopen(path.c_str(), "rb");
+  if (!f) return {};
+  std::string text;
+  char buf[4096];
+  size_t k;
+  while ((k = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, k);
+  std::fclose(f);
+  return parse_tune_file(text);
+}
+
+void write_tune_file(const std::string& path, const std::map<std::string, std::array<int, 3>>& m) {
+  if (path.empty()) return;
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos)  // create the directory chain (errors surface at fopen)
+    for (size_t p = path.find('/', 1); p != std::string::npos && p <= slash; p = path.find('/', p + 1))
+      mkdir(path.substr(0, p).c_str(), 0755);
+  const std::string tmp = path + ".tmp." + std::to_string((long long)getpid());
+  std::FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return;
+  std::fputs("{\n", f);
+  size_t n = 0;
+  for (const auto& kv : m)
+    std::fprintf(f, "  \"%s\": [%d, %d, %d]%s\n", kv.first.c_str(), kv.second[0], kv.second[1], kv.second[2],
+                 ++n < m.size() ? "," : "");
+  std::fputs("}\n", f);
+  const bool ok = std::fclose(f) == 0;
+  if (!ok || std::rename(tmp.c_str(), path.c_str()) != 0) std::remove(tmp.c_str());
+}
+
+std::string tune_key(const okmc_grid* g) {
+  int dev = 0;
+  cudaDeviceProp prop{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return "";
+  std::string name = prop.name;
+  for (char& ch : name)
+    if (ch == '"' || ch == '|') ch = '_';
+  return name + "|" + std::to_string(prop.multiProcessorCount) + "|" + std::to_string(g->n[0]) + "x" +
+         std::to_string(g->n[1]) + "x" + std::to_string(g->n[2]) + "|" + kTuneSchema;
+}
+
 // One launch of each pass in the chosen variants on the zeroed spectra (and the zero
 // field the grid starts with), so that the one-time launch setup of those kernels
 // (attributes, the occupancy query behind the L2 prefetch distance) happens here and
@@ -755,12 +846,27 @@ int autotune(okmc_grid* g) {
   const char* env = std::getenv("OKMC_TUNE");
   if (env && env[0] == '0') return warm_passes(g);
   const auto key = std::make_tuple(g->n[0], g->n[1], g->n[2]);
+  const std::string fkey = tune_key(g);
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       for (int p = 0; p < 3; ++p) g->variant[p] = it->second[p];
       return OKMC_OK;
+    }
+    if (!g_tune_file_read) {
+      g_tune_file = read_tune_file(tune_cache_path());
+      g_tune_file_read = true;
+    }
+    auto ft = fkey.empty() ? g_tune_file.end() : g_tune_file.find(fkey);
+    if (ft != g_tune_file.end()) {
+      bool ok = true;
+      for (int p = 0; p < 3; ++p) ok = ok && ((g->avail[p] >> ft->second[p]) & 1);
+      if (ok) {
+        for (int p = 0; p < 3; ++p) g->variant[p] = ft->second[p];
+        g_tune_cache[key] = ft->second;
+        return warm_passes(g);  // first grid of this shape in the process: one-time launch set-up
+      }
     }
   }
   const size_t sbytes = 6 * g->n[2] * g->P * 2 * tsize(g);
@@ -812,6 +918,13 @@ int autotune(okmc_grid* g) {
   if (e != cudaSuccess) return cuda_fail(g, e, "tune");
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune_cache[key] = {g->variant[0], g->variant[1], g->variant[2]};
+  if (!fkey.empty()) {
+    const std::string path = tune_cache_path();
+    auto merged = read_tune_file(path);
+    merged[fkey] = g_tune_cache[key];
+    write_tune_file(path, merged);
+    g_tune_file = merged;
+  }
   return OKMC_OK;
 }
 
@@ -951,6 +1064,14 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   c.C11 = d->C11;
   c.C12 = d->C12;
   c.C44 = d->C44;
+  {
+    const double rN = 1.0 / ((double)c.nx * c.ny * c.nz);
+    const double Cd[3] = {c.C11, c.C12, c.C44};
+    for (int a = 0; a < 3; ++a) {
+      c.fC[a] = (float)Cd[a];
+      c.fCs[a] = (float)(Cd[a] * rN);
+    }
+  }
   for (int a = 0; a < 3; ++a) c.rn[a] = (float)(1.0 / g->n[a]);
   c.pH = make_plan(g->H);
   c.pY = make_plan(g->n[1]);

@@ -289,6 +289,8 @@ struct PassCfg {
   int forward_only;    // pencil pass: stop after the forward z transform
   double q;            // fixed-point quantum of the eigenstrain input
   double C11, C12, C44;
+  float fC[3];         // C11, C12, C44 rounded to FP32 (the FP32 Green operator's constants)
+  float fCs[3];        // C11, C12, C44 / (nx ny nz), rounded to FP32 once from FP64
   LinePlan pH, pY, pZ;
   const void* twH;     // C2<T>[H]      w_H^k
   const void* twY;     // C2<T>[ny]
@@ -548,10 +550,19 @@ __device__ __forceinline__ void sigma_of(const C2<float>* e_in, float q0, float 
 // so the Nyquist index is -N/2); on Nyquist planes the operator is averaged over
 // the sign of the Nyquist components, which is what the real part of the inverse
 // of the full spectrum computes.
+// scale: 1/N (the solve) or 1 (unnormalised spectra).  The FP32 constants come ready from
+// the pass configuration, so no FP64 arithmetic or conversion runs per frequency (the FP64
+// pipe of this GPU is narrow, and the compiler may re-derive hoisted values per call).
 template <class T>
 __device__ __forceinline__ void green_point(C2<T>* e, int kx, int ky, int kz, const PassCfg& c, T scale) {
-  const GreenC<T> C{T(c.C11), T(c.C12), T(c.C44)};
-  const GreenC<T> Cs{T(c.C11 * (double)scale), T(c.C12 * (double)scale), T(c.C44 * (double)scale)};
+  GreenC<T> C, Cs;
+  if constexpr (sizeof(T) == 4) {
+    C = GreenC<T>{c.fC[0], c.fC[1], c.fC[2]};
+    Cs = scale == T(1) ? C : GreenC<T>{c.fCs[0], c.fCs[1], c.fCs[2]};
+  } else {
+    C = GreenC<T>{T(c.C11), T(c.C12), T(c.C44)};
+    Cs = GreenC<T>{T(c.C11 * (double)scale), T(c.C12 * (double)scale), T(c.C44 * (double)scale)};
+  }
   const int fx = kx < c.H ? kx : kx - c.nx;
   const int fy = ky < c.ny / 2 ? ky : ky - c.ny;
   const int fz = kz < c.nz / 2 ? kz : kz - c.nz;

@@ -450,6 +450,14 @@ extern "C" int okmc_solve_stress_static(const float* eps, float* sigma, const in
   c.C11 = C11;
   c.C12 = C12;
   c.C44 = C44;
+  {
+    const double rN = 1.0 / ((double)c.nx * c.ny * c.nz);
+    const double Cd[3] = {c.C11, c.C12, c.C44};
+    for (int a = 0; a < 3; ++a) {
+      c.fC[a] = (float)Cd[a];
+      c.fCs[a] = (float)(Cd[a] * rN);
+    }
+  }
   for (int a = 0; a < 3; ++a) c.rn[a] = (float)(1.0 / n[a]);
   c.pH = make_plan(H);
   c.pY = make_plan(n[1]);

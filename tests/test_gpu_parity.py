@@ -480,6 +480,55 @@ def test_variants_pinned_by_environment(monkeypatch):
     g.close()
 
 
+_TUNE_SCRIPT = r"""
+import json, sys
+sys.path.insert(0, sys.argv[1])
+from paper_2403_09158_gb300 import okmc as ok
+ok.load()
+g = ok.Grid((sys.argv[2] and int(sys.argv[2]) or 96,) * 3, 0.2855, 243.0, 145.0, 116.0)
+print(json.dumps(g.variants()))
+g.close()
+"""
+
+
+def _tune_run(tmp_path, cache, edge=96):
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, OKMC_TUNE_CACHE=str(cache))
+    env.pop('OKMC_VARIANTS', None)
+    env.pop('OKMC_TUNE', None)
+    r = subprocess.run([sys.executable, '-c', _TUNE_SCRIPT, root, str(edge)], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def test_tuner_picks_persist_across_processes(tmp_path):
+    """The tuner writes its picks per device and grid shape to the JSON cache file; a new
+    process with the same file adopts the recorded picks (a planted valid pick shows that
+    the file, not a new timing, decided); an unreadable file counts as empty."""
+    import json
+    cache = tmp_path / 'sub' / 'tune.json'
+    cur, avail = _tune_run(tmp_path, cache)
+    data = json.loads(cache.read_text())
+    keys = [k for k in data if '|96x96x96|' in k]
+    assert len(keys) == 1 and data[keys[0]] == cur
+    # plant another existing inverse-pass variant and check the next process takes it
+    other = [v for v in range(31) if (avail[2] >> v) & 1 and v != cur[2]]
+    assert other
+    data[keys[0]] = [cur[0], cur[1], other[0]]
+    cache.write_text(json.dumps(data))
+    cur2, _ = _tune_run(tmp_path, cache)
+    assert cur2 == [cur[0], cur[1], other[0]]
+    cache.write_text('{ not json')
+    cur3, _ = _tune_run(tmp_path, cache)
+    assert all((avail[p] >> cur3[p]) & 1 for p in range(3))
+    assert '|96x96x96|' in cache.read_text()
+
+
 # ------------------------------------------------------------------ graphs and batches
 def test_graph_replay_equals_kernel_by_kernel():
     w = config_small()
