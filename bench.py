@@ -533,9 +533,10 @@ def run_config(args, which):
 
 def run_batch(args):
     """Ensemble of 64 independent replicas (edges 64-192, 50-800 defects capped by box
-    volume, 300-600 K) advanced together: one CUDA graph launch per step runs every
-    replica's solve, energies and event.  Compared with the same replicas stepped
-    one after another (FP32) and with the single-replica FP64 path."""
+    volume, 300-600 K) advanced together: one CUDA graph launch per step, in the
+    batched-kernel form (persistent kernels over work lists of every replica) and in
+    the graph-branch form.  Compared with the same replicas stepped one after another
+    (FP32) and with the single-replica FP64 path."""
     import torch
 
     from paper_2403_09158_gb300 import okmc as ok
@@ -553,21 +554,24 @@ def run_batch(args):
     setup_s = time.perf_counter() - t0
     voxels = sum(int(np.prod(w.n)) for w in ws)
     Ts = [w.T_K for w in ws]
-    b = ok.Batch(grids, stream=stream.cuda_stream)
-    b.step(Ts, args.warmup)
-    torch.cuda.synchronize()
-    ev0 = sum(g.stats()['events'] for g in grids)
-    clk = Clocks(torch.cuda.current_device())
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(Ts, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device())
+    forms = {}
+    for form in (ok.BATCH_KERNELS, ok.BATCH_GRAPHS):
+        b = ok.Batch(grids, stream=stream.cuda_stream, mode=form)
+        b.step(Ts, args.warmup)
+        torch.cuda.synchronize()
+        ev0 = sum(g.stats()['events'] for g in grids)
+        e0.record(stream)
+        b.step(Ts, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        forms[form] = (e0.elapsed_time(e1), sum(g.stats()['events'] for g in grids) - ev0, b.mode())
+        b.close()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    events = sum(g.stats()['events'] for g in grids) - ev0
-    b.close()
+    ms, events, used = forms[ok.BATCH_KERNELS]
+    ms_graph = forms[ok.BATCH_GRAPHS][0]
     # the same replicas one after another, each with its own step graph
     for g, T in zip(grids, Ts):
         g.step(T, 1)
@@ -605,11 +609,16 @@ def run_batch(args):
                       'voxels': voxels, 'defects': sum(len(w.defects) for w in ws),
                       'l2': 'inputs larger than L2 (%.1f GB of fields)' % (voxels * 16 / 1e9)},
            'events_per_s': events / (ms / 1e3), 'setup_s': setup_s,
+           'form': 'batched persistent kernels: per edge class one branch of the three solve passes over '
+                   'work lists of (replica, plane / tile) items, then energies, event and field update over every '
+                   'replica; %d launches per step' % (3 * len({w.n for w in ws}) + 3),
+           'graph_branches_fp32': {'ms_per_step': ms_graph / args.steps, 'value': voxels * args.steps / (ms_graph / 1e3),
+                                   'note': 'each replica\'s own step as a branch of one graph (the other batch form)'},
            'sequential_fp32': {'ms_per_step': seq32_ms, 'value': voxels / (seq32_ms / 1e3)},
            'single_replica_fp64': {'ms_per_step_by_edge': fp64_ms, 'ms_per_ensemble_step': seq64_ms,
                                    'value': voxels / (seq64_ms / 1e3)},
            'vs_single_replica_fp64': (voxels / (ms / args.steps / 1e3)) / (voxels / (seq64_ms / 1e3)),
-           'gpu_launches': None, 'clocks': clocks}
+           'gpu_launches': (3 * len({w.n for w in ws}) + 3) * args.steps, 'clocks': clocks}
     print(json.dumps(out))
     return 0
 

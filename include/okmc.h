@@ -271,17 +271,31 @@ int okmc_set_kinetic_state(okmc_grid* g, const okmc_step_stats* s);
 int okmc_set_graphs(okmc_grid* g, int enable);
 
 /* Batches: many independent replicas (handles of any grid size and defect count on
- * the same GPU) advanced together.  okmc_batch_step captures every replica's step as
- * an independent branch of one CUDA graph and launches that graph n_steps times on
- * the batch stream, so the replicas' kernels overlap on the device.  params[n] and
- * stats[n] (nullable) are per replica; t_end must be 0.  The graph is re-captured
- * when a replica's mode or temperature changes or after okmc_set_defects on a
- * replica.  The handles stay owned by the
- * caller and must outlive the batch; their own streams are synchronised before the
- * batch runs.  Results are those of okmc_step on each handle alone. */
+ * the same GPU) advanced together, one CUDA graph launch per step on the batch stream.
+ * Two forms of that graph:
+ *   OKMC_BATCH_KERNELS: one persistent kernel per stage of the step (forward plane
+ *     pass, pencil pass, inverse plane pass, energies and rates, event, field update),
+ *     each walking a device work list of (replica, plane / tile / defect) items of
+ *     every replica, whatever its edge; six launches per step for the whole batch.
+ *     Needs FP32-field replicas with nx = ny and edges in {64, 96, 128, 160, 192, 256}.
+ *   OKMC_BATCH_GRAPHS: every replica's own step as an independent branch of the graph
+ *     (fork/join over private streams), so the replicas' kernels overlap.
+ * OKMC_BATCH_AUTO (the default) takes the kernels when every replica qualifies, else
+ * the branches.  params[n] and stats[n] (nullable) are per replica; t_end must be 0.
+ * The graph is rebuilt when a replica's mode or temperature changes, after
+ * okmc_set_defects on a replica, or after okmc_batch_set_mode.  The handles stay
+ * owned by the caller and must outlive the batch; their own streams are synchronised
+ * before the batch runs.  Results are those of okmc_step on each handle alone, bit for
+ * bit, in either form. */
 typedef struct okmc_batch okmc_batch;
+enum { OKMC_BATCH_AUTO = 0, OKMC_BATCH_KERNELS = 1, OKMC_BATCH_GRAPHS = 2 };
 int okmc_batch_create(okmc_grid* const* grids, int32_t n, void* stream, okmc_batch** out);
 int okmc_batch_step(okmc_batch* b, const okmc_step_params* params, int64_t n_steps, okmc_step_stats* stats);
+/* Chooses the form (OKMC_BATCH_*); OKMC_BATCH_KERNELS on a batch with a replica that
+ * does not qualify makes the next okmc_batch_step fail with OKMC_EINVAL.
+ * okmc_batch_get_mode reports the form the last step used (0 before the first). */
+int okmc_batch_set_mode(okmc_batch* b, int32_t mode);
+int okmc_batch_get_mode(const okmc_batch* b, int32_t* mode);
 int okmc_batch_destroy(okmc_batch* b);
 const char* okmc_batch_last_error(const okmc_batch* b);
 

@@ -702,20 +702,19 @@ struct EAcc<double> {
   __device__ __forceinline__ double value() const { return v; }
 };
 
+// The energies (and rates) of defect i, by one block of kEnergyThreads threads.
 template <class T>
-__global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_energies(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
-                                                             const DefGeo* __restrict__ G, const int* __restrict__ ptr,
-                                                             const int* __restrict__ off, const uint8_t* __restrict__ cnt,
-                                                             const double* __restrict__ alpha, const double* __restrict__ W,
-                                                             double pref, int want_cand, const int* __restrict__ order,
-                                                             double* __restrict__ E, double* __restrict__ Ec, RateArgs ra,
-                                                             DilatedLists dl) {
+__device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
+                                              const DefGeo* __restrict__ G, const int* __restrict__ ptr,
+                                              const int* __restrict__ off, const uint8_t* __restrict__ cnt,
+                                              const double* __restrict__ alpha, const double* __restrict__ W, double pref,
+                                              int want_cand, int i, double* __restrict__ E, double* __restrict__ Ec,
+                                              const RateArgs& ra, const DilatedLists& dl) {
   // per-warp partial sums: FP32 (sum, compensation) pairs for FP32 fields, converted to
   // FP64 only in the epilogue warp (each conversion of a warp costs a whole FP64 issue
   // slot, even with one lane active); FP64 sums for FP64 fields
   __shared__ T part[kEnergyThreads / 32][9];
   __shared__ T partc[kEnergyThreads / 32][9];
-  const int i = order ? order[blockIdx.x] : blockIdx.x;
   const size_t N = (size_t)n.x * n.y * n.z;
   const okmc_defect r = d[i];
   const DefGeo g = G[i];
@@ -872,6 +871,18 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
   }
 }
 
+template <class T>
+__global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_energies(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
+                                                             const DefGeo* __restrict__ G, const int* __restrict__ ptr,
+                                                             const int* __restrict__ off, const uint8_t* __restrict__ cnt,
+                                                             const double* __restrict__ alpha, const double* __restrict__ W,
+                                                             double pref, int want_cand, const int* __restrict__ order,
+                                                             double* __restrict__ E, double* __restrict__ Ec, RateArgs ra,
+                                                             DilatedLists dl) {
+  const int i = order ? order[blockIdx.x] : blockIdx.x;
+  energies_item<T>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, i, E, Ec, ra, dl);
+}
+
 // ---------------------------------------------------------------- events
 __device__ __forceinline__ void new_position(const int p[3], int j, int3 n, int q[3]) {
   const int L[3] = {2 * n.x, 2 * n.y, 2 * n.z};
@@ -889,11 +900,9 @@ __device__ __forceinline__ void new_position(const int p[3], int j, int3 n, int 
 // advance -ln(u2)/R_tot.  One block: per-thread sums over a contiguous chunk of
 // defects, a block scan, then the chunk that holds the target is walked.
 constexpr int kEventThreads = 1024;
-__global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __restrict__ d, int nd,
-                                                             const double* __restrict__ rates,
-                                                             const double* __restrict__ rsum, int3 n, uint32_t key0,
-                                                             uint32_t key1, Move* __restrict__ moves,
-                                                             DevState* __restrict__ st) {
+__device__ __forceinline__ void residence_item(okmc_defect* __restrict__ d, int nd, const double* __restrict__ rates,
+                                               const double* __restrict__ rsum, int3 n, uint32_t key0, uint32_t key1,
+                                               Move* __restrict__ moves, DevState* __restrict__ st) {
   __shared__ double wsum[kEventThreads / 32];
   __shared__ int sel_t, last_t;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
@@ -991,13 +1000,20 @@ __global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __rest
   st->step = step + 1;
 }
 
+__global__ void __launch_bounds__(kEventThreads) k_residence(okmc_defect* __restrict__ d, int nd,
+                                                             const double* __restrict__ rates,
+                                                             const double* __restrict__ rsum, int3 n, uint32_t key0,
+                                                             uint32_t key1, Move* __restrict__ moves,
+                                                             DevState* __restrict__ st) {
+  residence_item(d, nd, rates, rsum, n, key0, key1, moves, st);
+}
+
 // Fixed time step (Algorithm 1): delta t = 1/max nominal nu over mobile defects;
 // defect i fires when its Poisson count is > 0 (u_p > exp(-nu_i delta t)) and then
 // selects a jump on its own biased frequency line with u_s.  One block.
-__global__ void __launch_bounds__(kEventThreads) k_fixed_dt(okmc_defect* __restrict__ d, const DefGeo* __restrict__ G, int nd,
-                                                            const double* __restrict__ rates, double nu0, double kT,
-                                                            int3 n, uint32_t key0, uint32_t key1,
-                                                            Move* __restrict__ moves, DevState* __restrict__ st) {
+__device__ __forceinline__ void fixed_dt_item(okmc_defect* __restrict__ d, const DefGeo* __restrict__ G, int nd,
+                                              const double* __restrict__ rates, double nu0, double kT, int3 n, uint32_t key0,
+                                              uint32_t key1, Move* __restrict__ moves, DevState* __restrict__ st) {
   __shared__ double red[32];
   __shared__ int cnt_s;
   const int t = threadIdx.x;
@@ -1060,6 +1076,75 @@ __global__ void __launch_bounds__(kEventThreads) k_fixed_dt(okmc_defect* __restr
     st->events += cnt_s;
     st->step = step + 1;
   }
+}
+
+__global__ void __launch_bounds__(kEventThreads) k_fixed_dt(okmc_defect* __restrict__ d, const DefGeo* __restrict__ G, int nd,
+                                                            const double* __restrict__ rates, double nu0, double kT,
+                                                            int3 n, uint32_t key0, uint32_t key1,
+                                                            Move* __restrict__ moves, DevState* __restrict__ st) {
+  fixed_dt_item(d, G, nd, rates, nu0, kT, n, key0, key1, moves, st);
+}
+
+// ---------------------------------------------------------------- batched ensemble kernels
+// Persistent over a work list of (replica, k) items with k the position in the replica's
+// energies order: each block takes items blockIdx.x, blockIdx.x + gridDim.x, ...
+__global__ void __launch_bounds__(kEnergyThreads, 4) k_energies_batch(const BatchRep* __restrict__ reps,
+                                                                      const int2* __restrict__ items, int nitems) {
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const int2 w = items[it];
+    const BatchRep& r = reps[w.x];
+    energies_item<float>(r.sig, r.n, r.def, r.geo, r.ptr, r.off, r.cnt, r.alpha, r.W, r.pref, 1, r.order[w.y], r.E, r.Ec,
+                         r.ra, r.dl);
+    __syncthreads();  // the block's shared partial sums are reused by the next item
+  }
+}
+
+// One block per replica: its residence-time event or fixed-time step (Algorithm 1).
+__global__ void __launch_bounds__(kEventThreads) k_event_batch(const BatchRep* __restrict__ reps) {
+  const BatchRep& r = reps[blockIdx.x];
+  if (r.mode == OKMC_RESIDENCE)
+    residence_item(r.def, r.nd, r.ra.rates, r.ra.rsum, r.n, r.key0, r.key1, r.moves, r.state);
+  else
+    fixed_dt_item(r.def, r.geo, r.nd, r.ra.rates, r.nu0, r.kT, r.n, r.key0, r.key1, r.moves, r.state);
+}
+
+// Blocks (replica, slice): slice s of every move of the replica (old stencil out, new in;
+// exact in fixed point, in any order), kMoveSlices slices per replica.
+__global__ void __launch_bounds__(256) k_moves_batch(const BatchRep* __restrict__ reps) {
+  const BatchRep& r = reps[blockIdx.x];
+  const size_t N = (size_t)r.n.x * r.n.y * r.n.z;
+  const int nm = r.state->nmoves;
+  int32_t* eps = const_cast<int32_t*>(r.eps);
+  for (int k = 0; k < nm; ++k) {
+    const Move m = r.moves[k];
+    scatter_stencil<int32_t>(eps, r.n, N, r.geo[m.i], r.ptr, r.off, r.cnt, r.alpha, m.i, m.old_pos, -1, r.rq, r.lim, r.err,
+                             r.cfg.dirty, blockIdx.y, gridDim.y);
+    scatter_stencil<int32_t>(eps, r.n, N, r.geo[m.i], r.ptr, r.off, r.cnt, r.alpha, m.i, m.new_pos, +1, r.rq, r.lim, r.err,
+                             r.cfg.dirty, blockIdx.y, gridDim.y);
+  }
+}
+
+cudaError_t launch_energies_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  k_energies_batch<<<grid, kEnergyThreads, 0, st>>>(reps, items, nitems);
+  return cudaGetLastError();
+}
+cudaError_t launch_event_batch(const BatchRep* reps, int nrep, cudaStream_t st) {
+  k_event_batch<<<nrep, kEventThreads, 0, st>>>(reps);
+  return cudaGetLastError();
+}
+cudaError_t launch_moves_batch(const BatchRep* reps, int nrep, cudaStream_t st) {
+  k_moves_batch<<<dim3(nrep, kMoveSlices), 256, 0, st>>>(reps);
+  return cudaGetLastError();
+}
+int energies_batch_grid() {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_energies_batch, kEnergyThreads, 0) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return 152 * 4;
+  }
+  return sms * (per > 0 ? per : 1);
 }
 
 // ---------------------------------------------------------------- launchers

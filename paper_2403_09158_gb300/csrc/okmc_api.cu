@@ -60,6 +60,17 @@ template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
                             int want_cand, const int* order, double* E, double* Ec, RateArgs ra, const DilatedLists& dl, cudaStream_t st);
+// batched ensemble kernels (solve_fast.cu, defects.cu)
+bool batch_edge_supported(int nx, int ny, int nz);
+int pass_batch_grid(int pass, int n, int nitems);
+cudaError_t launch_pass_batch(int pass, int n, const BatchRep* reps, const int2* items, int nitems, int grid, int slot0,
+                              cudaStream_t st);
+cudaError_t upload_batch_cfg(int slot0, const PassCfg* cfgs, int n, cudaStream_t st);
+int batch_cfg_slots();
+cudaError_t launch_energies_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st);
+cudaError_t launch_event_batch(const BatchRep* reps, int nrep, cudaStream_t st);
+cudaError_t launch_moves_batch(const BatchRep* reps, int nrep, cudaStream_t st);
+int energies_batch_grid();
 cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
                              Move* moves, DevState* stt, cudaStream_t st);
 cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const double* rates, double nu0, double kT, int3 n,
@@ -263,7 +274,40 @@ struct okmc_batch {
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> ev;
   std::string err;
+  int mode = OKMC_BATCH_AUTO;  // requested form
+  int used = 0;                // form of the current graph
+  // batched kernels: replica records and work lists (planes, tiles, defects) on the device
+  BatchRep* d_reps = nullptr;
+  int2* d_items = nullptr;
+  int slot0 = -1, nslots = 0;  // constant-memory slots of the replicas' pass configurations
 };
+
+// Constant-memory slots for the pass configurations of batched replicas, handed out to
+// batches as contiguous ranges (first fit) and returned when a batch is rebuilt or destroyed.
+std::mutex g_slot_mu;
+std::vector<char> g_slot_used;
+
+static int acquire_slots(int n) {
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  if ((int)g_slot_used.size() != batch_cfg_slots()) g_slot_used.assign(batch_cfg_slots(), 0);
+  for (int s0 = 0; s0 + n <= (int)g_slot_used.size(); ++s0) {
+    bool free_run = true;
+    for (int k = 0; k < n && free_run; ++k) free_run = !g_slot_used[s0 + k];
+    if (free_run) {
+      for (int k = 0; k < n; ++k) g_slot_used[s0 + k] = 1;
+      return s0;
+    }
+  }
+  return -1;
+}
+
+static void release_slots(okmc_batch* b) {
+  if (b->slot0 < 0) return;
+  std::lock_guard<std::mutex> lk(g_slot_mu);
+  for (int k = 0; k < b->nslots; ++k) g_slot_used[b->slot0 + k] = 0;
+  b->slot0 = -1;
+  b->nslots = 0;
+}
 
 namespace {
 
@@ -1758,11 +1802,194 @@ int okmc_batch_destroy(okmc_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   for (auto s : b->side) cudaStreamDestroy(s);
   for (auto e : b->ev) cudaEventDestroy(e);
+  if (b->d_reps || b->d_items) {
+    std::lock_guard<std::recursive_mutex> lk(g_capture_mu);
+    cudaFree(b->d_reps);
+    cudaFree(b->d_items);
+  }
+  release_slots(b);
   delete b;
   return OKMC_OK;
 }
 
+int okmc_batch_set_mode(okmc_batch* b, int32_t mode) {
+  if (!b || (mode != OKMC_BATCH_AUTO && mode != OKMC_BATCH_KERNELS && mode != OKMC_BATCH_GRAPHS)) return OKMC_EINVAL;
+  if (mode != b->mode) {
+    b->mode = mode;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  return OKMC_OK;
+}
+
+int okmc_batch_get_mode(const okmc_batch* b, int32_t* mode) {
+  if (!b || !mode) return OKMC_EINVAL;
+  *mode = b->used;
+  return OKMC_OK;
+}
+
 const char* okmc_batch_last_error(const okmc_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+static bool batch_kernels_ok(const okmc_batch* b) {
+  for (const okmc_grid* g : b->grids)
+    if (fp64(g) || !g->fast || !batch_edge_supported(g->n[0], g->n[1], g->n[2]) || !g->d_order) return false;
+  return true;
+}
+
+// The batched-kernel form: one record per replica and work lists uploaded once; the
+// graph of a step holds, for each solve pass and edge class, one persistent launch over the
+// planes (tiles) of every replica of that edge, then over every replica the energies and
+// rates, the event and the field update (one persistent or one-block-per-replica launch
+// each).
+static int batch_build_kernels(okmc_batch* b) {
+  const int n = (int)b->grids.size();
+  std::vector<BatchRep> reps(n);
+  for (int i = 0; i < n; ++i) {
+    okmc_grid* g = b->grids[i];
+    const okmc_step_params& p = b->params[i];
+    BatchRep& r = reps[i];
+    r.cfg = g->cfg;
+    r.cfg.q = quantum(g);
+    r.cfg.ncomp = 6;
+    r.cfg.forward_only = 0;
+    r.cfg.dirty = g->d_dirty;
+    r.eps = (const int32_t*)g->eps;
+    r.spec = (C2<float>*)g->spec;
+    r.spec2 = (C2<float>*)g->spec2;
+    r.sig = (float*)g->sig;
+    r.def = g->d_def;
+    r.geo = g->d_geo;
+    r.ptr = g->d_ptr;
+    r.off = g->d_off;
+    r.cnt = g->d_cnt;
+    r.alpha = g->d_alpha;
+    r.W = g->d_W;
+    r.order = g->d_order;
+    r.E = g->d_E;
+    r.Ec = g->d_Ec;
+    const double kT = kBoltzmann * p.T_K;
+    r.ra.rates = g->d_rates;
+    r.ra.rsum = g->d_rsum;
+    r.ra.negb = &g->d_state->negative_barriers;
+    r.ra.nu0 = g->nu0;
+    r.ra.kT = kT;
+    r.ra.rkT = 1.0 / kT;
+    if (g->d_dl) r.dl = DilatedLists{g->d_dl, g->d_dl + 2 * g->nd, g->d_doff, g->d_dcnt, g->d_dscnt};
+    r.pref = -kKappa * g->h * g->h * g->h;
+    r.nu0 = g->nu0;
+    r.kT = kT;
+    r.moves = g->d_moves;
+    r.state = g->d_state;
+    r.err = g->d_err;
+    r.rq = 1.0 / quantum(g);
+    r.lim = qlimit(g);
+    r.key0 = (uint32_t)g->desc.seed;
+    r.key1 = (uint32_t)(g->desc.seed >> 32);
+    r.n = dims(g);
+    r.nd = g->nd;
+    r.mode = p.mode;
+  }
+  // work lists: per edge class (ny, nz) its planes and its tiles, then every replica's defects
+  struct Cls {
+    int ny, nz;
+    int plane0, nplane, tile0, ntile;
+  };
+  std::map<std::pair<int, int>, std::vector<int>> by_edge;
+  for (int i = 0; i < n; ++i) by_edge[{b->grids[i]->n[1], b->grids[i]->n[2]}].push_back(i);
+  std::vector<int2> items;
+  std::vector<Cls> cls;
+  for (const auto& kv : by_edge) {
+    Cls c{kv.first.first, kv.first.second, (int)items.size(), 0, 0, 0};
+    for (int i : kv.second)
+      for (int k = 0; k < 6 * b->grids[i]->n[2]; ++k) items.push_back(make_int2(i, k));
+    c.nplane = (int)items.size() - c.plane0;
+    c.tile0 = (int)items.size();
+    for (int i : kv.second)
+      for (int k = 0; k < (int)(b->grids[i]->P / 8); ++k) items.push_back(make_int2(i, k));
+    c.ntile = (int)items.size() - c.tile0;
+    cls.push_back(c);
+  }
+  const int e0 = (int)items.size();
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < b->grids[i]->nd; ++k) items.push_back(make_int2(i, k));
+  const int ne = (int)items.size() - e0;
+  cudaFree(b->d_reps);
+  cudaFree(b->d_items);
+  b->d_reps = nullptr;
+  b->d_items = nullptr;
+  release_slots(b);
+  b->slot0 = acquire_slots(n);
+  if (b->slot0 < 0) {
+    b->err = "batched kernels: more replicas in batches at once than the " + std::to_string(batch_cfg_slots()) +
+             " configuration slots";
+    return OKMC_ENOMEM;
+  }
+  b->nslots = n;
+  std::vector<PassCfg> cfgs(n);
+  for (int i = 0; i < n; ++i) cfgs[i] = reps[i].cfg;
+  cudaError_t e = upload_batch_cfg(b->slot0, cfgs.data(), n, b->side[n]);
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_reps, n * sizeof(BatchRep));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_items, items.size() * sizeof(int2));
+  if (e == cudaSuccess) e = cudaMemcpyAsync(b->d_reps, reps.data(), n * sizeof(BatchRep), cudaMemcpyHostToDevice, b->side[n]);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, b->side[n]);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->side[n]);
+  if (e != cudaSuccess) {
+    b->err = std::string("batch work lists: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? OKMC_ENOMEM : OKMC_ECUDA;
+  }
+  // persistent grids (and kernel attributes) before the capture: each launch gets every
+  // CTA (cluster) that fits on the device at once; the classes run one after another (a
+  // plane of a large edge costs many times one of a small edge, so splitting the device
+  // between concurrent classes by item count leaves it idle behind the largest class)
+  std::vector<std::array<int, 3>> grids(cls.size());
+  for (size_t k = 0; k < cls.size(); ++k) {
+    const Cls& c = cls[k];
+    for (int pass = 0; pass < 3; ++pass) {
+      grids[k][pass] = pass_batch_grid(pass, pass == 1 ? c.nz : c.ny, pass == 1 ? c.ntile : c.nplane);
+      if (grids[k][pass] <= 0) {
+        b->err = "batched kernels: no resident grid";
+        return OKMC_ECUDA;
+      }
+    }
+  }
+  const int egrid = std::min(std::max(ne, 1), energies_batch_grid());
+  while ((int)b->side.size() < n + 1 + (int)cls.size()) {
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return OKMC_ECUDA;
+    b->side.push_back(st);
+  }
+  while ((int)b->ev.size() < 2 * n + 1 + (int)cls.size()) {
+    cudaEvent_t ev;
+    if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return OKMC_ECUDA;
+    b->ev.push_back(ev);
+  }
+  cudaStream_t root = b->side[n];
+  cudaGraph_t graph = nullptr;
+  if (cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return OKMC_ECUDA;
+  const int2* it = b->d_items;
+  e = cudaSuccess;
+  for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass)
+    for (size_t k = 0; k < cls.size() && e == cudaSuccess; ++k) {
+      const Cls& c = cls[k];
+      e = pass == 1 ? launch_pass_batch(1, c.nz, b->d_reps, it + c.tile0, c.ntile, grids[k][1], b->slot0, root)
+                    : launch_pass_batch(pass, c.ny, b->d_reps, it + c.plane0, c.nplane, grids[k][pass], b->slot0, root);
+    }
+  if (e == cudaSuccess) e = launch_energies_batch(b->d_reps, it + e0, ne, egrid, root);
+  if (e == cudaSuccess) e = launch_event_batch(b->d_reps, n, root);
+  if (e == cudaSuccess) e = launch_moves_batch(b->d_reps, n, root);
+  cudaError_t e2 = cudaStreamEndCapture(root, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    b->err = std::string("batched kernels capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2);
+    return OKMC_ECUDA;
+  }
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return OKMC_ECUDA;
+  b->used = OKMC_BATCH_KERNELS;
+  return OKMC_OK;
+}
 
 // One graph holds every replica's step as an independent branch (fork/join on
 // private streams); each launch advances all replicas by one step, and their
@@ -1774,6 +2001,11 @@ static int batch_build(okmc_batch* b) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
+  const bool kern_ok = batch_kernels_ok(b);
+  if (b->mode == OKMC_BATCH_KERNELS && !kern_ok) {
+    b->err = "batched kernels need FP32-field replicas with nx = ny and edges in {64, 96, 128, 160, 192, 256}";
+    return OKMC_EINVAL;
+  }
   while ((int)b->side.size() < n + 1) {
     cudaStream_t s;
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return OKMC_ECUDA;
@@ -1784,6 +2016,7 @@ static int batch_build(okmc_batch* b) {
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return OKMC_ECUDA;
     b->ev.push_back(e);
   }
+  if (b->mode != OKMC_BATCH_GRAPHS && kern_ok) return batch_build_kernels(b);
   cudaStream_t root = b->side[n];
   cudaGraph_t graph = nullptr;
   if (cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return OKMC_ECUDA;
@@ -1815,6 +2048,7 @@ static int batch_build(okmc_batch* b) {
   if (e != cudaSuccess) return OKMC_ECUDA;
   e = cudaGraphInstantiate(&b->exec, graph, 0);
   cudaGraphDestroy(graph);
+  if (e == cudaSuccess) b->used = OKMC_BATCH_GRAPHS;
   return e == cudaSuccess ? OKMC_OK : OKMC_ECUDA;
 }
 

@@ -380,6 +380,40 @@ struct QTypes {
   int nt;
 };
 
+// One replica of a batched ensemble as the batched kernels see it (an array of these
+// lives in device memory): the pass configuration and buffers of its FP32 register-FFT
+// solve, and the defect-side arrays of its step.  Work lists pair a replica index with
+// a plane, a pencil tile or a defect (in the energies kernel's order).
+struct BatchRep {
+  PassCfg cfg;                // dirty flags set (the forward pass skips clean planes)
+  const int32_t* eps;         // fixed-point eigenstrain
+  C2<float>* spec;            // plane transforms of the eigenstrain (kept between solves)
+  C2<float>* spec2;           // Green operator output
+  float* sig;                 // stress
+  okmc_defect* def;
+  const DefGeo* geo;
+  const int* ptr;
+  const int* off;
+  const uint8_t* cnt;
+  const double* alpha;
+  const double* W;
+  const int* order;           // energies: defects largest stencil first
+  double* E;
+  double* Ec;
+  RateArgs ra;
+  DilatedLists dl;
+  double pref;                // -kappa h^3
+  double nu0, kT;
+  Move* moves;
+  DevState* state;
+  int* err;
+  double rq, lim;             // fixed-point scale and limit of the eigenstrain
+  uint32_t key0, key1;        // Philox key (the grid's seed)
+  int3 n;
+  int nd;
+  int mode;                   // OKMC_RESIDENCE or OKMC_FIXED_DT
+};
+
 __host__ __device__ __forceinline__ int pack_off(int dx, int dy, int dz) {
   return (dx + 512) | ((dy + 512) << 10) | ((dz + 512) << 20);
 }

@@ -151,12 +151,14 @@ __device__ __forceinline__ void put_col(cg::cluster_group& cluster, C2<float>* c
   base[(k % CPER) * LDC + y] = v;
 }
 
+// One (component, z) plane of the forward pass, by the CS CTAs of a cluster (cluster
+// rank h); smem_raw: nfwd_smem<H, NY>(CS) bytes of dynamic shared memory.  A clean plane
+// (dirty flag 0) returns at once in every CTA of the cluster alike.
 template <int H, int NY, int CS>
-__global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restrict__ eps, C2<float>* __restrict__ spec,
-                                                        PassCfg c) {
+__device__ __forceinline__ void plane_fwd_item(const int32_t* __restrict__ eps, C2<float>* __restrict__ spec,
+                                               const PassCfg& c, int plane, unsigned char* smem_raw) {
   using S = NShape<H, NY>;
   constexpr int CPER = H / CS, ROWS = NY / CS;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<float>* twH = reinterpret_cast<C2<float>*>(smem_raw);
   C2<float>* twY = twH + tw2_size<H>();
   C2<float>* untw = twY + tw2_size<NY>();
@@ -164,8 +166,7 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
   C2<float>* col = reinterpret_cast<C2<float>*>(after_tw);  // [CPER][LDC]
   C2<float>* xb = col + CPER * S::LDC;                            // [GR][XS]
   cg::cluster_group cluster = cg::this_cluster();
-  const int h = CS > 1 ? (int)cluster.block_rank() : 0;
-  const int plane = blockIdx.y;
+  const int h = CS > 1 ? (int)cluster.block_rank() % CS : 0;
   // a plane whose eigenstrain has not changed keeps its transform from the last pass
   // (every CTA of the cluster reads the same flag, so the whole cluster leaves)
   if (c.dirty && c.dirty[plane] == 0) return;
@@ -257,6 +258,13 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
   }
 }
 
+template <int H, int NY, int CS>
+__global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restrict__ eps, C2<float>* __restrict__ spec,
+                                                        PassCfg c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  plane_fwd_item<H, NY, CS>(eps, spec, c, blockIdx.y, smem_raw);
+}
+
 // pf > 0: first bring into L2 this CTA's columns of plane + pf, the plane whose
 // cluster will most likely take this one's place one wave later (pf = clusters
 // resident at once), so that the next wave's loads hit L2 while this wave transforms.
@@ -269,14 +277,16 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restric
 // carries two adjacent kx in one 16-byte store; the row phase then pairs the line
 // groups of a half-warp on rows 4 apart (with lines of 8 threads; rows 8 apart would
 // fall on the same banks at this pitch).
+// One plane of the inverse pass by the CS CTAs of a cluster; nplanes bounds the L2
+// prefetch of plane + pf (pf = 0: none).
 template <int H, int NY, int CS, int WIDE>
-__global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restrict__ spec, float* __restrict__ sig,
-                                                        PassCfg c, int pf) {
+__device__ __forceinline__ void plane_inv_item(const C2<float>* __restrict__ spec, float* __restrict__ sig,
+                                               const PassCfg& c, int plane, int pf, int nplanes,
+                                               unsigned char* smem_raw) {
   using S = NShape<H, NY>;
   constexpr int CPER = H / CS, ROWS = NY / CS;
   constexpr int LDR = WIDE == 2 ? H + 2 : S::LDR;
   static_assert(WIDE != 2 || S::NTH == 8, "the 16-byte copy-out pairs rows for lines of 8 threads");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<float>* twH = reinterpret_cast<C2<float>*>(smem_raw);
   C2<float>* twY = twH + tw2_size<H>();
   C2<float>* untw = twY + tw2_size<NY>();
@@ -284,12 +294,11 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
   C2<float>* rowb = reinterpret_cast<C2<float>*>(after_tw);  // [ROWS][LDR]
   C2<float>* xb = rowb + ROWS * LDR;
   cg::cluster_group cluster = cg::this_cluster();
-  const int h = CS > 1 ? (int)cluster.block_rank() : 0;
-  const int plane = blockIdx.y;
+  const int h = CS > 1 ? (int)cluster.block_rank() % CS : 0;
   const int tid = threadIdx.x;
   const size_t P = (size_t)(H + 1) * NY;
   if (CS > 1) cluster_arrive();
-  if (pf > 0 && plane + pf < (int)gridDim.y) {
+  if (pf > 0 && plane + pf < nplanes) {
     const char* nx = reinterpret_cast<const char*>(spec + (size_t)(plane + pf) * P + (size_t)h * CPER * NY);
     for (int i = tid; i < CPER * NY * 8 / 128; i += kNT) prefetch_l2(nx + (size_t)i * 128);
     if (h == 0) {
@@ -390,6 +399,13 @@ __global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restr
       reg_fft<true, H>(ld, XSkew<S::R2H>{R, 1}, st, twH, t, act);
     }
   }
+}
+
+template <int H, int NY, int CS, int WIDE>
+__global__ void __launch_bounds__(kNT, 2) k_plane_inv_n(const C2<float>* __restrict__ spec, float* __restrict__ sig,
+                                                        PassCfg c, int pf) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  plane_inv_item<H, NY, CS, WIDE>(spec, sig, c, blockIdx.y, pf, gridDim.y, smem_raw);
 }
 
 // Staged variant of the inverse plane pass: the CTA's CPER columns are one contiguous
@@ -525,14 +541,15 @@ __device__ __forceinline__ int tile_row(int r) { return (r & ~15) + ((r & 1) << 
 // are paired so that each half-warp holds 8 threads of each of two adjacent lines.  The
 // two layouts give the same arithmetic.  (8-byte copies allocate in L1, which two CTAs'
 // shared memory leave small, and so limit the loads in flight on the SM.)
+// One tile (8 consecutive ky at one kx, every kz, six components) of the pencil pass.
 template <int NZ, bool SWZ>
-__global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<float>* out, PassCfg c) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+__device__ __forceinline__ void pencil_item(const C2<float>* in, C2<float>* out, const PassCfg& c, int tile_index,
+                                            unsigned char* smem_raw) {
   C2<float>* twZ = reinterpret_cast<C2<float>*>(smem_raw);
   C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw + (sizeof(C2<float>) * tw2_size<NZ>() + 15) / 16 * 16);  // [comp * NZ + kz][8 or 9]
   const int tid = threadIdx.x;
   const size_t P = (size_t)(c.H + 1) * c.ny;
-  const size_t p0 = (size_t)blockIdx.x * kTW;
+  const size_t p0 = (size_t)tile_index * kTW;
   const int kx = (int)(p0 / c.ny), ky0 = (int)(p0 % c.ny);
   if constexpr (SWZ) {
     for (int idx = tid; idx < 6 * NZ * 4; idx += kT) {  // four 16-byte pieces per row
@@ -594,6 +611,12 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<f
     const int t8 = idx & (kTW - 1), row = row_of(idx >> 3);
     out[(size_t)row * P + p0 + t8] = tile[tile_at<SWZ>(row, t8)];
   }
+}
+
+template <int NZ, bool SWZ>
+__global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<float>* out, PassCfg c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pencil_item<NZ, SWZ>(in, out, c, blockIdx.x, smem_raw);
 }
 
 // ---------------------------------------------------------------- dispatch
@@ -687,11 +710,11 @@ cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg&
 
 // smallest cluster whose CTAs fit two per SM
 template <int H, int NY>
-constexpr bool ncs_fits(int cs) {
+__host__ __device__ constexpr bool ncs_fits(int cs) {
   return H % cs == 0 && NY % cs == 0 && nfwd_smem<H, NY>(cs) <= 112 * 1024 && ninv_smem<H, NY>(cs) <= 112 * 1024;
 }
 template <int H, int NY>
-constexpr int ncs() {
+__host__ __device__ constexpr int ncs() {
   return ncs_fits<H, NY>(1) ? 1 : ncs_fits<H, NY>(2) ? 2 : ncs_fits<H, NY>(4) ? 4 : 8;
 }
 
@@ -754,6 +777,109 @@ int pencil_variants() {
   return 3;
 }
 }  // namespace
+
+// ---------------------------------------------------------------- batched ensemble passes
+// Kernels over work lists of (replica, plane) or (replica, tile) items for an ensemble of
+// replicas of uneven edges, one kernel per pass and edge class, with the same bodies,
+// cluster sizes and results as the single-grid kernels.  Edges 64, 96, 128, 160, 192 and
+// 256 (nx = ny); other grids batch through graphs.
+#define OKMC_BATCH_EDGES(X) X(64, 32) X(96, 48) X(128, 64) X(160, 80) X(192, 96) X(256, 128)
+
+template <int H, int NY>
+__host__ __device__ constexpr int batch_inv_wide() {
+  return NShape<H, NY>::NTH == 8 && ninv_smem<H, NY>(ncs<H, NY>(), 2) <= kTwoPerSM ? 2 : 0;
+}
+
+// The pass configurations of batched replicas live in constant memory (slots handed out
+// to batches by the host), where the pass bodies read them as they read a kernel
+// parameter: immutable, so the compiler keeps or re-reads fields freely, whereas a
+// configuration in global memory must be re-read after every store the body makes.
+constexpr int kBatchSlots = 128;
+__constant__ PassCfg g_batch_cfg[kBatchSlots];
+
+cudaError_t upload_batch_cfg(int slot0, const PassCfg* cfgs, int n, cudaStream_t st) {
+  if (slot0 < 0 || n < 0 || slot0 + n > kBatchSlots) return cudaErrorInvalidValue;
+  return cudaMemcpyToSymbolAsync(g_batch_cfg, cfgs, n * sizeof(PassCfg), slot0 * sizeof(PassCfg), cudaMemcpyHostToDevice,
+                                 st);
+}
+int batch_cfg_slots() { return kBatchSlots; }
+
+// One work-list kernel per pass and edge class: cluster (plane passes, the edge's own
+// cluster size) or CTA (pencil) k runs item k of the list, a plane or tile of any replica
+// of that edge.  One item per CTA keeps the bodies at the register count of the
+// single-grid kernels (a persistent loop's state pushed them into spills).
+template <int H, int NY>
+__global__ void __launch_bounds__(kNT, 2) k_fwd_batch(const BatchRep* __restrict__ reps, const int2* __restrict__ items,
+                                                      int slot0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 w = items[blockIdx.x / ncs<H, NY>()];
+  plane_fwd_item<H, NY, ncs<H, NY>()>(reps[w.x].eps, reps[w.x].spec, g_batch_cfg[slot0 + w.x], w.y, smem_raw);
+}
+
+template <int NZ>
+__global__ void __launch_bounds__(kT, 2) k_pencil_batch(const BatchRep* __restrict__ reps, const int2* __restrict__ items,
+                                                        int slot0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 w = items[blockIdx.x];
+  pencil_item<NZ, true>(reps[w.x].spec, reps[w.x].spec2, g_batch_cfg[slot0 + w.x], w.y, smem_raw);
+}
+
+template <int H, int NY>
+__global__ void __launch_bounds__(kNT, 2) k_inv_batch(const BatchRep* __restrict__ reps, const int2* __restrict__ items,
+                                                      int slot0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int2 w = items[blockIdx.x / ncs<H, NY>()];
+  plane_inv_item<H, NY, ncs<H, NY>(), batch_inv_wide<H, NY>()>(reps[w.x].spec2, reps[w.x].sig, g_batch_cfg[slot0 + w.x],
+                                                                w.y, 0, 0, smem_raw);
+}
+
+bool batch_edge_supported(int nx, int ny, int nz) {
+  auto ok = [](int n) { return n == 64 || n == 96 || n == 128 || n == 160 || n == 192 || n == 256; };
+  return nx == ny && ok(ny) && ok(nz);
+}
+
+// dynamic shared memory of each batched pass for a replica of edge ny (plane passes) / nz
+size_t batch_smem(int pass, int n) {
+  switch (n) {
+#define OKMC_CASE(e, h)                                                          \
+  case e:                                                                      \
+    return pass == 0 ? nfwd_smem<h, e>(ncs<h, e>())                            \
+                     : pass == 1 ? pencil_fast_smem<e, true>()                 \
+                                 : ninv_smem<h, e>(ncs<h, e>(), batch_inv_wide<h, e>());
+    OKMC_BATCH_EDGES(OKMC_CASE)
+#undef OKMC_CASE
+    default: return 0;
+  }
+}
+
+// Grid of a batched pass (0 forward plane, 1 pencil, 2 inverse plane) over nitems items for
+// replicas of edge n (one cluster, or CTA, per item); 0 for an edge without batched kernels.
+int pass_batch_grid(int pass, int n, int nitems) {
+  switch (n) {
+#define OKMC_CASE(e, h) \
+  case e: return pass == 1 ? nitems : nitems * ncs<h, e>();
+    OKMC_BATCH_EDGES(OKMC_CASE)
+#undef OKMC_CASE
+    default: return 0;
+  }
+}
+
+// Launch batched pass `pass` for the replicas of edge n over their work list.
+cudaError_t launch_pass_batch(int pass, int n, const BatchRep* reps, const int2* items, int nitems, int grid, int slot0,
+                              cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  switch (n) {
+#define OKMC_CASE(e, h)                                                                                            \
+  case e:                                                                                                        \
+    if (pass == 0)                                                                                               \
+      return launch_k(k_fwd_batch<h, e>, dim3(grid), batch_smem(0, e), ncs<h, e>(), st, reps, items, slot0);    \
+    if (pass == 1) return launch_k(k_pencil_batch<e>, dim3(grid), batch_smem(1, e), 1, st, reps, items, slot0); \
+    return launch_k(k_inv_batch<h, e>, dim3(grid), batch_smem(2, e), ncs<h, e>(), st, reps, items, slot0);
+    OKMC_BATCH_EDGES(OKMC_CASE)
+#undef OKMC_CASE
+    default: return cudaErrorInvalidConfiguration;
+  }
+}
 
 // The fast path covers nx = ny in {32, 48, 64, 96, 128, 160, 192, 256, 320} and nz
 // in the same set.

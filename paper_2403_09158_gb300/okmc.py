@@ -22,6 +22,7 @@ IMMOBILE, ONE_D, THREE_D = 0, 1, 2
 MEAN_STRESS_ZERO, MEAN_STRAIN_ZERO = 0, 1
 FP32_FIELDS, FP64_FIELDS = 0, 1
 RESIDENCE, FIXED_DT = 0, 1
+BATCH_AUTO, BATCH_KERNELS, BATCH_GRAPHS = 0, 1, 2
 
 EXPORTED = [
     'okmc_grid_create', 'okmc_grid_destroy', 'okmc_last_error', 'okmc_set_stream', 'okmc_set_defects',
@@ -30,7 +31,8 @@ EXPORTED = [
     'okmc_dipole_self_terms', 'okmc_get_stencil', 'okmc_step',
     'okmc_get_stats', 'okmc_device_bytes', 'okmc_set_profiling', 'okmc_kernel_times', 'okmc_reset_kernel_times',
     'okmc_launch_shape', 'okmc_solve_stress_static', 'okmc_set_graphs', 'okmc_batch_create', 'okmc_batch_step',
-    'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_get_variants', 'okmc_set_variant',
+    'okmc_batch_destroy', 'okmc_batch_last_error', 'okmc_batch_set_mode', 'okmc_batch_get_mode', 'okmc_get_variants',
+    'okmc_set_variant',
     'okmc_set_kinetic_state', 'okmc_estimate_field_bytes', 'okmc_server_create', 'okmc_server_add_replica',
     'okmc_server_submit', 'okmc_server_wait', 'okmc_server_get_stats', 'okmc_server_last_error', 'okmc_server_destroy',
     'okmc_isotropic_stiffness', 'okmc_set_dislocations', 'okmc_point_dipole_energies', 'okmc_shift_energies',
@@ -129,6 +131,8 @@ def load(path=LIB_PATH):
         'okmc_batch_step': (C.c_int, [vp, C.POINTER(StepParams), i64, C.POINTER(StepStats)]),
         'okmc_batch_destroy': (C.c_int, [vp]),
         'okmc_batch_last_error': (C.c_char_p, [vp]),
+        'okmc_batch_set_mode': (C.c_int, [vp, i32]),
+        'okmc_batch_get_mode': (C.c_int, [vp, C.POINTER(i32)]),
         'okmc_get_variants': (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32)]),
         'okmc_set_kinetic_state': (C.c_int, [vp, C.POINTER(StepStats)]),
         'okmc_estimate_field_bytes': (C.c_size_t, [C.POINTER(GridDesc)]),
@@ -371,7 +375,7 @@ class Grid:
 class Batch:
     """Replicas advanced together by one CUDA graph launch per step (okmc_batch_*)."""
 
-    def __init__(self, grids, stream=None):
+    def __init__(self, grids, stream=None, mode=BATCH_AUTO):
         self.lib = load()
         self.grids = list(grids)
         arr = (C.c_void_p * len(self.grids))(*[g.h.value for g in self.grids])
@@ -380,6 +384,15 @@ class Batch:
         if rc != OKMC_OK:
             raise OkmcError(rc, 'okmc_batch_create failed')
         self.h = h
+        rc = self.lib.okmc_batch_set_mode(self.h, mode)
+        if rc != OKMC_OK:
+            raise OkmcError(rc, 'okmc_batch_set_mode failed')
+
+    def mode(self):
+        """The form the last step used (BATCH_KERNELS or BATCH_GRAPHS; 0 before the first)."""
+        m = C.c_int32()
+        self.lib.okmc_batch_get_mode(self.h, C.byref(m))
+        return m.value
 
     def step(self, T_K, n_steps=1, mode=RESIDENCE):
         n = len(self.grids)

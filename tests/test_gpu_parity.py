@@ -575,6 +575,63 @@ def test_batch_replicas_equal_alone():
         g.close()
 
 
+@pytest.mark.parametrize('mode', [ok.BATCH_KERNELS, ok.BATCH_GRAPHS])
+def test_batched_kernels_equal_alone(mode):
+    """An ensemble of replicas of uneven edges (64, 96, 128, 160, 192; one in fixed-time-step
+    mode) advanced by the batched persistent kernels (one per stage and edge class over
+    work lists) or by per-replica graph branches gives each replica its solo trajectory
+    bit for bit."""
+    small = dict(r111=(0.4, 1.2), r100=(0.4, 1.2))
+    edges = [64, 96, 128, 64, 160, 192]
+    cases = [scaled_population((e, e, e), 10 + 4 * k, seed=20 + k, **small) for k, e in enumerate(edges)]
+    Ts = [300.0 + 50.0 * k for k in range(len(cases))]
+    modes = [ok.RESIDENCE] * len(cases)
+    modes[3] = ok.FIXED_DT
+    alone = []
+    for w, T, m in zip(cases, Ts, modes):
+        g = ok.Grid(w.n, w.voxel_nm, *w.C, seed=91)
+        g.set_defects(w.defects)
+        st = g.step(T, 9, mode=m)
+        Ec, _ = g.candidate_energies()
+        alone.append((g.get_positions(), st, g.interaction_energies().copy(), Ec.copy()))
+        g.close()
+    grids = []
+    for w in cases:
+        g = ok.Grid(w.n, w.voxel_nm, *w.C, seed=91)
+        g.set_defects(w.defects)
+        grids.append(g)
+    batch = ok.Batch(grids, mode=mode)
+    batch.step(Ts, 4, mode=modes)
+    assert batch.mode() == mode
+    stats = batch.step(Ts, 5, mode=modes)
+    for (pos, st, E, Ec), g, s in zip(alone, grids, stats):
+        assert np.array_equal(g.get_positions(), pos)
+        assert s['clock'] == st['clock'] and s['events'] == st['events'] and s['steps'] == st['steps']
+        assert np.array_equal(g.interaction_energies(), E)
+        assert np.array_equal(g.candidate_energies()[0], Ec)
+    batch.close()
+    for g in grids:
+        g.close()
+
+
+def test_batched_kernels_refuse_unsupported_edges():
+    """BATCH_KERNELS with a replica outside the supported edges fails with EINVAL; AUTO
+    falls back to graph branches."""
+    w = scaled_population((48, 48, 48), 6, seed=5, r111=(0.4, 1.0), r100=(0.4, 1.0))
+    g = ok.Grid(w.n, w.voxel_nm, *w.C, seed=3)
+    g.set_defects(w.defects)
+    b = ok.Batch([g], mode=ok.BATCH_KERNELS)
+    with pytest.raises(ok.OkmcError) as e:
+        b.step([400.0], 1)
+    assert e.value.code == ok.OKMC_EINVAL
+    b.close()
+    b = ok.Batch([g])
+    b.step([400.0], 1)
+    assert b.mode() == ok.BATCH_GRAPHS
+    b.close()
+    g.close()
+
+
 # ------------------------------------------------------------------ dislocation lines (field dislocation mechanics)
 def _dislocation_case(n, h):
     """A clockwise 1/2[111] loop (off-grid centre, 48 vertices) and one period of a
