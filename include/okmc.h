@@ -331,12 +331,21 @@ int okmc_launch_shape(const okmc_grid* g, int32_t out[3]);
 /* Launch variants of the three FFT passes (forward plane pass = 0, pencil pass = 1,
  * inverse plane pass = 2), for diagnostics and tests.  okmc_grid_create times every
  * variant that exists for the grid's shape (three interleaved rounds, best of each)
- * and keeps variant 0 unless another is more than 2% faster; the choice is cached per
- * grid shape for the life of the process (the environment variable OKMC_TUNE=0 keeps
- * variant 0 without timing, e.g. under a profiler, and OKMC_VARIANTS=a,b,c pins
- * variants a, b and c of the three passes, each where it exists); the variants differ in
- * cluster size, threads per CTA and how data reaches shared memory, not in
- * arithmetic, so results are bitwise the same under every variant.
+ * and keeps variant 0 unless another is more than 2% faster.  The picks are kept per
+ * grid shape for the life of the process and in a JSON file keyed by device name, SM
+ * count, grid shape and variant schema: $OKMC_TUNE_CACHE (set and empty: no file),
+ * else $XDG_CACHE_HOME/okmc/tune.json or ~/.cache/okmc/tune.json; a shape found there
+ * is not timed again.  OKMC_TUNE=0 keeps variant 0 without timing (e.g. under a
+ * profiler) and OKMC_VARIANTS=a,b,c pins variants a, b and c of the three passes, each
+ * where it exists.  The variants differ in cluster size, threads per CTA and how data
+ * reaches shared memory, not in arithmetic, so results are bitwise the same under
+ * every variant.  Pencil variants: 0 swizzled tile by 16-byte asynchronous copies,
+ * 1 padded tile by 8-byte copies, 2 swizzled tile by TMA box copies onto an mbarrier
+ * (present when the driver encodes the spectra's tensor maps).  Variant 2 waits for its
+ * copies for at most 0.5 s: a CTA whose copies have not arrived by then sets the
+ * device error word and returns, and the next call that synchronises with the host
+ * (okmc_solve_stress with a host output, okmc_get_stats, okmc_step) returns
+ * OKMC_ETIMEOUT; the grid then stays failed, the context usable.
  * okmc_get_variants: current[p] = variant in use, available[p] = bit mask of the
  * variants that exist.  okmc_set_variant: OKMC_EINVAL if the variant does not exist
  * for this grid; drops captured step graphs. */

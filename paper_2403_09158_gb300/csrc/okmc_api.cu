@@ -85,7 +85,8 @@ cudaError_t launch_dipself(const C2<T>* spec, const PassCfg& c, const WBatch& b,
 template <class T>
 cudaError_t launch_dipole_energies(const T* sig, int3 n, const okmc_defect* def, const DefGeo* G, const double* D, int nd,
                                    double h3, double* E, double* Ec, cudaStream_t st);
-cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st);
+cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const CUtensorMap* tin,
+                               const CUtensorMap* tout, const PassCfg& c, cudaStream_t st);
 int pencil_variant_mask(const PassCfg& c);
 template <class T> int fdm_pencil_tile(int ny, int nz, size_t limit);
 int shift_positions_per_pass();
@@ -208,6 +209,10 @@ struct okmc_grid {
   void* sig = nullptr;
   void* spec = nullptr;
   void* spec2 = nullptr;  // fast path: Green operator output (spec keeps the plane transforms)
+  // fast path: spec and spec2 as 2-D float tensors of 6 nz rows of 2 P floats, for the
+  // TMA-staged pencil pass (valid when tm_ok)
+  CUtensorMap tm_spec{}, tm_spec2{};
+  bool tm_ok = false;
   int* d_dirty = nullptr;  // [6][nz] planes whose eigenstrain changed since their last transform
   void* tw = nullptr;
   void* ftw = nullptr;  // FP32 fields: twiddles with balanced magnitude errors, for the register-FFT passes
@@ -401,6 +406,45 @@ double qlimit(const okmc_grid* g) { return fp64(g) ? std::ldexp(1.0, 62) : 21474
 size_t qsize(const okmc_grid* g) { return fp64(g) ? 8 : 4; }
 size_t tsize(const okmc_grid* g) { return fp64(g) ? 8 : 4; }
 
+// Tensor map of a fast-path spectrum (spec or spec2), or nullptr when the grid has none
+const CUtensorMap* tmap(const okmc_grid* g, const void* spectrum) {
+  if (!g->tm_ok) return nullptr;
+  return spectrum == g->spec ? &g->tm_spec : spectrum == g->spec2 ? &g->tm_spec2 : nullptr;
+}
+
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point (no link
+// against the driver library)
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled_fn() {
+  static EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// A spectrum as the TMA pencil pass reads and writes it: 6 nz rows (comp * nz + kz) of
+// 2 P floats, boxes of 16 floats by min(nz, 256) or nz / 2 rows, 64-byte swizzle
+bool encode_spectrum_map(CUtensorMap* m, void* base, size_t P, int nz) {
+  EncodeTiledFn enc = encode_tiled_fn();
+  if (!enc) return false;
+  const cuuint64_t dim[2] = {(cuuint64_t)(2 * P), (cuuint64_t)(6 * (size_t)nz)};
+  const cuuint64_t stride[1] = {(cuuint64_t)(2 * P * sizeof(float))};
+  const cuuint32_t box[2] = {16u, (cuuint32_t)(nz <= 256 ? nz : nz / 2)};
+  const cuuint32_t estride[2] = {1u, 1u};
+  if (nz > 256 && (nz % 2 != 0 || nz / 2 > 256)) return false;
+  if (stride[0] % 16 != 0 || ((uintptr_t)base & 15) != 0) return false;
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dim, stride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int solve(okmc_grid* g) {
   if (g->sigma_valid) return OKMC_OK;
   PassCfg c = g->cfg;
@@ -419,7 +463,7 @@ int solve(okmc_grid* g) {
     c.dirty = g->d_dirty;
     OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, g->variant[0], g->eps, g->spec, c, g->st); }));
     c.dirty = nullptr;
-    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st); }));
+    OKMC_TRY(run(g, "pencil_green", [&] { return launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec2, tmap(g, g->spec), tmap(g, g->spec2), c, g->st); }));
     OKMC_TRY(run(g, "plane_inv", [&] { return launch_plane_fast(true, g->variant[2], g->spec2, g->sig, c, g->st); }));
   } else {
     OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<float, int32_t>((const int32_t*)g->eps, (C2<float>*)g->spec, c, g->st); }));
@@ -604,7 +648,7 @@ int build_self_terms(okmc_grid* g, bool want_W = true, bool want_D = false) {
     OKMC_TRY(run(g, "self_fields", [&] { return launch_wfields<Q>((Q*)g->eps, n, g->d_ptr, g->d_off, g->d_cnt, b, g->st); }));
     if (g->fast) {
       OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fast(false, g->variant[0], g->eps, g->spec, c, g->st); }));
-      OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec, c, g->st); }));
+      OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec, tmap(g, g->spec), tmap(g, g->spec), c, g->st); }));
     } else {
       OKMC_TRY(run(g, "plane_fwd", [&] { return launch_plane_fwd<T, Q>((const Q*)g->eps, (C2<T>*)g->spec, c, g->st); }));
       OKMC_TRY(run(g, "pencil_fwd", [&] { return launch_pencil<T>((C2<T>*)g->spec, c, g->st); }));
@@ -776,7 +820,7 @@ std::map<std::tuple<int, int, int>, std::array<int, 3>> g_tune_cache;  // shape 
 // or ~/.cache/okmc/tune.json.  It is read once per process; after each new tuning it is
 // rewritten with its current content merged in (a temporary file renamed over it, so a
 // reader never sees half a file).  An unreadable or malformed file counts as empty.
-constexpr const char* kTuneSchema = "passes-v2";  // bump when the variants of a pass change meaning
+constexpr const char* kTuneSchema = "passes-v3";  // bump when the variants of a pass change meaning
 bool g_tune_file_read = false;
 std::map<std::string, std::array<int, 3>> g_tune_file;
 
@@ -870,7 +914,7 @@ int warm_passes(okmc_grid* g) {
   if (e == cudaSuccess) e = cudaMemsetAsync(g->spec2, 0, sbytes, g->st);
   if (e == cudaSuccess) e = launch_plane_fast(false, g->variant[0], g->eps, g->spec, c, g->st);
   if (e == cudaSuccess)
-    e = launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st);
+    e = launch_pencil_fast(g->variant[1], (const C2<float>*)g->spec, (C2<float>*)g->spec2, tmap(g, g->spec), tmap(g, g->spec2), c, g->st);
   if (e == cudaSuccess) e = launch_plane_fast(true, g->variant[2], g->spec2, g->sig, c, g->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
   return e == cudaSuccess ? OKMC_OK : cuda_fail(g, e, "warm-up launches");
@@ -934,7 +978,7 @@ int autotune(okmc_grid* g) {
     if (g->avail[pass] == 1) continue;
     auto launch = [&](int v) {
       if (pass == 0) return launch_plane_fast(false, v, g->eps, g->spec, c, g->st);
-      return pass == 1 ? launch_pencil_fast(v, (const C2<float>*)g->spec, (C2<float>*)g->spec2, c, g->st)
+      return pass == 1 ? launch_pencil_fast(v, (const C2<float>*)g->spec, (C2<float>*)g->spec2, tmap(g, g->spec), tmap(g, g->spec2), c, g->st)
                        : launch_plane_fast(true, v, g->spec2, g->sig, c, g->st);
     };
     float best[8];
@@ -1138,7 +1182,9 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   }
   if (g->fast && (rc = dalloc(g, &g->spec2, 6 * g->n[2] * g->P * 2 * tsize(g)))) return cleanup(rc);
   if (g->fast) {
-    g->avail[1] = pencil_variant_mask(c);
+    g->tm_ok = encode_spectrum_map(&g->tm_spec, g->spec, g->P, g->n[2]) &&
+               encode_spectrum_map(&g->tm_spec2, g->spec2, g->P, g->n[2]);
+    g->avail[1] = pencil_variant_mask(c) & (g->tm_ok ? ~0 : ~4);  // variant 2 stages by TMA
     g->avail[2] = plane_inv_variant_mask(c);
   }
   if ((rc = dalloc(g, (void**)&g->d_dirty, sizeof(int) * 6 * g->n[2]))) return cleanup(rc);
@@ -1148,6 +1194,9 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
   if (cudaMemsetAsync(g->d_err, 0, sizeof(int), g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if (cudaStreamSynchronize(g->st) != cudaSuccess) return cleanup(OKMC_ECUDA);
   if ((rc = autotune(g))) return cleanup(rc);
+  // OKMC_TMA_EXTRA_TX=b (a test hook, taken after the tuner's launches): the TMA-staged
+  // pencil pass expects b bytes beyond its copies, so that its bounded wait runs out
+  if (const char* x = std::getenv("OKMC_TMA_EXTRA_TX")) c.tx_extra = std::max(0, std::min(atoi(x), 1 << 16));
   *out = g;
   return OKMC_OK;
 }
@@ -1327,8 +1376,9 @@ int okmc_get_positions(okmc_grid* g, int32_t* pos, int32_t n, int on_device) {
 int okmc_solve_stress(okmc_grid* g, void* sigma_out, int out_on_device) {
   if (!g) return OKMC_EINVAL;
   OKMC_TRY(solve(g));
-  if (sigma_out) return copy_out(g, sigma_out, g->sig, 6 * g->N * tsize(g), out_on_device);
-  return OKMC_OK;
+  if (!sigma_out) return OKMC_OK;
+  OKMC_TRY(copy_out(g, sigma_out, g->sig, 6 * g->N * tsize(g), out_on_device));
+  return out_on_device ? OKMC_OK : check_device_error(g);  // the copy synchronised the stream already
 }
 
 int okmc_eigenstrain(okmc_grid* g, void* eps_out, int out_on_device) {
@@ -1706,9 +1756,12 @@ int okmc_get_stencil(okmc_grid* g, int32_t i, int32_t c, int32_t* offs, int32_t*
 int okmc_get_stats(okmc_grid* g, okmc_step_stats* out) {
   if (!g || !out) return OKMC_EINVAL;
   DevState s;
+  int derr = 0;
   cudaError_t e = cudaMemcpyAsync(&s, g->d_state, sizeof(s), cudaMemcpyDeviceToHost, g->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&derr, g->d_err, sizeof(int), cudaMemcpyDeviceToHost, g->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
   if (e != cudaSuccess) return cuda_fail(g, e, "stats");
+  if (derr) return check_device_error(g);
   out->events = s.events;
   out->steps = s.step;
   out->solves = g->solves;

@@ -11,6 +11,7 @@
 //           the pencil pass reads TW consecutive ky at one kx for every kz.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -307,6 +308,8 @@ struct PassCfg {
   int* dirty;          // fast forward plane pass: per plane (c*nz + z) flag, nonzero when the
                        // plane's eigenstrain changed since its last transform (the pass skips
                        // clean planes and clears the flags it consumed); nullptr: every plane
+  int tx_extra;        // bytes a TMA-staged pass expects beyond its copies: 0, except where a
+                       // test makes that pass's bounded wait run out
 };
 
 // ---------------------------------------------------------------- defects

@@ -541,30 +541,11 @@ __device__ __forceinline__ int tile_row(int r) { return (r & ~15) + ((r & 1) << 
 // are paired so that each half-warp holds 8 threads of each of two adjacent lines.  The
 // two layouts give the same arithmetic.  (8-byte copies allocate in L1, which two CTAs'
 // shared memory leave small, and so limit the loads in flight on the SM.)
-// One tile (8 consecutive ky at one kx, every kz, six components) of the pencil pass.
+// Forward z FFTs, Green operator and inverse z FFTs of one tile (8 consecutive ky at one
+// kx, every kz, six components) held in shared memory in layout SWZ; ends on a barrier.
 template <int NZ, bool SWZ>
-__device__ __forceinline__ void pencil_item(const C2<float>* in, C2<float>* out, const PassCfg& c, int tile_index,
-                                            unsigned char* smem_raw) {
-  C2<float>* twZ = reinterpret_cast<C2<float>*>(smem_raw);
-  C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw + (sizeof(C2<float>) * tw2_size<NZ>() + 15) / 16 * 16);  // [comp * NZ + kz][8 or 9]
+__device__ __forceinline__ void pencil_tile(C2<float>* tile, const C2<float>* twZ, const PassCfg& c, int kx, int ky0) {
   const int tid = threadIdx.x;
-  const size_t P = (size_t)(c.H + 1) * c.ny;
-  const size_t p0 = (size_t)tile_index * kTW;
-  const int kx = (int)(p0 / c.ny), ky0 = (int)(p0 % c.ny);
-  if constexpr (SWZ) {
-    for (int idx = tid; idx < 6 * NZ * 4; idx += kT) {  // four 16-byte pieces per row
-      const int row = idx >> 2, t = 2 * (idx & 3);
-      cp_async16(tile + tile_at<true>(row, t), in + (size_t)row * P + p0 + t);
-    }
-  } else {
-    for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
-      const int t = idx & (kTW - 1), row = tile_row(idx >> 3);  // row = comp * NZ + kz
-      cp_async8(tile + row * kLDT + t, in + (size_t)row * P + p0 + t);
-    }
-  }
-  fill_tw2<NZ>(twZ, reinterpret_cast<const C2<float>*>(c.ftwZ));
-  cp_async_wait_all();
-  __syncthreads();
   constexpr int NTZ = reg_nt<NZ>(), GL = kT / NTZ, R2Z = RegPlan<NZ>::R2;
   int g = tid / NTZ, t = tid % NTZ;
   if (SWZ && NTZ == 16) {  // group 2w + b of warp w: lanes 8b + {0-7, 16-23}
@@ -607,10 +588,156 @@ __device__ __forceinline__ void pencil_item(const C2<float>* in, C2<float>* out,
     lines(std::true_type{});
     __syncthreads();
   }
+}
+
+// One tile of the pencil pass, staged by per-thread asynchronous copies.
+template <int NZ, bool SWZ>
+__device__ __forceinline__ void pencil_item(const C2<float>* in, C2<float>* out, const PassCfg& c, int tile_index,
+                                            unsigned char* smem_raw) {
+  C2<float>* twZ = reinterpret_cast<C2<float>*>(smem_raw);
+  C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw + (sizeof(C2<float>) * tw2_size<NZ>() + 15) / 16 * 16);  // [comp * NZ + kz][8 or 9]
+  const int tid = threadIdx.x;
+  const size_t P = (size_t)(c.H + 1) * c.ny;
+  const size_t p0 = (size_t)tile_index * kTW;
+  const int kx = (int)(p0 / c.ny), ky0 = (int)(p0 % c.ny);
+  if constexpr (SWZ) {
+    for (int idx = tid; idx < 6 * NZ * 4; idx += kT) {  // four 16-byte pieces per row
+      const int row = idx >> 2, t = 2 * (idx & 3);
+      cp_async16(tile + tile_at<true>(row, t), in + (size_t)row * P + p0 + t);
+    }
+  } else {
+    for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
+      const int t = idx & (kTW - 1), row = tile_row(idx >> 3);  // row = comp * NZ + kz
+      cp_async8(tile + row * kLDT + t, in + (size_t)row * P + p0 + t);
+    }
+  }
+  fill_tw2<NZ>(twZ, reinterpret_cast<const C2<float>*>(c.ftwZ));
+  cp_async_wait_all();
+  __syncthreads();
+  pencil_tile<NZ, SWZ>(tile, twZ, c, kx, ky0);
   for (int idx = tid; idx < 6 * NZ * kTW; idx += kT) {
-    const int t8 = idx & (kTW - 1), row = row_of(idx >> 3);
+    const int t8 = idx & (kTW - 1), row = SWZ ? idx >> 3 : tile_row(idx >> 3);
     out[(size_t)row * P + p0 + t8] = tile[tile_at<SWZ>(row, t8)];
   }
+}
+
+// ---- tensor-memory-access (TMA) staging of the pencil tile
+// The spectra seen as a 2-D float tensor of 6 * nz rows (row comp * nz + kz) of 2 * P
+// floats; a box is 16 floats (one tile row of 8 complex, 64 bytes) wide and TmaBox<NZ>
+// rows high, and the 64-byte swizzle of the tensor map lays it out exactly as
+// tile_at<true> (16-byte piece j of row r at piece j ^ ((r >> 1) & 3)) when the tile
+// starts on a 1024-byte boundary.
+template <int NZ>
+struct TmaBox {
+  static constexpr int BH = NZ <= 256 ? NZ : NZ / 2;  // a box spans at most 256 rows
+  static constexpr int NB = 6 * NZ / BH;
+  static constexpr unsigned kBytes = 6u * NZ * kTW * sizeof(C2<float>);
+};
+static_assert(TmaBox<320>::BH * 2 == 320 && TmaBox<320>::kBytes < (1u << 20), "box split / tx-count range");
+
+template <int NZ>
+__host__ __device__ constexpr size_t pencil_tma_smem() {
+  // twiddles, mbarrier (16 bytes), up to 1023 bytes to reach a 1024-byte boundary, tile
+  return (sizeof(C2<float>) * (size_t)tw2_size<NZ>() + 15) / 16 * 16 + 16 + 1023 + TmaBox<NZ>::kBytes;
+}
+
+namespace {
+constexpr unsigned long long kBulkWaitNs = 500000000ull;  // 0.5 s: a copy that slow has failed
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Wait for phase `parity` of the mbarrier to complete, giving up after kBulkWaitNs.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  const unsigned long long t0 = global_ns();
+  for (unsigned it = 0; it < (1u << 28); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 31) == 31 && global_ns() - t0 > kBulkWaitNs) return false;
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap* map, int x, int y, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, unsigned src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group [%0, {%1, %2}], [%3];\n" ::"l"(map), "r"(x), "r"(y),
+               "r"(src)
+               : "memory");
+}
+}  // namespace
+
+// One tile of the pencil pass, staged by TMA: one thread issues the tile's box loads onto
+// an mbarrier that every thread then waits on (bounded: on timeout the CTA records error
+// 6, waits once more, bounded, for the copies in flight, and returns without output);
+// after the transforms one thread stores the boxes back and waits until they have been
+// read out of shared memory.
+template <int NZ>
+__device__ __forceinline__ void pencil_item_tma(const CUtensorMap* tin, const CUtensorMap* tout, const PassCfg& c,
+                                                int tile_index, unsigned char* smem_raw) {
+  using B = TmaBox<NZ>;
+  constexpr unsigned TWB = (sizeof(C2<float>) * tw2_size<NZ>() + 15) / 16 * 16;
+  C2<float>* twZ = reinterpret_cast<C2<float>*>(smem_raw);
+  const unsigned s0 = (unsigned)__cvta_generic_to_shared(smem_raw);
+  const unsigned bar = s0 + TWB;
+  const unsigned ts = (s0 + TWB + 16 + 1023) & ~1023u;
+  C2<float>* tile = reinterpret_cast<C2<float>*>(smem_raw + (ts - s0));
+  const int tid = threadIdx.x;
+  const int p0 = tile_index * kTW;
+  const int kx = p0 / c.ny, ky0 = p0 % c.ny;
+  if (tid == 0) mbar_init(bar, 1);
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(bar, B::kBytes + (unsigned)c.tx_extra);
+#pragma unroll 1
+    for (int b = 0; b < B::NB; ++b) tma_load_2d(ts + (unsigned)b * B::BH * 64u, tin, 2 * p0, b * B::BH, bar);
+  }
+  fill_tw2<NZ>(twZ, reinterpret_cast<const C2<float>*>(c.ftwZ));
+  const bool ok = mbar_wait_bounded(bar, 0);
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) {
+      atomicExch(c.err, 6);
+      mbar_wait_bounded(bar, 0);
+    }
+    return;
+  }
+  pencil_tile<NZ, true>(tile, twZ, c, kx, ky0);
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // the tile's writes, visible to the bulk copies
+  __syncthreads();
+  if (tid == 0) {
+#pragma unroll 1
+    for (int b = 0; b < B::NB; ++b) tma_store_2d(tout, 2 * p0, b * B::BH, ts + (unsigned)b * B::BH * 64u);
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+  }
+}
+
+template <int NZ>
+__global__ void __launch_bounds__(kT, 2)
+    k_pencil_tma(const __grid_constant__ CUtensorMap tin, const __grid_constant__ CUtensorMap tout, PassCfg c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pencil_item_tma<NZ>(&tin, &tout, c, blockIdx.x, smem_raw);
 }
 
 template <int NZ, bool SWZ>
@@ -761,20 +888,27 @@ cudaError_t plane_pair(bool inverse, int variant, const void* in, void* out, con
 }
 
 template <int NZ>
-cudaError_t pencil_one(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st) {
+cudaError_t pencil_one(int variant, const C2<float>* in, C2<float>* out, const CUtensorMap* tin, const CUtensorMap* tout,
+                       const PassCfg& c, cudaStream_t st) {
   const size_t P = (size_t)(c.H + 1) * c.ny;
   const dim3 grid((unsigned)(P / kTW));
+  if (variant == 2) {
+    if (!tin || !tout) return cudaErrorInvalidValue;
+    return launch_k(k_pencil_tma<NZ>, grid, pencil_tma_smem<NZ>(), 1, st, *tin, *tout, c);
+  }
   if (variant == 1)
     return launch_k(k_pencil_fast<NZ, false>, grid, pencil_fast_smem<NZ, false>(), 1, st, in, out, c);
   return launch_k(k_pencil_fast<NZ, true>, grid, pencil_fast_smem<NZ, true>(), 1, st, in, out, c);
 }
 
-// Pencil variants (one tile per CTA, two CTAs per SM): 0 swizzled tile, 1 padded tile.
-// A persistent, double-buffered form (one CTA of 384 threads per SM) measured
-// 1.3-1.6x slower: the transform phase needs the warps more than the loads need hiding.
+// Pencil variants (one tile per CTA, two CTAs per SM): 0 swizzled tile by 16-byte
+// cp.async, 1 padded tile by 8-byte cp.async, 2 swizzled tile by TMA box copies (needs
+// the spectra's tensor maps).  A persistent, double-buffered form (one CTA of 384
+// threads per SM) measured 1.3-1.6x slower: the transform phase needs the warps more
+// than the loads need hiding.
 template <int NZ>
 int pencil_variants() {
-  return 3;
+  return 7;
 }
 }  // namespace
 
@@ -914,10 +1048,11 @@ int plane_inv_variant_mask(const PassCfg& c) {
   }
 }
 
-cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const PassCfg& c, cudaStream_t st) {
+cudaError_t launch_pencil_fast(int variant, const C2<float>* in, C2<float>* out, const CUtensorMap* tin,
+                               const CUtensorMap* tout, const PassCfg& c, cudaStream_t st) {
   switch (c.nz) {
 #define OKMC_CASE(n, h) \
-  case n: return pencil_one<n>(variant, in, out, c, st);
+  case n: return pencil_one<n>(variant, in, out, tin, tout, c, st);
     OKMC_FAST_EDGES(OKMC_CASE)
 #undef OKMC_CASE
     default: return cudaErrorInvalidConfiguration;

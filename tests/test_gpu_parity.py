@@ -4,6 +4,8 @@ Bars: stencils bit exact; stress relative L2 <= 1e-5 (FP32 fields) or 1e-10 (FP6
 fields); energies within 1e-4 eV (FP32) or 1e-8 eV (FP64); kinetic decisions equal
 given the same energies and Philox counters.
 """
+import time
+
 import numpy as np
 import pytest
 
@@ -433,7 +435,7 @@ def test_incremental_plane_transforms_equal_fresh_solve(mode):
 
 # ------------------------------------------------------------------ launch variants
 @pytest.mark.parametrize('n', [(48, 48, 48), (96, 96, 64), (128, 128, 32), (160, 160, 32), (192, 192, 32),
-                               (256, 256, 32), (320, 320, 32)])
+                               (256, 256, 32), (320, 320, 32), (64, 64, 256), (48, 48, 320)])
 def test_pass_variants_bitwise_equal(n):
     """Every launch variant of the FFT passes gives the same stress, bit for bit."""
     w = scaled_population(n, 20, seed=n[0], r111=(0.4, 1.0), r100=(0.4, 1.0))
@@ -455,6 +457,34 @@ def test_pass_variants_bitwise_equal(n):
         g.set_variant(p, cur[p])
     with pytest.raises(ok.OkmcError):
         g.set_variant(2, 30)
+    g.close()
+
+
+def test_bulk_copy_wait_gives_up_with_a_status(monkeypatch):
+    """The TMA-staged pencil pass waits on its copies with a bounded wait.  A test hook
+    makes it expect 16 bytes more than its copies bring, so the wait runs out: every CTA
+    records error code 6 and returns, the call that synchronises reports OKMC_ETIMEOUT,
+    and the context stays usable (a fresh grid solves to the same stress as variant 0)."""
+    w = scaled_population((32, 32, 32), 6, seed=5, r111=(0.4, 1.0), r100=(0.4, 1.0))
+    monkeypatch.setenv('OKMC_VARIANTS', '0,0,0')
+    monkeypatch.setenv('OKMC_TMA_EXTRA_TX', '16')
+    g = make_grid(w)  # self terms by variant 0
+    if not (g.variants()[1][1] >> 2) & 1:
+        g.close()
+        pytest.skip('no tensor maps on this device')
+    g.set_variant(1, 2)
+    t0 = time.time()
+    with pytest.raises(ok.OkmcError) as ei:
+        g.solve_stress()
+    assert ei.value.code == ok.OKMC_ETIMEOUT, ei.value
+    assert 0.4 < time.time() - t0 < 30.0
+    g.close()
+    monkeypatch.delenv('OKMC_TMA_EXTRA_TX')
+    g = make_grid(w)
+    ref = g.solve_stress()
+    g.set_variant(1, 2)
+    g.set_defects(w.defects)
+    assert np.array_equal(g.solve_stress(), ref)
     g.close()
 
 
