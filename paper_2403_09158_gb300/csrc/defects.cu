@@ -669,7 +669,7 @@ __device__ __forceinline__ void csum_add(CSum& a, float x) {
 }
 __device__ __forceinline__ double csum_value(const CSum& a) { return (double)a.s + (double)a.c; }
 
-constexpr int kEnergyThreads = 256;
+static_assert(kEnergyWarpEntries == 4 * 32, "one pass of the unrolled loop (U = 4) of one warp");
 
 
 template <class T>
@@ -702,8 +702,11 @@ struct EAcc<double> {
   __device__ __forceinline__ double value() const { return v; }
 };
 
-// The energies (and rates) of defect i, by one block of kEnergyThreads threads.
-template <class T>
+// The energies (and rates) of defect i, by a group of GS threads: the whole block
+// (GS = kEnergyThreads) or one warp (GS = 32, for a defect whose energy list has at most
+// kEnergyWarpEntries entries, one pass of the unrolled loop).  Thread gt of the group takes
+// entries first + gt + m * GS.
+template <class T, int GS>
 __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
                                               const DefGeo* __restrict__ G, const int* __restrict__ ptr,
                                               const int* __restrict__ off, const uint8_t* __restrict__ cnt,
@@ -713,12 +716,23 @@ __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n,
   // per-warp partial sums: FP32 (sum, compensation) pairs for FP32 fields, converted to
   // FP64 only in the epilogue warp (each conversion of a warp costs a whole FP64 issue
   // slot, even with one lane active); FP64 sums for FP64 fields
+  static_assert(GS == 32 || GS == kEnergyThreads, "a warp or the whole block");
   __shared__ T part[kEnergyThreads / 32][9];
   __shared__ T partc[kEnergyThreads / 32][9];
   const size_t N = (size_t)n.x * n.y * n.z;
+  const int gt = GS == 32 ? (int)(threadIdx.x & 31) : (int)threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool ep = GS == 32 || threadIdx.x < 32;  // the warp that runs the epilogue
   const okmc_defect r = d[i];
   const DefGeo g = G[i];
   const int c = r.pos[0] & 1, cp = 1 - c;
+  // the epilogue's inputs, loaded now so that they arrive while the sums run
+  double al = 0.0, wv = 0.0, es = 0.0;
+  if (ep && lane < 9) {
+    al = alpha[2 * i + (lane == 0 ? c : cp)];
+    wv = W[(size_t)i * 18 + c * 9 + lane];
+    es = G[i].escale;
+  }
   // the weights e_i (off-diagonals twice) in units of the defect's scale, whose FP64
   // value multiplies the sums at the end: every weight is 0, +-1 or +-2, exact in FP32,
   // whereas e itself rounded to FP32 (1/(2 sqrt 3) for a 1/2<111> loop: -1.8e-8
@@ -739,13 +753,13 @@ __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n,
   if (want_cand && dl.ptr && dl.ptr[2 * i + c] >= 0) {
     // the energy list: each voxel of the site and candidate stencils once, nine counts
     const int k_end = dl.end[2 * i + c];
-    for (int k0 = dl.ptr[2 * i + c] + threadIdx.x; k0 < k_end; k0 += U * blockDim.x) {
+    for (int k0 = dl.ptr[2 * i + c] + gt; k0 < k_end; k0 += U * GS) {
       T sv[U][6];
       unsigned long long cc[U];
       unsigned sc[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int k = k0 + u * blockDim.x;
+        const int k = k0 + u * GS;
         cc[u] = 0ull;
         sc[u] = 0u;
         if (k < k_end) {
@@ -760,7 +774,7 @@ __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n,
       }
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        if (k0 + u * (int)blockDim.x >= k_end) break;
+        if (k0 + u * GS >= k_end) break;
         T dot = T(0);
 #pragma unroll
         for (int a = 0; a < 6; ++a) dot += ew[a] * sv[u][a];
@@ -772,11 +786,11 @@ __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n,
   } else {
     {  // the site stencil
       const int k_end = ptr[2 * i + c + 1];
-      for (int k0 = ptr[2 * i + c] + threadIdx.x; k0 < k_end; k0 += U * blockDim.x) {
+      for (int k0 = ptr[2 * i + c] + gt; k0 < k_end; k0 += U * GS) {
         T sv[U][6], w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          const int k = k0 + u * blockDim.x;
+          const int k = k0 + u * GS;
           w[u] = T(0);
           if (k < k_end) {
             int dx, dy, dz;
@@ -789,7 +803,7 @@ __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n,
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-          if (k0 + u * (int)blockDim.x >= k_end) break;
+          if (k0 + u * GS >= k_end) break;
           T dot = T(0);
 #pragma unroll
           for (int a = 0; a < 6; ++a) dot += ew[a] * sv[u][a];
@@ -800,7 +814,7 @@ __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n,
     if (want_cand) {
       // candidate j sits at base(X + lambda_j) = base(X) + d_j, d_j in {-1,0}^3 (c = 0)
       // or {0,1}^3 (c = 1); per axis the shift is (s + 1)/2 - (1 - c) with s = +-1
-      for (int k = ptr[2 * i + cp] + threadIdx.x; k < ptr[2 * i + cp + 1]; k += blockDim.x) {
+      for (int k = ptr[2 * i + cp] + gt; k < ptr[2 * i + cp + 1]; k += GS) {
         int dx, dy, dz;
         unpack_off(off[k], dx, dy, dz);
         const T w = T(cnt[k]);
@@ -819,31 +833,37 @@ __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n,
     }
   }
   // warp reduction of the accumulators (compensated pairs stay FP32), FP64 across warps
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int wid = threadIdx.x >> 5;
+  double tot = 0.0;
+  if constexpr (GS == 32) {
 #pragma unroll
-  for (int j = 0; j < 9; ++j) {
-    acc[j].warp_reduce();
-    if (lane == 0) {
-      if constexpr (sizeof(T) == 4) {
-        part[wid][j] = acc[j].v.s;
-        partc[wid][j] = acc[j].v.c;
-      } else {
-        part[wid][j] = acc[j].v;
-        partc[wid][j] = T(0);
+    for (int j = 0; j < 9; ++j) {
+      acc[j].warp_reduce();
+      if (lane == j) tot = acc[j].value();
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+      acc[j].warp_reduce();
+      if (lane == 0) {
+        if constexpr (sizeof(T) == 4) {
+          part[wid][j] = acc[j].v.s;
+          partc[wid][j] = acc[j].v.c;
+        } else {
+          part[wid][j] = acc[j].v;
+          partc[wid][j] = T(0);
+        }
       }
     }
+    __syncthreads();
+    // epilogue on warp 0, one lane per position (lane 0: the site, lane 1 + j: jump j),
+    // so the FP64 work (sums, energies, Boltzmann factors) runs side by side
+    if (threadIdx.x >= 32) return;
+    if (lane < 9)
+      for (int w2 = 0; w2 < GS / 32; ++w2) tot += (double)part[w2][lane] + (double)partc[w2][lane];
   }
-  __syncthreads();
-  // epilogue on warp 0, one lane per position (lane 0: the site, lane 1 + j: jump j),
-  // so the FP64 work (sums, energies, Boltzmann factors) runs side by side
-  if (threadIdx.x >= 32) return;
-  double tot = 0.0;
-  if (lane < 9)
-    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += (double)part[w2][lane] + (double)partc[w2][lane];
   double ej = 0.0;
-  const double es = G[i].escale;  // read again here rather than held in registers
-  if (lane == 0) ej = pref * es * alpha[2 * i + c] * tot - W[(size_t)i * 18 + c * 9];
-  else if (lane < 9) ej = pref * es * alpha[2 * i + cp] * tot - W[(size_t)i * 18 + c * 9 + lane];
+  if (lane < 9) ej = pref * es * al * tot - wv;
   const double e0 = __shfl_sync(0xffffffffu, ej, 0);
   if (lane == 0) E[i] = e0;
   if (!want_cand) return;
@@ -871,6 +891,9 @@ __device__ __forceinline__ void energies_item(const T* __restrict__ sig, int3 n,
   }
 }
 
+// Blocks 0 .. nbig - 1 take the defects order[0 .. nbig - 1] (the large lists, largest
+// first) one per block; each later block takes the next kEnergyThreads / 32 defects of
+// the order, one per warp.
 template <class T>
 __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_energies(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
                                                              const DefGeo* __restrict__ G, const int* __restrict__ ptr,
@@ -878,9 +901,13 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
                                                              const double* __restrict__ alpha, const double* __restrict__ W,
                                                              double pref, int want_cand, const int* __restrict__ order,
                                                              double* __restrict__ E, double* __restrict__ Ec, RateArgs ra,
-                                                             DilatedLists dl) {
-  const int i = order ? order[blockIdx.x] : blockIdx.x;
-  energies_item<T>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, i, E, Ec, ra, dl);
+                                                             DilatedLists dl, int nd, int nbig) {
+  if ((int)blockIdx.x < nbig) {
+    energies_item<T, kEnergyThreads>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, order[blockIdx.x], E, Ec, ra, dl);
+  } else {
+    const int k = nbig + ((int)blockIdx.x - nbig) * (kEnergyThreads / 32) + (int)(threadIdx.x >> 5);
+    if (k < nd) energies_item<T, 32>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, order[k], E, Ec, ra, dl);
+  }
 }
 
 // ---------------------------------------------------------------- events
@@ -1086,15 +1113,24 @@ __global__ void __launch_bounds__(kEventThreads) k_fixed_dt(okmc_defect* __restr
 }
 
 // ---------------------------------------------------------------- batched ensemble kernels
-// Persistent over a work list of (replica, k) items with k the position in the replica's
-// energies order: each block takes items blockIdx.x, blockIdx.x + gridDim.x, ...
+// Persistent over a work list of (replica, k) items with k >= 0 the position in the
+// replica's energies order of a large list (one block), or k = -p - 1 for the small lists
+// at positions p .. p + kEnergyThreads / 32 - 1 (one warp each): each block takes items
+// blockIdx.x, blockIdx.x + gridDim.x, ...
 __global__ void __launch_bounds__(kEnergyThreads, 4) k_energies_batch(const BatchRep* __restrict__ reps,
                                                                       const int2* __restrict__ items, int nitems) {
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const int2 w = items[it];
     const BatchRep& r = reps[w.x];
-    energies_item<float>(r.sig, r.n, r.def, r.geo, r.ptr, r.off, r.cnt, r.alpha, r.W, r.pref, 1, r.order[w.y], r.E, r.Ec,
-                         r.ra, r.dl);
+    if (w.y >= 0) {
+      energies_item<float, kEnergyThreads>(r.sig, r.n, r.def, r.geo, r.ptr, r.off, r.cnt, r.alpha, r.W, r.pref, 1,
+                                           r.order[w.y], r.E, r.Ec, r.ra, r.dl);
+    } else {  // order positions -w.y - 1 + warp, one small list per warp
+      const int k = -w.y - 1 + (int)(threadIdx.x >> 5);
+      if (k < r.nd)
+        energies_item<float, 32>(r.sig, r.n, r.def, r.geo, r.ptr, r.off, r.cnt, r.alpha, r.W, r.pref, 1, r.order[k], r.E,
+                                 r.Ec, r.ra, r.dl);
+    }
     __syncthreads();  // the block's shared partial sums are reused by the next item
   }
 }
@@ -1230,10 +1266,14 @@ cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
-                            int want_cand, const int* order, double* E, double* Ec, RateArgs ra, const DilatedLists& dl,
-                            cudaStream_t st) {
+                            int want_cand, const int* order, int nbig, double* E, double* Ec, RateArgs ra,
+                            const DilatedLists& dl, cudaStream_t st) {
   if (nd == 0) return cudaSuccess;
-  k_energies<T><<<nd, kEnergyThreads, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, order, E, Ec, ra, dl);
+  if (nbig < 0 || nbig > nd) return cudaErrorInvalidValue;
+  constexpr int per = kEnergyThreads / 32;
+  const int grid = nbig + (nd - nbig + per - 1) / per;
+  k_energies<T><<<grid, kEnergyThreads, 0, st>>>(sig, n, d, G, ptr, off, cnt, alpha, W, pref, want_cand, order, E, Ec, ra,
+                                                  dl, nd, nbig);
   return cudaGetLastError();
 }
 cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
@@ -1268,10 +1308,10 @@ template cudaError_t launch_selfterm<double>(const C2<double>*, const PassCfg&, 
                                             const double2*, const double2*, double*, int, const double*, double, double*,
                                             cudaStream_t);
 template cudaError_t launch_energies<float>(const float*, int3, const okmc_defect*, const DefGeo*, int, const int*, const int*,
-                                           const uint8_t*, const double*, const double*, double, int, const int*, double*,
-                                           double*, RateArgs, const DilatedLists&, cudaStream_t);
+                                           const uint8_t*, const double*, const double*, double, int, const int*, int,
+                                           double*, double*, RateArgs, const DilatedLists&, cudaStream_t);
 template cudaError_t launch_energies<double>(const double*, int3, const okmc_defect*, const DefGeo*, int, const int*,
                                             const int*, const uint8_t*, const double*, const double*, double, int, const int*,
-                                            double*, double*, RateArgs, const DilatedLists&, cudaStream_t);
+                                            int, double*, double*, RateArgs, const DilatedLists&, cudaStream_t);
 
 }  // namespace okmc

@@ -59,7 +59,8 @@ cudaError_t launch_selfterm(const C2<T>* spec, const PassCfg& c, const WBatch& b
 template <class T>
 cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd, const int* ptr,
                             const int* off, const uint8_t* cnt, const double* alpha, const double* W, double pref,
-                            int want_cand, const int* order, double* E, double* Ec, RateArgs ra, const DilatedLists& dl, cudaStream_t st);
+                            int want_cand, const int* order, int nbig, double* E, double* Ec, RateArgs ra, const DilatedLists& dl,
+                            cudaStream_t st);
 // batched ensemble kernels (solve_fast.cu, defects.cu)
 bool batch_edge_supported(int nx, int ny, int nz);
 int pass_batch_grid(int pass, int n, int nitems);
@@ -233,7 +234,8 @@ struct okmc_grid {
   bool dip_valid = false;   // d_D holds the current defects' dipole self parts
   double* d_E = nullptr;
   double* d_Ec = nullptr;
-  int* d_order = nullptr;  // defects by decreasing stencil size (energy block order)
+  int* d_order = nullptr;  // defects by decreasing energy-list length (energies order)
+  int nbig = 0;            // the first nbig of the order take a block each, the rest a warp
   double* d_rates = nullptr;
   double* d_rsum = nullptr;
   Move* d_moves = nullptr;
@@ -498,9 +500,9 @@ int energies(okmc_grid* g, int want_cand, double kT = 0.0) {
   return run(g, "energies", [&] {
     if (fp64(g))
       return launch_energies<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
-                                     g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->d_E, g->d_Ec, ra, dl, g->st);
+                                     g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->nbig, g->d_E, g->d_Ec, ra, dl, g->st);
     return launch_energies<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
-                                  g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->d_E, g->d_Ec, ra, dl, g->st);
+                                  g->d_alpha, g->d_W, pref, want_cand, g->d_order, g->nbig, g->d_E, g->d_Ec, ra, dl, g->st);
   });
 }
 
@@ -684,7 +686,10 @@ int build_self_terms(okmc_grid* g, bool want_W = true, bool want_D = false) {
 }
 
 // Dilated candidate lists of every (defect, class): sizes, offsets, fill.
-int build_dilated_lists(okmc_grid* g) {
+// The energy lists (each voxel of the site and candidate stencils once, nine counts) of
+// every defect and site class; work[i] receives the longer of defect i's two lists, or
+// the site plus candidate stencil entries where a class has no list.
+int build_dilated_lists(okmc_grid* g, const std::vector<int>& nnz, std::vector<int>& work) {
   const int nd = g->nd;
   int* d_n = nullptr;
   OKMC_TRY(dalloc(g, (void**)&d_n, 2 * nd * sizeof(int)));
@@ -705,6 +710,12 @@ int build_dilated_lists(okmc_grid* g) {
     if (cnt[k] > 0) tot += cnt[k];
   }
   if (tot > 0x7fffffffll) return fail(g, OKMC_ENOMEM, "too many dilated stencil entries");
+  work.assign(nd, 0);
+  for (int i = 0; i < nd; ++i)
+    for (int c = 0; c < 2; ++c) {
+      const int k = 2 * i + c;
+      work[i] = std::max(work[i], cnt[k] >= 0 ? cnt[k] : nnz[k] + nnz[2 * i + 1 - c]);
+    }
   OKMC_TRY(dalloc(g, (void**)&g->d_dl, 4 * nd * sizeof(int)));
   OKMC_TRY(dalloc(g, (void**)&g->d_doff, (size_t)tot * sizeof(int)));
   OKMC_TRY(dalloc(g, (void**)&g->d_dcnt, (size_t)tot * sizeof(unsigned long long)));
@@ -744,6 +755,7 @@ void free_defects(okmc_grid* g) {
     *b = nullptr;
   }
   g->nd = 0;
+  g->nbig = 0;
 }
 
 // Kernels of one step (solve, energies + rates, event, incremental field update)
@@ -1289,11 +1301,11 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_state, 0, sizeof(DevState), g->st);
     if (e != cudaSuccess) return cuda_fail(g, e, "upload");
     g->solves = 0;
-    std::vector<int> ptr(2 * n1 + 1, 0);
+    std::vector<int> ptr(2 * n1 + 1, 0), nnz;
     if (nd) {
       OKMC_TRY(run(g, "defect_setup", [&] { return launch_defect_setup(g->d_def, g->d_geo, nd, g->h, g->st); }));
       OKMC_TRY(run(g, "stencil_count", [&] { return launch_stencil_count(g->d_geo, nd, g->d_nnz, g->d_sumcnt, g->st); }));
-      std::vector<int> nnz(2 * nd);
+      nnz.resize(2 * nd);
       e = cudaMemcpyAsync(nnz.data(), g->d_nnz, 2 * nd * sizeof(int), cudaMemcpyDeviceToHost, g->st);
       if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
       if (e != cudaSuccess) return cuda_fail(g, e, "stencil sizes");
@@ -1303,12 +1315,6 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
         tot += nnz[k];
       }
       ptr[2 * nd] = (int)tot;
-      std::vector<int> order(nd);
-      for (int i = 0; i < nd; ++i) order[i] = i;
-      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nnz[2 * x] + nnz[2 * x + 1] > nnz[2 * y] + nnz[2 * y + 1]; });
-      e = cudaMemcpyAsync(g->d_order, order.data(), nd * sizeof(int), cudaMemcpyHostToDevice, g->st);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
-      if (e != cudaSuccess) return cuda_fail(g, e, "energy order");
       if (tot > 0x7fffffffll) return fail(g, OKMC_ENOMEM, "too many stencil entries");
       OKMC_TRY(dalloc(g, (void**)&g->d_off, (size_t)tot * sizeof(int)));
       OKMC_TRY(dalloc(g, (void**)&g->d_cnt, (size_t)tot));
@@ -1323,7 +1329,18 @@ int okmc_set_defects(okmc_grid* g, const okmc_defect* defs, int32_t nd) {
         return launch_stencil_fill(g->d_geo, nd, g->d_ptr, g->d_sumcnt, g->d_off, g->d_cnt, g->d_alpha, g->d_err, g->st);
       }));
       OKMC_TRY(check_device_error(g));
-      OKMC_TRY(build_dilated_lists(g));
+      std::vector<int> work;
+      OKMC_TRY(build_dilated_lists(g, nnz, work));
+      // energies order: longest energy list first; the nbig lists longer than one pass of
+      // a warp take a block each, the rest one warp each
+      std::vector<int> order(nd);
+      for (int i = 0; i < nd; ++i) order[i] = i;
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+      g->nbig = 0;
+      while (g->nbig < nd && work[order[g->nbig]] > kEnergyWarpEntries) ++g->nbig;
+      e = cudaMemcpyAsync(g->d_order, order.data(), nd * sizeof(int), cudaMemcpyHostToDevice, g->st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+      if (e != cudaSuccess) return cuda_fail(g, e, "energy order");
       OKMC_TRY((fp64(g) ? build_self_terms<double, int64_t>(g) : build_self_terms<float, int32_t>(g)));
     }
     g->dip_valid = false;
@@ -1962,9 +1979,13 @@ static int batch_build_kernels(okmc_batch* b) {
     c.ntile = (int)items.size() - c.tile0;
     cls.push_back(c);
   }
+  // energies: a block per long list (order position k), then a warp per short list
+  // (k = -p - 1 names the kEnergyThreads / 32 lists from order position p on)
   const int e0 = (int)items.size();
   for (int i = 0; i < n; ++i)
-    for (int k = 0; k < b->grids[i]->nd; ++k) items.push_back(make_int2(i, k));
+    for (int k = 0; k < b->grids[i]->nbig; ++k) items.push_back(make_int2(i, k));
+  for (int i = 0; i < n; ++i)
+    for (int p = b->grids[i]->nbig; p < b->grids[i]->nd; p += kEnergyThreads / 32) items.push_back(make_int2(i, -p - 1));
   const int ne = (int)items.size() - e0;
   cudaFree(b->d_reps);
   cudaFree(b->d_items);

@@ -383,6 +383,11 @@ struct QTypes {
   int nt;
 };
 
+// The energies kernel: a block of kEnergyThreads threads per defect whose energy list is
+// longer than kEnergyWarpEntries entries, one warp per defect otherwise.
+constexpr int kEnergyThreads = 256;
+constexpr int kEnergyWarpEntries = 128;
+
 // One replica of a batched ensemble as the batched kernels see it (an array of these
 // lives in device memory): the pass configuration and buffers of its FP32 register-FFT
 // solve, and the defect-side arrays of its step.  Work lists pair a replica index with
