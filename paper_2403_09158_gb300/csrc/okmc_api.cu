@@ -993,10 +993,10 @@ int autotune(okmc_grid* g) {
       return pass == 1 ? launch_pencil_fast(v, (const C2<float>*)g->spec, (C2<float>*)g->spec2, tmap(g, g->spec), tmap(g, g->spec2), c, g->st)
                        : launch_plane_fast(true, v, g->spec2, g->sig, c, g->st);
     };
-    float best[8];
-    for (int v = 0; v < 8; ++v) best[v] = 1e30f;
+    float best[16];
+    for (int v = 0; v < 16; ++v) best[v] = 1e30f;
     for (int round = 0; round < 3 && e == cudaSuccess; ++round) {
-      for (int v = 0; v < 8 && e == cudaSuccess; ++v) {
+      for (int v = 0; v < 16 && e == cudaSuccess; ++v) {
         if (!((g->avail[pass] >> v) & 1)) continue;
         e = launch(v);
         if (e == cudaSuccess) e = cudaEventRecord(a, g->st);
@@ -1009,7 +1009,7 @@ int autotune(okmc_grid* g) {
       }
     }
     int pick = 0;
-    for (int v = 1; v < 8; ++v)
+    for (int v = 1; v < 16; ++v)
       if (best[v] < 0.98f * best[0] && best[v] < best[pick]) pick = v;
     g->variant[pass] = pick;
   }
