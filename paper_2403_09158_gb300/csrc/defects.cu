@@ -910,6 +910,145 @@ __global__ void __launch_bounds__(kEnergyThreads, sizeof(T) == 4 ? 4 : 2) k_ener
   }
 }
 
+// ---------------------------------------------------------------- energies by chunks
+// Chunk slot w of the energy lists, by one warp: the entries of one pass of the unrolled
+// loop (each lane U of them, all loads issued before the first use), the nine sums
+// accumulated per lane as in energies_item, combined across the warp, and stored as FP64
+// (site sum, then jump j).  A slot beyond the current class's list stores nothing.
+template <class T>
+__device__ __forceinline__ void energy_chunk(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
+                                             const DefGeo* __restrict__ G, const DilatedLists& dl, const ChunkArgs& ca,
+                                             int w) {
+  constexpr int U = kEnergyWarpEntries / 32;
+  const int lane = threadIdx.x & 31;
+  const int i = ca.cdef[w];
+  const int k = w - ca.c0[i];
+  int pos[3];
+  for (int a = 0; a < 3; ++a) pos[a] = d[i].pos[a];
+  const int c = pos[0] & 1;
+  const int first = dl.ptr[2 * i + c] + k * kEnergyWarpEntries;
+  const int k_end = min(first + kEnergyWarpEntries, dl.end[2 * i + c]);
+  if (first >= k_end) return;
+  const size_t N = (size_t)n.x * n.y * n.z;
+  T ew[6];
+  bool use[6];
+  for (int a = 0; a < 6; ++a) {
+    ew[a] = T(G[i].ew[a]);
+    use[a] = ew[a] != T(0);
+  }
+  const int bx = floor_div2(pos[0]), by = floor_div2(pos[1]), bz = floor_div2(pos[2]);
+  EAcc<T> acc[9];
+  for (int j = 0; j < 9; ++j) acc[j].zero();
+  T sv[U][6];
+  unsigned long long cc[U];
+  unsigned sc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int kk = first + lane + 32 * u;
+    cc[u] = 0ull;
+    sc[u] = 0u;
+    if (kk < k_end) {
+      int ux, uy, uz;
+      unpack_off(dl.off[kk], ux, uy, uz);
+      cc[u] = dl.cnt[kk];
+      sc[u] = dl.scnt[kk];
+      const size_t v = ((size_t)wrap(bz + uz, n.z) * n.y + wrap(by + uy, n.y)) * n.x + wrap(bx + ux, n.x);
+#pragma unroll
+      for (int a = 0; a < 6; ++a) sv[u][a] = use[a] ? __ldg(sig + a * N + v) : T(0);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    if (first + lane + 32 * u >= k_end) break;
+    T dot = T(0);
+#pragma unroll
+    for (int a = 0; a < 6; ++a) dot += ew[a] * sv[u][a];
+    if (sc[u]) acc[0].add(T(sc[u]) * dot);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[1 + j].add(T((unsigned)(cc[u] >> (8 * j)) & 255u) * dot);
+  }
+  // lane j keeps sum j (FP32 moves), then one conversion per warp
+  EAcc<T> mine;
+  mine.zero();
+#pragma unroll
+  for (int j = 0; j < 9; ++j) {
+    acc[j].warp_reduce();
+    if (lane == j) mine = acc[j];
+  }
+  if (lane < 9) ca.part[(size_t)w * 9 + lane] = mine.value();
+}
+
+// Defects 3q, 3q + 1, 3q + 2 by one warp, nine lanes each (lane 9g + j: defect 3q + g,
+// position j: the site, then jump j - 1): the chunk sums in slot order, the energies,
+// and, with ra.rates set, the biased jump frequencies and their sum, as in energies_item.
+__device__ __forceinline__ void energy_finish(const okmc_defect* __restrict__ d, const DefGeo* __restrict__ G,
+                                              const DilatedLists& dl, const ChunkArgs& ca,
+                                              const double* __restrict__ alpha, const double* __restrict__ W,
+                                              double pref, int nd, int q, double* __restrict__ E,
+                                              double* __restrict__ Ec, const RateArgs& ra) {
+  const int lane = threadIdx.x & 31, grp = lane / 9, j = lane - 9 * grp;
+  const int i = 3 * q + grp;
+  const bool act = grp < 3 && i < nd;
+  double ej = 0.0, Em = 0.0, z = 1.0;
+  unsigned allowed = 0u;
+  if (act) {
+    // every load that does not depend on the site class first (both classes' values),
+    // then the class's chunk sums (every defect has at least one chunk)
+    const int p0 = d[i].pos[0];
+    Em = d[i].Em_eV;
+    const int s0 = ca.c0[i];
+    const int b0 = dl.ptr[2 * i], b1 = dl.ptr[2 * i + 1], e0_ = dl.end[2 * i], e1_ = dl.end[2 * i + 1];
+    const double a0 = alpha[2 * i], a1 = alpha[2 * i + 1];
+    const double w0 = W[(size_t)i * 18 + j], w1 = W[(size_t)i * 18 + 9 + j];
+    const double es = G[i].escale;
+    allowed = G[i].allowed;
+    z = G[i].z;
+    const double* P = ca.part + (size_t)s0 * 9 + j;
+    double tot = P[0];
+    const int c = p0 & 1;
+    const int nch = ((c ? e1_ - b1 : e0_ - b0) + kEnergyWarpEntries - 1) / kEnergyWarpEntries;
+    for (int k = 1; k < nch; ++k) tot += P[(size_t)k * 9];
+    const double al = (j == 0) == (c == 0) ? a0 : a1;  // alpha of the site's class, or of the other class for a jump
+    ej = pref * es * al * tot - (c ? w1 : w0);
+  }
+  const double e0 = __shfl_sync(0xffffffffu, ej, (9 * grp) & 31);
+  if (act && j == 0) E[i] = e0;
+  if (act && j >= 1) Ec[(size_t)i * 8 + j - 1] = ej;
+  if (!ra.rates) return;
+  // biased jump frequencies nu_j = (nu0/z) exp(-(E_m + (E_j - E_0)/2)/kT) of the
+  // allowed jumps (Eqs. biased_forward/backward_boltzmann, prefactor 1/z)
+  double nu = 0.0;
+  int neg = 0;
+  if (act && j >= 1) {
+    if (allowed >> (j - 1) & 1) {
+      const double barrier = Em + 0.5 * (ej - e0);
+      neg = barrier < 0.0;
+      nu = (ra.nu0 / z) * exp(-barrier * ra.rkT);
+    }
+    ra.rates[(size_t)i * 8 + j - 1] = nu;
+  }
+  double sum = 0.0;  // in jump order, as the frequency line walks them
+  for (int jj = 0; jj < 8; ++jj) sum += __shfl_sync(0xffffffffu, nu, (9 * grp + 1 + jj) & 31);
+  neg = __reduce_add_sync(0xffffffffu, neg);
+  if (act && j == 0) ra.rsum[i] = sum;
+  if (lane == 0 && neg) atomicAdd(reinterpret_cast<unsigned long long*>(ra.negb), (unsigned long long)neg);
+}
+
+template <class T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 3) k_energy_chunks(const T* __restrict__ sig, int3 n, const okmc_defect* __restrict__ d,
+                                                       const DefGeo* __restrict__ G, DilatedLists dl, ChunkArgs ca) {
+  const int w = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5);
+  if (w < ca.nchunk) energy_chunk<T>(sig, n, d, G, dl, ca, w);
+}
+
+__global__ void __launch_bounds__(64) k_energy_finish(const okmc_defect* __restrict__ d, const DefGeo* __restrict__ G,
+                                                      DilatedLists dl, ChunkArgs ca, const double* __restrict__ alpha,
+                                                      const double* __restrict__ W, double pref, int nd,
+                                                      double* __restrict__ E, double* __restrict__ Ec, RateArgs ra) {
+  const int q = (int)blockIdx.x * 2 + (int)(threadIdx.x >> 5);
+  if (3 * q < nd) energy_finish(d, G, dl, ca, alpha, W, pref, nd, q, E, Ec, ra);
+}
+
 // ---------------------------------------------------------------- events
 __device__ __forceinline__ void new_position(const int p[3], int j, int3 n, int q[3]) {
   const int L[3] = {2 * n.x, 2 * n.y, 2 * n.z};
@@ -1113,29 +1252,26 @@ __global__ void __launch_bounds__(kEventThreads) k_fixed_dt(okmc_defect* __restr
 }
 
 // ---------------------------------------------------------------- batched ensemble kernels
-// Persistent over a work list of (replica, k) items with k >= 0 the position in the
-// replica's energies order of a large list (one block), or k = -p - 1 for the small lists
-// at positions p .. p + kEnergyThreads / 32 - 1 (one warp each): each block takes items
-// blockIdx.x, blockIdx.x + gridDim.x, ...
-__global__ void __launch_bounds__(kEnergyThreads, 4) k_energies_batch(const BatchRep* __restrict__ reps,
-                                                                      const int2* __restrict__ items, int nitems) {
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+// One block per replica: its residence-time event or fixed-time step (Algorithm 1).
+// The two passes of the chunked energies over work lists of (replica, chunk slot) and
+// (replica, warp of three defects) items, one item per warp, persistent.
+__global__ void __launch_bounds__(256, 4) k_energy_chunks_batch(const BatchRep* __restrict__ reps,
+                                                             const int2* __restrict__ items, int nitems) {
+  for (int it = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); it < nitems; it += (int)gridDim.x * 8) {
     const int2 w = items[it];
     const BatchRep& r = reps[w.x];
-    if (w.y >= 0) {
-      energies_item<float, kEnergyThreads>(r.sig, r.n, r.def, r.geo, r.ptr, r.off, r.cnt, r.alpha, r.W, r.pref, 1,
-                                           r.order[w.y], r.E, r.Ec, r.ra, r.dl);
-    } else {  // order positions -w.y - 1 + warp, one small list per warp
-      const int k = -w.y - 1 + (int)(threadIdx.x >> 5);
-      if (k < r.nd)
-        energies_item<float, 32>(r.sig, r.n, r.def, r.geo, r.ptr, r.off, r.cnt, r.alpha, r.W, r.pref, 1, r.order[k], r.E,
-                                 r.Ec, r.ra, r.dl);
-    }
-    __syncthreads();  // the block's shared partial sums are reused by the next item
+    energy_chunk<float>(r.sig, r.n, r.def, r.geo, r.dl, r.ca, w.y);
+  }
+}
+__global__ void __launch_bounds__(256) k_energy_finish_batch(const BatchRep* __restrict__ reps,
+                                                             const int2* __restrict__ items, int nitems) {
+  for (int it = (int)blockIdx.x * 8 + (int)(threadIdx.x >> 5); it < nitems; it += (int)gridDim.x * 8) {
+    const int2 w = items[it];
+    const BatchRep& r = reps[w.x];
+    energy_finish(r.def, r.geo, r.dl, r.ca, r.alpha, r.W, r.pref, r.nd, w.y, r.E, r.Ec, r.ra);
   }
 }
 
-// One block per replica: its residence-time event or fixed-time step (Algorithm 1).
 __global__ void __launch_bounds__(kEventThreads) k_event_batch(const BatchRep* __restrict__ reps) {
   const BatchRep& r = reps[blockIdx.x];
   if (r.mode == OKMC_RESIDENCE)
@@ -1160,9 +1296,14 @@ __global__ void __launch_bounds__(256) k_moves_batch(const BatchRep* __restrict_
   }
 }
 
-cudaError_t launch_energies_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st) {
+cudaError_t launch_energy_chunks_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st) {
   if (nitems == 0) return cudaSuccess;
-  k_energies_batch<<<grid, kEnergyThreads, 0, st>>>(reps, items, nitems);
+  k_energy_chunks_batch<<<grid, 256, 0, st>>>(reps, items, nitems);
+  return cudaGetLastError();
+}
+cudaError_t launch_energy_finish_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st) {
+  if (nitems == 0) return cudaSuccess;
+  k_energy_finish_batch<<<grid, 256, 0, st>>>(reps, items, nitems);
   return cudaGetLastError();
 }
 cudaError_t launch_event_batch(const BatchRep* reps, int nrep, cudaStream_t st) {
@@ -1176,9 +1317,9 @@ cudaError_t launch_moves_batch(const BatchRep* reps, int nrep, cudaStream_t st) 
 int energies_batch_grid() {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_energies_batch, kEnergyThreads, 0) != cudaSuccess) {
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_energy_chunks_batch, 256, 0) != cudaSuccess) {
     (void)cudaGetLastError();
-    return 152 * 4;
+    return 152 * 8;
   }
   return sms * (per > 0 ? per : 1);
 }
@@ -1276,6 +1417,23 @@ cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const De
                                                   dl, nd, nbig);
   return cudaGetLastError();
 }
+template <class T>
+cudaError_t launch_energy_chunks(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd,
+                                 const DilatedLists& dl, const ChunkArgs& ca, const double* alpha, const double* W,
+                                 double pref, double* E, double* Ec, RateArgs ra, cudaStream_t st) {
+  if (nd == 0) return cudaSuccess;
+  if (ca.nchunk <= 0) return cudaErrorInvalidValue;
+  k_energy_chunks<T><<<(ca.nchunk + 7) / 8, 256, 0, st>>>(sig, n, d, G, dl, ca);
+  const int nq = (nd + 2) / 3;
+  k_energy_finish<<<(nq + 1) / 2, 64, 0, st>>>(d, G, dl, ca, alpha, W, pref, nd, E, Ec, ra);
+  return cudaGetLastError();
+}
+template cudaError_t launch_energy_chunks<float>(const float*, int3, const okmc_defect*, const DefGeo*, int,
+                                                 const DilatedLists&, const ChunkArgs&, const double*, const double*,
+                                                 double, double*, double*, RateArgs, cudaStream_t);
+template cudaError_t launch_energy_chunks<double>(const double*, int3, const okmc_defect*, const DefGeo*, int,
+                                                  const DilatedLists&, const ChunkArgs&, const double*, const double*,
+                                                  double, double*, double*, RateArgs, cudaStream_t);
 cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
                              Move* moves, DevState* stt, cudaStream_t st) {
   k_residence<<<1, kEventThreads, 0, st>>>(d, nd, rates, rsum, n, (uint32_t)seed, (uint32_t)(seed >> 32), moves, stt);

@@ -68,7 +68,12 @@ cudaError_t launch_pass_batch(int pass, int n, const BatchRep* reps, const int2*
                               cudaStream_t st);
 cudaError_t upload_batch_cfg(int slot0, const PassCfg* cfgs, int n, cudaStream_t st);
 int batch_cfg_slots();
-cudaError_t launch_energies_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st);
+cudaError_t launch_energy_chunks_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st);
+cudaError_t launch_energy_finish_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st);
+template <class T>
+cudaError_t launch_energy_chunks(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd,
+                                 const DilatedLists& dl, const ChunkArgs& ca, const double* alpha, const double* W,
+                                 double pref, double* E, double* Ec, RateArgs ra, cudaStream_t st);
 cudaError_t launch_event_batch(const BatchRep* reps, int nrep, cudaStream_t st);
 cudaError_t launch_moves_batch(const BatchRep* reps, int nrep, cudaStream_t st);
 int energies_batch_grid();
@@ -247,6 +252,10 @@ struct okmc_grid {
   int* d_doff = nullptr;                // dilated lists: packed offsets
   unsigned long long* d_dcnt = nullptr; // energy lists: eight candidate counts
   uint8_t* d_dscnt = nullptr;           // energy lists: site counts
+  int* d_cdef = nullptr;                // energies by chunks: the defect of each chunk slot
+  int* d_c0 = nullptr;                  // the first chunk slot of each defect
+  double* d_cpart = nullptr;            // [nchunk][9] chunk sums
+  int nchunk = 0;                       // chunk slots; 0: a defect has no energy list (per-defect kernel)
   void* d_bg = nullptr;     // [6][nz][ny][nx] fixed-point plastic strain of the dislocation lines (or none)
   std::vector<okmc_defect> h_def;
   bool sigma_valid = false;
@@ -497,6 +506,16 @@ int energies(okmc_grid* g, int want_cand, double kT = 0.0) {
     dl.cnt = g->d_dcnt;
     dl.scnt = g->d_dscnt;
   }
+  if (want_cand && g->nchunk > 0) {
+    const ChunkArgs ca{g->d_cdef, g->d_c0, g->d_cpart, g->nchunk};
+    return run(g, "energies", [&] {
+      if (fp64(g))
+        return launch_energy_chunks<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, dl, ca, g->d_alpha,
+                                            g->d_W, pref, g->d_E, g->d_Ec, ra, g->st);
+      return launch_energy_chunks<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, dl, ca, g->d_alpha,
+                                         g->d_W, pref, g->d_E, g->d_Ec, ra, g->st);
+    });
+  }
   return run(g, "energies", [&] {
     if (fp64(g))
       return launch_energies<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, g->d_ptr, g->d_off, g->d_cnt,
@@ -724,7 +743,29 @@ int build_dilated_lists(okmc_grid* g, const std::vector<int>& nnz, std::vector<i
   if (e != cudaSuccess) return cuda_fail(g, e, "dilated list offsets");
   DilatedLists dl{g->d_dl, g->d_dl + 2 * nd, g->d_doff, g->d_dcnt, g->d_dscnt};
   OKMC_TRY(run(g, "dilate_fill", [&] { return launch_dilate_fill(g->d_geo, nd, g->d_ptr, g->d_off, g->d_cnt, dl, g->d_err, g->st); }));
-  return check_device_error(g);
+  OKMC_TRY(check_device_error(g));
+  // chunk slots of the energies: ceil(max(len(i, 0), len(i, 1)) / kEnergyWarpEntries) per
+  // defect, in defect order; none when any defect has no energy list
+  g->nchunk = 0;
+  bool lists = true;
+  for (int k = 0; k < 2 * nd; ++k) lists = lists && cnt[k] >= 0;
+  if (!lists) return OKMC_OK;
+  std::vector<int> c0(nd), cdef;
+  for (int i = 0; i < nd; ++i) {
+    c0[i] = (int)cdef.size();
+    const int len = std::max(cnt[2 * i], cnt[2 * i + 1]);
+    for (int k = 0; k < (len + kEnergyWarpEntries - 1) / kEnergyWarpEntries; ++k) cdef.push_back(i);
+  }
+  if (cdef.empty()) return OKMC_OK;
+  OKMC_TRY(dalloc(g, (void**)&g->d_cdef, cdef.size() * sizeof(int)));
+  OKMC_TRY(dalloc(g, (void**)&g->d_c0, nd * sizeof(int)));
+  OKMC_TRY(dalloc(g, (void**)&g->d_cpart, cdef.size() * 9 * sizeof(double)));
+  e = cudaMemcpyAsync(g->d_cdef, cdef.data(), cdef.size() * sizeof(int), cudaMemcpyHostToDevice, g->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->d_c0, c0.data(), nd * sizeof(int), cudaMemcpyHostToDevice, g->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->st);
+  if (e != cudaSuccess) return cuda_fail(g, e, "energy chunks");
+  g->nchunk = (int)cdef.size();
+  return OKMC_OK;
 }
 
 int voxelise_all(okmc_grid* g) {
@@ -749,13 +790,15 @@ void free_defects(okmc_grid* g) {
                    (void**)&g->d_alpha, (void**)&g->d_sumcnt, (void**)&g->d_nnz, (void**)&g->d_W, (void**)&g->d_D,
                    (void**)&g->d_dip, (void**)&g->d_E,
                    (void**)&g->d_Ec, (void**)&g->d_order, (void**)&g->d_rates, (void**)&g->d_rsum, (void**)&g->d_moves, (void**)&g->d_pos,
-                   (void**)&g->d_dl, (void**)&g->d_doff, (void**)&g->d_dcnt, (void**)&g->d_dscnt};
+                   (void**)&g->d_dl, (void**)&g->d_doff, (void**)&g->d_dcnt, (void**)&g->d_dscnt,
+                   (void**)&g->d_cdef, (void**)&g->d_c0, (void**)&g->d_cpart};
   for (void** b : bufs) {
     dfree(g, *b);
     *b = nullptr;
   }
   g->nd = 0;
   g->nbig = 0;
+  g->nchunk = 0;
 }
 
 // Kernels of one step (solve, energies + rates, event, incremental field update)
@@ -1902,7 +1945,9 @@ const char* okmc_batch_last_error(const okmc_batch* b) { return b ? b->err.c_str
 
 static bool batch_kernels_ok(const okmc_batch* b) {
   for (const okmc_grid* g : b->grids)
-    if (fp64(g) || !g->fast || !batch_edge_supported(g->n[0], g->n[1], g->n[2]) || !g->d_order) return false;
+    if (fp64(g) || !g->fast || !batch_edge_supported(g->n[0], g->n[1], g->n[2]) || !g->d_order ||
+        (g->nd > 0 && g->nchunk == 0))
+      return false;
   return true;
 }
 
@@ -1945,6 +1990,7 @@ static int batch_build_kernels(okmc_batch* b) {
     r.ra.kT = kT;
     r.ra.rkT = 1.0 / kT;
     if (g->d_dl) r.dl = DilatedLists{g->d_dl, g->d_dl + 2 * g->nd, g->d_doff, g->d_dcnt, g->d_dscnt};
+    r.ca = ChunkArgs{g->d_cdef, g->d_c0, g->d_cpart, g->nchunk};
     r.pref = -kKappa * g->h * g->h * g->h;
     r.nu0 = g->nu0;
     r.kT = kT;
@@ -1979,14 +2025,15 @@ static int batch_build_kernels(okmc_batch* b) {
     c.ntile = (int)items.size() - c.tile0;
     cls.push_back(c);
   }
-  // energies: a block per long list (order position k), then a warp per short list
-  // (k = -p - 1 names the kEnergyThreads / 32 lists from order position p on)
+  // energies: every replica's chunk slots, then its warps of three defects
   const int e0 = (int)items.size();
   for (int i = 0; i < n; ++i)
-    for (int k = 0; k < b->grids[i]->nbig; ++k) items.push_back(make_int2(i, k));
-  for (int i = 0; i < n; ++i)
-    for (int p = b->grids[i]->nbig; p < b->grids[i]->nd; p += kEnergyThreads / 32) items.push_back(make_int2(i, -p - 1));
+    for (int w = 0; w < b->grids[i]->nchunk; ++w) items.push_back(make_int2(i, w));
   const int ne = (int)items.size() - e0;
+  const int f0 = (int)items.size();
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; 3 * q < b->grids[i]->nd; ++q) items.push_back(make_int2(i, q));
+  const int nf = (int)items.size() - f0;
   cudaFree(b->d_reps);
   cudaFree(b->d_items);
   b->d_reps = nullptr;
@@ -2027,7 +2074,7 @@ static int batch_build_kernels(okmc_batch* b) {
       }
     }
   }
-  const int egrid = std::min(std::max(ne, 1), energies_batch_grid());
+  const int egrid = energies_batch_grid();  // resident blocks of 8 warps (one item per warp)
   while ((int)b->side.size() < n + 1 + (int)cls.size()) {
     cudaStream_t st;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return OKMC_ECUDA;
@@ -2049,7 +2096,8 @@ static int batch_build_kernels(okmc_batch* b) {
       e = pass == 1 ? launch_pass_batch(1, c.nz, b->d_reps, it + c.tile0, c.ntile, grids[k][1], b->slot0, root)
                     : launch_pass_batch(pass, c.ny, b->d_reps, it + c.plane0, c.nplane, grids[k][pass], b->slot0, root);
     }
-  if (e == cudaSuccess) e = launch_energies_batch(b->d_reps, it + e0, ne, egrid, root);
+  if (e == cudaSuccess) e = launch_energy_chunks_batch(b->d_reps, it + e0, ne, std::max(1, std::min(egrid, (ne + 7) / 8)), root);
+  if (e == cudaSuccess) e = launch_energy_finish_batch(b->d_reps, it + f0, nf, std::max(1, std::min(egrid, (nf + 7) / 8)), root);
   if (e == cudaSuccess) e = launch_event_batch(b->d_reps, n, root);
   if (e == cudaSuccess) e = launch_moves_batch(b->d_reps, n, root);
   cudaError_t e2 = cudaStreamEndCapture(root, &graph);

@@ -376,6 +376,19 @@ struct DilatedLists {
   const uint8_t* scnt;            // count of the site stencil
 };
 
+// Energies by fixed chunks of the energy lists: defect i owns the chunk slots
+// c0[i] .. c0[i] + ceil(max(len(i, 0), len(i, 1)) / kEnergyWarpEntries) - 1, of which its
+// current site class c uses the first ceil(len(i, c) / kEnergyWarpEntries); slot w holds
+// entries c0 + w * kEnergyWarpEntries on of the class-c list.  One warp sums one chunk
+// into part[w][9] (site, then the eight jumps), and the finishing pass adds a defect's
+// chunks in slot order.
+struct ChunkArgs {
+  const int* cdef;  // [nchunk] the defect of each slot
+  const int* c0;    // [nd] the first slot of each defect
+  double* part;     // [nchunk][9] chunk sums
+  int nchunk;
+};
+
 // Unit eigenstrain tensors of the defect types present (at most eight: four
 // 1/2<111> loop axes, three <100> loop axes, the dilatational SIA cluster).
 struct QTypes {
@@ -410,6 +423,7 @@ struct BatchRep {
   double* Ec;
   RateArgs ra;
   DilatedLists dl;
+  ChunkArgs ca;               // energies by chunks of the energy lists
   double pref;                // -kappa h^3
   double nu0, kT;
   Move* moves;
