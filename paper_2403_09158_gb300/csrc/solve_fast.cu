@@ -746,181 +746,6 @@ __global__ void __launch_bounds__(kT, 2) k_pencil_fast(const C2<float>* in, C2<f
   pencil_item<NZ, SWZ>(in, out, c, blockIdx.x, smem_raw);
 }
 
-// ---- persistent inverse plane pass, staged by bulk copies
-// One cluster of CS CTAs (kPT threads, one CTA per SM) loops over the planes p =
-// cluster, cluster + clusters, ...  Each CTA's CPER columns of a plane are one contiguous
-// block of the kx-major spectrum, fetched by one bulk copy (plus the Nyquist column in
-// rank 0) into one of two stage buffers: the next plane's copy is in flight while this
-// plane is transformed.  Per plane: inverse column FFTs in place in the stage (column
-// cc's outputs rotated by cc positions, so that the copy-out, which reads rows of column
-// pairs, spreads each warp's reads evenly over the banks), the wide 16-byte copy-out to
-// the row owners, and the row FFTs from the row buffer to sigma.  Two cluster barriers
-// per plane: A (every row buffer free: the previous plane's rows are done) is waited on
-// only after the column FFTs, B (every copy-out landed) before the rows.  A stage wait
-// that runs out (kBulkWaitNs) records error 6; the CTA then waits once more, bounded,
-// for its copies in flight, and runs its remaining planes through the barriers only.
-template <int H, int NY, int CS>
-__host__ __device__ constexpr size_t pinv_smem() {
-  return plane_tw_bytes<H, NY>() + 16 + sizeof(C2<float>) * (2 * (size_t)(H / CS + 1) * NY + (size_t)(NY / CS) * (H + 2));
-}
-// smallest cluster (<= 8) whose CTA fits MINB CTAs in the shared memory of one SM; 0: none
-template <int H, int NY, int MINB>
-__host__ __device__ constexpr int pinv_cs() {
-  constexpr size_t lim = MINB == 1 ? 227 * 1024 : 113 * 1024;
-  return (pinv_smem<H, NY, 1>() <= lim) ? 1
-         : (H % 2 == 0 && NY % 2 == 0 && pinv_smem<H, NY, 2>() <= lim) ? 2
-         : (H % 4 == 0 && NY % 4 == 0 && pinv_smem<H, NY, 4>() <= lim) ? 4
-         : (H % 8 == 0 && NY % 8 == 0 && pinv_smem<H, NY, 8>() <= lim) ? 8
-                                                                        : 0;
-}
-// the persistent pass needs lines of 8 threads for the rows (the 16-byte copy-out's row
-// pairing), an even column count per CTA, columns a multiple of 16 long, and at most 16
-// values per thread in step 1 of both line FFTs (longer ones spill)
-template <int H, int NY, int MINB>
-__host__ __device__ constexpr bool pinv_ok() {
-  return pinv_cs<H, NY, MINB>() != 0 && reg_nt<H>() == 8 && (H / (pinv_cs<H, NY, MINB>() ? pinv_cs<H, NY, MINB>() : 1)) % 2 == 0 &&
-         NY % 16 == 0 && RegPlan<H>::R2 <= 16 && RegPlan<NY>::R2 <= 16;
-}
-
-namespace {
-__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-// cluster barrier halves with the default (release / acquire) semantics
-__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.aligned;\n" ::: "memory"); }
-__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory"); }
-}  // namespace
-
-template <int H, int NY, int CS, int kPT, int MINB>
-__global__ void __launch_bounds__(kPT, MINB) k_plane_inv_p(const C2<float>* __restrict__ spec, float* __restrict__ sig,
-                                                           PassCfg c, int nplanes) {
-  constexpr int CPER = H / CS, ROWS = NY / CS, LDR = H + 2;
-  constexpr int NTY = reg_nt<NY>(), GC = kPT / NTY, NTH = reg_nt<H>(), GR = kPT / NTH;
-  constexpr int R2Y = RegPlan<NY>::R2, R2H = RegPlan<H>::R2;
-  constexpr int SLOT = (CPER + 1) * NY;  // complex per stage buffer (the CTA's columns, then the Nyquist column)
-  static_assert(NTH == 8 && CPER % 2 == 0 && NY % 16 == 0, "16-byte copy-out and row pairing");
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C2<float>* twH = reinterpret_cast<C2<float>*>(smem_raw);
-  C2<float>* twY = twH + tw2_size<H>();
-  C2<float>* untw = twY + tw2_size<NY>();
-  const unsigned s0 = (unsigned)__cvta_generic_to_shared(smem_raw);
-  const unsigned bar0 = s0 + (unsigned)plane_tw_bytes<H, NY>();  // two mbarriers
-  C2<float>* stage = reinterpret_cast<C2<float>*>(smem_raw + plane_tw_bytes<H, NY>() + 16);
-  C2<float>* rowb = stage + 2 * SLOT;  // [ROWS][LDR]
-  cg::cluster_group cluster = cg::this_cluster();
-  const int h = CS > 1 ? (int)cluster.block_rank() : 0;
-  const int tid = threadIdx.x;
-  const size_t P = (size_t)(H + 1) * NY;
-  const unsigned bytes = (unsigned)(CPER * NY * 8) + (h == 0 ? (unsigned)(NY * 8) : 0u) + (unsigned)c.tx_extra;
-  auto issue = [&](int plane, int b) {  // one thread
-    const unsigned bar = bar0 + 8u * b;
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(stage + b * SLOT);
-    mbar_arrive_expect_tx(bar, bytes);
-    bulk_load(dst, spec + (size_t)plane * P + (size_t)h * CPER * NY, CPER * NY * 8, bar);
-    if (h == 0) bulk_load(dst + CPER * NY * 8, spec + (size_t)plane * P + (size_t)H * NY, NY * 8, bar);
-  };
-  if (tid == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar0 + 8, 1);
-  }
-  __syncthreads();
-  int p = blockIdx.y;
-  const int stride = gridDim.y;
-  if (tid == 0 && p < nplanes) issue(p, 0);
-  fill_tw2<H>(twH, reinterpret_cast<const C2<float>*>(c.ftwH));
-  fill_tw2<NY>(twY, reinterpret_cast<const C2<float>*>(c.ftwY));
-  for (int i = tid; i <= H; i += kPT) untw[i] = reinterpret_cast<const C2<float>*>(c.ftwU)[i];
-  if (CS > 1) cl_arrive();  // barrier A, first phase: every CTA of the cluster is running
-  bool failed = false;
-  for (int it = 0; p < nplanes; ++it, p += stride) {
-    const int b = it & 1;
-    C2<float>* stg = stage + b * SLOT;
-    // the other buffer was last read by the previous plane's copy-out, before barrier B
-    if (!failed && tid == 0 && p + stride < nplanes) issue(p + stride, b ^ 1);
-    if (!failed) {
-      const bool ok = mbar_wait_bounded(bar0 + 8u * b, (unsigned)(it >> 1) & 1u);
-      if (__syncthreads_or(!ok)) {
-        failed = true;
-        if (tid == 0) {
-          atomicExch(c.err, 6);
-          mbar_wait_bounded(bar0 + 8u * b, (unsigned)(it >> 1) & 1u);
-          if (p + stride < nplanes) mbar_wait_bounded(bar0 + 8u * (b ^ 1), (unsigned)((it + 1) >> 1) & 1u);
-        }
-      }
-    }
-    if (!failed) {  // inverse columns along y, in place; column cc's output k at (k + cc) mod NY
-      const int g = tid / NTY, t = tid % NTY;
-      const C2<float>* nyq = stg + CPER * NY;
-      for (int c0 = 0; c0 < CPER; c0 += GC) {
-        const bool act = c0 + g < CPER;
-        const int cc = act ? c0 + g : 0;
-        C2<float>* col = stg + cc * NY;
-        const bool packed = (h == 0 && cc == 0);
-        const int sh = cc;
-        auto ld = [&](int i) {
-          const C2<float> A = col[i];
-          if (!packed) return A;
-          const C2<float> B = nyq[i];
-          return C2<float>{A.x - B.y, A.y + B.x};  // A + i B
-        };
-        auto st = [&](int k, C2<float> v) {
-          const int q = k + sh;
-          col[q >= NY ? q - NY : q] = v;
-        };
-        reg_fft<true, NY>(ld, XSkew<R2Y>{col, 1}, st, twY, t, act);
-      }
-    }
-    // the stage's generic writes, ordered before the bulk copy that refills it
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    __syncthreads();
-    if (CS > 1) cl_wait();  // barrier A: every row buffer of the cluster is free
-    if (!failed) {
-      // row k, columns j, j + 1 in one 16-byte store into the owner's row buffer
-      for (int e = tid; e < NY * (CPER / 2); e += kPT) {
-        const int j = 2 * (e % (CPER / 2)), k = e / (CPER / 2);
-        const int q0 = k + j, q1 = q0 + 1;
-        const C2<float> v0 = stg[j * NY + (q0 >= NY ? q0 - NY : q0)], v1 = stg[(j + 1) * NY + (q1 >= NY ? q1 - NY : q1)];
-        const int owner = k / ROWS;
-        C2<float>* base = (CS > 1 && owner != h) ? cluster.map_shared_rank(rowb, owner) : rowb;
-        *reinterpret_cast<float4*>(base + (k % ROWS) * LDR + h * CPER + j) = make_float4(v0.x, v0.y, v1.x, v1.y);
-      }
-    }
-    if (CS > 1) {  // barrier B: every copy-out into this CTA's row buffer has landed
-      cl_arrive();
-      cl_wait();
-    } else {
-      __syncthreads();
-    }
-    if (!failed) {  // rows along x (the row pairing of the 16-byte layout)
-      const int g = tid / NTH, t = tid % NTH;
-      for (int r0 = 0; r0 < ROWS; r0 += GR) {
-        const int yr = r0 + (g >> 3) * 8 + ((g >> 1) & 3) + (g & 1) * 4;
-        const bool act = yr < ROWS;
-        const int yl = act ? yr : 0;
-        C2<float>* R = rowb + yl * LDR;
-        auto ld = [&](int k) {
-          if (k == 0) {
-            const C2<float> q0 = R[0];
-            return C2<float>{q0.x + q0.y, q0.x - q0.y};
-          }
-          const C2<float> Xk = R[k], Xc = conjg(R[H - k]);
-          const C2<float> E = Xk + Xc;
-          const C2<float> O = cmul_rn(conjg(untw[k]), Xk - Xc);
-          return C2<float>{E.x - O.y, E.y + O.x};
-        };
-        C2<float>* orow = reinterpret_cast<C2<float>*>(sig + ((size_t)p * NY + h * ROWS + yl) * (2 * H));
-        auto st = [&](int k, C2<float> v) { orow[k] = v; };
-        reg_fft<true, H>(ld, XSkew<R2H>{R, 1}, st, twH, t, act);
-      }
-    }
-    if (CS > 1) cl_arrive();  // barrier A, next phase: this CTA's rows are done
-    else __syncthreads();
-  }
-  if (CS > 1) cl_wait();
-}
-
 // ---------------------------------------------------------------- dispatch
 namespace {
 template <class K, class... Args>
@@ -1045,32 +870,11 @@ cudaError_t plane_inv_staged(const void* in, void* out, const PassCfg& c, cudaSt
 // per SM, 3 with 256 threads and three CTAs per SM (registers capped at 85); 4 as 0,
 // with the next wave's columns prefetched into L2; 5 and 6 as 0 and 4 with the wide
 // copy-out of the column outputs; 7 as 6 with 16-byte stores in the copy-out (lines of
-// 8 threads, nx >= 128, and only while the wider rows keep two CTAs per SM); 8 the
-// persistent pass (k_plane_inv_p: one CTA of 512 threads per SM, columns by bulk copies
-// into two stage buffers, the next plane's copy in flight during this plane's transforms);
-// 9 the same with two CTAs of 256 threads per SM (smaller CTAs, larger clusters).
+// 8 threads, nx >= 128, and only while the wider rows keep two CTAs per SM).
 template <int H, int NY>
 int plane_inv_variants() {
   constexpr bool w16 = NShape<H, NY>::NTH == 8 && ninv_smem<H, NY>(ncs<H, NY>(), 2) <= kTwoPerSM;
-  return 1 | 16 | 32 | 64 | (w16 ? 128 : 0) | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0) |
-         (pinv_ok<H, NY, 1>() ? 256 : 0) | (pinv_ok<H, NY, 2>() ? 512 : 0);
-}
-
-// MINB 1: one CTA of 512 threads per SM; MINB 2: two CTAs of 256 threads per SM
-template <int H, int NY, int MINB>
-cudaError_t plane_inv_persistent(const void* in, void* out, const PassCfg& c, cudaStream_t st) {
-  if constexpr (!pinv_ok<H, NY, MINB>()) {
-    return cudaErrorInvalidConfiguration;
-  } else {
-    constexpr int CS = pinv_cs<H, NY, MINB>(), NT = MINB == 1 ? 512 : 256;
-    constexpr size_t smem = pinv_smem<H, NY, CS>();
-    static const int resident = resident_clusters(k_plane_inv_p<H, NY, CS, NT, MINB>, CS, smem, NT);
-    if (resident <= 0) return cudaErrorInvalidConfiguration;
-    const int nplanes = c.ncomp * c.nz;
-    const dim3 grid(CS, std::min(nplanes, resident));
-    return launch_kb(k_plane_inv_p<H, NY, CS, NT, MINB>, grid, NT, smem, CS, st, static_cast<const C2<float>*>(in),
-                     static_cast<float*>(out), c, nplanes);
-  }
+  return 1 | 16 | 32 | 64 | (w16 ? 128 : 0) | (stage_cs<H, NY>(kTwoPerSM) ? 2 : 0) | (stage_cs<H, NY>(kThreePerSM) ? 4 | 8 : 0);
 }
 
 template <int H, int NY>
@@ -1078,8 +882,6 @@ cudaError_t plane_pair(bool inverse, int variant, const void* in, void* out, con
   if (inverse && variant == 1) return plane_inv_staged<H, NY, stage_cs<H, NY>(kTwoPerSM), 256, 2>(in, out, c, st);
   if (inverse && variant == 2) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 128, 3>(in, out, c, st);
   if (inverse && variant == 3) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 256, 3>(in, out, c, st);
-  if (inverse && variant == 8) return plane_inv_persistent<H, NY, 1>(in, out, c, st);
-  if (inverse && variant == 9) return plane_inv_persistent<H, NY, 2>(in, out, c, st);
   if (!inverse) return plane_pair_n<H, NY, ncs<H, NY>()>(false, in, out, c, st);
   return plane_pair_n<H, NY, ncs<H, NY>()>(true, in, out, c, st, variant == 4 || variant == 6 || variant == 7,
                                           variant == 7 ? 2 : (variant == 5 || variant == 6) ? 1 : 0);

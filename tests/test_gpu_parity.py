@@ -488,34 +488,6 @@ def test_bulk_copy_wait_gives_up_with_a_status(monkeypatch):
     g.close()
 
 
-def test_persistent_plane_pass_wait_gives_up_with_a_status(monkeypatch):
-    """The persistent inverse plane pass (variant 8) waits on its stage copies with a
-    bounded wait.  With 16 bytes more expected than its copies bring, every CTA records
-    error code 6, runs its remaining planes through the cluster barriers only, and
-    returns; the solve reports OKMC_ETIMEOUT and a fresh grid on variant 8 still solves
-    to the stress of variant 0."""
-    w = scaled_population((128, 128, 32), 6, seed=7, r111=(0.4, 1.0), r100=(0.4, 1.0))
-    monkeypatch.setenv('OKMC_VARIANTS', '0,0,0')
-    monkeypatch.setenv('OKMC_TMA_EXTRA_TX', '16')
-    g = make_grid(w)
-    if not (g.variants()[1][2] >> 8) & 1:
-        g.close()
-        pytest.skip('no persistent inverse pass for this shape')
-    g.set_variant(2, 8)
-    t0 = time.time()
-    with pytest.raises(ok.OkmcError) as ei:
-        g.solve_stress()
-    assert ei.value.code == ok.OKMC_ETIMEOUT, ei.value
-    assert 0.4 < time.time() - t0 < 30.0
-    g.close()
-    monkeypatch.delenv('OKMC_TMA_EXTRA_TX')
-    g = make_grid(w)
-    ref = g.solve_stress()
-    g.set_variant(2, 8)
-    assert np.array_equal(g.solve_stress(), ref)
-    g.close()
-
-
 def test_variants_pinned_by_environment(monkeypatch):
     """OKMC_VARIANTS=a,b,c pins each pass's variant where it exists (no timing), and
     steps captured on a pinned grid follow the tuned grid's trajectory bit for bit."""
