@@ -611,14 +611,14 @@ def run_batch(args):
            'events_per_s': events / (ms / 1e3), 'setup_s': setup_s,
            'form': 'batched persistent kernels: per edge class one branch of the three solve passes over '
                    'work lists of (replica, plane / tile) items, then energies, event and field update over every '
-                   'replica; %d launches per step' % (3 * len({w.n for w in ws}) + 3),
+                   'replica; %d launches per step' % (3 * len({w.n for w in ws}) + 4),
            'graph_branches_fp32': {'ms_per_step': ms_graph / args.steps, 'value': voxels * args.steps / (ms_graph / 1e3),
                                    'note': 'each replica\'s own step as a branch of one graph (the other batch form)'},
            'sequential_fp32': {'ms_per_step': seq32_ms, 'value': voxels / (seq32_ms / 1e3)},
            'single_replica_fp64': {'ms_per_step_by_edge': fp64_ms, 'ms_per_ensemble_step': seq64_ms,
                                    'value': voxels / (seq64_ms / 1e3)},
            'vs_single_replica_fp64': (voxels / (ms / args.steps / 1e3)) / (voxels / (seq64_ms / 1e3)),
-           'gpu_launches': (3 * len({w.n for w in ws}) + 3) * args.steps, 'clocks': clocks}
+           'gpu_launches': (3 * len({w.n for w in ws}) + 4) * args.steps, 'clocks': clocks}
     print(json.dumps(out))
     return 0
 

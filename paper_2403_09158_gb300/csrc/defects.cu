@@ -1419,21 +1419,24 @@ cudaError_t launch_energies(const T* sig, int3 n, const okmc_defect* d, const De
 }
 template <class T>
 cudaError_t launch_energy_chunks(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd,
-                                 const DilatedLists& dl, const ChunkArgs& ca, const double* alpha, const double* W,
-                                 double pref, double* E, double* Ec, RateArgs ra, cudaStream_t st) {
+                                 const DilatedLists& dl, const ChunkArgs& ca, cudaStream_t st) {
   if (nd == 0) return cudaSuccess;
   if (ca.nchunk <= 0) return cudaErrorInvalidValue;
   k_energy_chunks<T><<<(ca.nchunk + 7) / 8, 256, 0, st>>>(sig, n, d, G, dl, ca);
+  return cudaGetLastError();
+}
+template cudaError_t launch_energy_chunks<float>(const float*, int3, const okmc_defect*, const DefGeo*, int,
+                                                 const DilatedLists&, const ChunkArgs&, cudaStream_t);
+template cudaError_t launch_energy_chunks<double>(const double*, int3, const okmc_defect*, const DefGeo*, int,
+                                                  const DilatedLists&, const ChunkArgs&, cudaStream_t);
+cudaError_t launch_energy_finish(const okmc_defect* d, const DefGeo* G, int nd, const DilatedLists& dl,
+                                 const ChunkArgs& ca, const double* alpha, const double* W, double pref, double* E,
+                                 double* Ec, RateArgs ra, cudaStream_t st) {
+  if (nd == 0) return cudaSuccess;
   const int nq = (nd + 2) / 3;
   k_energy_finish<<<(nq + 1) / 2, 64, 0, st>>>(d, G, dl, ca, alpha, W, pref, nd, E, Ec, ra);
   return cudaGetLastError();
 }
-template cudaError_t launch_energy_chunks<float>(const float*, int3, const okmc_defect*, const DefGeo*, int,
-                                                 const DilatedLists&, const ChunkArgs&, const double*, const double*,
-                                                 double, double*, double*, RateArgs, cudaStream_t);
-template cudaError_t launch_energy_chunks<double>(const double*, int3, const okmc_defect*, const DefGeo*, int,
-                                                  const DilatedLists&, const ChunkArgs&, const double*, const double*,
-                                                  double, double*, double*, RateArgs, cudaStream_t);
 cudaError_t launch_residence(okmc_defect* d, int nd, const double* rates, const double* rsum, int3 n, uint64_t seed,
                              Move* moves, DevState* stt, cudaStream_t st) {
   k_residence<<<1, kEventThreads, 0, st>>>(d, nd, rates, rsum, n, (uint32_t)seed, (uint32_t)(seed >> 32), moves, stt);

@@ -72,8 +72,10 @@ cudaError_t launch_energy_chunks_batch(const BatchRep* reps, const int2* items, 
 cudaError_t launch_energy_finish_batch(const BatchRep* reps, const int2* items, int nitems, int grid, cudaStream_t st);
 template <class T>
 cudaError_t launch_energy_chunks(const T* sig, int3 n, const okmc_defect* d, const DefGeo* G, int nd,
-                                 const DilatedLists& dl, const ChunkArgs& ca, const double* alpha, const double* W,
-                                 double pref, double* E, double* Ec, RateArgs ra, cudaStream_t st);
+                                 const DilatedLists& dl, const ChunkArgs& ca, cudaStream_t st);
+cudaError_t launch_energy_finish(const okmc_defect* d, const DefGeo* G, int nd, const DilatedLists& dl,
+                                 const ChunkArgs& ca, const double* alpha, const double* W, double pref, double* E,
+                                 double* Ec, RateArgs ra, cudaStream_t st);
 cudaError_t launch_event_batch(const BatchRep* reps, int nrep, cudaStream_t st);
 cudaError_t launch_moves_batch(const BatchRep* reps, int nrep, cudaStream_t st);
 int energies_batch_grid();
@@ -508,12 +510,13 @@ int energies(okmc_grid* g, int want_cand, double kT = 0.0) {
   }
   if (want_cand && g->nchunk > 0) {
     const ChunkArgs ca{g->d_cdef, g->d_c0, g->d_cpart, g->nchunk};
-    return run(g, "energies", [&] {
+    OKMC_TRY(run(g, "energies", [&] {
       if (fp64(g))
-        return launch_energy_chunks<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, dl, ca, g->d_alpha,
-                                            g->d_W, pref, g->d_E, g->d_Ec, ra, g->st);
-      return launch_energy_chunks<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, dl, ca, g->d_alpha,
-                                         g->d_W, pref, g->d_E, g->d_Ec, ra, g->st);
+        return launch_energy_chunks<double>((const double*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, dl, ca, g->st);
+      return launch_energy_chunks<float>((const float*)g->sig, dims(g), g->d_def, g->d_geo, g->nd, dl, ca, g->st);
+    }));
+    return run(g, "energies_finish", [&] {
+      return launch_energy_finish(g->d_def, g->d_geo, g->nd, dl, ca, g->d_alpha, g->d_W, pref, g->d_E, g->d_Ec, ra, g->st);
     });
   }
   return run(g, "energies", [&] {

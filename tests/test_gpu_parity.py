@@ -310,6 +310,30 @@ def test_invalid_inputs_rejected():
     assert e.value.code == ok.OKMC_ENOMEM
 
 
+@pytest.mark.parametrize('precision', [ok.FP32_FIELDS, ok.FP64_FIELDS])
+def test_empty_defect_set(precision):
+    """No defects (a degenerate input): the stress is zero everywhere, the energies are
+    empty, a step is refused with OKMC_ESTATE, and defects set afterwards give the stress,
+    energies and trajectory of a fresh grid bit for bit."""
+    w = scaled_population((64, 64, 64), 8, seed=11, r111=(0.4, 1.0), r100=(0.4, 1.0))
+    g = ok.Grid(w.n, w.voxel_nm, *w.C, precision=precision, seed=11)
+    g.set_defects(w.defects[:0])
+    assert not g.solve_stress().any()
+    assert g.interaction_energies().shape == (0,)
+    with pytest.raises(ok.OkmcError) as e:
+        g.step(500.0, 1)
+    assert e.value.code == ok.OKMC_ESTATE
+    g.set_defects(w.defects)
+    ref = make_grid(w, precision)
+    assert np.array_equal(g.solve_stress(), ref.solve_stress())
+    assert np.array_equal(g.candidate_energies()[0], ref.candidate_energies()[0])
+    st, st_ref = g.step(500.0, 4), ref.step(500.0, 4)
+    assert np.array_equal(g.get_positions(), ref.get_positions())
+    assert st['clock'] == st_ref['clock']
+    g.close()
+    ref.close()
+
+
 # ------------------------------------------------------------------ full-size configurations
 def _sample(w, big_nm, n_other, seed):
     """Every loop with R > big_nm, the largest loops of each type up to 32 in all when
