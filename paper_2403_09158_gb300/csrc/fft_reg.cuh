@@ -233,6 +233,20 @@ struct XPad {
   C2<float>* p;
   __device__ __forceinline__ C2<float>& operator()(int n1, int k2) const { return p[n1 * (R2 + 1) + k2]; }
 };
+// Slot of k2 in row n1 of the exchange (n1, k2 < R2): a bijection on each row and on
+// each column of slots, so that the row writes (fixed k2) and the column reads (fixed n1)
+// of a line group both meet R2 distinct slots mod R2.  k2 XOR n1 for power-of-two R2 (one
+// logic instruction with a compile-time k2 or n1), (k2 + n1) mod R2 otherwise.
+template <int R2>
+__device__ __forceinline__ int xskew(int n1, int k2) {
+  if constexpr ((R2 & (R2 - 1)) == 0) {
+    return k2 ^ n1;
+  } else {
+    int m = k2 + n1;
+    if (m >= R2) m -= R2;
+    return m;
+  }
+}
 // exchange slots inside a strided line of L elements, skewed so that both the row
 // writes and the column reads hit distinct banks
 template <int R2>
@@ -240,9 +254,7 @@ struct XSkew {
   C2<float>* p;
   int s;
   __device__ __forceinline__ C2<float>& operator()(int n1, int k2) const {  // n1 < R2
-    int m = k2 + n1;
-    if (m >= R2) m -= R2;
-    return p[s * (n1 * R2 + m)];
+    return p[s * (n1 * R2 + xskew<R2>(n1, k2))];
   }
 };
 

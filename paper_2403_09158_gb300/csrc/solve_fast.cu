@@ -516,15 +516,16 @@ __device__ __forceinline__ int tile_at(int row, int col) {
   return SWZ ? row * kTW + (col ^ (row & 6)) : row * kLDT + col;
 }
 
-// Exchange slots of a line of the swizzled tile (the skew of XSkew, rows r0 + n1 * R2 + m)
+// Exchange slots of a line of the swizzled tile (the skew of XSkew, rows r0 + n1 * R2 + m).
+// With m = k2 XOR n1 (R2 = 16), the eight lanes of a line in a half-warp still meet all
+// eight values of m mod 8, as with the additive skew, so the two lines of opposite
+// column parity that share the half-warp stay on disjoint banks.
 template <int R2>
 struct XSwz {
   C2<float>* tile;
   int r0, col;
   __device__ __forceinline__ C2<float>& operator()(int n1, int k2) const {  // n1 < R2
-    int m = k2 + n1;
-    if (m >= R2) m -= R2;
-    return tile[tile_at<true>(r0 + n1 * R2 + m, col)];
+    return tile[tile_at<true>(r0 + n1 * R2 + xskew<R2>(n1, k2), col)];
   }
 };
 
