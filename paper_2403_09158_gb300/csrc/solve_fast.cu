@@ -332,10 +332,12 @@ __device__ __forceinline__ void plane_inv_item(const C2<float>* __restrict__ spe
     for (int c0 = 0; c0 < CPER; c0 += S::GC) {
       const bool act = c0 + g < CPER;
       const int kx = h * CPER + (act ? c0 + g : 0);
-      if (c0 > 0) load_cols(c0);
+      if (WIDE == 0 && c0 > 0) load_cols(c0);
       if constexpr (WIDE != 0) {
         auto st = [&](int k, C2<float> v) { xg[k] = v; };
         reg_fft_loaded<true, NY>(line, XPad<S::R2Y>{xg}, st, twY, t, act);
+        // the next group's loads fly during the copy-out and its barriers
+        if (c0 + S::GC < CPER) load_cols(c0 + S::GC);
         __syncthreads();
         if (CS > 1 && c0 == 0) cluster_wait();
         constexpr int GC = S::GC;
