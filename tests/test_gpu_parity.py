@@ -330,6 +330,14 @@ def test_empty_defect_set(precision):
     st, st_ref = g.step(500.0, 4), ref.step(500.0, 4)
     assert np.array_equal(g.get_positions(), ref.get_positions())
     assert st['clock'] == st_ref['clock']
+    # only immobile defects (<100> loops): energies as usual, a step is refused
+    still = make_defects([ok.LOOP_100, ok.LOOP_100], np.array([[10, 10, 10], [70, 40, 90]]), [0, 2], [0.8, 1.1], [0, 0],
+                         [0.1, 0.1], [ok.IMMOBILE, ok.IMMOBILE])
+    g.set_defects(still)
+    assert np.all(np.isfinite(g.interaction_energies()))
+    with pytest.raises(ok.OkmcError) as e:
+        g.step(500.0, 1)
+    assert e.value.code == ok.OKMC_ESTATE
     g.close()
     ref.close()
 
