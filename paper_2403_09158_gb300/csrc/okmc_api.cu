@@ -2062,10 +2062,8 @@ static int batch_build_kernels(okmc_batch* b) {
     b->err = std::string("batch work lists: ") + cudaGetErrorString(e);
     return e == cudaErrorMemoryAllocation ? OKMC_ENOMEM : OKMC_ECUDA;
   }
-  // persistent grids (and kernel attributes) before the capture: each launch gets every
-  // CTA (cluster) that fits on the device at once; the classes run one after another (a
-  // plane of a large edge costs many times one of a small edge, so splitting the device
-  // between concurrent classes by item count leaves it idle behind the largest class)
+  // grids (one CTA, or cluster, per item of the class's list) and kernel attributes
+  // before the capture
   std::vector<std::array<int, 3>> grids(cls.size());
   for (size_t k = 0; k < cls.size(); ++k) {
     const Cls& c = cls[k];
@@ -2093,12 +2091,21 @@ static int batch_build_kernels(okmc_batch* b) {
   if (cudaStreamBeginCapture(root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return OKMC_ECUDA;
   const int2* it = b->d_items;
   e = cudaSuccess;
-  for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass)
+  // each pass: the edge classes as parallel branches (a class's tail overlaps the
+  // others' blocks), joined before the next pass
+  for (int pass = 0; pass < 3 && e == cudaSuccess; ++pass) {
+    e = cudaEventRecord(b->ev[2 * n], root);
     for (size_t k = 0; k < cls.size() && e == cudaSuccess; ++k) {
       const Cls& c = cls[k];
-      e = pass == 1 ? launch_pass_batch(1, c.nz, b->d_reps, it + c.tile0, c.ntile, grids[k][1], b->slot0, root)
-                    : launch_pass_batch(pass, c.ny, b->d_reps, it + c.plane0, c.nplane, grids[k][pass], b->slot0, root);
+      cudaStream_t sk = b->side[n + 1 + k];
+      e = cudaStreamWaitEvent(sk, b->ev[2 * n], 0);
+      if (e == cudaSuccess)
+        e = pass == 1 ? launch_pass_batch(1, c.nz, b->d_reps, it + c.tile0, c.ntile, grids[k][1], b->slot0, sk)
+                      : launch_pass_batch(pass, c.ny, b->d_reps, it + c.plane0, c.nplane, grids[k][pass], b->slot0, sk);
+      if (e == cudaSuccess) e = cudaEventRecord(b->ev[2 * n + 1 + k], sk);
     }
+    for (size_t k = 0; k < cls.size() && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(root, b->ev[2 * n + 1 + k], 0);
+  }
   if (e == cudaSuccess) e = launch_energy_chunks_batch(b->d_reps, it + e0, ne, std::max(1, std::min(egrid, (ne + 7) / 8)), root);
   if (e == cudaSuccess) e = launch_energy_finish_batch(b->d_reps, it + f0, nf, std::max(1, std::min(egrid, (nf + 7) / 8)), root);
   if (e == cudaSuccess) e = launch_event_batch(b->d_reps, n, root);
