@@ -233,6 +233,28 @@ def test_incremental_field_equals_fresh_voxelisation():
     g2.close()
 
 
+def test_long_run_at_full_size_stays_exact():
+    """10 000 residence-time steps and 200 fixed-time steps (Algorithm 1) of the 256^3
+    workload with 2000 defects: the eigenstrain updated move by move equals a fresh
+    voxelisation of the final positions bit for bit, and so do the stress and every
+    site and candidate energy (the solve of a field that was built incrementally and
+    of a fresh one differ in nothing)."""
+    w = config_large()
+    g = make_grid(w)
+    st = g.step(w.T_K, 10000)
+    assert st['events'] == 10000
+    st = g.step(w.T_K, 200, mode=ok.FIXED_DT)
+    assert st['steps'] == 10200 and st['events'] > 10000
+    fresh = make_grid(w)
+    fresh.set_defects(g.get_defects())
+    assert np.array_equal(g.eigenstrain(), fresh.eigenstrain())
+    assert np.array_equal(g.solve_stress(), fresh.solve_stress())
+    assert np.array_equal(g.interaction_energies(), fresh.interaction_energies())
+    assert np.array_equal(g.candidate_energies()[0], fresh.candidate_energies()[0])
+    g.close()
+    fresh.close()
+
+
 def test_residence_steps_follow_oracle_decisions():
     w = config_small()
     seed = 4242
