@@ -1003,6 +1003,8 @@ __device__ __forceinline__ void energy_finish(const okmc_defect* __restrict__ d,
     const double es = G[i].escale;
     allowed = G[i].allowed;
     z = G[i].z;
+    // every energy list holds at least the voxels of the site stencil, so every defect
+    // owns at least one chunk slot and uses at least one
     const double* P = ca.part + (size_t)s0 * 9 + j;
     double tot = P[0];
     const int c = p0 & 1;
