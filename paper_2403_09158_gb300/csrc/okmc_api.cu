@@ -86,6 +86,7 @@ cudaError_t launch_fixed_dt(okmc_defect* d, const DefGeo* G, int nd, const doubl
 bool fast_solve_supported(const PassCfg& c);
 cudaError_t launch_plane_fast(bool inverse, int variant, const void* in, void* out, const PassCfg& c, cudaStream_t st);
 int plane_inv_variant_mask(const PassCfg& c);
+int plane_fwd_variant_mask(const PassCfg& c);
 template <class T, class QT>
 cudaError_t launch_dipself(const C2<T>* spec, const PassCfg& c, const WBatch& b, const QT* qtab, const double2* phx,
                            const double2* phy, const double2* phz, double* partial, int nblocks, const double* alpha,
@@ -1243,6 +1244,7 @@ int okmc_grid_create(const okmc_grid_desc* d, okmc_grid** out) {
     g->tm_ok = encode_spectrum_map(&g->tm_spec, g->spec, g->P, g->n[2]) &&
                encode_spectrum_map(&g->tm_spec2, g->spec2, g->P, g->n[2]);
     g->avail[1] = pencil_variant_mask(c) & (g->tm_ok ? ~0 : ~4);  // variant 2 stages by TMA
+    g->avail[0] = plane_fwd_variant_mask(c);
     g->avail[2] = plane_inv_variant_mask(c);
   }
   if ((rc = dalloc(g, (void**)&g->d_dirty, sizeof(int) * 6 * g->n[2]))) return cleanup(rc);

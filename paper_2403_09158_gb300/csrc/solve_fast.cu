@@ -154,9 +154,12 @@ __device__ __forceinline__ void put_col(cg::cluster_group& cluster, C2<float>* c
 // One (component, z) plane of the forward pass, by the CS CTAs of a cluster (cluster
 // rank h); smem_raw: nfwd_smem<H, NY>(CS) bytes of dynamic shared memory.  A clean plane
 // (dirty flag 0) returns at once in every CTA of the cluster alike.
+// pf > 0: first bring into L2 this CTA's rows of plane + pf (when that plane is dirty),
+// the plane whose cluster will most likely take this one's place a wave later.
 template <int H, int NY, int CS>
 __device__ __forceinline__ void plane_fwd_item(const int32_t* __restrict__ eps, C2<float>* __restrict__ spec,
-                                               const PassCfg& c, int plane, unsigned char* smem_raw) {
+                                               const PassCfg& c, int plane, unsigned char* smem_raw, int pf = 0,
+                                               int nplanes = 0) {
   using S = NShape<H, NY>;
   constexpr int CPER = H / CS, ROWS = NY / CS;
   C2<float>* twH = reinterpret_cast<C2<float>*>(smem_raw);
@@ -172,6 +175,10 @@ __device__ __forceinline__ void plane_fwd_item(const int32_t* __restrict__ eps, 
   if (c.dirty && c.dirty[plane] == 0) return;
   if (CS > 1) cluster_arrive();
   const int tid = threadIdx.x;
+  if (pf > 0 && plane + pf < nplanes && (!c.dirty || c.dirty[plane + pf] != 0)) {
+    const char* nx_rows = reinterpret_cast<const char*>(eps + ((size_t)(plane + pf) * NY + (size_t)h * ROWS) * (2 * H));
+    for (int i = tid; i < ROWS * 2 * H * 4 / 128; i += kNT) prefetch_l2(nx_rows + (size_t)i * 128);
+  }
   const size_t P = (size_t)(H + 1) * NY;
   const float q = (float)c.q;
   const int g = tid / S::NTH, t = tid % S::NTH;
@@ -260,9 +267,9 @@ __device__ __forceinline__ void plane_fwd_item(const int32_t* __restrict__ eps, 
 
 template <int H, int NY, int CS>
 __global__ void __launch_bounds__(kNT, 2) k_plane_fwd_n(const int32_t* __restrict__ eps, C2<float>* __restrict__ spec,
-                                                        PassCfg c) {
+                                                        PassCfg c, int pf) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  plane_fwd_item<H, NY, CS>(eps, spec, c, blockIdx.y, smem_raw);
+  plane_fwd_item<H, NY, CS>(eps, spec, c, blockIdx.y, smem_raw, pf, gridDim.y);
 }
 
 // pf > 0: first bring into L2 this CTA's columns of plane + pf, the plane whose
@@ -834,8 +841,9 @@ cudaError_t plane_pair_n(bool inverse, const void* in, void* out, const PassCfg&
     return launch_k(k_plane_inv_n<H, NY, CS, 0>, grid, ninv_smem<H, NY>(CS), CS, st,
                     static_cast<const C2<float>*>(in), static_cast<float*>(out), c, pf);
   }
+  static const int fwave = resident_clusters(k_plane_fwd_n<H, NY, CS>, CS, nfwd_smem<H, NY>(CS));
   return launch_k(k_plane_fwd_n<H, NY, CS>, grid, nfwd_smem<H, NY>(CS), CS, st, static_cast<const int32_t*>(in),
-                  static_cast<C2<float>*>(out), c);
+                  static_cast<C2<float>*>(out), c, wide == 1 ? fwave : 0);
 }
 
 // smallest cluster whose CTAs fit two per SM
@@ -885,7 +893,7 @@ cudaError_t plane_pair(bool inverse, int variant, const void* in, void* out, con
   if (inverse && variant == 1) return plane_inv_staged<H, NY, stage_cs<H, NY>(kTwoPerSM), 256, 2>(in, out, c, st);
   if (inverse && variant == 2) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 128, 3>(in, out, c, st);
   if (inverse && variant == 3) return plane_inv_staged<H, NY, stage_cs<H, NY>(kThreePerSM), 256, 3>(in, out, c, st);
-  if (!inverse) return plane_pair_n<H, NY, ncs<H, NY>()>(false, in, out, c, st);
+  if (!inverse) return plane_pair_n<H, NY, ncs<H, NY>()>(false, in, out, c, st, false, variant == 1 ? 1 : 0);
   return plane_pair_n<H, NY, ncs<H, NY>()>(true, in, out, c, st, variant == 4 || variant == 6 || variant == 7,
                                           variant == 7 ? 2 : (variant == 5 || variant == 6) ? 1 : 0);
 }
@@ -1039,6 +1047,10 @@ cudaError_t launch_plane_fast(bool inverse, int variant, const void* in, void* o
     default: return cudaErrorInvalidConfiguration;
   }
 }
+
+// bit v set: forward-pass variant v exists for this grid (0 plain, 1 with the L2
+// prefetch of the next wave's dirty planes)
+int plane_fwd_variant_mask(const PassCfg&) { return 3; }
 
 // bit v set: inverse-pass variant v exists for this grid
 int plane_inv_variant_mask(const PassCfg& c) {
