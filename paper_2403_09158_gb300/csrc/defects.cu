@@ -1316,6 +1316,8 @@ cudaError_t launch_moves_batch(const BatchRep* reps, int nrep, cudaStream_t st) 
   k_moves_batch<<<dim3(nrep, kMoveSlices), 256, 0, st>>>(reps);
   return cudaGetLastError();
 }
+// Blocks of the batched chunked-energies kernel resident on the device at once (its
+// persistent grid; one work item per warp).
 int energies_batch_grid() {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||

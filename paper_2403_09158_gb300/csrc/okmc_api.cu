@@ -710,8 +710,9 @@ int build_self_terms(okmc_grid* g, bool want_W = true, bool want_D = false) {
 
 // Dilated candidate lists of every (defect, class): sizes, offsets, fill.
 // The energy lists (each voxel of the site and candidate stencils once, nine counts) of
-// every defect and site class; work[i] receives the longer of defect i's two lists, or
-// the site plus candidate stencil entries where a class has no list.
+// every defect and site class, and the chunk slots of the chunked energies over them
+// (none when a defect has no list); work[i] receives the longer of defect i's two lists,
+// or the site plus candidate stencil entries where a class has no list.
 int build_dilated_lists(okmc_grid* g, const std::vector<int>& nnz, std::vector<int>& work) {
   const int nd = g->nd;
   int* d_n = nullptr;
